@@ -1,0 +1,300 @@
+#!/usr/bin/env python
+"""Throughput of the fused SSP-RK3 vielbein-LB + Cahn-Hilliard step on one or more GB300s.
+
+Metric: node-velocity updates per second, NVU/s = 16 * N_theta * N_phi * steps / time (a full
+three-stage step counts once), on the 1024 x 2048 FP32 torus coarsening workload (R = 2, r = 1,
+tau = 0.6, A = 0.5, kappa = 5e-4, M = 2.5e-3, noise +-0.01), with the HBM roofline of the stage
+kernel, an end-to-end figure through the C ABI with host buffers, and the FP64 CPU oracle timed
+on a bounded sample as a reported baseline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (torchrun) runs N independent replicas, one per GPU (weak scaling; the step itself needs
+no collective).  Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "coarsen_torus_1024x2048"
+METRIC = "node-velocity updates/s"
+UNIT = "NVU/s"
+BYTES_PER_NODE_STEP = {"f32": 544, "f64": 1088}  # 17 arrays: 5 reads + 3 writes per node over 3 stages
+PKEYS = ["R", "r", "n_theta", "n_phi", "dt", "tau", "M", "A", "kappa", "geometry", "advection", "ch_mode"]
+STAGE_SRC = os.path.join(ROOT, "paper_1904_10070_gb300", "csrc", "vlb_stage.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "stage_kernel_fp32_uw3_coarsen_1024x2048.md")
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def _traffic_per_launch():
+    """DRAM bytes per stage launch from the committed ncu summary, if it was taken on this source."""
+    try:
+        txt = open(TRAFFIC_FILE).read()
+    except OSError:
+        return None
+    src_hash = hashlib.sha256(open(STAGE_SRC, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in txt.splitlines():
+        if ":" in line and line.startswith("- "):
+            k, v = line[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("stage_source_sha256_16") != src_hash:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.lines:
+            return None
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(rows: int = 64, steps: int = 2):
+    """The FP64 oracle as it stands, on a rows x 2048 sub-grid of the workload (single-threaded numpy)."""
+    from oracle import vlb_oracle as O
+    from paper_1904_10070_gb300 import inputs
+    w = inputs.workload(WORKLOAD)
+    p = dict(w["params"])
+    p["n_theta"] = rows
+    op = O.Params(**{k: p[k] for k in PKEYS})
+    geo = O.Geometry(op)
+    phi = inputs.noise(1, rows, p["n_phi"], 0.01)
+    f, ph = O.init_state(np.ones_like(phi), 0 * phi, 0 * phi, phi)
+    t0 = time.perf_counter()
+    O.run(f, ph, geo, steps)
+    dt = time.perf_counter() - t0
+    return {"value": 16.0 * rows * p["n_phi"] * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"FP64 numpy oracle, {steps} SSP-RK3 steps on a {rows}x{p['n_phi']} sub-grid of the "
+                      f"workload (same parameters), {dt:.1f} s"}
+
+
+def run_reference(args):
+    """--impl reference: the oracle timed per step on a bounded sample sized for a few minutes in total."""
+    from oracle import vlb_oracle as O
+    from paper_1904_10070_gb300 import inputs
+    w = inputs.workload(WORKLOAD)
+    p = dict(w["params"])
+    budget_s, node_rate = 120.0, 1.6e4  # node-steps/s of the numpy oracle on a wide grid (measured)
+    rows = int(max(1, min(64, budget_s * node_rate / (p["n_phi"] * (args.steps + args.warmup)))))
+    p["n_theta"] = rows
+    op = O.Params(**{k: p[k] for k in PKEYS})
+    geo = O.Geometry(op)
+    phi = inputs.noise(1, rows, p["n_phi"], 0.01)
+    f, ph = O.init_state(np.ones_like(phi), 0 * phi, 0 * phi, phi)
+    for _ in range(args.warmup):
+        f, ph = O.step(f, ph, geo)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f, ph = O.step(f, ph, geo)
+    dt = time.perf_counter() - t0
+    val = 16.0 * rows * p["n_phi"] * args.steps / dt
+    sample = f"FP64 numpy oracle, {args.steps} steps on a {rows}x{p['n_phi']} sub-grid of the workload"
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "grid": [rows, p["n_phi"]], "sample": True},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = _args()
+    world, rank, local = _dist()
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+    import torch
+    from paper_1904_10070_gb300 import inputs, vlb
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    w = inputs.workload(WORKLOAD)
+    p = w["params"]
+    N = p["n_theta"] * p["n_phi"]
+    params = vlb.make_params(**{k: p[k] for k in PKEYS}, precision=vlb.FP32)
+    solver = vlb.Solver(params)
+    stream = solver.stream
+    solver.set_fields(w["rho"], w["ut"], w["up"], w["phi"])
+    for _ in range(args.warmup):
+        vlb.vlb_step(solver.h, 1)
+    torch.cuda.synchronize()
+    barrier()
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        barrier()
+        ev0.record(stream)
+        vlb.vlb_step(solver.h, args.steps)
+        ev1.record(stream)
+        ev1.synchronize()
+        torch.cuda.synchronize()
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    clocks = clk.summary()
+    tot = solver.totals()
+    if not np.all(np.isfinite(tot)):
+        raise SystemExit(f"non-finite totals after the timed steps: {tot}")
+
+    # end to end through the C ABI with pinned host buffers: set fields -> K steps -> read fields
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).pin_memory().numpy()  # noqa: E731
+    h_in = [pin(w["rho"]), pin(w["ut"]), pin(w["up"]), pin(w["phi"])]
+    h_out = [pin(np.empty((p["n_theta"], p["n_phi"]))) for _ in range(5)]
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    vlb.vlb_set_fields(solver.h, *h_in)
+    vlb.vlb_step(solver.h, args.steps)
+    vlb.vlb_get_fields(solver.h, p["n_theta"], p["n_phi"], out=h_out)
+    e2e_s = time.perf_counter() - t0
+    barrier()
+
+    if dist is not None:
+        t = torch.tensor([ms, e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, e2e_s = float(t[0]), float(t[1])
+    solver.close()
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    value = world * 16.0 * N * args.steps / (ms * 1e-3)
+    peaks, peak_kind = _peaks()
+    step_s = ms * 1e-3 / args.steps
+    launch_s = step_s / 3.0
+    alg_bytes_launch = BYTES_PER_NODE_STEP["f32"] * N / 3.0
+    achieved = alg_bytes_launch / launch_s / 1e9
+    traffic = _traffic_per_launch()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [p["n_theta"], p["n_phi"]], "R": p["R"], "r": p["r"],
+                   "precision": "fp32 state, fp64 coefficients and sums", "advection": "uw3",
+                   "ch_mode": "hydrodynamic", "parallelism": f"replicas x{world}",
+                   "l2": "no flush: the step streams 3 x 17 arrays = 428 MB per step through a 126 MB L2"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                     "kernel": "stage_kernel<float,UW3,HYDRO>",
+                     "peak_source": f"{peak_kind} hbm_gbs (copy)",
+                     "algorithmic_bytes_per_launch": alg_bytes_launch},
+        "e2e": {"value": world * 16.0 * N * args.steps / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": 4 * N * 8 / args.steps, "d2h_bytes_per_step": 5 * N * 8 / args.steps,
+                "what": "vlb_set_fields (host) + vlb_step(K) + vlb_get_fields (host), wall clock"},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,145 @@
+/*
+ * vlb.h -- C ABI of the GB300 vielbein lattice-Boltzmann + Cahn-Hilliard solver.
+ *
+ * Method: Ambrus, Busuioc, Wagner, Paillusson & Kusumaatmaja, "Multicomponent flow on curved
+ * surfaces: a vielbein lattice Boltzmann approach" (arXiv:1904.10070).
+ *
+ * The solver advances, on a periodic (theta, varphi) grid of a torus of radii R > r (or of a
+ * flat periodic L_x x L_y = 2 pi R x 2 pi r domain):
+ *   - 16 fluid distributions f_ij on the Q = 4 Gauss-Hermite velocity set (Sec. 2.3, Eq. vmatrix),
+ *     obeying the torus Boltzmann equation with BGK collisions (Eq. boltz_tor, Eq. feq),
+ *   - the order parameter phi, obeying the Cahn-Hilliard equation solved by finite differences
+ *     (Eq. CH with the chemical potential of Eq. mu and the force of Eq. pbin).
+ * Space: conservative flux form, linear 3rd-order upwind ("UW3") or WENO5-JS face values.
+ * Time: three-stage SSP Runge-Kutta.  One fused CUDA kernel per Runge-Kutta stage.
+ *
+ * Conventions for every call:
+ *   - Host arrays are [N_theta][N_phi] row-major doubles (varphi fastest) and belong to the
+ *     caller; they are only accessed during the call.  f16 arrays are [16][N_theta][N_phi] with
+ *     population k = 4 i + j, i the theta-hat velocity index and j the varphi-hat index, v_i
+ *     ordered as in Eq. vmatrix (v_1 < v_2 < v_3 < v_4).
+ *   - Velocities are vielbein (orthonormal-frame) components; rho is the number density n (m = 1).
+ *   - Device memory is owned by the caller: one workspace of vlb_workspace_bytes() bytes, at
+ *     least 256-byte aligned, which the library sub-allocates and never frees.  The handle
+ *     itself is allocated by the library and released by vlb_destroy().
+ *   - All GPU work is issued on the caller's stream (a cudaStream_t passed as void*; NULL is
+ *     the legacy default stream).  Calls that return host data synchronise that stream.
+ *   - Every call returns a vlb_status; nothing aborts, throws or traps.  vlb_last_error()
+ *     gives a message for the last failure (per handle, or per thread for handle-less calls).
+ *   - A handle is not thread-safe.
+ */
+#ifndef VLB_H
+#define VLB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vlb_handle vlb_handle;
+
+typedef enum {
+  VLB_OK = 0,
+  VLB_ERR_ARG = -1,       /* invalid argument or parameter                                 */
+  VLB_ERR_CUDA = -2,      /* a CUDA runtime call failed (message in vlb_last_error)         */
+  VLB_ERR_UNSTABLE = -3,  /* a diagnostic found a non-finite value or |u| > 2 (blow-up)      */
+  VLB_ERR_TIMEOUT = -4,   /* a bounded device-side wait gave up                             */
+  VLB_ERR_WORKSPACE = -5  /* workspace missing, too small or misaligned                     */
+} vlb_status;
+
+enum { VLB_TORUS = 0, VLB_FLAT = 1 };
+enum { VLB_FP64 = 0, VLB_FP32 = 1 };
+enum { VLB_UW3 = 0, VLB_WENO5 = 1 };
+enum { VLB_HYDRO = 0, VLB_DIFFUSIVE = 1 };
+
+/* Problem definition.  Sec. 2 (Eqs. Landau, mu, CH, boltz_tor, nu) and App. A (Eq. torus).
+ * tau may be +infinity (no collisions).  Flat geometry: J = 1, Gamma = 0, dx = 2 pi R / N_phi,
+ * dy = 2 pi r / N_theta.  Nodes sit at theta_q = q 2pi/N_theta, varphi_s = s 2pi/N_phi. */
+typedef struct {
+  int32_t geometry;    /* VLB_TORUS or VLB_FLAT                                            */
+  int32_t n_theta;     /* N_theta >= 4 (>= 6 for WENO5)                                    */
+  int32_t n_phi;       /* N_phi >= 1 (1 = azimuthally symmetric)                           */
+  int32_t precision;   /* VLB_FP64 or VLB_FP32 (FP32 state; FP64 coefficients and sums)    */
+  int32_t advection;   /* VLB_UW3 or VLB_WENO5                                             */
+  int32_t ch_mode;     /* VLB_HYDRO, or VLB_DIFFUSIVE: no CH advection and no force (Sec. 4.1.1) */
+  int32_t diag_every;  /* steps between finiteness checks inside vlb_step; 0 = never       */
+  int32_t reserved;    /* must be 0                                                        */
+  double R, r;         /* torus radii, R > r > 0 (flat: domain 2 pi R x 2 pi r)            */
+  double dt;           /* time step > 0                                                     */
+  double tau;          /* BGK relaxation time > 0 (nu = tau, Eq. nu)                        */
+  double M;            /* mobility >= 0 (Eq. CH)                                            */
+  double A, kappa;     /* free-energy parameters (Eq. Landau), A >= 0, kappa >= 0           */
+} vlb_params;
+
+/* Bytes of device workspace that vlb_create needs for these parameters; 0 if they are invalid. */
+size_t vlb_workspace_bytes(const vlb_params* p);
+
+/* Largest time step the explicit scheme is expected to be stable at (host-only, no GPU):
+ * min over (a) advection  dt <= 1 / (v_max (1/h_theta + 1/h_phi,min)), v_max = sqrt(3 + sqrt 6);
+ *          (b) BGK        dt <= 2.5 tau  (SSP-RK3 reaches -2.51 on the real axis);
+ *          (c) Cahn-Hilliard  dt <= 2.5 / (M lambda (kappa lambda + 2 A)),
+ *              lambda = 4/h_theta^2 + 4/h_phi,min^2, h_phi,min = (R - r) dvarphi on the torus.
+ * Returns VLB_ERR_ARG for invalid parameters (dt itself is not checked). */
+vlb_status vlb_max_stable_dt(const vlb_params* p, double* dt_out);
+
+/* Create a solver on the current CUDA device.  d_workspace: caller-owned device memory of at
+ * least vlb_workspace_bytes(p) bytes, 256-byte aligned.  cuda_stream: cudaStream_t or NULL.
+ * The state is zero until vlb_set_fields or vlb_set_state. */
+vlb_status vlb_create(const vlb_params* p, void* d_workspace, size_t bytes, void* cuda_stream,
+                      vlb_handle** out);
+
+/* Release the handle (not the workspace).  NULL is accepted. */
+vlb_status vlb_destroy(vlb_handle* h);
+
+/* Initialise from macroscopic fields (host [N_theta][N_phi] doubles): f_k := f^eq_k(rho, u)
+ * (Eq. feq, the initialisation of Sec. 4), phi := phi.  Synchronous. */
+vlb_status vlb_set_fields(vlb_handle* h, const double* rho, const double* u_th, const double* u_ph,
+                          const double* phi);
+
+/* Checkpoint / restore of the full state: f16 is [16][N_theta][N_phi], phi [N_theta][N_phi].
+ * In FP32 mode set rounds to FP32 and get widens exactly.  Synchronous. */
+vlb_status vlb_set_state(vlb_handle* h, const double* f16, const double* phi);
+vlb_status vlb_get_state(vlb_handle* h, double* f16, double* phi);
+
+/* Advance nsteps SSP-RK3 steps (3 fused-stage launches per step), asynchronously on the stream.
+ * With diag_every > 0 the totals are checked every diag_every steps and at the end, the
+ * stream is synchronised, and VLB_ERR_UNSTABLE is returned if a value was non-finite or
+ * max |u| exceeded 2. */
+vlb_status vlb_step(vlb_handle* h, int64_t nsteps);
+
+/* Macroscopic fields (host [N_theta][N_phi] doubles; any pointer may be NULL to skip):
+ * rho = n, u = vielbein velocity (Sec. 2.3 moments), phi, and
+ * mu = -A phi (1 - phi^2) - kappa Delta phi (Eq. mu, second-order Laplace-Beltrami).  Synchronous. */
+vlb_status vlb_get_fields(vlb_handle* h, double* rho, double* u_th, double* u_ph, double* phi,
+                          double* mu);
+
+/* Conserved totals and diagnostics, reduced in FP64 on the GPU:
+ * out[0] = sum n sqrt(g) dtheta dvarphi, out[1] = sum phi sqrt(g) dtheta dvarphi,
+ * out[2] = Psi (Eq. Landau, central differences), out[3] = max |u|.  Synchronous. */
+vlb_status vlb_get_totals(vlb_handle* h, double out[4]);
+
+/* Total interface length L_I (Sec. 4: every neighbour pair with phi phi' < 0 adds the shared
+ * edge, r dtheta across varphi and (R + r cos theta_{q+1/2}) dvarphi across theta), reduced in
+ * FP64 on the GPU; the domain length is L_d = 4 pi^2 r R / L_I (Eq. cart_scaling_L0).  Synchronous. */
+vlb_status vlb_interface_length(vlb_handle* h, double* out);
+
+/* Device pointers of the resident state (for zero-copy readers on the same device):
+ * f: 16 arrays of n_theta*n_phi elements spaced *stride elements apart, then phi at
+ * f + 16 * stride.  Elements are double (FP64) or float (FP32).  The pointers stay valid until
+ * vlb_destroy; reading them while a vlb_step is in flight on another stream races. */
+vlb_status vlb_state_device(vlb_handle* h, void** f, int64_t* stride);
+
+/* Steps taken since the last set call. */
+vlb_status vlb_steps_done(const vlb_handle* h, int64_t* out);
+
+/* Message of the last failure on h (or of the calling thread's last handle-less failure when
+ * h is NULL).  Never NULL; empty when there was none. */
+const char* vlb_last_error(const vlb_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VLB_H */

@@ -137,11 +137,14 @@ class Geometry:
     All arrays have shape (N_theta, 1) so that they broadcast over varphi.
     """
 
-    def __init__(self, p: Params):
+    def __init__(self, p: Params, rows=None):
+        """`rows` (optional) restricts the tables to the given theta-row indices of the full grid,
+        for evaluating the scheme on a window cut out of a larger grid (see step_window)."""
         self.p = p
         self.dth = 2.0 * math.pi / p.n_theta
         self.dph = 2.0 * math.pi / p.n_phi
-        th = np.arange(p.n_theta, dtype=np.float64) * self.dth
+        idx = np.arange(p.n_theta) if rows is None else np.asarray(rows)
+        th = idx.astype(np.float64) * self.dth
         self.theta = th[:, None]
         if p.geometry == TORUS:
             a = p.r / p.R
@@ -150,10 +153,10 @@ class Geometry:
             self.Jm = 1.0 + a * np.cos(th - 0.5 * self.dth)[:, None]
             self.Gamma = np.sin(th)[:, None] / (p.R * self.J)
         else:
-            self.J = np.ones((p.n_theta, 1))
-            self.Jp = np.ones((p.n_theta, 1))
-            self.Jm = np.ones((p.n_theta, 1))
-            self.Gamma = np.zeros((p.n_theta, 1))
+            self.J = np.ones((th.size, 1))
+            self.Jp = np.ones((th.size, 1))
+            self.Jm = np.ones((th.size, 1))
+            self.Gamma = np.zeros((th.size, 1))
         self.sqrtg = p.r * p.R * self.J
         self.dA = self.sqrtg * self.dth * self.dph  # area element of one cell
 
@@ -318,6 +321,23 @@ def step(f, phi, geo: Geometry):
     Lf, Lp = rhs(f2, p2, geo)
     return (f / 3.0 + 2.0 / 3.0 * (f2 + dt * Lf),
             phi / 3.0 + 2.0 / 3.0 * (p2 + dt * Lp))
+
+
+def step_window(f, phi, p: Params, q: int, s: int, half: int = 12):
+    """One step of the full periodic grid, evaluated only at node (q, s).
+
+    A (2 half + 1)^2 window around the node is cut out (periodically) and stepped as if it were
+    periodic itself; the wrong wrap-around at the window edges travels at most 3 nodes per
+    Runge-Kutta stage (the widest stencil, WENO5 advection), so with half >= 9 the centre is
+    exactly the full-grid result.  Returns (f[:, :, centre], phi[centre]).
+    """
+    rows = np.arange(q - half, q + half + 1) % p.n_theta
+    cols = np.arange(s - half, s + half + 1) % p.n_phi
+    geo = Geometry(p, rows=rows)
+    fw = f[:, :, rows][:, :, :, cols]
+    pw = phi[rows][:, cols]
+    f1, p1 = step(fw, pw, geo)
+    return f1[:, :, half, half], p1[half, half]
 
 
 def run(f, phi, geo: Geometry, nsteps: int):

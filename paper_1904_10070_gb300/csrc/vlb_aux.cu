@@ -1,0 +1,244 @@
+// Initialisation, state conversion, field read-out and FP64 diagnostic reductions.
+//
+// These kernels run once per set/get call or once per diagnostic, not per time step.  All of
+// their arithmetic is done in FP64 (the FP32 state is widened on load), so the read-outs and the
+// conserved totals carry no FP32 rounding beyond that of the state itself.
+#include <math.h>
+
+#include "vlb_internal.cuh"
+
+namespace vlb {
+
+namespace {
+
+constexpr int TOTAL_BLOCKS = 512;
+constexpr int TOTAL_THREADS = 256;
+constexpr int NSUM = 8;
+
+struct VD {
+  double v[4], w[4];
+};
+
+VD make_vd() {
+  const VelocityConsts c = velocity_consts();
+  VD d;
+  for (int i = 0; i < 4; ++i) {
+    d.v[i] = c.v[i];
+    d.w[i] = c.w[i];
+  }
+  return d;
+}
+
+__device__ __forceinline__ int wrapi(int x, int n) {
+  x %= n;
+  return x < 0 ? x + n : x;
+}
+
+// f := f^eq(rho, u) (Eq. feq), phi := phi; evaluated in FP64, rounded once.
+template <typename T>
+__global__ void init_feq_kernel(T* state, int64_t stride, const double* rho, const double* ut, const double* up,
+                                const double* phi, int64_t n, VD vd) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    const double nn = rho[idx], a = ut[idx], b = up[idx];
+    const double usq = a * a + b * b;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const double xi = vd.v[i] * a + vd.v[j] * b;
+        const double poly = 1.0 + xi + 0.5 * (xi * xi - usq) + xi * (xi * xi - 3.0 * usq) / 6.0;
+        state[(4 * i + j) * stride + idx] = (T)(nn * vd.w[i] * vd.w[j] * poly);
+      }
+    state[NPOP * stride + idx] = (T)phi[idx];
+  }
+}
+
+template <typename T>
+__global__ void convert_in_kernel(T* state, int64_t stride, const double* src, int64_t n) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n * NARR;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = idx / n, i = idx - k * n;
+    state[k * stride + i] = (T)src[idx];
+  }
+}
+
+template <typename T>
+__global__ void convert_out_kernel(double* dst, const T* state, int64_t stride, int64_t n) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n * NARR;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = idx / n, i = idx - k * n;
+    dst[idx] = (double)state[k * stride + i];
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void node_moments(const T* state, int64_t stride, int64_t idx, const VD& vd, double& n,
+                                             double& ut, double& up) {
+  double row[4] = {0, 0, 0, 0}, col[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const double x = (double)state[(4 * i + j) * stride + idx];
+      row[i] += x;
+      col[j] += x;
+    }
+  n = (row[0] + row[1]) + (row[2] + row[3]);
+  ut = (vd.v[0] * row[0] + vd.v[1] * row[1] + vd.v[2] * row[2] + vd.v[3] * row[3]) / n;
+  up = (vd.v[0] * col[0] + vd.v[1] * col[1] + vd.v[2] * col[2] + vd.v[3] * col[3]) / n;
+}
+
+// rho, u (Sec. 2.3 moments), phi and mu (Eq. mu) in FP64.
+template <typename T>
+__global__ void fields_kernel(const T* state, int64_t stride, const double* coefd, int nt, int ns, double A,
+                              double kappa, double* rho, double* ut, double* up, double* phi, double* mu, VD vd) {
+  const int64_t n = (int64_t)nt * ns;
+  const T* ph = state + NPOP * stride;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(idx / ns), s = (int)(idx - (int64_t)q * ns);
+    double nn, a, b;
+    node_moments(state, stride, idx, vd, nn, a, b);
+    rho[idx] = nn;
+    ut[idx] = a;
+    up[idx] = b;
+    const double p0 = (double)ph[idx];
+    const double pn = (double)ph[(int64_t)wrapi(q + 1, nt) * ns + s];
+    const double ps = (double)ph[(int64_t)wrapi(q - 1, nt) * ns + s];
+    const double pe = (double)ph[(int64_t)q * ns + wrapi(s + 1, ns)];
+    const double pw = (double)ph[(int64_t)q * ns + wrapi(s - 1, ns)];
+    const double lap = coefd[C_LT * nt + q] * (coefd[C_JP * nt + q] * (pn - p0) - coefd[C_JM * nt + q] * (p0 - ps)) +
+                       coefd[C_LP * nt + q] * (pe - 2.0 * p0 + pw);
+    phi[idx] = p0;
+    mu[idx] = -A * p0 * (1.0 - p0 * p0) - kappa * lap;
+  }
+}
+
+// Per-block FP64 partial sums: mass, phi total, Psi (Eq. Landau), max |u|, non-finite count, L_I.
+template <typename T>
+__global__ void __launch_bounds__(TOTAL_THREADS) totals_kernel(const T* state, int64_t stride, const double* coefd,
+                                                               int nt, int ns, double r, double A, double kappa,
+                                                               double gt, double edge_p, double* partials, VD vd) {
+  const int64_t n = (int64_t)nt * ns;
+  const T* ph = state + NPOP * stride;
+  double acc[NSUM] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(idx / ns), s = (int)(idx - (int64_t)q * ns);
+    double nn, a, b;
+    node_moments(state, stride, idx, vd, nn, a, b);
+    const double dA = coefd[C_DA * nt + q];
+    const double p0 = (double)ph[idx];
+    const double pn = (double)ph[(int64_t)wrapi(q + 1, nt) * ns + s];
+    const double ps = (double)ph[(int64_t)wrapi(q - 1, nt) * ns + s];
+    const double pe = (double)ph[(int64_t)q * ns + wrapi(s + 1, ns)];
+    const double pw = (double)ph[(int64_t)q * ns + wrapi(s - 1, ns)];
+    const double g1 = (pn - ps) * gt, g2 = (pe - pw) * coefd[C_GP * nt + q];
+    const double om = 1.0 - p0 * p0;
+    acc[0] += nn * dA;
+    acc[1] += p0 * dA;
+    acc[2] += (0.25 * A * om * om + 0.5 * kappa * (g1 * g1 + g2 * g2)) * dA;
+    const double umag = sqrt(a * a + b * b);
+    acc[3] = fmax(acc[3], umag);
+    if (!isfinite(nn) || !isfinite(umag) || !isfinite(p0)) acc[4] += 1.0;
+    if (p0 * pe < 0.0) acc[5] += edge_p;                     // neighbour across varphi: r dtheta
+    if (p0 * pn < 0.0) acc[5] += coefd[C_EDGE * nt + q];     // neighbour across theta
+  }
+  // warp then block reduction in a fixed order
+  __shared__ double red[TOTAL_THREADS / 32][NSUM];
+#pragma unroll
+  for (int k = 0; k < NSUM; ++k) {
+    double x = acc[k];
+    for (int o = 16; o > 0; o >>= 1) {
+      const double y = __shfl_down_sync(0xffffffffu, x, o);
+      x = (k == 3) ? fmax(x, y) : x + y;
+    }
+    acc[k] = x;
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0)
+    for (int k = 0; k < NSUM; ++k) red[wid][k] = acc[k];
+  __syncthreads();
+  if (threadIdx.x < NSUM) {
+    const int k = threadIdx.x;
+    double x = (k == 3) ? 0.0 : 0.0;
+    for (int w = 0; w < TOTAL_THREADS / 32; ++w) x = (k == 3) ? fmax(x, red[w][k]) : x + red[w][k];
+    partials[blockIdx.x * NSUM + k] = x;
+  }
+}
+
+__global__ void totals_final_kernel(const double* partials, int nb, double* out) {
+  const int k = threadIdx.x;
+  if (k >= NSUM) return;
+  double x = 0.0;
+  for (int b = 0; b < nb; ++b) x = (k == 3) ? fmax(x, partials[b * NSUM + k]) : x + partials[b * NSUM + k];
+  out[k] = x;
+}
+
+int grid_for(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+int totals_blocks() { return TOTAL_BLOCKS; }
+
+template <typename T>
+cudaError_t launch_init_feq(T* state, int64_t stride, const double* rho, const double* ut, const double* up,
+                            const double* phi, int64_t n, cudaStream_t s) {
+  init_feq_kernel<T><<<grid_for(n), 256, 0, s>>>(state, stride, rho, ut, up, phi, n, make_vd());
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_convert_in(T* state, int64_t stride, const double* src, int64_t n, cudaStream_t s) {
+  convert_in_kernel<T><<<grid_for(n * NARR), 256, 0, s>>>(state, stride, src, n);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_convert_out(double* dst, const T* state, int64_t stride, int64_t n, cudaStream_t s) {
+  convert_out_kernel<T><<<grid_for(n * NARR), 256, 0, s>>>(dst, state, stride, n);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_fields(const T* state, int64_t stride, const double* coefd, int nt, int ns, double A, double kappa,
+                          double* rho, double* ut, double* up, double* phi, double* mu, cudaStream_t s) {
+  fields_kernel<T><<<grid_for((int64_t)nt * ns), 256, 0, s>>>(state, stride, coefd, nt, ns, A, kappa, rho, ut, up,
+                                                             phi, mu, make_vd());
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_totals(const T* state, int64_t stride, const double* coefd, int nt, int ns, double R, double r,
+                          double A, double kappa, int geometry, double* partials, int n_blocks, double* out,
+                          cudaStream_t s) {
+  (void)R;
+  (void)geometry;
+  const double dth = 2.0 * M_PI / nt;
+  const double gt = 1.0 / (2.0 * r * dth);
+  const double edge_p = r * dth;
+  totals_kernel<T><<<n_blocks, TOTAL_THREADS, 0, s>>>(state, stride, coefd, nt, ns, r, A, kappa, gt, edge_p, partials,
+                                                      make_vd());
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  totals_final_kernel<<<1, 32, 0, s>>>(partials, n_blocks, out);
+  return cudaGetLastError();
+}
+
+#define VLB_INST(T)                                                                                              \
+  template cudaError_t launch_init_feq<T>(T*, int64_t, const double*, const double*, const double*,              \
+                                          const double*, int64_t, cudaStream_t);                                  \
+  template cudaError_t launch_convert_in<T>(T*, int64_t, const double*, int64_t, cudaStream_t);                 \
+  template cudaError_t launch_convert_out<T>(double*, const T*, int64_t, int64_t, cudaStream_t);                \
+  template cudaError_t launch_fields<T>(const T*, int64_t, const double*, int, int, double, double, double*,     \
+                                        double*, double*, double*, double*, cudaStream_t);                        \
+  template cudaError_t launch_totals<T>(const T*, int64_t, const double*, int, int, double, double, double,      \
+                                        double, int, double*, int, double*, cudaStream_t);
+VLB_INST(float)
+VLB_INST(double)
+#undef VLB_INST
+
+}  // namespace vlb

@@ -1,0 +1,496 @@
+// C ABI of libvlb: parameter validation, geometry tables, workspace layout and the step driver.
+//
+// Geometry (App. A): x = (R + r cos theta) cos varphi, y = (R + r cos theta) sin varphi,
+// z = r sin theta; metric g_phiphi = (R + r cos theta)^2, g_thth = r^2; vielbein
+// e_phi = 1/(R + r cos theta), e_theta = 1/r; the only connection coefficient is
+// Gamma = sin theta / (R + r cos theta) (Eq. conn_torus).  The tables below are evaluated in
+// FP64 per theta row and rounded once to the state precision.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <atomic>
+#include <new>
+
+#include "vlb_internal.cuh"
+
+// Raises the handle's device flag when a diagnostic vector shows an unstable state.
+cudaError_t vlb_internal_flag(const double* diag, int* flag, cudaStream_t s);
+
+struct vlb_handle {
+  vlb_params p;
+  cudaStream_t stream;
+  int device;
+  int64_t N;       // n_theta * n_phi
+  int64_t stride;  // elements between state arrays
+  size_t esize;    // 4 or 8
+  unsigned char* ws;
+  size_t ws_bytes;
+  void* U[3];          // U^n, U^(1), U^(2)
+  void* coefT;         // [NCOEF][n_theta] in state precision
+  double* coefD;       // [NCOEF][n_theta] FP64
+  double* staging;     // 17 N doubles
+  double* partials;    // totals_blocks() * 8
+  double* totals;      // 8 doubles (read-out)
+  double* diag;        // 8 doubles (last in-step diagnostic)
+  int* flag;           // device flag: diagnostics found an unstable state
+  int64_t steps_done;
+  char err[512];
+};
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+vlb_status fail(vlb_handle* h, vlb_status st, const char* fmt, ...) __attribute__((format(printf, 3, 4)));
+vlb_status fail(vlb_handle* h, vlb_status st, const char* fmt, ...) {
+  char* dst = h ? h->err : g_err;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(dst, 512, fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+#define VLB_CUDA(h, call)                                                                          \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess)                                                                         \
+      return fail((h), VLB_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                  __LINE__);                                                                       \
+  } while (0)
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+bool params_ok(const vlb_params* p, char* why, size_t n) {
+  if (!p) return snprintf(why, n, "params is NULL"), false;
+  if (p->geometry != VLB_TORUS && p->geometry != VLB_FLAT) return snprintf(why, n, "geometry must be 0 or 1"), false;
+  if (p->precision != VLB_FP64 && p->precision != VLB_FP32) return snprintf(why, n, "precision must be 0 or 1"), false;
+  if (p->advection != VLB_UW3 && p->advection != VLB_WENO5) return snprintf(why, n, "advection must be 0 or 1"), false;
+  if (p->ch_mode != VLB_HYDRO && p->ch_mode != VLB_DIFFUSIVE) return snprintf(why, n, "ch_mode must be 0 or 1"), false;
+  const int nt_min = p->advection == VLB_WENO5 ? 6 : 4;
+  if (p->n_theta < nt_min) return snprintf(why, n, "n_theta must be >= %d", nt_min), false;
+  if (p->n_phi < 1) return snprintf(why, n, "n_phi must be >= 1"), false;
+  if (p->n_theta > 65535 * 16) return snprintf(why, n, "n_theta must be <= %d", 65535 * 16), false;
+  if ((int64_t)p->n_theta * p->n_phi > (int64_t)1 << 31) return snprintf(why, n, "grid larger than 2^31 nodes"), false;
+  if (p->diag_every < 0) return snprintf(why, n, "diag_every must be >= 0"), false;
+  if (p->reserved != 0) return snprintf(why, n, "reserved must be 0"), false;
+  if (!(p->r > 0.0) || !(p->R > 0.0) || !isfinite(p->r) || !isfinite(p->R))
+    return snprintf(why, n, "radii must be finite and positive"), false;
+  if (p->geometry == VLB_TORUS && !(p->R > p->r)) return snprintf(why, n, "torus needs R > r"), false;
+  if (!(p->dt > 0.0) || !isfinite(p->dt)) return snprintf(why, n, "dt must be finite and > 0"), false;
+  if (!(p->tau > 0.0)) return snprintf(why, n, "tau must be > 0 (inf allowed)"), false;
+  if (!(p->M >= 0.0) || !(p->A >= 0.0) || !(p->kappa >= 0.0) || !isfinite(p->M) || !isfinite(p->A) ||
+      !isfinite(p->kappa))
+    return snprintf(why, n, "M, A, kappa must be finite and >= 0"), false;
+  return true;
+}
+
+struct Layout {
+  int64_t N, stride;
+  size_t esize;
+  size_t off_coefT, off_coefD, off_U[3], off_staging, off_partials, off_totals, off_diag, off_flag, total;
+};
+
+Layout layout(const vlb_params* p) {
+  Layout L;
+  L.N = (int64_t)p->n_theta * p->n_phi;
+  L.stride = (int64_t)align_up((size_t)L.N, 64);
+  L.esize = p->precision == VLB_FP64 ? 8 : 4;
+  size_t off = 0;
+  L.off_coefT = off;
+  off = align_up(off + (size_t)vlb::NCOEF * p->n_theta * L.esize, 256);
+  L.off_coefD = off;
+  off = align_up(off + (size_t)vlb::NCOEF * p->n_theta * 8, 256);
+  for (int k = 0; k < 3; ++k) {
+    L.off_U[k] = off;
+    off = align_up(off + (size_t)vlb::NARR * L.stride * L.esize, 256);
+  }
+  L.off_staging = off;
+  off = align_up(off + (size_t)vlb::NARR * L.N * 8, 256);
+  L.off_partials = off;
+  off = align_up(off + (size_t)vlb::totals_blocks() * 8 * 8, 256);
+  L.off_totals = off;
+  off = align_up(off + 8 * 8, 256);
+  L.off_diag = off;
+  off = align_up(off + 8 * 8, 256);
+  L.off_flag = off;
+  off = align_up(off + 256, 256);
+  L.total = off;
+  return L;
+}
+
+// Row tables in FP64 (see RowCoef for the meaning of each entry).
+void row_tables(const vlb_params* p, double* out) {
+  const int nt = p->n_theta;
+  const double dth = 2.0 * M_PI / nt, dph = 2.0 * M_PI / p->n_phi;
+  const bool torus = p->geometry == VLB_TORUS;
+  const double a = torus ? p->r / p->R : 0.0;
+  for (int q = 0; q < nt; ++q) {
+    const double th = q * dth;
+    const double J = 1.0 + a * cos(th);
+    const double Jp = 1.0 + a * cos(th + 0.5 * dth);
+    const double Jm = 1.0 + a * cos(th - 0.5 * dth);
+    out[vlb::C_J * nt + q] = J;
+    out[vlb::C_JP * nt + q] = Jp;
+    out[vlb::C_JM * nt + q] = Jm;
+    out[vlb::C_CT * nt + q] = 1.0 / (p->r * J * dth);
+    out[vlb::C_CP * nt + q] = 1.0 / (p->R * J * dph);
+    out[vlb::C_GAM * nt + q] = torus ? sin(th) / (p->R * J) : 0.0;
+    out[vlb::C_LT * nt + q] = 1.0 / (p->r * p->r * J * dth * dth);
+    out[vlb::C_LP * nt + q] = 1.0 / (p->R * p->R * J * J * dph * dph);
+    out[vlb::C_GP * nt + q] = 1.0 / (2.0 * p->R * J * dph);
+    out[vlb::C_DA * nt + q] = p->r * p->R * J * dth * dph;
+    out[vlb::C_EDGE * nt + q] = torus ? (p->R + p->r * cos(th + 0.5 * dth)) * dph : p->R * dph;
+  }
+}
+
+template <typename T>
+vlb_status run_steps(vlb_handle* h, int64_t nsteps) {
+  const vlb_params& p = h->p;
+  vlb::StageArgs<T> a;
+  a.coef = (const T*)h->coefT;
+  a.nt = p.n_theta;
+  a.ns = p.n_phi;
+  a.stride = h->stride;
+  a.dt = (T)p.dt;
+  a.inv_tau = (T)(1.0 / p.tau);
+  a.M = (T)p.M;
+  a.A = (T)p.A;
+  a.kappa = (T)p.kappa;
+  a.gt = (T)(1.0 / (2.0 * p.r * (2.0 * M_PI / p.n_theta)));
+  T* U0 = (T*)h->U[0];
+  T* U1 = (T*)h->U[1];
+  T* U2 = (T*)h->U[2];
+  for (int64_t n = 0; n < nsteps; ++n) {
+    // SSP-RK3 (Shu & Osher 1988): U1 = U + dt L(U); U2 = 3/4 U + 1/4 (U1 + dt L(U1));
+    // U <- 1/3 U + 2/3 (U2 + dt L(U2))
+    a.fin = U0; a.f0 = nullptr; a.fout = U1; a.a0 = (T)0; a.b = (T)1;
+    VLB_CUDA(h, vlb::launch_stage<T>(a, p.advection, p.ch_mode, h->stream));
+    a.fin = U1; a.f0 = U0; a.fout = U2; a.a0 = (T)0.75; a.b = (T)0.25;
+    VLB_CUDA(h, vlb::launch_stage<T>(a, p.advection, p.ch_mode, h->stream));
+    a.fin = U2; a.f0 = U0; a.fout = U0; a.a0 = (T)(1.0 / 3.0); a.b = (T)(2.0 / 3.0);
+    VLB_CUDA(h, vlb::launch_stage<T>(a, p.advection, p.ch_mode, h->stream));
+    h->steps_done++;
+    if (p.diag_every > 0 && (h->steps_done % p.diag_every == 0 || n + 1 == nsteps)) {
+      VLB_CUDA(h, vlb::launch_totals<T>(U0, h->stride, h->coefD, p.n_theta, p.n_phi, p.R, p.r, p.A, p.kappa,
+                                        p.geometry, h->partials, vlb::totals_blocks(), h->diag, h->stream));
+      VLB_CUDA(h, vlb_internal_flag(h->diag, h->flag, h->stream));
+    }
+  }
+  return VLB_OK;
+}
+
+template <typename T>
+vlb_status totals_impl(vlb_handle* h) {
+  const vlb_params& p = h->p;
+  VLB_CUDA(h, vlb::launch_totals<T>((const T*)h->U[0], h->stride, h->coefD, p.n_theta, p.n_phi, p.R, p.r, p.A,
+                                    p.kappa, p.geometry, h->partials, vlb::totals_blocks(), h->totals, h->stream));
+  return VLB_OK;
+}
+
+vlb_status check_handle(vlb_handle* h) {
+  if (!h) return fail(nullptr, VLB_ERR_ARG, "handle is NULL");
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(h, VLB_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  if (dev != h->device) {
+    e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return fail(h, VLB_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+  }
+  return VLB_OK;
+}
+
+}  // namespace
+
+// Flags an unstable state: non-finite values or |u| > 2 in the diagnostic vector.
+__global__ void vlb_flag_kernel(const double* diag, int* flag) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const double m = diag[0], um = diag[3], bad = diag[4];
+    if (bad > 0.0 || !(um <= 2.0) || !isfinite(m)) *flag = 1;
+  }
+}
+
+cudaError_t vlb_internal_flag(const double* diag, int* flag, cudaStream_t s) {
+  vlb_flag_kernel<<<1, 32, 0, s>>>(diag, flag);
+  return cudaGetLastError();
+}
+
+namespace vlb {
+
+// Velocity set of Eq. vmatrix, weights w_k = Q!/He_{Q+1}(v_k)^2 and the derivative kernel
+// K_{i,m} = -w_i sum_{l<Q} He_{l+1}(v_i) He_l(v_m) / l!  (Sec. 2.3), in FP64.
+static double he(int n, double x) {
+  double a = 1.0, b = x;
+  if (n == 0) return a;
+  for (int m = 1; m < n; ++m) {
+    const double c = x * b - m * a;
+    a = b;
+    b = c;
+  }
+  return b;
+}
+
+VelocityConsts velocity_consts() {
+  VelocityConsts c;
+  const double s6 = sqrt(6.0);
+  c.v[0] = -sqrt(3.0 + s6);
+  c.v[1] = -sqrt(3.0 - s6);
+  c.v[2] = sqrt(3.0 - s6);
+  c.v[3] = sqrt(3.0 + s6);
+  for (int i = 0; i < 4; ++i) {
+    const double h5 = he(5, c.v[i]);
+    c.w[i] = 24.0 / (h5 * h5);
+  }
+  for (int i = 0; i < 4; ++i)
+    for (int m = 0; m < 4; ++m) {
+      double s = 0.0, fact = 1.0;
+      for (int l = 0; l < 4; ++l) {
+        if (l > 0) fact *= l;
+        s += he(l + 1, c.v[i]) * he(l, c.v[m]) / fact;
+      }
+      c.K[i][m] = -c.w[i] * s;
+    }
+  return c;
+}
+
+}  // namespace vlb
+
+extern "C" {
+
+size_t vlb_workspace_bytes(const vlb_params* p) {
+  char why[256];
+  if (!params_ok(p, why, sizeof why)) {
+    fail(nullptr, VLB_ERR_ARG, "%s", why);
+    return 0;
+  }
+  return layout(p).total;
+}
+
+vlb_status vlb_max_stable_dt(const vlb_params* p, double* dt_out) {
+  char why[256];
+  if (!dt_out) return fail(nullptr, VLB_ERR_ARG, "dt_out is NULL");
+  vlb_params q = p ? *p : vlb_params{};
+  if (p) q.dt = 1.0;  // dt itself is not validated here
+  if (!params_ok(p ? &q : nullptr, why, sizeof why)) return fail(nullptr, VLB_ERR_ARG, "%s", why);
+  const double dth = 2.0 * M_PI / p->n_theta, dph = 2.0 * M_PI / p->n_phi;
+  const double ht = p->r * dth;
+  const double hp = (p->geometry == VLB_TORUS ? (p->R - p->r) : p->R) * dph;
+  const double vmax = sqrt(3.0 + sqrt(6.0));
+  double dt = 1.0 / (vmax * (1.0 / ht + (p->n_phi > 1 ? 1.0 / hp : 0.0)));
+  if (isfinite(p->tau)) dt = fmin(dt, 2.5 * p->tau);
+  const double lam = 4.0 / (ht * ht) + (p->n_phi > 1 ? 4.0 / (hp * hp) : 0.0);
+  const double ch = p->M * lam * (p->kappa * lam + 2.0 * p->A);
+  if (ch > 0.0) dt = fmin(dt, 2.5 / ch);
+  *dt_out = dt;
+  return VLB_OK;
+}
+
+vlb_status vlb_create(const vlb_params* p, void* d_workspace, size_t bytes, void* cuda_stream, vlb_handle** out) {
+  char why[256];
+  if (!out) return fail(nullptr, VLB_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!params_ok(p, why, sizeof why)) return fail(nullptr, VLB_ERR_ARG, "%s", why);
+  const Layout L = layout(p);
+  if (!d_workspace) return fail(nullptr, VLB_ERR_WORKSPACE, "workspace is NULL");
+  if (((uintptr_t)d_workspace) % 256 != 0) return fail(nullptr, VLB_ERR_WORKSPACE, "workspace not 256-byte aligned");
+  if (bytes < L.total)
+    return fail(nullptr, VLB_ERR_WORKSPACE, "workspace too small: %zu < %zu bytes", bytes, L.total);
+  vlb_handle* h = new (std::nothrow) vlb_handle();
+  if (!h) return fail(nullptr, VLB_ERR_ARG, "out of host memory");
+  h->p = *p;
+  h->stream = (cudaStream_t)cuda_stream;
+  h->N = L.N;
+  h->stride = L.stride;
+  h->esize = L.esize;
+  h->ws = (unsigned char*)d_workspace;
+  h->ws_bytes = bytes;
+  h->coefT = h->ws + L.off_coefT;
+  h->coefD = (double*)(h->ws + L.off_coefD);
+  for (int k = 0; k < 3; ++k) h->U[k] = h->ws + L.off_U[k];
+  h->staging = (double*)(h->ws + L.off_staging);
+  h->partials = (double*)(h->ws + L.off_partials);
+  h->totals = (double*)(h->ws + L.off_totals);
+  h->diag = (double*)(h->ws + L.off_diag);
+  h->flag = (int*)(h->ws + L.off_flag);
+  h->steps_done = 0;
+  h->err[0] = 0;
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e != cudaSuccess) {
+    delete h;
+    return fail(nullptr, VLB_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  }
+  // geometry tables
+  const int nt = p->n_theta;
+  double* tab = (double*)malloc(sizeof(double) * vlb::NCOEF * nt);
+  void* tabT = malloc(L.esize * vlb::NCOEF * nt);
+  if (!tab || !tabT) {
+    free(tab);
+    free(tabT);
+    delete h;
+    return fail(nullptr, VLB_ERR_ARG, "out of host memory");
+  }
+  row_tables(p, tab);
+  for (int i = 0; i < vlb::NCOEF * nt; ++i) {
+    if (L.esize == 8)
+      ((double*)tabT)[i] = tab[i];
+    else
+      ((float*)tabT)[i] = (float)tab[i];
+  }
+  e = cudaMemcpyAsync(h->coefD, tab, sizeof(double) * vlb::NCOEF * nt, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->coefT, tabT, L.esize * vlb::NCOEF * nt, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + L.off_U[0], 0, L.off_staging - L.off_U[0], h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  free(tab);
+  free(tabT);
+  if (e != cudaSuccess) {
+    delete h;
+    return fail(nullptr, VLB_ERR_CUDA, "vlb_create upload: %s", cudaGetErrorString(e));
+  }
+  *out = h;
+  return VLB_OK;
+}
+
+vlb_status vlb_destroy(vlb_handle* h) {
+  delete h;
+  return VLB_OK;
+}
+
+vlb_status vlb_set_fields(vlb_handle* h, const double* rho, const double* u_th, const double* u_ph, const double* phi) {
+  vlb_status st = check_handle(h);
+  if (st) return st;
+  if (!rho || !u_th || !u_ph || !phi) return fail(h, VLB_ERR_ARG, "vlb_set_fields: NULL input");
+  const size_t nb = sizeof(double) * h->N;
+  double* s = h->staging;
+  VLB_CUDA(h, cudaMemcpyAsync(s, rho, nb, cudaMemcpyHostToDevice, h->stream));
+  VLB_CUDA(h, cudaMemcpyAsync(s + h->N, u_th, nb, cudaMemcpyHostToDevice, h->stream));
+  VLB_CUDA(h, cudaMemcpyAsync(s + 2 * h->N, u_ph, nb, cudaMemcpyHostToDevice, h->stream));
+  VLB_CUDA(h, cudaMemcpyAsync(s + 3 * h->N, phi, nb, cudaMemcpyHostToDevice, h->stream));
+  if (h->esize == 8)
+    VLB_CUDA(h, vlb::launch_init_feq<double>((double*)h->U[0], h->stride, s, s + h->N, s + 2 * h->N, s + 3 * h->N,
+                                             h->N, h->stream));
+  else
+    VLB_CUDA(h, vlb::launch_init_feq<float>((float*)h->U[0], h->stride, s, s + h->N, s + 2 * h->N, s + 3 * h->N,
+                                            h->N, h->stream));
+  VLB_CUDA(h, cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
+  VLB_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->steps_done = 0;
+  return VLB_OK;
+}
+
+vlb_status vlb_set_state(vlb_handle* h, const double* f16, const double* phi) {
+  vlb_status st = check_handle(h);
+  if (st) return st;
+  if (!f16 || !phi) return fail(h, VLB_ERR_ARG, "vlb_set_state: NULL input");
+  const size_t nb = sizeof(double) * h->N;
+  VLB_CUDA(h, cudaMemcpyAsync(h->staging, f16, 16 * nb, cudaMemcpyHostToDevice, h->stream));
+  VLB_CUDA(h, cudaMemcpyAsync(h->staging + 16 * h->N, phi, nb, cudaMemcpyHostToDevice, h->stream));
+  if (h->esize == 8)
+    VLB_CUDA(h, vlb::launch_convert_in<double>((double*)h->U[0], h->stride, h->staging, h->N, h->stream));
+  else
+    VLB_CUDA(h, vlb::launch_convert_in<float>((float*)h->U[0], h->stride, h->staging, h->N, h->stream));
+  VLB_CUDA(h, cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
+  VLB_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->steps_done = 0;
+  return VLB_OK;
+}
+
+vlb_status vlb_get_state(vlb_handle* h, double* f16, double* phi) {
+  vlb_status st = check_handle(h);
+  if (st) return st;
+  if (!f16 || !phi) return fail(h, VLB_ERR_ARG, "vlb_get_state: NULL output");
+  if (h->esize == 8)
+    VLB_CUDA(h, vlb::launch_convert_out<double>(h->staging, (const double*)h->U[0], h->stride, h->N, h->stream));
+  else
+    VLB_CUDA(h, vlb::launch_convert_out<float>(h->staging, (const float*)h->U[0], h->stride, h->N, h->stream));
+  const size_t nb = sizeof(double) * h->N;
+  VLB_CUDA(h, cudaMemcpyAsync(f16, h->staging, 16 * nb, cudaMemcpyDeviceToHost, h->stream));
+  VLB_CUDA(h, cudaMemcpyAsync(phi, h->staging + 16 * h->N, nb, cudaMemcpyDeviceToHost, h->stream));
+  VLB_CUDA(h, cudaStreamSynchronize(h->stream));
+  return VLB_OK;
+}
+
+vlb_status vlb_step(vlb_handle* h, int64_t nsteps) {
+  vlb_status st = check_handle(h);
+  if (st) return st;
+  if (nsteps < 0) return fail(h, VLB_ERR_ARG, "nsteps must be >= 0");
+  st = h->esize == 8 ? run_steps<double>(h, nsteps) : run_steps<float>(h, nsteps);
+  if (st) return st;
+  if (h->p.diag_every > 0 && nsteps > 0) {
+    int flag = 0;
+    VLB_CUDA(h, cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    VLB_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (flag) return fail(h, VLB_ERR_UNSTABLE, "unstable state: non-finite value or |u| > 2 after %lld steps",
+                          (long long)h->steps_done);
+  }
+  return VLB_OK;
+}
+
+vlb_status vlb_get_fields(vlb_handle* h, double* rho, double* u_th, double* u_ph, double* phi, double* mu) {
+  vlb_status st = check_handle(h);
+  if (st) return st;
+  const vlb_params& p = h->p;
+  double* s = h->staging;
+  const int64_t N = h->N;
+  if (h->esize == 8)
+    VLB_CUDA(h, vlb::launch_fields<double>((const double*)h->U[0], h->stride, h->coefD, p.n_theta, p.n_phi, p.A,
+                                           p.kappa, s, s + N, s + 2 * N, s + 3 * N, s + 4 * N, h->stream));
+  else
+    VLB_CUDA(h, vlb::launch_fields<float>((const float*)h->U[0], h->stride, h->coefD, p.n_theta, p.n_phi, p.A,
+                                          p.kappa, s, s + N, s + 2 * N, s + 3 * N, s + 4 * N, h->stream));
+  double* outs[5] = {rho, u_th, u_ph, phi, mu};
+  for (int k = 0; k < 5; ++k)
+    if (outs[k])
+      VLB_CUDA(h, cudaMemcpyAsync(outs[k], s + k * N, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream));
+  VLB_CUDA(h, cudaStreamSynchronize(h->stream));
+  return VLB_OK;
+}
+
+vlb_status vlb_get_totals(vlb_handle* h, double out[4]) {
+  vlb_status st = check_handle(h);
+  if (st) return st;
+  if (!out) return fail(h, VLB_ERR_ARG, "out is NULL");
+  st = h->esize == 8 ? totals_impl<double>(h) : totals_impl<float>(h);
+  if (st) return st;
+  double t[8];
+  VLB_CUDA(h, cudaMemcpyAsync(t, h->totals, sizeof t, cudaMemcpyDeviceToHost, h->stream));
+  VLB_CUDA(h, cudaStreamSynchronize(h->stream));
+  for (int k = 0; k < 4; ++k) out[k] = t[k];
+  return VLB_OK;
+}
+
+vlb_status vlb_interface_length(vlb_handle* h, double* out) {
+  vlb_status st = check_handle(h);
+  if (st) return st;
+  if (!out) return fail(h, VLB_ERR_ARG, "out is NULL");
+  st = h->esize == 8 ? totals_impl<double>(h) : totals_impl<float>(h);
+  if (st) return st;
+  double t[8];
+  VLB_CUDA(h, cudaMemcpyAsync(t, h->totals, sizeof t, cudaMemcpyDeviceToHost, h->stream));
+  VLB_CUDA(h, cudaStreamSynchronize(h->stream));
+  *out = t[5];
+  return VLB_OK;
+}
+
+vlb_status vlb_state_device(vlb_handle* h, void** f, int64_t* stride) {
+  if (!h) return fail(nullptr, VLB_ERR_ARG, "handle is NULL");
+  if (!f || !stride) return fail(h, VLB_ERR_ARG, "NULL output");
+  *f = h->U[0];
+  *stride = h->stride;
+  return VLB_OK;
+}
+
+vlb_status vlb_steps_done(const vlb_handle* h, int64_t* out) {
+  if (!h) return fail(nullptr, VLB_ERR_ARG, "handle is NULL");
+  if (!out) return fail(const_cast<vlb_handle*>(h), VLB_ERR_ARG, "NULL output");
+  *out = h->steps_done;
+  return VLB_OK;
+}
+
+const char* vlb_last_error(const vlb_handle* h) { return h ? h->err : g_err; }
+
+}  // extern "C"

@@ -1,0 +1,76 @@
+// Internal declarations shared by the translation units of libvlb (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/vlb.h"
+
+namespace vlb {
+
+constexpr int NPOP = 16;  // Q^2 populations, k = 4 i + j
+constexpr int NARR = 17;  // 16 populations + phi per state buffer
+
+// Per-theta-row coefficient tables, one array of n_theta entries per field (SoA).
+// Computed in FP64 on the host (App. A geometry) and rounded once to the state precision.
+enum RowCoef : int {
+  C_J = 0,   // J_q = 1 + a cos theta_q                       (sqrt g = r R J)
+  C_JP,      // J_{q+1/2}
+  C_JM,      // J_{q-1/2}
+  C_CT,      // 1 / (r J_q dtheta)        theta-divergence prefactor
+  C_CP,      // 1 / (R J_q dvarphi)       varphi-divergence prefactor
+  C_GAM,     // Gamma_q = sin theta_q / (R J_q)   (Eq. conn_torus)
+  C_LT,      // 1 / (r^2 J_q dtheta^2)    Laplace-Beltrami, theta part
+  C_LP,      // 1 / (R^2 J_q^2 dvarphi^2) Laplace-Beltrami, varphi part
+  C_GP,      // 1 / (2 R J_q dvarphi)     central varphi gradient
+  C_DA,      // sqrt(g) dtheta dvarphi    area element (kept in FP64 only)
+  C_EDGE,    // (R + r cos theta_{q+1/2}) dvarphi   interface edge across theta (FP64 only)
+  NCOEF
+};
+
+// Velocity-space constants (Sec. 2.3): roots v, weights w, derivative kernel K (K~ = K diag v).
+struct VelocityConsts {
+  double v[4];
+  double w[4];
+  double K[4][4];
+};
+VelocityConsts velocity_consts();  // computed from the Hermite definitions in FP64
+
+template <typename T>
+struct StageArgs {
+  const T* fin;     // state read by the right-hand side (17 arrays)
+  const T* f0;      // U^n for the Runge-Kutta combination (unused when a0 == 0)
+  T* fout;          // output state (may alias f0 at the same node)
+  const T* coef;    // [NCOEF][n_theta]
+  int nt, ns;
+  int64_t stride;   // elements between consecutive arrays
+  T a0, b, dt;      // U_out = a0 U0 + b (U_in + dt L(U_in))
+  T inv_tau, M, A, kappa, gt;  // gt = 1 / (2 r dtheta)
+};
+
+// Host launchers (vlb_stage.cu).
+template <typename T>
+cudaError_t launch_stage(const StageArgs<T>& a, int advection, int ch_mode, cudaStream_t s);
+cudaError_t upload_velocity_consts();  // per device, once
+
+// Auxiliary kernels (vlb_aux.cu).  Staging arrays are FP64 [n_theta][n_phi].
+template <typename T>
+cudaError_t launch_init_feq(T* state, int64_t stride, const double* rho, const double* ut,
+                            const double* up, const double* phi, int64_t n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_convert_in(T* state, int64_t stride, const double* src, int64_t n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_convert_out(double* dst, const T* state, int64_t stride, int64_t n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_fields(const T* state, int64_t stride, const double* coefd, int nt, int ns, double A,
+                          double kappa, double* rho, double* ut, double* up, double* phi, double* mu,
+                          cudaStream_t s);
+// partials: n_blocks x 8 doubles; out: 8 doubles
+// out[0] mass, out[1] phi total, out[2] Psi, out[3] max|u|, out[4] non-finite count, out[5] L_I
+template <typename T>
+cudaError_t launch_totals(const T* state, int64_t stride, const double* coefd, int nt, int ns, double R,
+                          double r, double A, double kappa, int geometry, double* partials, int n_blocks,
+                          double* out, cudaStream_t s);
+int totals_blocks();
+
+}  // namespace vlb

@@ -1,0 +1,219 @@
+"""Thin ctypes binding of libvlb (include/vlb.h): argument marshalling only.
+
+Every step of the time integration runs in the CUDA library; this module converts numpy
+arrays to pointers, allocates the caller-owned device workspace with PyTorch and passes
+PyTorch's current CUDA stream.  If the library has not been built, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libvlb.so")
+
+VLB_OK, VLB_ERR_ARG, VLB_ERR_CUDA, VLB_ERR_UNSTABLE, VLB_ERR_TIMEOUT, VLB_ERR_WORKSPACE = 0, -1, -2, -3, -4, -5
+TORUS, FLAT = 0, 1
+FP64, FP32 = 0, 1
+UW3, WENO5 = 0, 1
+HYDRO, DIFFUSIVE = 0, 1
+
+# every entry point declared in include/vlb.h
+EXPORTS = ["vlb_workspace_bytes", "vlb_max_stable_dt", "vlb_create", "vlb_destroy", "vlb_set_fields",
+           "vlb_set_state", "vlb_get_state", "vlb_step", "vlb_get_fields", "vlb_get_totals",
+           "vlb_interface_length", "vlb_state_device", "vlb_steps_done", "vlb_last_error"]
+
+
+class vlb_params(ctypes.Structure):
+    _fields_ = [("geometry", ctypes.c_int32), ("n_theta", ctypes.c_int32), ("n_phi", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("advection", ctypes.c_int32), ("ch_mode", ctypes.c_int32),
+                ("diag_every", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("R", ctypes.c_double), ("r", ctypes.c_double), ("dt", ctypes.c_double),
+                ("tau", ctypes.c_double), ("M", ctypes.c_double), ("A", ctypes.c_double),
+                ("kappa", ctypes.c_double)]
+
+
+def make_params(R, r, n_theta, n_phi, dt, tau, M, A, kappa, geometry=TORUS, precision=FP64, advection=UW3,
+                ch_mode=HYDRO, diag_every=0) -> vlb_params:
+    return vlb_params(geometry=geometry, n_theta=n_theta, n_phi=n_phi, precision=precision, advection=advection,
+                      ch_mode=ch_mode, diag_every=diag_every, reserved=0, R=R, r=r, dt=dt, tau=tau, M=M, A=A,
+                      kappa=kappa)
+
+
+class VlbError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"vlb status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libvlb.so (built by paper_1904_10070_gb300.build); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_1904_10070_gb300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    P, D, I32, I64, S = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+    PP = ctypes.POINTER(vlb_params)
+    L.vlb_workspace_bytes.argtypes, L.vlb_workspace_bytes.restype = [PP], S
+    L.vlb_max_stable_dt.argtypes, L.vlb_max_stable_dt.restype = [PP, D], I32
+    L.vlb_create.argtypes, L.vlb_create.restype = [PP, P, S, P, ctypes.POINTER(P)], I32
+    L.vlb_destroy.argtypes, L.vlb_destroy.restype = [P], I32
+    L.vlb_set_fields.argtypes, L.vlb_set_fields.restype = [P, D, D, D, D], I32
+    L.vlb_set_state.argtypes, L.vlb_set_state.restype = [P, D, D], I32
+    L.vlb_get_state.argtypes, L.vlb_get_state.restype = [P, D, D], I32
+    L.vlb_step.argtypes, L.vlb_step.restype = [P, I64], I32
+    L.vlb_get_fields.argtypes, L.vlb_get_fields.restype = [P, D, D, D, D, D], I32
+    L.vlb_get_totals.argtypes, L.vlb_get_totals.restype = [P, D], I32
+    L.vlb_interface_length.argtypes, L.vlb_interface_length.restype = [P, D], I32
+    L.vlb_state_device.argtypes, L.vlb_state_device.restype = [P, ctypes.POINTER(P), ctypes.POINTER(I64)], I32
+    L.vlb_steps_done.argtypes, L.vlb_steps_done.restype = [P, ctypes.POINTER(I64)], I32
+    L.vlb_last_error.argtypes, L.vlb_last_error.restype = [P], ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _dptr(a: np.ndarray | None):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _check(st: int, handle=None):
+    if st != VLB_OK:
+        msg = lib().vlb_last_error(handle).decode()
+        raise VlbError(st, msg)
+
+
+def vlb_workspace_bytes(p: vlb_params) -> int:
+    return lib().vlb_workspace_bytes(ctypes.byref(p))
+
+
+def vlb_max_stable_dt(p: vlb_params) -> float:
+    out = ctypes.c_double()
+    _check(lib().vlb_max_stable_dt(ctypes.byref(p), ctypes.byref(out)))
+    return out.value
+
+
+def vlb_create(p: vlb_params, workspace_ptr: int, nbytes: int, stream_ptr: int):
+    h = ctypes.c_void_p()
+    _check(lib().vlb_create(ctypes.byref(p), ctypes.c_void_p(workspace_ptr), nbytes, ctypes.c_void_p(stream_ptr),
+                            ctypes.byref(h)))
+    return h
+
+
+def vlb_destroy(h):
+    _check(lib().vlb_destroy(h))
+
+
+def vlb_set_fields(h, rho, ut, up, phi):
+    arrs = [np.ascontiguousarray(x, dtype=np.float64) for x in (rho, ut, up, phi)]
+    _check(lib().vlb_set_fields(h, *[_dptr(x) for x in arrs]), h)
+
+
+def vlb_set_state(h, f16, phi):
+    f16 = np.ascontiguousarray(f16, dtype=np.float64)
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    _check(lib().vlb_set_state(h, _dptr(f16), _dptr(phi)), h)
+
+
+def vlb_get_state(h, n_theta, n_phi):
+    f16 = np.empty((16, n_theta, n_phi))
+    phi = np.empty((n_theta, n_phi))
+    _check(lib().vlb_get_state(h, _dptr(f16), _dptr(phi)), h)
+    return f16, phi
+
+
+def vlb_step(h, nsteps: int):
+    _check(lib().vlb_step(h, nsteps), h)
+
+
+def vlb_get_fields(h, n_theta, n_phi, out=None):
+    """Returns (rho, u_theta, u_phi, phi, mu) as new arrays, or fills the 5 arrays in `out`."""
+    arrs = out if out is not None else [np.empty((n_theta, n_phi)) for _ in range(5)]
+    _check(lib().vlb_get_fields(h, *[_dptr(x) for x in arrs]), h)
+    return tuple(arrs)
+
+
+def vlb_get_totals(h) -> np.ndarray:
+    out = np.empty(4)
+    _check(lib().vlb_get_totals(h, _dptr(out)), h)
+    return out
+
+
+def vlb_interface_length(h) -> float:
+    out = ctypes.c_double()
+    _check(lib().vlb_interface_length(h, ctypes.byref(out)), h)
+    return out.value
+
+
+def vlb_state_device(h):
+    p = ctypes.c_void_p()
+    s = ctypes.c_int64()
+    _check(lib().vlb_state_device(h, ctypes.byref(p), ctypes.byref(s)), h)
+    return p.value, s.value
+
+
+def vlb_steps_done(h) -> int:
+    s = ctypes.c_int64()
+    _check(lib().vlb_steps_done(h, ctypes.byref(s)), h)
+    return s.value
+
+
+class Solver:
+    """A solver handle plus its torch-allocated device workspace on the current device/stream."""
+
+    def __init__(self, params: vlb_params, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("vlb.Solver needs a CUDA device")
+        self.p = params
+        self.nbytes = vlb_workspace_bytes(params)
+        if self.nbytes == 0:
+            _check(VLB_ERR_ARG)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.workspace = torch.empty(self.nbytes, dtype=torch.uint8, device="cuda")
+        self.h = vlb_create(params, self.workspace.data_ptr(), self.nbytes, self.stream.cuda_stream)
+
+    @property
+    def shape(self):
+        return (self.p.n_theta, self.p.n_phi)
+
+    def set_fields(self, rho, ut, up, phi):
+        vlb_set_fields(self.h, rho, ut, up, phi)
+
+    def set_state(self, f16, phi):
+        vlb_set_state(self.h, f16, phi)
+
+    def get_state(self):
+        return vlb_get_state(self.h, *self.shape)
+
+    def step(self, n: int):
+        vlb_step(self.h, n)
+
+    def fields(self):
+        return vlb_get_fields(self.h, *self.shape)
+
+    def totals(self):
+        return vlb_get_totals(self.h)
+
+    def interface_length(self):
+        return vlb_interface_length(self.h)
+
+    def close(self):
+        if self.h is not None:
+            vlb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,124 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on identical seeded inputs.
+
+Gates: FP64 mode <= 1e-12 relative in rho, u, phi (and mu, the full f state); FP32 mode
+<= 2e-5 relative.  Relative error is ||x - x_ref|| / max(||x_ref||, 1e-3 sqrt(N)).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import vlb_oracle as O
+from paper_1904_10070_gb300 import inputs, vlb
+from tests.gpu_helpers import oracle_fields, oracle_params, rel_err, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+FP32_TOL = 2e-5
+
+
+def _random_fields(nt, ns, seed, amp_u=0.05):
+    rng = np.random.default_rng(seed)
+    rho = 1.0 + 0.1 * rng.uniform(-1, 1, (nt, ns))
+    ut = amp_u * rng.uniform(-1, 1, (nt, ns))
+    up = amp_u * rng.uniform(-1, 1, (nt, ns))
+    phi = np.tanh(2.0 * rng.uniform(-1, 1, (nt, ns)))
+    return rho, ut, up, phi
+
+
+def _compare(p, rho, ut, up, phi, steps, precision, tol):
+    (g_rho, g_ut, g_up, g_phi, g_mu), (g_f, _), g_tot = run_gpu(p, rho, ut, up, phi, steps, precision)
+    op = oracle_params(p)
+    geo = O.Geometry(op)
+    f, ph = O.init_state(rho, ut, up, phi)
+    f, ph = O.run(f, ph, geo, steps)
+    o_rho, o_ut, o_up, o_phi, o_mu = oracle_fields(f, ph, geo)
+    errs = {"rho": rel_err(g_rho, o_rho), "u_th": rel_err(g_ut, o_ut), "u_ph": rel_err(g_up, o_up),
+            "phi": rel_err(g_phi, o_phi), "mu": rel_err(g_mu, o_mu),
+            "f": rel_err(g_f, f.reshape(16, *ph.shape))}
+    bad = {k: v for k, v in errs.items() if not v <= tol}
+    assert not bad, f"relative errors above {tol}: {errs}"
+    o_tot = O.totals(f, ph, geo)
+    np.testing.assert_allclose(g_tot[:3], o_tot[:3], rtol=max(tol, 1e-12) * 10, atol=1e-12)
+    return errs
+
+
+def test_drop_torus_32x64_fp64_500_steps():
+    w = inputs.workload("drop_torus_32x64")
+    errs = _compare(w["params"], w["rho"], w["ut"], w["up"], w["phi"], 500, vlb.FP64, FP64_TOL)
+    print("fp64 drop 500 steps", errs)
+
+
+def test_drop_torus_32x64_fp32_500_steps():
+    w = inputs.workload("drop_torus_32x64")
+    errs = _compare(w["params"], w["rho"], w["ut"], w["up"], w["phi"], 500, vlb.FP32, FP32_TOL)
+    print("fp32 drop 500 steps", errs)
+
+
+CASES = [
+    # (n_theta, n_phi, geometry, advection, ch_mode): ragged tiles, tiny grids, N_phi = 1, both schemes
+    (37, 45, vlb.TORUS, vlb.UW3, vlb.HYDRO),
+    (37, 45, vlb.TORUS, vlb.WENO5, vlb.HYDRO),
+    (40, 70, vlb.FLAT, vlb.UW3, vlb.HYDRO),
+    (33, 66, vlb.TORUS, vlb.UW3, vlb.DIFFUSIVE),
+    (18, 40, vlb.FLAT, vlb.WENO5, vlb.DIFFUSIVE),
+    (6, 7, vlb.TORUS, vlb.WENO5, vlb.HYDRO),
+    (4, 5, vlb.TORUS, vlb.UW3, vlb.HYDRO),
+    (64, 1, vlb.TORUS, vlb.UW3, vlb.HYDRO),
+    (24, 1, vlb.TORUS, vlb.WENO5, vlb.HYDRO),
+    (17, 33, vlb.TORUS, vlb.UW3, vlb.HYDRO),
+]
+
+
+@pytest.mark.parametrize("nt,ns,geom,adv,mode", CASES)
+@pytest.mark.parametrize("precision", [vlb.FP64, vlb.FP32])
+def test_ragged_and_degenerate_grids(nt, ns, geom, adv, mode, precision):
+    p = dict(geometry=geom, R=2.3, r=1.0, n_theta=nt, n_phi=ns, dt=2e-3, tau=0.2, M=0.05, A=0.3, kappa=0.01,
+             advection=adv, ch_mode=mode)
+    rho, ut, up, phi = _random_fields(nt, ns, seed=nt * 1000 + ns)
+    _compare(p, rho, ut, up, phi, 15, precision, FP64_TOL if precision == vlb.FP64 else FP32_TOL)
+
+
+def test_no_collision_limit_tau_infinite():
+    p = dict(geometry=vlb.TORUS, R=2.0, r=0.7, n_theta=20, n_phi=36, dt=2e-3, tau=math.inf, M=0.05, A=0.3,
+             kappa=0.01, advection=vlb.UW3, ch_mode=vlb.HYDRO)
+    rho, ut, up, phi = _random_fields(20, 36, seed=5)
+    _compare(p, rho, ut, up, phi, 10, vlb.FP64, FP64_TOL)
+
+
+def test_state_roundtrip_and_checkpoint_resume_bitwise():
+    w = inputs.workload("drop_torus_32x64")
+    from tests.gpu_helpers import gpu_params
+    a = vlb.Solver(gpu_params(w["params"], vlb.FP32))
+    a.set_fields(w["rho"], w["ut"], w["up"], w["phi"])
+    a.step(40)
+    f_mid, phi_mid = a.get_state()
+    a.step(40)
+    f_end, phi_end = a.get_state()
+    b = vlb.Solver(gpu_params(w["params"], vlb.FP32))
+    b.set_state(f_mid, phi_mid)
+    f_chk, phi_chk = b.get_state()
+    np.testing.assert_array_equal(f_chk, f_mid)
+    np.testing.assert_array_equal(phi_chk, phi_mid)
+    b.step(40)
+    f2, phi2 = b.get_state()
+    np.testing.assert_array_equal(f2, f_end)
+    np.testing.assert_array_equal(phi2, phi_end)
+    assert vlb.vlb_steps_done(b.h) == 40
+    a.close()
+    b.close()
+
+
+def test_interface_length_matches_oracle():
+    nt, ns = 48, 80
+    p = dict(geometry=vlb.TORUS, R=2.5, r=1.0, n_theta=nt, n_phi=ns, dt=1e-3, tau=0.5, M=0.05, A=0.3, kappa=0.01,
+             advection=vlb.UW3, ch_mode=vlb.HYDRO)
+    phi = inputs.noise(9, nt, ns, 0.5)
+    from tests.gpu_helpers import gpu_params
+    s = vlb.Solver(gpu_params(p))
+    s.set_fields(np.ones_like(phi), 0 * phi, 0 * phi, phi)
+    L = s.interface_length()
+    ref = O.interface_length(phi, O.Geometry(oracle_params(p)))
+    assert abs(L - ref) <= 1e-12 * ref
+    s.close()
