@@ -37,7 +37,7 @@ __device__ __forceinline__ int wrapi(int x, int n) {
 // f := f^eq(rho, u) (Eq. feq), phi := phi; evaluated in FP64, rounded once.
 template <typename T>
 __global__ void init_feq_kernel(T* state, int64_t stride, const double* rho, const double* ut, const double* up,
-                                const double* phi, int64_t n, VD vd) {
+                                const double* phi, int64_t n, double n0, VD vd) {
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
     const double nn = rho[idx], a = ut[idx], b = up[idx];
     const double usq = a * a + b * b;
@@ -46,34 +46,39 @@ __global__ void init_feq_kernel(T* state, int64_t stride, const double* rho, con
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const double xi = vd.v[i] * a + vd.v[j] * b;
-        const double poly = 1.0 + xi + 0.5 * (xi * xi - usq) + xi * (xi * xi - 3.0 * usq) / 6.0;
-        state[(4 * i + j) * stride + idx] = (T)(nn * vd.w[i] * vd.w[j] * poly);
+        const double pm1 = xi + 0.5 * (xi * xi - usq) + xi * (xi * xi - 3.0 * usq) / 6.0;
+        // stored deviation g = f^eq - n0 w_i w_j = w_i w_j ((n - n0) + n (poly - 1))
+        state[(4 * i + j) * stride + idx] = (T)(vd.w[i] * vd.w[j] * ((nn - n0) + nn * pm1));
       }
     state[NPOP * stride + idx] = (T)phi[idx];
   }
 }
 
+__device__ __forceinline__ double ref_pop(int k, double n0, const VD& vd) {
+  return k < NPOP ? n0 * vd.w[k >> 2] * vd.w[k & 3] : 0.0;
+}
+
 template <typename T>
-__global__ void convert_in_kernel(T* state, int64_t stride, const double* src, int64_t n) {
+__global__ void convert_in_kernel(T* state, int64_t stride, const double* src, int64_t n, double n0, VD vd) {
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n * NARR;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t k = idx / n, i = idx - k * n;
-    state[k * stride + i] = (T)src[idx];
+    state[k * stride + i] = (T)(src[idx] - ref_pop((int)k, n0, vd));
   }
 }
 
 template <typename T>
-__global__ void convert_out_kernel(double* dst, const T* state, int64_t stride, int64_t n) {
+__global__ void convert_out_kernel(double* dst, const T* state, int64_t stride, int64_t n, double n0, VD vd) {
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n * NARR;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t k = idx / n, i = idx - k * n;
-    dst[idx] = (double)state[k * stride + i];
+    dst[idx] = (double)state[k * stride + i] + ref_pop((int)k, n0, vd);
   }
 }
 
 template <typename T>
-__device__ __forceinline__ void node_moments(const T* state, int64_t stride, int64_t idx, const VD& vd, double& n,
-                                             double& ut, double& up) {
+__device__ __forceinline__ void node_moments(const T* state, int64_t stride, int64_t idx, const VD& vd, double n0,
+                                             double& n, double& ut, double& up) {
   double row[4] = {0, 0, 0, 0}, col[4] = {0, 0, 0, 0};
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -83,7 +88,7 @@ __device__ __forceinline__ void node_moments(const T* state, int64_t stride, int
       row[i] += x;
       col[j] += x;
     }
-  n = (row[0] + row[1]) + (row[2] + row[3]);
+  n = n0 + ((row[0] + row[1]) + (row[2] + row[3]));
   ut = (vd.v[0] * row[0] + vd.v[1] * row[1] + vd.v[2] * row[2] + vd.v[3] * row[3]) / n;
   up = (vd.v[0] * col[0] + vd.v[1] * col[1] + vd.v[2] * col[2] + vd.v[3] * col[3]) / n;
 }
@@ -91,13 +96,13 @@ __device__ __forceinline__ void node_moments(const T* state, int64_t stride, int
 // rho, u (Sec. 2.3 moments), phi and mu (Eq. mu) in FP64.
 template <typename T>
 __global__ void fields_kernel(const T* state, int64_t stride, const double* coefd, int nt, int ns, double A,
-                              double kappa, double* rho, double* ut, double* up, double* phi, double* mu, VD vd) {
+                              double kappa, double n0, double* rho, double* ut, double* up, double* phi, double* mu, VD vd) {
   const int64_t n = (int64_t)nt * ns;
   const T* ph = state + NPOP * stride;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
     const int q = (int)(idx / ns), s = (int)(idx - (int64_t)q * ns);
     double nn, a, b;
-    node_moments(state, stride, idx, vd, nn, a, b);
+    node_moments(state, stride, idx, vd, n0, nn, a, b);
     rho[idx] = nn;
     ut[idx] = a;
     up[idx] = b;
@@ -117,14 +122,15 @@ __global__ void fields_kernel(const T* state, int64_t stride, const double* coef
 template <typename T>
 __global__ void __launch_bounds__(TOTAL_THREADS) totals_kernel(const T* state, int64_t stride, const double* coefd,
                                                                int nt, int ns, double r, double A, double kappa,
-                                                               double gt, double edge_p, double* partials, VD vd) {
+                                                               double n0, double gt, double edge_p, double* partials,
+                                                               VD vd) {
   const int64_t n = (int64_t)nt * ns;
   const T* ph = state + NPOP * stride;
   double acc[NSUM] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
     const int q = (int)(idx / ns), s = (int)(idx - (int64_t)q * ns);
     double nn, a, b;
-    node_moments(state, stride, idx, vd, nn, a, b);
+    node_moments(state, stride, idx, vd, n0, nn, a, b);
     const double dA = coefd[C_DA * nt + q];
     const double p0 = (double)ph[idx];
     const double pn = (double)ph[(int64_t)wrapi(q + 1, nt) * ns + s];
@@ -186,42 +192,42 @@ int totals_blocks() { return TOTAL_BLOCKS; }
 
 template <typename T>
 cudaError_t launch_init_feq(T* state, int64_t stride, const double* rho, const double* ut, const double* up,
-                            const double* phi, int64_t n, cudaStream_t s) {
-  init_feq_kernel<T><<<grid_for(n), 256, 0, s>>>(state, stride, rho, ut, up, phi, n, make_vd());
+                            const double* phi, int64_t n, double n0, cudaStream_t s) {
+  init_feq_kernel<T><<<grid_for(n), 256, 0, s>>>(state, stride, rho, ut, up, phi, n, n0, make_vd());
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_convert_in(T* state, int64_t stride, const double* src, int64_t n, cudaStream_t s) {
-  convert_in_kernel<T><<<grid_for(n * NARR), 256, 0, s>>>(state, stride, src, n);
+cudaError_t launch_convert_in(T* state, int64_t stride, const double* src, int64_t n, double n0, cudaStream_t s) {
+  convert_in_kernel<T><<<grid_for(n * NARR), 256, 0, s>>>(state, stride, src, n, n0, make_vd());
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_convert_out(double* dst, const T* state, int64_t stride, int64_t n, cudaStream_t s) {
-  convert_out_kernel<T><<<grid_for(n * NARR), 256, 0, s>>>(dst, state, stride, n);
+cudaError_t launch_convert_out(double* dst, const T* state, int64_t stride, int64_t n, double n0, cudaStream_t s) {
+  convert_out_kernel<T><<<grid_for(n * NARR), 256, 0, s>>>(dst, state, stride, n, n0, make_vd());
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_fields(const T* state, int64_t stride, const double* coefd, int nt, int ns, double A, double kappa,
-                          double* rho, double* ut, double* up, double* phi, double* mu, cudaStream_t s) {
-  fields_kernel<T><<<grid_for((int64_t)nt * ns), 256, 0, s>>>(state, stride, coefd, nt, ns, A, kappa, rho, ut, up,
-                                                             phi, mu, make_vd());
+                          double n0, double* rho, double* ut, double* up, double* phi, double* mu, cudaStream_t s) {
+  fields_kernel<T><<<grid_for((int64_t)nt * ns), 256, 0, s>>>(state, stride, coefd, nt, ns, A, kappa, n0, rho, ut,
+                                                             up, phi, mu, make_vd());
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_totals(const T* state, int64_t stride, const double* coefd, int nt, int ns, double R, double r,
-                          double A, double kappa, int geometry, double* partials, int n_blocks, double* out,
-                          cudaStream_t s) {
+                          double A, double kappa, double n0, int geometry, double* partials, int n_blocks,
+                          double* out, cudaStream_t s) {
   (void)R;
   (void)geometry;
   const double dth = 2.0 * M_PI / nt;
   const double gt = 1.0 / (2.0 * r * dth);
   const double edge_p = r * dth;
-  totals_kernel<T><<<n_blocks, TOTAL_THREADS, 0, s>>>(state, stride, coefd, nt, ns, r, A, kappa, gt, edge_p, partials,
-                                                      make_vd());
+  totals_kernel<T><<<n_blocks, TOTAL_THREADS, 0, s>>>(state, stride, coefd, nt, ns, r, A, kappa, n0, gt, edge_p,
+                                                      partials, make_vd());
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   totals_final_kernel<<<1, 32, 0, s>>>(partials, n_blocks, out);
@@ -230,13 +236,13 @@ cudaError_t launch_totals(const T* state, int64_t stride, const double* coefd, i
 
 #define VLB_INST(T)                                                                                              \
   template cudaError_t launch_init_feq<T>(T*, int64_t, const double*, const double*, const double*,              \
-                                          const double*, int64_t, cudaStream_t);                                  \
-  template cudaError_t launch_convert_in<T>(T*, int64_t, const double*, int64_t, cudaStream_t);                 \
-  template cudaError_t launch_convert_out<T>(double*, const T*, int64_t, int64_t, cudaStream_t);                \
-  template cudaError_t launch_fields<T>(const T*, int64_t, const double*, int, int, double, double, double*,     \
-                                        double*, double*, double*, double*, cudaStream_t);                        \
+                                          const double*, int64_t, double, cudaStream_t);                          \
+  template cudaError_t launch_convert_in<T>(T*, int64_t, const double*, int64_t, double, cudaStream_t);         \
+  template cudaError_t launch_convert_out<T>(double*, const T*, int64_t, int64_t, double, cudaStream_t);        \
+  template cudaError_t launch_fields<T>(const T*, int64_t, const double*, int, int, double, double, double,     \
+                                        double*, double*, double*, double*, double*, cudaStream_t);               \
   template cudaError_t launch_totals<T>(const T*, int64_t, const double*, int, int, double, double, double,      \
-                                        double, int, double*, int, double*, cudaStream_t);
+                                        double, double, int, double*, int, double*, cudaStream_t);
 VLB_INST(float)
 VLB_INST(double)
 #undef VLB_INST

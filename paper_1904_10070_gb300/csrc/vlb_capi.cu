@@ -36,6 +36,7 @@ struct vlb_handle {
   double* totals;      // 8 doubles (read-out)
   double* diag;        // 8 doubles (last in-step diagnostic)
   int* flag;           // device flag: diagnostics found an unstable state
+  double n0;           // reference density of the stored deviations g = f - n0 w_i w_j
   int64_t steps_done;
   char err[512];
 };
@@ -142,6 +143,19 @@ void row_tables(const vlb_params* p, double* out) {
     out[vlb::C_LT * nt + q] = 1.0 / (p->r * p->r * J * dth * dth);
     out[vlb::C_LP * nt + q] = 1.0 / (p->R * p->R * J * J * dph * dph);
     out[vlb::C_GP * nt + q] = 1.0 / (2.0 * p->R * J * dph);
+    // Rest-state residual E(q) = -D[J](q) / (r J dtheta) - Gamma (UW3 flux differences of the
+    // J row values, v > 0 and v < 0); WENO5 advects the full J f, leaving E = -Gamma.
+    const double gam = out[vlb::C_GAM * nt + q];
+    if (p->advection == VLB_UW3) {
+      auto Jat = [&](int d) { return 1.0 + a * cos(th + d * dth); };
+      const double dpos = (Jat(-2) - 6.0 * Jat(-1) + 3.0 * Jat(0) + 2.0 * Jat(1)) / 6.0;
+      const double dneg = (-2.0 * Jat(-1) - 3.0 * Jat(0) + 6.0 * Jat(1) - Jat(2)) / 6.0;
+      out[vlb::C_EP * nt + q] = -dpos / (p->r * J * dth) - gam;
+      out[vlb::C_EN * nt + q] = -dneg / (p->r * J * dth) - gam;
+    } else {
+      out[vlb::C_EP * nt + q] = -gam;
+      out[vlb::C_EN * nt + q] = -gam;
+    }
     out[vlb::C_DA * nt + q] = p->r * p->R * J * dth * dph;
     out[vlb::C_EDGE * nt + q] = torus ? (p->R + p->r * cos(th + 0.5 * dth)) * dph : p->R * dph;
   }
@@ -161,22 +175,23 @@ vlb_status run_steps(vlb_handle* h, int64_t nsteps) {
   a.A = (T)p.A;
   a.kappa = (T)p.kappa;
   a.gt = (T)(1.0 / (2.0 * p.r * (2.0 * M_PI / p.n_theta)));
+  a.n0 = (T)h->n0;
   T* U0 = (T*)h->U[0];
   T* U1 = (T*)h->U[1];
   T* U2 = (T*)h->U[2];
   for (int64_t n = 0; n < nsteps; ++n) {
     // SSP-RK3 (Shu & Osher 1988): U1 = U + dt L(U); U2 = 3/4 U + 1/4 (U1 + dt L(U1));
     // U <- 1/3 U + 2/3 (U2 + dt L(U2))
-    a.fin = U0; a.f0 = nullptr; a.fout = U1; a.a0 = (T)0; a.b = (T)1;
+    a.fin = U0; a.f0 = nullptr; a.fout = U1; a.b = (T)1;
     VLB_CUDA(h, vlb::launch_stage<T>(a, p.advection, p.ch_mode, h->stream));
-    a.fin = U1; a.f0 = U0; a.fout = U2; a.a0 = (T)0.75; a.b = (T)0.25;
+    a.fin = U1; a.f0 = U0; a.fout = U2; a.b = (T)0.25;
     VLB_CUDA(h, vlb::launch_stage<T>(a, p.advection, p.ch_mode, h->stream));
-    a.fin = U2; a.f0 = U0; a.fout = U0; a.a0 = (T)(1.0 / 3.0); a.b = (T)(2.0 / 3.0);
+    a.fin = U2; a.f0 = U0; a.fout = U0; a.b = (T)(2.0 / 3.0);
     VLB_CUDA(h, vlb::launch_stage<T>(a, p.advection, p.ch_mode, h->stream));
     h->steps_done++;
     if (p.diag_every > 0 && (h->steps_done % p.diag_every == 0 || n + 1 == nsteps)) {
       VLB_CUDA(h, vlb::launch_totals<T>(U0, h->stride, h->coefD, p.n_theta, p.n_phi, p.R, p.r, p.A, p.kappa,
-                                        p.geometry, h->partials, vlb::totals_blocks(), h->diag, h->stream));
+                                        h->n0, p.geometry, h->partials, vlb::totals_blocks(), h->diag, h->stream));
       VLB_CUDA(h, vlb_internal_flag(h->diag, h->flag, h->stream));
     }
   }
@@ -187,7 +202,8 @@ template <typename T>
 vlb_status totals_impl(vlb_handle* h) {
   const vlb_params& p = h->p;
   VLB_CUDA(h, vlb::launch_totals<T>((const T*)h->U[0], h->stride, h->coefD, p.n_theta, p.n_phi, p.R, p.r, p.A,
-                                    p.kappa, p.geometry, h->partials, vlb::totals_blocks(), h->totals, h->stream));
+                                    p.kappa, h->n0, p.geometry, h->partials, vlb::totals_blocks(), h->totals,
+                                    h->stream));
   return VLB_OK;
 }
 
@@ -316,6 +332,7 @@ vlb_status vlb_create(const vlb_params* p, void* d_workspace, size_t bytes, void
   h->diag = (double*)(h->ws + L.off_diag);
   h->flag = (int*)(h->ws + L.off_flag);
   h->steps_done = 0;
+  h->n0 = 1.0;
   h->err[0] = 0;
   cudaError_t e = cudaGetDevice(&h->device);
   if (e != cudaSuccess) {
@@ -364,6 +381,11 @@ vlb_status vlb_set_fields(vlb_handle* h, const double* rho, const double* u_th, 
   vlb_status st = check_handle(h);
   if (st) return st;
   if (!rho || !u_th || !u_ph || !phi) return fail(h, VLB_ERR_ARG, "vlb_set_fields: NULL input");
+  // reference density of the stored deviations: the mean input density
+  double acc = 0.0;
+  for (int64_t i = 0; i < h->N; ++i) acc += rho[i];
+  if (!isfinite(acc)) return fail(h, VLB_ERR_ARG, "vlb_set_fields: non-finite density");
+  h->n0 = acc / (double)h->N;
   const size_t nb = sizeof(double) * h->N;
   double* s = h->staging;
   VLB_CUDA(h, cudaMemcpyAsync(s, rho, nb, cudaMemcpyHostToDevice, h->stream));
@@ -372,10 +394,10 @@ vlb_status vlb_set_fields(vlb_handle* h, const double* rho, const double* u_th, 
   VLB_CUDA(h, cudaMemcpyAsync(s + 3 * h->N, phi, nb, cudaMemcpyHostToDevice, h->stream));
   if (h->esize == 8)
     VLB_CUDA(h, vlb::launch_init_feq<double>((double*)h->U[0], h->stride, s, s + h->N, s + 2 * h->N, s + 3 * h->N,
-                                             h->N, h->stream));
+                                             h->N, h->n0, h->stream));
   else
     VLB_CUDA(h, vlb::launch_init_feq<float>((float*)h->U[0], h->stride, s, s + h->N, s + 2 * h->N, s + 3 * h->N,
-                                            h->N, h->stream));
+                                            h->N, h->n0, h->stream));
   VLB_CUDA(h, cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
   VLB_CUDA(h, cudaStreamSynchronize(h->stream));
   h->steps_done = 0;
@@ -386,13 +408,17 @@ vlb_status vlb_set_state(vlb_handle* h, const double* f16, const double* phi) {
   vlb_status st = check_handle(h);
   if (st) return st;
   if (!f16 || !phi) return fail(h, VLB_ERR_ARG, "vlb_set_state: NULL input");
+  double acc = 0.0;
+  for (int64_t i = 0; i < 16 * h->N; ++i) acc += f16[i];
+  if (!isfinite(acc)) return fail(h, VLB_ERR_ARG, "vlb_set_state: non-finite populations");
+  h->n0 = acc / (double)h->N;
   const size_t nb = sizeof(double) * h->N;
   VLB_CUDA(h, cudaMemcpyAsync(h->staging, f16, 16 * nb, cudaMemcpyHostToDevice, h->stream));
   VLB_CUDA(h, cudaMemcpyAsync(h->staging + 16 * h->N, phi, nb, cudaMemcpyHostToDevice, h->stream));
   if (h->esize == 8)
-    VLB_CUDA(h, vlb::launch_convert_in<double>((double*)h->U[0], h->stride, h->staging, h->N, h->stream));
+    VLB_CUDA(h, vlb::launch_convert_in<double>((double*)h->U[0], h->stride, h->staging, h->N, h->n0, h->stream));
   else
-    VLB_CUDA(h, vlb::launch_convert_in<float>((float*)h->U[0], h->stride, h->staging, h->N, h->stream));
+    VLB_CUDA(h, vlb::launch_convert_in<float>((float*)h->U[0], h->stride, h->staging, h->N, h->n0, h->stream));
   VLB_CUDA(h, cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
   VLB_CUDA(h, cudaStreamSynchronize(h->stream));
   h->steps_done = 0;
@@ -404,9 +430,11 @@ vlb_status vlb_get_state(vlb_handle* h, double* f16, double* phi) {
   if (st) return st;
   if (!f16 || !phi) return fail(h, VLB_ERR_ARG, "vlb_get_state: NULL output");
   if (h->esize == 8)
-    VLB_CUDA(h, vlb::launch_convert_out<double>(h->staging, (const double*)h->U[0], h->stride, h->N, h->stream));
+    VLB_CUDA(h, vlb::launch_convert_out<double>(h->staging, (const double*)h->U[0], h->stride, h->N, h->n0,
+                                                h->stream));
   else
-    VLB_CUDA(h, vlb::launch_convert_out<float>(h->staging, (const float*)h->U[0], h->stride, h->N, h->stream));
+    VLB_CUDA(h, vlb::launch_convert_out<float>(h->staging, (const float*)h->U[0], h->stride, h->N, h->n0,
+                                               h->stream));
   const size_t nb = sizeof(double) * h->N;
   VLB_CUDA(h, cudaMemcpyAsync(f16, h->staging, 16 * nb, cudaMemcpyDeviceToHost, h->stream));
   VLB_CUDA(h, cudaMemcpyAsync(phi, h->staging + 16 * h->N, nb, cudaMemcpyDeviceToHost, h->stream));
@@ -438,10 +466,10 @@ vlb_status vlb_get_fields(vlb_handle* h, double* rho, double* u_th, double* u_ph
   const int64_t N = h->N;
   if (h->esize == 8)
     VLB_CUDA(h, vlb::launch_fields<double>((const double*)h->U[0], h->stride, h->coefD, p.n_theta, p.n_phi, p.A,
-                                           p.kappa, s, s + N, s + 2 * N, s + 3 * N, s + 4 * N, h->stream));
+                                           p.kappa, h->n0, s, s + N, s + 2 * N, s + 3 * N, s + 4 * N, h->stream));
   else
     VLB_CUDA(h, vlb::launch_fields<float>((const float*)h->U[0], h->stride, h->coefD, p.n_theta, p.n_phi, p.A,
-                                          p.kappa, s, s + N, s + 2 * N, s + 3 * N, s + 4 * N, h->stream));
+                                          p.kappa, h->n0, s, s + N, s + 2 * N, s + 3 * N, s + 4 * N, h->stream));
   double* outs[5] = {rho, u_th, u_ph, phi, mu};
   for (int k = 0; k < 5; ++k)
     if (outs[k])

@@ -23,10 +23,23 @@ enum RowCoef : int {
   C_LT,      // 1 / (r^2 J_q dtheta^2)    Laplace-Beltrami, theta part
   C_LP,      // 1 / (R^2 J_q^2 dvarphi^2) Laplace-Beltrami, varphi part
   C_GP,      // 1 / (2 R J_q dvarphi)     central varphi gradient
+  C_EP,      // rest-state residual for v_i > 0 (see below)
+  C_EN,      // rest-state residual for v_i < 0
   C_DA,      // sqrt(g) dtheta dvarphi    area element (kept in FP64 only)
   C_EDGE,    // (R + r cos theta_{q+1/2}) dvarphi   interface edge across theta (FP64 only)
   NCOEF
 };
+
+// Storage: the populations are kept as g_k = f_k - n0 w_i w_j, the deviation from the rest
+// equilibrium at a reference density n0 (fixed at set time).  Every term of the right-hand side is
+// linear in f except the BGK equilibrium and the WENO weights, so the reference part is carried
+// through exact identities of the Q = 4 kernel: (K w)_i = -v_i w_i and (K (v w))_i = w_i (1 - v_i^2).
+// The reference part of the force, inertial and UW3 advection terms then collapses to
+//   n0 w_i w_j [ v_i (E_sign(v_i)(q) + F^theta) + v_j F^phi ],
+// with E_pos/neg(q) = -D_pos/neg[J](q) / (r J_q dtheta) - Gamma_q the discrete residual of the
+// continuum cancellation between the J-flux and the inertial term (E = -Gamma for WENO5, whose
+// theta-advection acts on the full J f).  The state therefore keeps FP32 resolution on the
+// small deviations that carry the dynamics instead of on f ~ n w_i w_j.
 
 // Velocity-space constants (Sec. 2.3): roots v, weights w, derivative kernel K (K~ = K diag v).
 struct VelocityConsts {
@@ -39,38 +52,38 @@ VelocityConsts velocity_consts();  // computed from the Hermite definitions in F
 template <typename T>
 struct StageArgs {
   const T* fin;     // state read by the right-hand side (17 arrays)
-  const T* f0;      // U^n for the Runge-Kutta combination (unused when a0 == 0)
+  const T* f0;      // U^n for the Runge-Kutta combination (NULL in the first stage)
   T* fout;          // output state (may alias f0 at the same node)
   const T* coef;    // [NCOEF][n_theta]
   int nt, ns;
   int64_t stride;   // elements between consecutive arrays
-  T a0, b, dt;      // U_out = a0 U0 + b (U_in + dt L(U_in))
+  T b, dt;         // U_out = U0 + b (U_in - U0 + dt L(U_in)); without U0: U_in + dt L(U_in)
   T inv_tau, M, A, kappa, gt;  // gt = 1 / (2 r dtheta)
+  T n0;             // reference density of the stored deviations
 };
 
 // Host launchers (vlb_stage.cu).
 template <typename T>
 cudaError_t launch_stage(const StageArgs<T>& a, int advection, int ch_mode, cudaStream_t s);
-cudaError_t upload_velocity_consts();  // per device, once
 
 // Auxiliary kernels (vlb_aux.cu).  Staging arrays are FP64 [n_theta][n_phi].
 template <typename T>
 cudaError_t launch_init_feq(T* state, int64_t stride, const double* rho, const double* ut,
-                            const double* up, const double* phi, int64_t n, cudaStream_t s);
+                            const double* up, const double* phi, int64_t n, double n0, cudaStream_t s);
 template <typename T>
-cudaError_t launch_convert_in(T* state, int64_t stride, const double* src, int64_t n, cudaStream_t s);
+cudaError_t launch_convert_in(T* state, int64_t stride, const double* src, int64_t n, double n0, cudaStream_t s);
 template <typename T>
-cudaError_t launch_convert_out(double* dst, const T* state, int64_t stride, int64_t n, cudaStream_t s);
+cudaError_t launch_convert_out(double* dst, const T* state, int64_t stride, int64_t n, double n0, cudaStream_t s);
 template <typename T>
 cudaError_t launch_fields(const T* state, int64_t stride, const double* coefd, int nt, int ns, double A,
-                          double kappa, double* rho, double* ut, double* up, double* phi, double* mu,
+                          double kappa, double n0, double* rho, double* ut, double* up, double* phi, double* mu,
                           cudaStream_t s);
 // partials: n_blocks x 8 doubles; out: 8 doubles
 // out[0] mass, out[1] phi total, out[2] Psi, out[3] max|u|, out[4] non-finite count, out[5] L_I
 template <typename T>
 cudaError_t launch_totals(const T* state, int64_t stride, const double* coefd, int nt, int ns, double R,
-                          double r, double A, double kappa, int geometry, double* partials, int n_blocks,
-                          double* out, cudaStream_t s);
+                          double r, double A, double kappa, double n0, int geometry, double* partials,
+                          int n_blocks, double* out, cudaStream_t s);
 int totals_blocks();
 
 }  // namespace vlb

@@ -3,7 +3,9 @@
 // One launch evaluates, for every node of the periodic (theta, varphi) grid,
 //   L_f   = right-hand side of Eq. boltz_tor with BGK collisions (Sec. 2.3),
 //   L_phi = right-hand side of Eq. CH with mu from Eq. mu and the force of Eq. pbin,
-// and writes U_out = a0 U^n + b (U_in + dt L(U_in)) -- one stage of SSP-RK3 in Shu-Osher form.
+// and writes U_out = U^n + b (U_in - U^n + dt L(U_in)) -- one stage of SSP-RK3 in Shu-Osher form
+// (b = 1, 1/4, 2/3), written so that the weights only multiply small increments.  The populations
+// are stored as deviations g = f - n0 w_i w_j from the rest equilibrium (vlb_internal.cuh).
 //
 // Tiling: a CTA owns a 16 (theta) x 32 (varphi) tile; 256 threads, each thread two nodes.
 // Shared memory holds, for the tile plus its halo:
@@ -24,7 +26,7 @@ constexpr int TYT = 8;       // thread rows
 constexpr int NQ = 2;        // nodes per thread along theta
 constexpr int TQ = TYT * NQ; // tile height along theta
 constexpr int NTHREADS = TS * TYT;
-constexpr int NCT = 9;       // coefficient rows staged in shared memory (C_J .. C_GP)
+constexpr int NCT = 11;      // coefficient rows staged in shared memory (C_J .. C_EN)
 
 template <typename T>
 struct VConst {
@@ -89,7 +91,7 @@ __device__ __forceinline__ T flux_diff(const T (&x)[7]) {
 }
 
 template <typename T, int ADV, int CH>
-__global__ void __launch_bounds__(NTHREADS, 2) stage_kernel(StageArgs<T> a, VConst<T> vc) {
+__global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? (ADV == VLB_UW3 ? 3 : 2) : 1) stage_kernel(StageArgs<T> a, VConst<T> vc) {
   using S = Smem<T, ADV>;
   constexpr int H = S::H, BQ = S::BQ, BS = S::BS, PQ = S::PQ, PS = S::PS, MQ = S::MQ, MS = S::MS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -164,11 +166,13 @@ __global__ void __launch_bounds__(NTHREADS, 2) stage_kernel(StageArgs<T> a, VCon
           row[i] += x;
           col[j] += x;
         }
-      const T n = (row[0] + row[1]) + (row[2] + row[3]);
+      // n = n0 + sum g (the reference part carries no momentum: sum_k w_i w_j v = 0)
+      const T dn = (row[0] + row[1]) + (row[2] + row[3]);
       const T mt = vc.v[0] * row[0] + vc.v[1] * row[1] + vc.v[2] * row[2] + vc.v[3] * row[3];
       const T mp = vc.v[0] * col[0] + vc.v[1] * col[1] + vc.v[2] * col[2] + vc.v[3] * col[3];
       const int mi = mr * MS + mc;
-      sn[mi] = n;
+      const T n = a.n0 + dn;
+      sn[mi] = dn;
       sut[mi] = mt / n;
       sup[mi] = mp / n;
       const T* pp = sphi + (mr + 1) * PS + (mc + 1);
@@ -191,9 +195,10 @@ __global__ void __launch_bounds__(NTHREADS, 2) stage_kernel(StageArgs<T> a, VCon
     const int mi = (lr + 1) * MS + (lc + 1);
     const int pi = (lr + 2) * PS + (lc + 2);
 
-    const T n = sn[mi], ut = sut[mi], up = sup[mi], ph = sphi[pi];
-    const T J = sco[C_J * BQ + fr];
+    const T dn = sn[mi], ut = sut[mi], up = sup[mi], ph = sphi[pi];
+    const T n = a.n0 + dn;
     const T ct = sco[C_CT * BQ + fr], cp = sco[C_CP * BQ + fr], gam = sco[C_GAM * BQ + fr];
+    const T Ep = sco[C_EP * BQ + fr], En = sco[C_EN * BQ + fr];
     const T mu_c = smu[mi], mu_n = smu[mi + MS], mu_s = smu[mi - MS], mu_e = smu[mi + 1], mu_w = smu[mi - 1];
 
     // Cahn-Hilliard: M Delta mu - div(u phi) (Eq. CH), flux form with mean face values
@@ -214,18 +219,20 @@ __global__ void __launch_bounds__(NTHREADS, 2) stage_kernel(StageArgs<T> a, VCon
 
     const int64_t gidx = (int64_t)q * ns + s;
     {
-      const T pout = Lphi * a.dt + ph;
-      T o = a.b * pout;
-      if (a.f0) o += a.a0 * a.f0[NPOP * stride + gidx];
+      T o = Lphi * a.dt + ph;
+      if (a.f0) {
+        const T p0 = a.f0[NPOP * stride + gidx];
+        o = p0 + a.b * ((ph - p0) + Lphi * a.dt);
+      }
       a.fout[NPOP * stride + gidx] = o;
     }
 
-    // populations at the node
-    T f[NPOP];
+    // population deviations at the node
+    T g[NPOP];
 #pragma unroll
-    for (int k = 0; k < NPOP; ++k) f[k] = sf[k * BQ * BS + fr * BS + fc];
+    for (int k = 0; k < NPOP; ++k) g[k] = sf[k * BQ * BS + fr * BS + fc];
 
-    // theta-direction weights J_{q+d} of G = J f, d = -3..3
+    // theta-direction weights J_{q+d}, d = -3..3
     T Jw[7];
 #pragma unroll
     for (int d = 0; d < 7; ++d) Jw[d] = (d >= 3 - H && d <= 3 + H) ? sco[C_J * BQ + fr + d - 3] : T(0);
@@ -236,42 +243,53 @@ __global__ void __launch_bounds__(NTHREADS, 2) stage_kernel(StageArgs<T> a, VCon
 
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      // varphi-derivative operands: h_m = (-F^phi - Gamma v_i v_m) f_{i m}; K~ = K diag(v) (Sec. 2.3)
+      // varphi-derivative operands h_m = (-F^phi - Gamma v_i v_m) g_{i m}; K~ = K diag(v) (Sec. 2.3)
       const T gvi = gam * vc.v[i];
       T h[4];
 #pragma unroll
-      for (int mm = 0; mm < 4; ++mm) h[mm] = (-Fp - gvi * vc.v[mm]) * f[4 * i + mm];
+      for (int mm = 0; mm < 4; ++mm) h[mm] = (-Fp - gvi * vc.v[mm]) * g[4 * i + mm];
       const T ai = vc.v[i] * ut;
-      const T nwi = n * vc.w[i];
+      const T n0wi = a.n0 * vc.w[i];
+      // reference part: v_i (E(q) + F^theta) per row and sign
+      const T refi = vc.v[i] * ((i >= 2 ? Ep : En) + Ft);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int k = 4 * i + j;
-        // advection along theta of G = J f, and along varphi of f (Eq. boltz_tor)
+        const T fref = n0wi * vc.w[j];
+        // advection along theta of G = J f and along varphi of f (Eq. boltz_tor); the reference
+        // part of f is constant in varphi and, for UW3, handled through E(q)
         T xt[7], xp[7];
 #pragma unroll
         for (int d = 0; d < 7; ++d) {
           const bool in = (d >= 3 - H && d <= 3 + H);
-          xt[d] = in ? Jw[d] * sf[k * BQ * BS + (fr + d - 3) * BS + fc] : T(0);
+          const T gt_d = sf[k * BQ * BS + (fr + d - 3) * BS + fc];
+          xt[d] = in ? Jw[d] * (ADV == VLB_UW3 ? gt_d : gt_d + fref) : T(0);
           xp[d] = in ? sf[k * BQ * BS + fr * BS + fc + d - 3] : T(0);
         }
         const T Dt = (i >= 2) ? flux_diff<T, ADV, true>(xt) : flux_diff<T, ADV, false>(xt);
         const T Dp = (j >= 2) ? flux_diff<T, ADV, true>(xp) : flux_diff<T, ADV, false>(xp);
         T rhs = -(vc.v[i] * ct) * Dt - (vc.v[j] * cp) * Dp;
-        // force and inertial terms: (Gamma v_j^2 - F^theta) df/dv_theta + sum_m K_jm h_m
+        // force and inertial terms on the deviation: (Gamma v_j^2 - F^theta) dg/dv_theta + sum_m K_jm h_m
         T dvt = T(0), dvp = T(0);
 #pragma unroll
         for (int mm = 0; mm < 4; ++mm) {
-          dvt += vc.K[i][mm] * f[4 * mm + j];
+          dvt += vc.K[i][mm] * g[4 * mm + j];
           dvp += vc.K[j][mm] * h[mm];
         }
         rhs += (gam * vc.v[j] * vc.v[j] - Ft) * dvt + dvp;
-        // BGK towards the third-order Hermite equilibrium (Eq. feq)
+        // same terms (and UW3 theta-advection) on the reference part n0 w_i w_j, in closed form
+        rhs += fref * (refi + vc.v[j] * Fp);
+        // BGK towards the third-order Hermite equilibrium (Eq. feq):
+        // f^eq - n0 w_i w_j = w_i w_j (dn + n (poly - 1))
         const T xi = ai + vc.v[j] * up;
-        const T feq = nwi * vc.w[j] * (c0 + xi * (c0 + xi * (T(0.5) + xi * sixth)));
-        rhs += a.inv_tau * (feq - f[k]);
-        const T fnew = rhs * a.dt + f[k];
-        T o = a.b * fnew;
-        if (a.f0) o += a.a0 * a.f0[k * stride + gidx];
+        const T pm1 = xi * (c0 + xi * (T(0.5) + xi * sixth)) - T(0.5) * usq;
+        const T geq = vc.w[i] * vc.w[j] * (dn + n * pm1);
+        rhs += a.inv_tau * (geq - g[k]);
+        T o = rhs * a.dt + g[k];
+        if (a.f0) {
+          const T g0 = a.f0[k * stride + gidx];
+          o = g0 + a.b * ((g[k] - g0) + rhs * a.dt);
+        }
         a.fout[k * stride + gidx] = o;
       }
     }

@@ -1,0 +1,75 @@
+"""Parity at the full sizes of the measured workloads, in the launch configuration bench.py times.
+
+1024 x 2048 (FP32, UW3, hydrodynamic): one GPU step from a perturbed state is compared at sampled
+nodes with the oracle evaluated node by node (oracle.vlb_oracle.step_window), including the grid
+corners, the wrap-around seams, tile boundaries and the rows theta = 0, pi.
+128 x 384 stripe: an azimuthally symmetric state stays symmetric, so every varphi column of the GPU
+run must equal the oracle's N_phi = 1 run of the same stripe.
+"""
+import numpy as np
+import pytest
+
+from oracle import vlb_oracle as O
+from paper_1904_10070_gb300 import inputs, vlb
+from tests.gpu_helpers import gpu_params, oracle_params, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+def test_coarsening_1024x2048_fp32_sampled_nodes():
+    w = inputs.workload("coarsen_torus_1024x2048")
+    p = dict(w["params"])
+    p["dt"] = 5e-5  # a larger step than the workload's, so that one step moves the state visibly
+    nt, ns = p["n_theta"], p["n_phi"]
+    rng = np.random.default_rng(2024)
+    rho = 1.0 + 0.05 * inputs.noise(7, nt, ns, 1.0)
+    ut = 0.03 * inputs.noise(8, nt, ns, 1.0)
+    up = 0.03 * inputs.noise(9, nt, ns, 1.0)
+    phi = np.tanh(3.0 * inputs.noise(10, nt, ns, 1.0))
+    s = vlb.Solver(gpu_params(p, vlb.FP32))
+    s.set_fields(rho, ut, up, phi)
+    s.step(3)
+    f0, phi0 = s.get_state()          # FP32 state, widened exactly
+    s.step(1)
+    f1, phi1 = s.get_state()
+    s.close()
+    f0 = f0.reshape(4, 4, nt, ns)
+    f1 = f1.reshape(4, 4, nt, ns)
+    op = oracle_params(p)
+    nodes = [(0, 0), (0, ns - 1), (nt - 1, 0), (nt - 1, ns - 1), (nt // 2, ns // 2), (nt // 4, 1),
+             (15, 31), (16, 32), (15, 32), (16, 31), (nt // 2 - 1, 0), (3 * nt // 4, ns - 2)]
+    nodes += [(int(a), int(b)) for a, b in zip(rng.integers(0, nt, 20), rng.integers(0, ns, 20))]
+    worst_f = worst_p = worst_inc = 0.0
+    for q, c in nodes:
+        fo, po = O.step_window(f0, phi0, op, q, c)
+        fg, pg = f1[:, :, q, c], phi1[q, c]
+        scale = np.max(np.abs(fo))
+        worst_f = max(worst_f, np.max(np.abs(fg - fo)) / scale)
+        worst_p = max(worst_p, abs(pg - po) / max(1.0, abs(po)))
+        inc = np.max(np.abs(fo - f0[:, :, q, c]))
+        worst_inc = max(worst_inc, np.max(np.abs((fg - f0[:, :, q, c]) - (fo - f0[:, :, q, c]))) / max(inc, 1e-30))
+    print(f"full-size sampled: f {worst_f:.2e}, phi {worst_p:.2e}, increment {worst_inc:.2e}")
+    assert worst_f <= 2e-5 and worst_p <= 2e-5
+    assert worst_inc <= 1e-2  # the step's own increment is resolved to better than 1%
+
+
+@pytest.mark.parametrize("precision,tol", [(vlb.FP64, 1e-11), (vlb.FP32, 2e-5)])
+def test_stripe_128x384_columns_match_axisymmetric_oracle(precision, tol):
+    w = inputs.workload("stripe_torus_128x384")
+    p = dict(w["params"])
+    steps = 2000
+    s = vlb.Solver(gpu_params(p, precision))
+    s.set_fields(w["rho"], w["ut"], w["up"], w["phi"])
+    s.step(steps)
+    g_rho, g_ut, g_up, g_phi, _ = s.fields()
+    s.close()
+    p1 = dict(p)
+    p1["n_phi"] = 1
+    op = oracle_params(p1)
+    geo = O.Geometry(op)
+    f, ph = O.init_state(w["rho"][:, :1], w["ut"][:, :1], w["up"][:, :1], w["phi"][:, :1])
+    f, ph = O.run(f, ph, geo, steps)
+    n, ut, up = O.moments(f)
+    for name, g, o in (("rho", g_rho, n), ("u_th", g_ut, ut), ("u_ph", g_up, up), ("phi", g_phi, ph)):
+        err = rel_err(g, np.broadcast_to(o, g.shape))
+        assert err <= tol, (name, err)
