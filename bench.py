@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "coarsen_torus_1024x2048"
 METRIC = "node-velocity updates/s"
 UNIT = "NVU/s"
-BYTES_PER_NODE_STEP = {"f32": 544, "f64": 1088}  # 17 arrays: 5 reads + 3 writes per node over 3 stages
+BYTES_PER_NODE_STEP = {"f32": 576, "f64": 1088}  # 18 (FP32) or 17 (FP64) arrays: 5 reads + 3 writes per node over 3 stages
 PKEYS = ["R", "r", "n_theta", "n_phi", "dt", "tau", "M", "A", "kappa", "geometry", "advection", "ch_mode"]
 STAGE_SRC = os.path.join(ROOT, "paper_1904_10070_gb300", "csrc", "vlb_stage.cu")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "stage_kernel_fp32_uw3_coarsen_1024x2048.md")
@@ -141,50 +141,55 @@ def _dist():
     return world, rank, local
 
 
-def cpu_baseline(rows: int = 64, steps: int = 2):
-    """The FP64 oracle as it stands, on a rows x 2048 sub-grid of the workload (single-threaded numpy)."""
+def _oracle_sample(rows: int):
     from oracle import vlb_oracle as O
     from paper_1904_10070_gb300 import inputs
     w = inputs.workload(WORKLOAD)
     p = dict(w["params"])
     p["n_theta"] = rows
-    op = O.Params(**{k: p[k] for k in PKEYS})
-    geo = O.Geometry(op)
+    geo = O.Geometry(O.Params(**{k: p[k] for k in PKEYS}))
     phi = inputs.noise(1, rows, p["n_phi"], 0.01)
     f, ph = O.init_state(np.ones_like(phi), 0 * phi, 0 * phi, phi)
+    return O, geo, f, ph, p["n_phi"]
+
+
+def _calibrated_rows(target_s: float, steps: int) -> int:
+    """theta rows of a 2048-wide sub-grid that the oracle steps `steps` times in about target_s seconds."""
+    O, geo, f, ph, ns = _oracle_sample(16)
+    t0 = time.perf_counter()
+    O.step(f, ph, geo)
+    rate = 16 * ns / (time.perf_counter() - t0)  # node-steps per second
+    return int(max(1, min(1024, target_s * rate / (ns * steps))))
+
+
+def cpu_baseline(steps: int = 2, target_s: float = 15.0):
+    """The FP64 oracle as it stands, on a bounded sub-grid of the workload (single-threaded numpy)."""
+    rows = _calibrated_rows(target_s, steps)
+    O, geo, f, ph, ns = _oracle_sample(rows)
     t0 = time.perf_counter()
     O.run(f, ph, geo, steps)
     dt = time.perf_counter() - t0
-    return {"value": 16.0 * rows * p["n_phi"] * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"FP64 numpy oracle, {steps} SSP-RK3 steps on a {rows}x{p['n_phi']} sub-grid of the "
+    return {"value": 16.0 * rows * ns * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"FP64 numpy oracle, {steps} SSP-RK3 steps on a {rows}x{ns} sub-grid of the "
                       f"workload (same parameters), {dt:.1f} s"}
 
 
 def run_reference(args):
     """--impl reference: the oracle timed per step on a bounded sample sized for a few minutes in total."""
-    from oracle import vlb_oracle as O
-    from paper_1904_10070_gb300 import inputs
-    w = inputs.workload(WORKLOAD)
-    p = dict(w["params"])
-    budget_s, node_rate = 120.0, 1.6e4  # node-steps/s of the numpy oracle on a wide grid (measured)
-    rows = int(max(1, min(64, budget_s * node_rate / (p["n_phi"] * (args.steps + args.warmup)))))
-    p["n_theta"] = rows
-    op = O.Params(**{k: p[k] for k in PKEYS})
-    geo = O.Geometry(op)
-    phi = inputs.noise(1, rows, p["n_phi"], 0.01)
-    f, ph = O.init_state(np.ones_like(phi), 0 * phi, 0 * phi, phi)
+    rows = _calibrated_rows(120.0, args.steps + args.warmup)
+    O, geo, f, ph, ns = _oracle_sample(rows)
     for _ in range(args.warmup):
         f, ph = O.step(f, ph, geo)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         f, ph = O.step(f, ph, geo)
     dt = time.perf_counter() - t0
-    val = 16.0 * rows * p["n_phi"] * args.steps / dt
-    sample = f"FP64 numpy oracle, {args.steps} steps on a {rows}x{p['n_phi']} sub-grid of the workload"
+    val = 16.0 * rows * ns * args.steps / dt
+    sample = f"FP64 numpy oracle, {args.steps} steps on a {rows}x{ns} sub-grid of the workload"
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "grid": [rows, p["n_phi"]], "sample": True},
+            "data": "synthetic", "config": {"workload": WORKLOAD, "grid": [rows, ns], "sample": True},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

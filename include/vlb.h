@@ -99,7 +99,8 @@ vlb_status vlb_set_fields(vlb_handle* h, const double* rho, const double* u_th, 
                           const double* phi);
 
 /* Checkpoint / restore of the full state: f16 is [16][N_theta][N_phi], phi [N_theta][N_phi].
- * In FP32 mode set rounds to FP32 and get widens exactly.  Synchronous. */
+ * A state written by vlb_get_state and read back by vlb_set_state (on this or a new handle with
+ * the same parameters) continues bit for bit.  Synchronous. */
 vlb_status vlb_set_state(vlb_handle* h, const double* f16, const double* phi);
 vlb_status vlb_get_state(vlb_handle* h, double* f16, double* phi);
 
@@ -125,10 +126,12 @@ vlb_status vlb_get_totals(vlb_handle* h, double out[4]);
  * FP64 on the GPU; the domain length is L_d = 4 pi^2 r R / L_I (Eq. cart_scaling_L0).  Synchronous. */
 vlb_status vlb_interface_length(vlb_handle* h, double* out);
 
-/* Device pointers of the resident state (for zero-copy readers on the same device):
- * f: 16 arrays of n_theta*n_phi elements spaced *stride elements apart, then phi at
- * f + 16 * stride.  Elements are double (FP64) or float (FP32).  The pointers stay valid until
- * vlb_destroy; reading them while a vlb_step is in flight on another stream races. */
+/* Device pointer of the resident state (for zero-copy readers on the same device): arrays of
+ * n_theta*n_phi elements spaced *stride elements apart -- 16 population deviations
+ * g_k = f_k - n0 w_i w_j (n0: the area-weighted mean density at the last set call, rounded to
+ * 20 significant bits), then phi; in FP32 mode phi is the float pair (hi at 16 * stride, lo at
+ * 17 * stride).  Elements are double (FP64) or float (FP32).  Valid until vlb_destroy; reading
+ * it while a vlb_step is in flight on another stream races. */
 vlb_status vlb_state_device(vlb_handle* h, void** f, int64_t* stride);
 
 /* Steps taken since the last set call. */

@@ -34,6 +34,21 @@ __device__ __forceinline__ int wrapi(int x, int n) {
   return x < 0 ? x + n : x;
 }
 
+// phi as stored: one array in FP64 mode, hi + lo in FP32 mode.
+template <typename T>
+__device__ __forceinline__ void store_phi(T* state, int64_t stride, int64_t idx, double v) {
+  const T hi = (T)v;
+  state[NPOP * stride + idx] = hi;
+  if (sizeof(T) == 4) state[(NPOP + 1) * stride + idx] = (T)(v - (double)hi);
+}
+
+template <typename T>
+__device__ __forceinline__ double load_phi(const T* state, int64_t stride, int64_t idx) {
+  double v = (double)state[NPOP * stride + idx];
+  if (sizeof(T) == 4) v += (double)state[(NPOP + 1) * stride + idx];
+  return v;
+}
+
 // f := f^eq(rho, u) (Eq. feq), phi := phi; evaluated in FP64, rounded once.
 template <typename T>
 __global__ void init_feq_kernel(T* state, int64_t stride, const double* rho, const double* ut, const double* up,
@@ -50,7 +65,7 @@ __global__ void init_feq_kernel(T* state, int64_t stride, const double* rho, con
         // stored deviation g = f^eq - n0 w_i w_j = w_i w_j ((n - n0) + n (poly - 1))
         state[(4 * i + j) * stride + idx] = (T)(vd.w[i] * vd.w[j] * ((nn - n0) + nn * pm1));
       }
-    state[NPOP * stride + idx] = (T)phi[idx];
+    store_phi(state, stride, idx, phi[idx]);
   }
 }
 
@@ -63,7 +78,10 @@ __global__ void convert_in_kernel(T* state, int64_t stride, const double* src, i
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n * NARR;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t k = idx / n, i = idx - k * n;
-    state[k * stride + i] = (T)(src[idx] - ref_pop((int)k, n0, vd));
+    if (k == NPOP)
+      store_phi(state, stride, i, src[idx]);
+    else
+      state[k * stride + i] = (T)(src[idx] - ref_pop((int)k, n0, vd));
   }
 }
 
@@ -72,7 +90,7 @@ __global__ void convert_out_kernel(double* dst, const T* state, int64_t stride, 
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n * NARR;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t k = idx / n, i = idx - k * n;
-    dst[idx] = (double)state[k * stride + i] + ref_pop((int)k, n0, vd);
+    dst[idx] = k == NPOP ? load_phi(state, stride, i) : (double)state[k * stride + i] + ref_pop((int)k, n0, vd);
   }
 }
 
@@ -98,7 +116,6 @@ template <typename T>
 __global__ void fields_kernel(const T* state, int64_t stride, const double* coefd, int nt, int ns, double A,
                               double kappa, double n0, double* rho, double* ut, double* up, double* phi, double* mu, VD vd) {
   const int64_t n = (int64_t)nt * ns;
-  const T* ph = state + NPOP * stride;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
     const int q = (int)(idx / ns), s = (int)(idx - (int64_t)q * ns);
     double nn, a, b;
@@ -106,11 +123,11 @@ __global__ void fields_kernel(const T* state, int64_t stride, const double* coef
     rho[idx] = nn;
     ut[idx] = a;
     up[idx] = b;
-    const double p0 = (double)ph[idx];
-    const double pn = (double)ph[(int64_t)wrapi(q + 1, nt) * ns + s];
-    const double ps = (double)ph[(int64_t)wrapi(q - 1, nt) * ns + s];
-    const double pe = (double)ph[(int64_t)q * ns + wrapi(s + 1, ns)];
-    const double pw = (double)ph[(int64_t)q * ns + wrapi(s - 1, ns)];
+    const double p0 = load_phi(state, stride, idx);
+    const double pn = load_phi(state, stride, (int64_t)wrapi(q + 1, nt) * ns + s);
+    const double ps = load_phi(state, stride, (int64_t)wrapi(q - 1, nt) * ns + s);
+    const double pe = load_phi(state, stride, (int64_t)q * ns + wrapi(s + 1, ns));
+    const double pw = load_phi(state, stride, (int64_t)q * ns + wrapi(s - 1, ns));
     const double lap = coefd[C_LT * nt + q] * (coefd[C_JP * nt + q] * (pn - p0) - coefd[C_JM * nt + q] * (p0 - ps)) +
                        coefd[C_LP * nt + q] * (pe - 2.0 * p0 + pw);
     phi[idx] = p0;
@@ -125,18 +142,17 @@ __global__ void __launch_bounds__(TOTAL_THREADS) totals_kernel(const T* state, i
                                                                double n0, double gt, double edge_p, double* partials,
                                                                VD vd) {
   const int64_t n = (int64_t)nt * ns;
-  const T* ph = state + NPOP * stride;
   double acc[NSUM] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
     const int q = (int)(idx / ns), s = (int)(idx - (int64_t)q * ns);
     double nn, a, b;
     node_moments(state, stride, idx, vd, n0, nn, a, b);
     const double dA = coefd[C_DA * nt + q];
-    const double p0 = (double)ph[idx];
-    const double pn = (double)ph[(int64_t)wrapi(q + 1, nt) * ns + s];
-    const double ps = (double)ph[(int64_t)wrapi(q - 1, nt) * ns + s];
-    const double pe = (double)ph[(int64_t)q * ns + wrapi(s + 1, ns)];
-    const double pw = (double)ph[(int64_t)q * ns + wrapi(s - 1, ns)];
+    const double p0 = load_phi(state, stride, idx);
+    const double pn = load_phi(state, stride, (int64_t)wrapi(q + 1, nt) * ns + s);
+    const double ps = load_phi(state, stride, (int64_t)wrapi(q - 1, nt) * ns + s);
+    const double pe = load_phi(state, stride, (int64_t)q * ns + wrapi(s + 1, ns));
+    const double pw = load_phi(state, stride, (int64_t)q * ns + wrapi(s - 1, ns));
     const double g1 = (pn - ps) * gt, g2 = (pe - pw) * coefd[C_GP * nt + q];
     const double om = 1.0 - p0 * p0;
     acc[0] += nn * dA;

@@ -107,7 +107,7 @@ Layout layout(const vlb_params* p) {
   off = align_up(off + (size_t)vlb::NCOEF * p->n_theta * 8, 256);
   for (int k = 0; k < 3; ++k) {
     L.off_U[k] = off;
-    off = align_up(off + (size_t)vlb::NARR * L.stride * L.esize, 256);
+    off = align_up(off + (size_t)vlb::state_arrays(L.esize) * L.stride * L.esize, 256);
   }
   L.off_staging = off;
   off = align_up(off + (size_t)vlb::NARR * L.N * 8, 256);
@@ -159,6 +159,30 @@ void row_tables(const vlb_params* p, double* out) {
     out[vlb::C_DA * nt + q] = p->r * p->R * J * dth * dph;
     out[vlb::C_EDGE * nt + q] = torus ? (p->R + p->r * cos(th + 0.5 * dth)) * dph : p->R * dph;
   }
+}
+
+// Reference density n0 of the stored deviations: the area-weighted mean density
+// sum_q J_q sum_s n_qs / (N_phi sum_q J_q), rounded to 20 significant bits.  The scheme conserves
+// sum n sqrt(g), so a state restored from a checkpoint reproduces the same n0 (and bitwise the same
+// stored deviations).  `n_at(q, s)` returns the density at a node.
+template <typename F>
+bool reference_density(const vlb_params& p, F n_at, double* out) {
+  const double dth = 2.0 * M_PI / p.n_theta;
+  const double a = p.geometry == VLB_TORUS ? p.r / p.R : 0.0;
+  double num = 0.0, den = 0.0;
+  for (int q = 0; q < p.n_theta; ++q) {
+    const double J = 1.0 + a * cos(q * dth);
+    double row = 0.0;
+    for (int s = 0; s < p.n_phi; ++s) row += n_at(q, s);
+    num += J * row;
+    den += J * p.n_phi;
+  }
+  const double mean = num / den;
+  if (!isfinite(mean) || !(mean > 0.0)) return false;
+  int e = 0;
+  const double m = frexp(mean, &e);
+  *out = ldexp(nearbyint(ldexp(m, 20)), e - 20);
+  return true;
 }
 
 template <typename T>
@@ -381,11 +405,9 @@ vlb_status vlb_set_fields(vlb_handle* h, const double* rho, const double* u_th, 
   vlb_status st = check_handle(h);
   if (st) return st;
   if (!rho || !u_th || !u_ph || !phi) return fail(h, VLB_ERR_ARG, "vlb_set_fields: NULL input");
-  // reference density of the stored deviations: the mean input density
-  double acc = 0.0;
-  for (int64_t i = 0; i < h->N; ++i) acc += rho[i];
-  if (!isfinite(acc)) return fail(h, VLB_ERR_ARG, "vlb_set_fields: non-finite density");
-  h->n0 = acc / (double)h->N;
+  const int ns = h->p.n_phi;
+  if (!reference_density(h->p, [&](int q, int s) { return rho[(int64_t)q * ns + s]; }, &h->n0))
+    return fail(h, VLB_ERR_ARG, "vlb_set_fields: density must be finite with a positive mean");
   const size_t nb = sizeof(double) * h->N;
   double* s = h->staging;
   VLB_CUDA(h, cudaMemcpyAsync(s, rho, nb, cudaMemcpyHostToDevice, h->stream));
@@ -408,10 +430,15 @@ vlb_status vlb_set_state(vlb_handle* h, const double* f16, const double* phi) {
   vlb_status st = check_handle(h);
   if (st) return st;
   if (!f16 || !phi) return fail(h, VLB_ERR_ARG, "vlb_set_state: NULL input");
-  double acc = 0.0;
-  for (int64_t i = 0; i < 16 * h->N; ++i) acc += f16[i];
-  if (!isfinite(acc)) return fail(h, VLB_ERR_ARG, "vlb_set_state: non-finite populations");
-  h->n0 = acc / (double)h->N;
+  const int ns = h->p.n_phi;
+  const int64_t N = h->N;
+  auto dens = [&](int q, int s) {
+    double x = 0.0;
+    for (int k = 0; k < 16; ++k) x += f16[k * N + (int64_t)q * ns + s];
+    return x;
+  };
+  if (!reference_density(h->p, dens, &h->n0))
+    return fail(h, VLB_ERR_ARG, "vlb_set_state: populations must be finite with a positive mean density");
   const size_t nb = sizeof(double) * h->N;
   VLB_CUDA(h, cudaMemcpyAsync(h->staging, f16, 16 * nb, cudaMemcpyHostToDevice, h->stream));
   VLB_CUDA(h, cudaMemcpyAsync(h->staging + 16 * h->N, phi, nb, cudaMemcpyHostToDevice, h->stream));

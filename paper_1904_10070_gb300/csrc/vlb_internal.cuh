@@ -9,7 +9,9 @@
 namespace vlb {
 
 constexpr int NPOP = 16;  // Q^2 populations, k = 4 i + j
-constexpr int NARR = 17;  // 16 populations + phi per state buffer
+constexpr int NARR = 17;  // host/staging layout: 16 populations + phi
+// Device state arrays: 16 population deviations, phi, and in FP32 mode the low part of phi.
+constexpr int state_arrays(size_t esize) { return esize == 4 ? NARR + 1 : NARR; }
 
 // Per-theta-row coefficient tables, one array of n_theta entries per field (SoA).
 // Computed in FP64 on the host (App. A geometry) and rounded once to the state precision.
@@ -40,6 +42,12 @@ enum RowCoef : int {
 // continuum cancellation between the J-flux and the inertial term (E = -Gamma for WENO5, whose
 // theta-advection acts on the full J f).  The state therefore keeps FP32 resolution on the
 // small deviations that carry the dynamics instead of on f ~ n w_i w_j.
+//
+// In FP32 mode phi is stored as hi + lo (two FP32 arrays, |lo| <= ulp(hi)/2): the kappa Delta phi
+// term multiplies the storage rounding of phi by 4 kappa / h^2, and with a single FP32 array that
+// rounding alone sets the FP32-vs-FP64 difference of the velocity.  The arithmetic stays FP32: hi
+// differences of neighbouring nodes are exact, lo enters the Laplacian and, to first order, the
+// cubic term of mu, and the Runge-Kutta update is an error-free float sum.
 
 // Velocity-space constants (Sec. 2.3): roots v, weights w, derivative kernel K (K~ = K diag v).
 struct VelocityConsts {

@@ -5,7 +5,8 @@
 //   L_phi = right-hand side of Eq. CH with mu from Eq. mu and the force of Eq. pbin,
 // and writes U_out = U^n + b (U_in - U^n + dt L(U_in)) -- one stage of SSP-RK3 in Shu-Osher form
 // (b = 1, 1/4, 2/3), written so that the weights only multiply small increments.  The populations
-// are stored as deviations g = f - n0 w_i w_j from the rest equilibrium (vlb_internal.cuh).
+// are stored as deviations g = f - n0 w_i w_j from the rest equilibrium, and in FP32 mode phi is
+// carried as an unevaluated float pair hi + lo (vlb_internal.cuh explains both).
 //
 // Tiling: a CTA owns a 16 (theta) x 32 (varphi) tile; 256 threads, each thread two nodes.
 // Shared memory holds, for the tile plus its halo:
@@ -48,7 +49,8 @@ struct Smem {
   static constexpr int UT_OFF = N_OFF + MQ * MS;
   static constexpr int UP_OFF = UT_OFF + MQ * MS;
   static constexpr int MU_OFF = UP_OFF + MQ * MS;
-  static constexpr int CO_OFF = MU_OFF + MQ * MS;
+  static constexpr int PHL_OFF = MU_OFF + MQ * MS;                       // phi low part (FP32 only)
+  static constexpr int CO_OFF = PHL_OFF + (sizeof(T) == 4 ? PQ * PS : 0);
   static constexpr int TOTAL = CO_OFF + NCT * BQ;
   static constexpr size_t BYTES = sizeof(T) * (size_t)TOTAL;
 };
@@ -103,6 +105,8 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? (ADV == VLB_UW3 ? 3
   T* sup = sm + S::UP_OFF;
   T* smu = sm + S::MU_OFF;
   T* sco = sm + S::CO_OFF;
+  T* sphl = sm + S::PHL_OFF;
+  constexpr bool DF = sizeof(T) == 4;  // phi as a float pair
 
   const int nt = a.nt, ns = a.ns;
   const int64_t stride = a.stride;
@@ -134,6 +138,7 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? (ADV == VLB_UW3 ? 3
       const int r = idx / PS, c = idx % PS;
       const int gq = wrap(q0 + r - 2, nt), gs = wrap(s0 + c - 2, ns);
       sphi[idx] = __ldg(phin + (int64_t)gq * ns + gs);
+      if (DF) sphl[idx] = __ldg(phin + stride + (int64_t)gq * ns + gs);
     }
     for (int idx = tid; idx < NCT * BQ; idx += NTHREADS) {
       const int k = idx / BQ, r = idx % BQ;
@@ -175,12 +180,25 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? (ADV == VLB_UW3 ? 3
       sn[mi] = dn;
       sut[mi] = mt / n;
       sup[mi] = mp / n;
-      const T* pp = sphi + (mr + 1) * PS + (mc + 1);
+      const int pidx = (mr + 1) * PS + (mc + 1);
+      const T* pp = sphi + pidx;
       const int cr = mr + H - 1;
       const T ph = pp[0];
-      const T lap = sco[C_LT * BQ + cr] * (sco[C_JP * BQ + cr] * (pp[PS] - ph) - sco[C_JM * BQ + cr] * (ph - pp[-PS])) +
-                    sco[C_LP * BQ + cr] * (pp[1] - T(2) * ph + pp[-1]);
-      smu[mi] = -a.A * ph * (T(1) - ph * ph) - a.kappa * lap;
+      // neighbour differences of phi = hi + lo: the hi differences are exact for nearby values
+      T dN = pp[PS] - ph, dS = ph - pp[-PS], dE = pp[1] - ph, dW = ph - pp[-1], lo = T(0);
+      if (DF) {
+        const T* pl = sphl + pidx;
+        lo = pl[0];
+        dN += pl[PS] - lo;
+        dS += lo - pl[-PS];
+        dE += pl[1] - lo;
+        dW += lo - pl[-1];
+      }
+      const T lap = sco[C_LT * BQ + cr] * (sco[C_JP * BQ + cr] * dN - sco[C_JM * BQ + cr] * dS) +
+                    sco[C_LP * BQ + cr] * (dE - dW);
+      // phi (1 - phi^2) at hi + lo, to first order in lo
+      const T cubic = ph * (T(1) - ph * ph) + (T(1) - T(3) * ph * ph) * lo;
+      smu[mi] = -a.A * cubic - a.kappa * lap;
     }
   }
   __syncthreads();
@@ -219,12 +237,25 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? (ADV == VLB_UW3 ? 3
 
     const int64_t gidx = (int64_t)q * ns + s;
     {
-      T o = Lphi * a.dt + ph;
+      const T lo = DF ? sphl[pi] : T(0);
+      T base = ph, base_lo = lo, inc = Lphi * a.dt;
       if (a.f0) {
-        const T p0 = a.f0[NPOP * stride + gidx];
-        o = p0 + a.b * ((ph - p0) + Lphi * a.dt);
+        base = a.f0[NPOP * stride + gidx];
+        base_lo = DF ? a.f0[(NPOP + 1) * stride + gidx] : T(0);
+        inc = a.b * (((ph - base) + (lo - base_lo)) + inc);
       }
-      a.fout[NPOP * stride + gidx] = o;
+      if (DF) {
+        // (hi, lo) <- (base, base_lo) + inc with an error-free sum, then renormalised
+        const T s1 = base + inc;
+        const T bb = s1 - base;
+        const T err = (base - (s1 - bb)) + (inc - bb);
+        const T lo2 = base_lo + err;
+        const T hi_out = s1 + lo2;
+        a.fout[NPOP * stride + gidx] = hi_out;
+        a.fout[(NPOP + 1) * stride + gidx] = lo2 - (hi_out - s1);
+      } else {
+        a.fout[NPOP * stride + gidx] = base + inc;
+      }
     }
 
     // population deviations at the node
