@@ -155,11 +155,12 @@ def _oracle_sample(rows: int):
 
 def _calibrated_rows(target_s: float, steps: int) -> int:
     """theta rows of a 2048-wide sub-grid that the oracle steps `steps` times in about target_s seconds."""
-    O, geo, f, ph, ns = _oracle_sample(16)
+    O, geo, f, ph, ns = _oracle_sample(32)
     t0 = time.perf_counter()
     O.step(f, ph, geo)
-    rate = 16 * ns / (time.perf_counter() - t0)  # node-steps per second
-    return int(max(1, min(1024, target_s * rate / (ns * steps))))
+    rate = 32 * ns / (time.perf_counter() - t0)  # node-steps per second
+    # larger grids run slower per node (memory-bound numpy temporaries): keep a factor 2 of margin
+    return int(max(1, min(512, 0.5 * target_s * rate / (ns * steps))))
 
 
 def cpu_baseline(steps: int = 2, target_s: float = 15.0):
