@@ -9,48 +9,48 @@
 // carried as an unevaluated float pair hi + lo (vlb_internal.cuh explains both).
 //
 // Tiling: a CTA owns a 16 (theta) x 32 (varphi) tile; 256 threads, each thread two nodes.
-// Shared memory holds, for the tile plus its halo:
-//   - the 16 populations on the cross-shaped region the upwind stencils reach (halo 2 for UW3,
-//     3 for WENO5) -- every global element is read once per CTA with coalesced loads;
-//   - phi with a halo of 2 (corners included: mu is needed one node outside the tile);
-//   - the moments n, u and the chemical potential mu on the tile plus a halo of 1;
-//   - the per-row geometric coefficients of the rows the CTA touches.
-// Periodic wrap-around is done on the load indices, so tiles may be ragged and grids tiny.
+// Phase 1 stages, with asynchronous global->shared copies (cp.async, 16-byte chunks when the row
+// length allows it), a box of H rows (2 for UW3, 3 for WENO5) and 4 columns around the tile for
+// the 16 populations and phi, the U^n values of the tile itself, and the row coefficients.
+// Phase 2 computes the moments and mu on the tile plus a halo of 1; phase 3 the right-hand sides
+// and the Runge-Kutta combination.  Periodic wrap-around is resolved on the load addresses, so
+// ragged tiles and tiny grids take the same path (with scalar copies).
 #include "vlb_internal.cuh"
 
 namespace vlb {
 
 namespace {
 
-constexpr int TS = 32;       // tile width along varphi (one warp)
-constexpr int TYT = 8;       // thread rows
-constexpr int NQ = 2;        // nodes per thread along theta
-constexpr int TQ = TYT * NQ; // tile height along theta
+constexpr int TS = 32;        // tile width along varphi (one warp)
+constexpr int TYT = 8;        // thread rows
+constexpr int NQ = 2;         // nodes per thread along theta
+constexpr int TQ = TYT * NQ;  // tile height along theta
 constexpr int NTHREADS = TS * TYT;
-constexpr int NCT = 11;      // coefficient rows staged in shared memory (C_J .. C_EN)
+constexpr int HS = 4;         // box columns on each side (>= stencil reach, keeps 16-byte alignment)
+constexpr int NCT = 11;       // coefficient rows staged in shared memory (C_J .. C_EN)
 
 template <typename T>
 struct VConst {
   T v[4], w[4], K[4][4];
+  T ww[4][4];  // w_i w_j
 };
-
-template <int ADV>
-struct Halo { static constexpr int H = (ADV == VLB_UW3) ? 2 : 3; };
 
 template <typename T, int ADV>
 struct Smem {
-  static constexpr int H = Halo<ADV>::H;
-  static constexpr int BQ = TQ + 2 * H, BS = TS + 2 * H;  // population box
-  static constexpr int PQ = TQ + 4, PS = TS + 4;          // phi box (halo 2)
-  static constexpr int MQ = TQ + 2, MS = TS + 2;          // moment / mu box (halo 1)
+  static constexpr bool DF = sizeof(T) == 4;
+  static constexpr int H = (ADV == VLB_UW3) ? 2 : 3;
+  static constexpr int NST = DF ? NARR + 1 : NARR;  // state arrays
+  static constexpr int BQ = TQ + 2 * H, BS = TS + 2 * HS;  // staged box
+  static constexpr int MQ = TQ + 2, MS = TS + 2;           // moment / mu box (halo 1)
   static constexpr int F_OFF = 0;
   static constexpr int PHI_OFF = F_OFF + NPOP * BQ * BS;
-  static constexpr int N_OFF = PHI_OFF + PQ * PS;
+  static constexpr int PHL_OFF = PHI_OFF + BQ * BS;
+  static constexpr int U0_OFF = PHL_OFF + (DF ? BQ * BS : 0);
+  static constexpr int N_OFF = U0_OFF + NST * TQ * TS;
   static constexpr int UT_OFF = N_OFF + MQ * MS;
   static constexpr int UP_OFF = UT_OFF + MQ * MS;
   static constexpr int MU_OFF = UP_OFF + MQ * MS;
-  static constexpr int PHL_OFF = MU_OFF + MQ * MS;                       // phi low part (FP32 only)
-  static constexpr int CO_OFF = PHL_OFF + (sizeof(T) == 4 ? PQ * PS : 0);
+  static constexpr int CO_OFF = MU_OFF + MQ * MS;
   static constexpr int TOTAL = CO_OFF + NCT * BQ;
   static constexpr size_t BYTES = sizeof(T) * (size_t)TOTAL;
 };
@@ -59,6 +59,25 @@ __device__ __forceinline__ int wrap(int x, int n) {
   x %= n;
   return x < 0 ? x + n : x;
 }
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src));
+}
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async_scalar(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_u32(dst)), "l"(src), "n"(BYTES));
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::);
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
 // Fifth-order WENO-JS face value between g2 and g3 of the window g0..g4, upwind from g0's side.
 template <typename T>
@@ -79,72 +98,103 @@ __device__ __forceinline__ T weno5(T g0, T g1, T g2, T g3, T g4) {
   return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
 }
 
-// Flux difference g_{+1/2} - g_{-1/2} at the centre of a 7-point window x[0..6] (centre x[3]).
-template <typename T, int ADV, bool POS>
-__device__ __forceinline__ T flux_diff(const T (&x)[7]) {
-  if (ADV == VLB_UW3) {
-    // UW3 faces (-x_{i-1} + 5 x_i + 2 x_{i+1})/6 (v > 0), mirrored for v < 0, differenced.
-    if (POS) return (x[1] - T(6) * x[2] + T(3) * x[3] + T(2) * x[4]) * (T(1) / T(6));
-    return (-T(2) * x[2] - T(3) * x[3] + T(6) * x[4] - x[5]) * (T(1) / T(6));
+// WENO5 flux difference face_{+1/2} - face_{-1/2} at the centre x[3] of a 7-point window.
+template <typename T, bool POS>
+__device__ __forceinline__ T weno_diff(const T (&x)[7]) {
+  if (POS) return weno5(x[1], x[2], x[3], x[4], x[5]) - weno5(x[0], x[1], x[2], x[3], x[4]);
+  return weno5(x[6], x[5], x[4], x[3], x[2]) - weno5(x[5], x[4], x[3], x[2], x[1]);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Phase 1: asynchronous staging of the box (populations, phi), U^n and the row coefficients.
+// ---------------------------------------------------------------------------------------------
+template <typename T, int ADV>
+__device__ __forceinline__ void stage_loads(const StageArgs<T>& a, T* sm, int tid, int q0, int s0) {
+  using S = Smem<T, ADV>;
+  constexpr int H = S::H, BQ = S::BQ, BS = S::BS;
+  constexpr int VEC = 16 / sizeof(T);  // elements per 16-byte chunk
+  constexpr int CPR = BS / VEC;        // chunks per box row
+  constexpr int NBOX = NPOP + 1 + (S::DF ? 1 : 0);  // populations, phi (, phi lo): consecutive boxes
+  static_assert(S::PHI_OFF == NPOP * BQ * BS && (!S::DF || S::PHL_OFF == (NPOP + 1) * BQ * BS), "box layout");
+  const int nt = a.nt, ns = a.ns;
+  const int64_t stride = a.stride;
+  T* sf = sm + S::F_OFF;
+  T* su0 = sm + S::U0_OFF;
+  const bool fast = (ns % VEC == 0) && ns >= BS && nt >= BQ;
+  if (fast) {
+    // Box rows wrap at most once (nt >= BQ); chunk columns start at multiples of VEC and never
+    // straddle the seam because ns % VEC == 0, so every chunk is one aligned 16-byte copy.
+    for (int idx = tid; idx < NBOX * BQ * CPR; idx += NTHREADS) {
+      const int k = idx / (BQ * CPR);
+      const int rem = idx - k * (BQ * CPR);
+      const int r = rem / CPR, ch = rem - r * CPR;
+      int gq = q0 + r - H;
+      gq += gq < 0 ? nt : (gq >= nt ? -nt : 0);
+      int gs = s0 - HS + ch * VEC;
+      gs += gs < 0 ? ns : (gs >= ns ? -ns : 0);
+      cp_async16(sf + (k * BQ + r) * BS + ch * VEC, a.fin + k * stride + (int64_t)gq * ns + gs);
+    }
+    if (a.f0) {
+      constexpr int CT = TS / VEC;
+      for (int idx = tid; idx < S::NST * TQ * CT; idx += NTHREADS) {
+        const int k = idx / (TQ * CT);
+        const int rem = idx - k * (TQ * CT);
+        const int r = rem / CT, ch = rem - r * CT;
+        const int gq = q0 + r, gs = s0 + ch * VEC;
+        if (gq < nt && gs < ns)
+          cp_async16(su0 + (k * TQ + r) * TS + ch * VEC, a.f0 + k * stride + (int64_t)gq * ns + gs);
+      }
+    }
   } else {
-    if (POS) return weno5(x[1], x[2], x[3], x[4], x[5]) - weno5(x[0], x[1], x[2], x[3], x[4]);
-    return weno5(x[6], x[5], x[4], x[3], x[2]) - weno5(x[5], x[4], x[3], x[2], x[1]);
+    for (int idx = tid; idx < NBOX * BQ * BS; idx += NTHREADS) {
+      const int k = idx / (BQ * BS);
+      const int rem = idx - k * (BQ * BS);
+      const int r = rem / BS, c = rem - r * BS;
+      const int gq = wrap(q0 + r - H, nt), gs = wrap(s0 + c - HS, ns);
+      cp_async_scalar<sizeof(T)>(sf + (k * BQ + r) * BS + c, a.fin + k * stride + (int64_t)gq * ns + gs);
+    }
+    if (a.f0) {
+      for (int idx = tid; idx < S::NST * TQ * TS; idx += NTHREADS) {
+        const int k = idx / (TQ * TS);
+        const int rem = idx - k * (TQ * TS);
+        const int r = rem / TS, c = rem - r * TS;
+        const int gq = q0 + r, gs = s0 + c;
+        if (gq < nt && gs < ns)
+          cp_async_scalar<sizeof(T)>(su0 + (k * TQ + r) * TS + c, a.f0 + k * stride + (int64_t)gq * ns + gs);
+      }
+    }
   }
+  T* sco = sm + S::CO_OFF;
+  for (int idx = tid; idx < NCT * BQ; idx += NTHREADS) {
+    const int k = idx / BQ, r = idx - k * BQ;
+    sco[idx] = __ldg(a.coef + (int64_t)k * nt + wrap(q0 + r - H, nt));
+  }
+  cp_async_wait_all();
 }
 
 template <typename T, int ADV, int CH>
-__global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? (ADV == VLB_UW3 ? 3 : 2) : 1) stage_kernel(StageArgs<T> a, VConst<T> vc) {
+__global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel(StageArgs<T> a, VConst<T> vc) {
   using S = Smem<T, ADV>;
-  constexpr int H = S::H, BQ = S::BQ, BS = S::BS, PQ = S::PQ, PS = S::PS, MQ = S::MQ, MS = S::MS;
+  constexpr bool DF = S::DF;
+  constexpr int H = S::H, BQ = S::BQ, BS = S::BS, MQ = S::MQ, MS = S::MS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   T* sf = sm + S::F_OFF;
   T* sphi = sm + S::PHI_OFF;
+  T* sphl = sm + S::PHL_OFF;
+  T* su0 = sm + S::U0_OFF;
   T* sn = sm + S::N_OFF;
   T* sut = sm + S::UT_OFF;
   T* sup = sm + S::UP_OFF;
   T* smu = sm + S::MU_OFF;
   T* sco = sm + S::CO_OFF;
-  T* sphl = sm + S::PHL_OFF;
-  constexpr bool DF = sizeof(T) == 4;  // phi as a float pair
 
   const int nt = a.nt, ns = a.ns;
   const int64_t stride = a.stride;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TS + tx;
   const int s0 = blockIdx.x * TS, q0 = blockIdx.y * TQ;
 
-  // ---- phase 1: stage populations (cross), phi (box) and row coefficients ----
-  {
-    constexpr int PA = TQ * BS;            // interior rows, full width
-    constexpr int PF = PA + 2 * H * TS;    // + halo rows, interior columns
-    for (int idx = tid; idx < PF; idx += NTHREADS) {
-      int r, c;
-      if (idx < PA) {
-        r = H + idx / BS;
-        c = idx % BS;
-      } else {
-        const int j = idx - PA, hr = j / TS;
-        c = H + j % TS;
-        r = hr < H ? hr : hr + TQ;
-      }
-      const int gq = wrap(q0 + r - H, nt), gs = wrap(s0 + c - H, ns);
-      const T* src = a.fin + (int64_t)gq * ns + gs;
-      T* dst = sf + r * BS + c;
-#pragma unroll
-      for (int k = 0; k < NPOP; ++k) dst[k * BQ * BS] = __ldg(src + k * stride);
-    }
-    const T* phin = a.fin + NPOP * stride;
-    for (int idx = tid; idx < PQ * PS; idx += NTHREADS) {
-      const int r = idx / PS, c = idx % PS;
-      const int gq = wrap(q0 + r - 2, nt), gs = wrap(s0 + c - 2, ns);
-      sphi[idx] = __ldg(phin + (int64_t)gq * ns + gs);
-      if (DF) sphl[idx] = __ldg(phin + stride + (int64_t)gq * ns + gs);
-    }
-    for (int idx = tid; idx < NCT * BQ; idx += NTHREADS) {
-      const int k = idx / BQ, r = idx % BQ;
-      sco[idx] = __ldg(a.coef + (int64_t)k * nt + wrap(q0 + r - H, nt));
-    }
-  }
+  stage_loads<T, ADV>(a, sm, tid, q0, s0);
   __syncthreads();
 
   // ---- phase 2: moments (Sec. 2.3) and mu (Eq. mu) on the tile plus a halo of 1 (cross) ----
@@ -155,13 +205,14 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? (ADV == VLB_UW3 ? 3
       int mr, mc;
       if (idx < PA) {
         mr = 1 + idx / MS;
-        mc = idx % MS;
+        mc = idx - (mr - 1) * MS;
       } else {
         const int j = idx - PA;
         mr = (j < TS) ? 0 : MQ - 1;
-        mc = 1 + j % TS;
+        mc = 1 + (j < TS ? j : j - TS);
       }
-      const T* fp = sf + (mr + H - 1) * BS + (mc + H - 1);
+      const int bi = (mr + H - 1) * BS + (mc + HS - 1);  // box index of this position
+      const T* fp = sf + bi;
       T row[4] = {T(0), T(0), T(0), T(0)}, col[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
       for (int i = 0; i < 4; ++i)
@@ -171,26 +222,25 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? (ADV == VLB_UW3 ? 3
           row[i] += x;
           col[j] += x;
         }
-      // n = n0 + sum g (the reference part carries no momentum: sum_k w_i w_j v = 0)
+      // n = n0 + sum g (the reference part carries no momentum); v_1 = -v_4, v_2 = -v_3
       const T dn = (row[0] + row[1]) + (row[2] + row[3]);
-      const T mt = vc.v[0] * row[0] + vc.v[1] * row[1] + vc.v[2] * row[2] + vc.v[3] * row[3];
-      const T mp = vc.v[0] * col[0] + vc.v[1] * col[1] + vc.v[2] * col[2] + vc.v[3] * col[3];
+      const T mt = vc.v[3] * (row[3] - row[0]) + vc.v[2] * (row[2] - row[1]);
+      const T mp = vc.v[3] * (col[3] - col[0]) + vc.v[2] * (col[2] - col[1]);
       const int mi = mr * MS + mc;
-      const T n = a.n0 + dn;
+      const T inv_n = recip(a.n0 + dn);
       sn[mi] = dn;
-      sut[mi] = mt / n;
-      sup[mi] = mp / n;
-      const int pidx = (mr + 1) * PS + (mc + 1);
-      const T* pp = sphi + pidx;
+      sut[mi] = mt * inv_n;
+      sup[mi] = mp * inv_n;
+      const T* pp = sphi + bi;
       const int cr = mr + H - 1;
       const T ph = pp[0];
       // neighbour differences of phi = hi + lo: the hi differences are exact for nearby values
-      T dN = pp[PS] - ph, dS = ph - pp[-PS], dE = pp[1] - ph, dW = ph - pp[-1], lo = T(0);
+      T dN = pp[BS] - ph, dS = ph - pp[-BS], dE = pp[1] - ph, dW = ph - pp[-1], lo = T(0);
       if (DF) {
-        const T* pl = sphl + pidx;
+        const T* pl = sphl + bi;
         lo = pl[0];
-        dN += pl[PS] - lo;
-        dS += lo - pl[-PS];
+        dN += pl[BS] - lo;
+        dS += lo - pl[-BS];
         dE += pl[1] - lo;
         dW += lo - pl[-1];
       }
@@ -204,19 +254,20 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? (ADV == VLB_UW3 ? 3
   __syncthreads();
 
   // ---- phase 3: right-hand sides and the Runge-Kutta combination, per node ----
+  const T sixth = T(1) / T(6);
 #pragma unroll 1
   for (int m = 0; m < NQ; ++m) {
     const int lr = ty + TYT * m, lc = tx;
     const int q = q0 + lr, s = s0 + lc;
     if (q >= nt || s >= ns) continue;
-    const int fr = lr + H, fc = lc + H;
+    const int fr = lr + H, fc = lc + HS;
+    const int bi = fr * BS + fc;
     const int mi = (lr + 1) * MS + (lc + 1);
-    const int pi = (lr + 2) * PS + (lc + 2);
+    const int ui = lr * TS + lc;
 
-    const T dn = sn[mi], ut = sut[mi], up = sup[mi], ph = sphi[pi];
+    const T dn = sn[mi], ut = sut[mi], up = sup[mi], ph = sphi[bi];
     const T n = a.n0 + dn;
     const T ct = sco[C_CT * BQ + fr], cp = sco[C_CP * BQ + fr], gam = sco[C_GAM * BQ + fr];
-    const T Ep = sco[C_EP * BQ + fr], En = sco[C_EN * BQ + fr];
     const T mu_c = smu[mi], mu_n = smu[mi + MS], mu_s = smu[mi - MS], mu_e = smu[mi + 1], mu_w = smu[mi - 1];
 
     // Cahn-Hilliard: M Delta mu - div(u phi) (Eq. CH), flux form with mean face values
@@ -224,24 +275,24 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? (ADV == VLB_UW3 ? 3
                     sco[C_LP * BQ + fr] * (mu_e - T(2) * mu_c + mu_w));
     T Ft = T(0), Fp = T(0);
     if (CH == VLB_HYDRO) {
-      const T Xn = sco[C_J * BQ + fr + 1] * sut[mi + MS] * sphi[pi + PS];
-      const T Xs = sco[C_J * BQ + fr - 1] * sut[mi - MS] * sphi[pi - PS];
-      const T Ye = sup[mi + 1] * sphi[pi + 1];
-      const T Yw = sup[mi - 1] * sphi[pi - 1];
+      const T Xn = sco[C_J * BQ + fr + 1] * sut[mi + MS] * sphi[bi + BS];
+      const T Xs = sco[C_J * BQ + fr - 1] * sut[mi - MS] * sphi[bi - BS];
+      const T Ye = sup[mi + 1] * sphi[bi + 1];
+      const T Yw = sup[mi - 1] * sphi[bi - 1];
       Lphi -= T(0.5) * (ct * (Xn - Xs) + cp * (Ye - Yw));
       // n F = -phi grad mu (Eq. pbin), central differences
-      const T pn = ph / n;
+      const T pn = ph * recip(n);
       Ft = -pn * (mu_n - mu_s) * a.gt;
       Fp = -pn * (mu_e - mu_w) * sco[C_GP * BQ + fr];
     }
 
     const int64_t gidx = (int64_t)q * ns + s;
     {
-      const T lo = DF ? sphl[pi] : T(0);
+      const T lo = DF ? sphl[bi] : T(0);
       T base = ph, base_lo = lo, inc = Lphi * a.dt;
       if (a.f0) {
-        base = a.f0[NPOP * stride + gidx];
-        base_lo = DF ? a.f0[(NPOP + 1) * stride + gidx] : T(0);
+        base = su0[NPOP * TQ * TS + ui];
+        base_lo = DF ? su0[(NPOP + 1) * TQ * TS + ui] : T(0);
         inc = a.b * (((ph - base) + (lo - base_lo)) + inc);
       }
       if (DF) {
@@ -261,16 +312,22 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? (ADV == VLB_UW3 ? 3
     // population deviations at the node
     T g[NPOP];
 #pragma unroll
-    for (int k = 0; k < NPOP; ++k) g[k] = sf[k * BQ * BS + fr * BS + fc];
+    for (int k = 0; k < NPOP; ++k) g[k] = sf[k * BQ * BS + bi];
 
-    // theta-direction weights J_{q+d}, d = -3..3
-    T Jw[7];
-#pragma unroll
-    for (int d = 0; d < 7; ++d) Jw[d] = (d >= 3 - H && d <= 3 + H) ? sco[C_J * BQ + fr + d - 3] : T(0);
+    // UW3 advection weights: the theta flux difference of G = J g with ct/6 folded in, over
+    // d = -2..1 (v > 0) and d = -1..2 (v < 0); the varphi difference is scaled by cp/6.
+    const T ct6 = ct * sixth, cp6 = cp * sixth;
+    const T Jm1 = sco[C_J * BQ + fr - 1], J0 = sco[C_J * BQ + fr], Jp1 = sco[C_J * BQ + fr + 1];
+    const T wp0 = ct6 * sco[C_J * BQ + fr - 2], wp1 = T(-6) * ct6 * Jm1, wp2 = T(3) * ct6 * J0,
+            wp3 = T(2) * ct6 * Jp1;
+    const T wn0 = T(-2) * ct6 * Jm1, wn1 = T(-3) * ct6 * J0, wn2 = T(6) * ct6 * Jp1,
+            wn3 = -ct6 * sco[C_J * BQ + fr + 2];
 
     const T usq = ut * ut + up * up;
     const T c0 = T(1) - T(0.5) * usq;
-    const T sixth = T(1) / T(6);
+    const T hu = T(-0.5) * usq;
+    const T ntau = n * a.inv_tau, dntau = dn * a.inv_tau;
+    const T Ep = sco[C_EP * BQ + fr], En = sco[C_EN * BQ + fr];
 
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -280,26 +337,35 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? (ADV == VLB_UW3 ? 3
 #pragma unroll
       for (int mm = 0; mm < 4; ++mm) h[mm] = (-Fp - gvi * vc.v[mm]) * g[4 * i + mm];
       const T ai = vc.v[i] * ut;
-      const T n0wi = a.n0 * vc.w[i];
-      // reference part: v_i (E(q) + F^theta) per row and sign
-      const T refi = vc.v[i] * ((i >= 2 ? Ep : En) + Ft);
+      // The BGK relaxation and the closed-form reference part share the factor w_i w_j:
+      //   (f^eq - n0 w w)/tau + n0 w w [v_i (E(q) + F^theta) + v_j F^phi]
+      //   = w_i w_j [ (dn + n (poly - 1))/tau + n0 v_i (E + F^theta) + n0 v_j F^phi ]
+      const T ci = dntau + a.n0 * vc.v[i] * ((i >= 2 ? Ep : En) + Ft);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int k = 4 * i + j;
-        const T fref = n0wi * vc.w[j];
-        // advection along theta of G = J f and along varphi of f (Eq. boltz_tor); the reference
-        // part of f is constant in varphi and, for UW3, handled through E(q)
-        T xt[7], xp[7];
+        const T* fk = sf + k * BQ * BS + bi;
+        T rhs;
+        if (ADV == VLB_UW3) {
+          const T Dt = (i >= 2) ? wp0 * fk[-2 * BS] + wp1 * fk[-BS] + wp2 * g[k] + wp3 * fk[BS]
+                                : wn0 * fk[-BS] + wn1 * g[k] + wn2 * fk[BS] + wn3 * fk[2 * BS];
+          const T Dp = (j >= 2) ? (fk[-2] - T(6) * fk[-1] + T(3) * g[k] + T(2) * fk[1])
+                                : (T(-2) * fk[-1] - T(3) * g[k] + T(6) * fk[1] - fk[2]);
+          rhs = -(vc.v[i] * Dt) - (vc.v[j] * cp6) * Dp;
+        } else {
+          // WENO5 is nonlinear: theta reconstruction of the full G = J (g + n0 w_i w_j); along
+          // varphi the reference part is a constant, which the reconstruction passes through.
+          const T fref = a.n0 * vc.ww[i][j];
+          T xt[7], xp[7];
 #pragma unroll
-        for (int d = 0; d < 7; ++d) {
-          const bool in = (d >= 3 - H && d <= 3 + H);
-          const T gt_d = sf[k * BQ * BS + (fr + d - 3) * BS + fc];
-          xt[d] = in ? Jw[d] * (ADV == VLB_UW3 ? gt_d : gt_d + fref) : T(0);
-          xp[d] = in ? sf[k * BQ * BS + fr * BS + fc + d - 3] : T(0);
+          for (int d = 0; d < 7; ++d) {
+            xt[d] = sco[C_J * BQ + fr + d - 3] * (fk[(d - 3) * BS] + fref);
+            xp[d] = fk[d - 3];
+          }
+          const T Dt = (i >= 2) ? weno_diff<T, true>(xt) : weno_diff<T, false>(xt);
+          const T Dp = (j >= 2) ? weno_diff<T, true>(xp) : weno_diff<T, false>(xp);
+          rhs = -(vc.v[i] * ct) * Dt - (vc.v[j] * cp) * Dp;
         }
-        const T Dt = (i >= 2) ? flux_diff<T, ADV, true>(xt) : flux_diff<T, ADV, false>(xt);
-        const T Dp = (j >= 2) ? flux_diff<T, ADV, true>(xp) : flux_diff<T, ADV, false>(xp);
-        T rhs = -(vc.v[i] * ct) * Dt - (vc.v[j] * cp) * Dp;
         // force and inertial terms on the deviation: (Gamma v_j^2 - F^theta) dg/dv_theta + sum_m K_jm h_m
         T dvt = T(0), dvp = T(0);
 #pragma unroll
@@ -308,18 +374,17 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? (ADV == VLB_UW3 ? 3
           dvp += vc.K[j][mm] * h[mm];
         }
         rhs += (gam * vc.v[j] * vc.v[j] - Ft) * dvt + dvp;
-        // same terms (and UW3 theta-advection) on the reference part n0 w_i w_j, in closed form
-        rhs += fref * (refi + vc.v[j] * Fp);
-        // BGK towards the third-order Hermite equilibrium (Eq. feq):
-        // f^eq - n0 w_i w_j = w_i w_j (dn + n (poly - 1))
+        // BGK towards the third-order Hermite equilibrium (Eq. feq) plus the reference part
         const T xi = ai + vc.v[j] * up;
-        const T pm1 = xi * (c0 + xi * (T(0.5) + xi * sixth)) - T(0.5) * usq;
-        const T geq = vc.w[i] * vc.w[j] * (dn + n * pm1);
-        rhs += a.inv_tau * (geq - g[k]);
-        T o = rhs * a.dt + g[k];
+        const T pm1 = xi * (c0 + xi * (T(0.5) + xi * sixth)) + hu;
+        const T X = ntau * pm1 + (ci + a.n0 * vc.v[j] * Fp);
+        rhs += vc.ww[i][j] * X - a.inv_tau * g[k];
+        T o;
         if (a.f0) {
-          const T g0 = a.f0[k * stride + gidx];
+          const T g0 = su0[k * TQ * TS + ui];
           o = g0 + a.b * ((g[k] - g0) + rhs * a.dt);
+        } else {
+          o = rhs * a.dt + g[k];
         }
         a.fout[k * stride + gidx] = o;
       }
@@ -334,7 +399,10 @@ VConst<T> make_vconst() {
   for (int i = 0; i < 4; ++i) {
     c.v[i] = (T)d.v[i];
     c.w[i] = (T)d.w[i];
-    for (int m = 0; m < 4; ++m) c.K[i][m] = (T)d.K[i][m];
+    for (int m = 0; m < 4; ++m) {
+      c.K[i][m] = (T)d.K[i][m];
+      c.ww[i][m] = (T)(d.w[i] * d.w[m]);
+    }
   }
   return c;
 }

