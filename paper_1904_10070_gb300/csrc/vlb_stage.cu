@@ -108,7 +108,7 @@ __device__ __forceinline__ T weno_diff(const T (&x)[7]) {
 // ---------------------------------------------------------------------------------------------
 // Phase 1: asynchronous staging of the box (populations, phi), U^n and the row coefficients.
 // ---------------------------------------------------------------------------------------------
-template <typename T, int ADV>
+template <typename T, int ADV, bool F0>
 __device__ __forceinline__ void stage_loads(const StageArgs<T>& a, T* sm, int tid, int q0, int s0) {
   using S = Smem<T, ADV>;
   constexpr int H = S::H, BQ = S::BQ, BS = S::BS;
@@ -123,26 +123,36 @@ __device__ __forceinline__ void stage_loads(const StageArgs<T>& a, T* sm, int ti
   const bool fast = (ns % VEC == 0) && ns >= BS && nt >= BQ;
   if (fast) {
     // Box rows wrap at most once (nt >= BQ); chunk columns start at multiples of VEC and never
-    // straddle the seam because ns % VEC == 0, so every chunk is one aligned 16-byte copy.
-    for (int idx = tid; idx < NBOX * BQ * CPR; idx += NTHREADS) {
-      const int k = idx / (BQ * CPR);
-      const int rem = idx - k * (BQ * CPR);
-      const int r = rem / CPR, ch = rem - r * CPR;
+    // straddle the seam because ns % VEC == 0, so every chunk is one aligned 16-byte copy.  Each
+    // thread owns fixed box positions and walks through the arrays, so the index arithmetic is
+    // done once per position, not once per copy.
+    for (int pos = tid; pos < BQ * CPR; pos += NTHREADS) {
+      const int r = pos / CPR, ch = pos - r * CPR;
       int gq = q0 + r - H;
       gq += gq < 0 ? nt : (gq >= nt ? -nt : 0);
       int gs = s0 - HS + ch * VEC;
       gs += gs < 0 ? ns : (gs >= ns ? -ns : 0);
-      cp_async16(sf + (k * BQ + r) * BS + ch * VEC, a.fin + k * stride + (int64_t)gq * ns + gs);
+      const T* src = a.fin + (int64_t)gq * ns + gs;
+      T* dst = sf + r * BS + ch * VEC;
+#pragma unroll
+      for (int k = 0; k < NBOX; ++k) cp_async16(dst + k * BQ * BS, src + k * stride);
     }
-    if (a.f0) {
-      constexpr int CT = TS / VEC;
-      for (int idx = tid; idx < S::NST * TQ * CT; idx += NTHREADS) {
-        const int k = idx / (TQ * CT);
-        const int rem = idx - k * (TQ * CT);
-        const int r = rem / CT, ch = rem - r * CT;
+    if (F0) {
+      // the tile's U^n: TQ x TS/VEC chunk positions, the arrays split between thread halves
+      constexpr int CT = TS / VEC, NPOS = TQ * CT;
+      constexpr int GROUPS = NTHREADS / NPOS > 0 ? NTHREADS / NPOS : 1;
+      constexpr int PER = (S::NST + GROUPS - 1) / GROUPS;
+      for (int t = tid; t < NPOS * GROUPS; t += NTHREADS) {
+        const int pos = t % NPOS, grp = t / NPOS;
+        const int r = pos / CT, ch = pos - r * CT;
         const int gq = q0 + r, gs = s0 + ch * VEC;
-        if (gq < nt && gs < ns)
-          cp_async16(su0 + (k * TQ + r) * TS + ch * VEC, a.f0 + k * stride + (int64_t)gq * ns + gs);
+        if (gq < nt && gs < ns) {
+          const T* src = a.f0 + (int64_t)gq * ns + gs;
+          T* dst = su0 + r * TS + ch * VEC;
+          const int k0 = grp * PER, k1 = k0 + PER < S::NST ? k0 + PER : S::NST;
+#pragma unroll 4
+          for (int k = k0; k < k1; ++k) cp_async16(dst + k * TQ * TS, src + k * stride);
+        }
       }
     }
   } else {
@@ -153,7 +163,7 @@ __device__ __forceinline__ void stage_loads(const StageArgs<T>& a, T* sm, int ti
       const int gq = wrap(q0 + r - H, nt), gs = wrap(s0 + c - HS, ns);
       cp_async_scalar<sizeof(T)>(sf + (k * BQ + r) * BS + c, a.fin + k * stride + (int64_t)gq * ns + gs);
     }
-    if (a.f0) {
+    if (F0) {
       for (int idx = tid; idx < S::NST * TQ * TS; idx += NTHREADS) {
         const int k = idx / (TQ * TS);
         const int rem = idx - k * (TQ * TS);
@@ -172,7 +182,8 @@ __device__ __forceinline__ void stage_loads(const StageArgs<T>& a, T* sm, int ti
   cp_async_wait_all();
 }
 
-template <typename T, int ADV, int CH>
+// F0: the stage combines with U^n (stages 2 and 3); the first stage writes U_in + dt L(U_in).
+template <typename T, int ADV, int CH, bool F0>
 __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel(StageArgs<T> a, VConst<T> vc) {
   using S = Smem<T, ADV>;
   constexpr bool DF = S::DF;
@@ -194,7 +205,7 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TS + tx;
   const int s0 = blockIdx.x * TS, q0 = blockIdx.y * TQ;
 
-  stage_loads<T, ADV>(a, sm, tid, q0, s0);
+  stage_loads<T, ADV, F0>(a, sm, tid, q0, s0);
   __syncthreads();
 
   // ---- phase 2: moments (Sec. 2.3) and mu (Eq. mu) on the tile plus a halo of 1 (cross) ----
@@ -290,7 +301,7 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel
     {
       const T lo = DF ? sphl[bi] : T(0);
       T base = ph, base_lo = lo, inc = Lphi * a.dt;
-      if (a.f0) {
+      if (F0) {
         base = su0[NPOP * TQ * TS + ui];
         base_lo = DF ? su0[(NPOP + 1) * TQ * TS + ui] : T(0);
         inc = a.b * (((ph - base) + (lo - base_lo)) + inc);
@@ -380,7 +391,7 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel
         const T X = ntau * pm1 + (ci + a.n0 * vc.v[j] * Fp);
         rhs += vc.ww[i][j] * X - a.inv_tau * g[k];
         T o;
-        if (a.f0) {
+        if (F0) {
           const T g0 = su0[k * TQ * TS + ui];
           o = g0 + a.b * ((g[k] - g0) + rhs * a.dt);
         } else {
@@ -407,22 +418,28 @@ VConst<T> make_vconst() {
   return c;
 }
 
-template <typename T, int ADV, int CH>
-cudaError_t launch_one(const StageArgs<T>& a, cudaStream_t st) {
+template <typename T, int ADV, int CH, bool F0>
+cudaError_t launch_variant(const StageArgs<T>& a, cudaStream_t st) {
   using S = Smem<T, ADV>;
   static int configured_mask = 0;  // one bit per device id < 32
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev >= 32 || !(configured_mask & (1 << dev))) {
-    e = cudaFuncSetAttribute(stage_kernel<T, ADV, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::BYTES);
+    e = cudaFuncSetAttribute(stage_kernel<T, ADV, CH, F0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)S::BYTES);
     if (e != cudaSuccess) return e;
     if (dev < 32) configured_mask |= (1 << dev);
   }
   static const VConst<T> vc = make_vconst<T>();
   dim3 grid((a.ns + TS - 1) / TS, (a.nt + TQ - 1) / TQ);
-  stage_kernel<T, ADV, CH><<<grid, dim3(TS, TYT), S::BYTES, st>>>(a, vc);
+  stage_kernel<T, ADV, CH, F0><<<grid, dim3(TS, TYT), S::BYTES, st>>>(a, vc);
   return cudaGetLastError();
+}
+
+template <typename T, int ADV, int CH>
+cudaError_t launch_one(const StageArgs<T>& a, cudaStream_t st) {
+  return a.f0 ? launch_variant<T, ADV, CH, true>(a, st) : launch_variant<T, ADV, CH, false>(a, st);
 }
 
 }  // namespace
