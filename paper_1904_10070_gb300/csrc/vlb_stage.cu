@@ -41,7 +41,7 @@ struct Smem {
   static constexpr int H = (ADV == VLB_UW3) ? 2 : 3;
   static constexpr int NST = DF ? NARR + 1 : NARR;  // state arrays
   static constexpr int BQ = TQ + 2 * H, BS = TS + 2 * HS;  // staged box
-  static constexpr int MQ = TQ + 2, MS = TS + 2;           // moment / mu box (halo 1)
+  static constexpr int MQ = TQ + 2, MS = TS + 4;           // moment / mu box: halo 1, column origin -2
   static constexpr int F_OFF = 0;
   static constexpr int PHI_OFF = F_OFF + NPOP * BQ * BS;
   static constexpr int PHL_OFF = PHI_OFF + BQ * BS;
@@ -71,9 +71,11 @@ __device__ __forceinline__ void cp_async_scalar(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_u32(dst)), "l"(src), "n"(BYTES));
 }
 
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\n" ::);
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
@@ -137,6 +139,7 @@ __device__ __forceinline__ void stage_loads(const StageArgs<T>& a, T* sm, int ti
 #pragma unroll
       for (int k = 0; k < NBOX; ++k) cp_async16(dst + k * BQ * BS, src + k * stride);
     }
+    cp_async_commit();
     if (F0) {
       // the tile's U^n: TQ x TS/VEC chunk positions, the arrays split between thread halves
       constexpr int CT = TS / VEC, NPOS = TQ * CT;
@@ -163,6 +166,7 @@ __device__ __forceinline__ void stage_loads(const StageArgs<T>& a, T* sm, int ti
       const int gq = wrap(q0 + r - H, nt), gs = wrap(s0 + c - HS, ns);
       cp_async_scalar<sizeof(T)>(sf + (k * BQ + r) * BS + c, a.fin + k * stride + (int64_t)gq * ns + gs);
     }
+    cp_async_commit();
     if (F0) {
       for (int idx = tid; idx < S::NST * TQ * TS; idx += NTHREADS) {
         const int k = idx / (TQ * TS);
@@ -179,11 +183,181 @@ __device__ __forceinline__ void stage_loads(const StageArgs<T>& a, T* sm, int ti
     const int k = idx / BQ, r = idx - k * BQ;
     sco[idx] = __ldg(a.coef + (int64_t)k * nt + wrap(q0 + r - H, nt));
   }
-  cp_async_wait_all();
+  cp_async_commit();  // second group: U^n (empty in the first stage)
+}
+
+
+// ---------------------------------------------------------------------------------------------
+// Packed FP32 pairs: two horizontally adjacent nodes share one thread, one float2 lane each, so
+// the per-population arithmetic issues as FFMA2/FADD2/FMUL2 and shared/global accesses are 8 bytes.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+__device__ __forceinline__ void st2(float* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
+
+// (hi, lo) <- (base, base_lo) + inc with an error-free sum, renormalised (one lane)
+__device__ __forceinline__ void df_add(float base, float base_lo, float inc, float& hi, float& lo) {
+  const float s1 = base + inc;
+  const float bb = s1 - base;
+  const float err = (base - (s1 - bb)) + (inc - bb);
+  const float lo2 = base_lo + err;
+  hi = s1 + lo2;
+  lo = lo2 - (hi - s1);
+}
+
+// Phase 3 of the FP32 UW3 stage for the node pair (lr, lc), (lr, lc + 1) of the tile; the same
+// arithmetic as the scalar path, lane by lane.
+template <int CH, bool F0>
+__device__ __forceinline__ void phase3_pair(const StageArgs<float>& a, const VConst<float>& vc, float* sm, int tid,
+                                            int q0, int s0) {
+  using S = Smem<float, VLB_UW3>;
+  constexpr int H = S::H, BQ = S::BQ, BS = S::BS, MS = S::MS;
+  const float* sf = sm + S::F_OFF;
+  const float* sphi = sm + S::PHI_OFF;
+  const float* sphl = sm + S::PHL_OFF;
+  const float* su0 = sm + S::U0_OFF;
+  const float* sn = sm + S::N_OFF;
+  const float* sut = sm + S::UT_OFF;
+  const float* sup = sm + S::UP_OFF;
+  const float* smu = sm + S::MU_OFF;
+  const float* sco = sm + S::CO_OFF;
+  const int lr = tid / (TS / 2), lc = 2 * (tid % (TS / 2));
+  const int q = q0 + lr, s = s0 + lc;
+  if (q >= a.nt || s >= a.ns) return;  // n_phi is even here, so s + 1 < n_phi as well
+  const int64_t stride = a.stride;
+  const int fr = lr + H;
+  const int bi = fr * BS + lc + HS;      // even: 8-byte aligned pairs
+  const int mi = (lr + 1) * MS + lc + 2;  // even
+  const int ui = lr * TS + lc;
+  const float sixth = 1.0f / 6.0f;
+
+  const float2 dn = ld2(sn + mi), ut = ld2(sut + mi), up = ld2(sup + mi), ph = ld2(sphi + bi);
+  const float2 n = add2(dn, f2(a.n0));
+  const float ct = sco[C_CT * BQ + fr], cp = sco[C_CP * BQ + fr], gam = sco[C_GAM * BQ + fr];
+  const float lt = sco[C_LT * BQ + fr], lp = sco[C_LP * BQ + fr];
+  const float Jp = sco[C_JP * BQ + fr], Jm = sco[C_JM * BQ + fr];
+  const float2 muC = ld2(smu + mi), muN = ld2(smu + mi + MS), muS = ld2(smu + mi - MS);
+  const float2 muL = ld2(smu + mi - 2), muR = ld2(smu + mi + 2);
+  const float2 muE = make_float2(muC.y, muR.x), muW = make_float2(muL.y, muC.x);
+
+  // Cahn-Hilliard: M Delta mu - div(u phi) (Eq. CH), flux form with mean face values
+  float2 lapmu = mul2(f2(lt), sub2(mul2(f2(Jp), sub2(muN, muC)), mul2(f2(Jm), sub2(muC, muS))));
+  lapmu = fma2(f2(lp), add2(sub2(muE, muC), sub2(muW, muC)), lapmu);
+  float2 Lphi = mul2(f2(a.M), lapmu);
+  float2 Ft = f2(0.0f), Fp = f2(0.0f);
+  if (CH == VLB_HYDRO) {
+    const float2 Xn = mul2(f2(sco[C_J * BQ + fr + 1]), mul2(ld2(sut + mi + MS), ld2(sphi + bi + BS)));
+    const float2 Xs = mul2(f2(sco[C_J * BQ + fr - 1]), mul2(ld2(sut + mi - MS), ld2(sphi + bi - BS)));
+    const float2 upL = ld2(sup + mi - 2), upR = ld2(sup + mi + 2);
+    const float2 phL = ld2(sphi + bi - 2), phR = ld2(sphi + bi + 2);
+    const float2 Ye = mul2(make_float2(up.y, upR.x), make_float2(ph.y, phR.x));
+    const float2 Yw = mul2(make_float2(upL.y, up.x), make_float2(phL.y, ph.x));
+    Lphi = sub2(Lphi, mul2(f2(0.5f), fma2(f2(ct), sub2(Xn, Xs), mul2(f2(cp), sub2(Ye, Yw)))));
+    // n F = -phi grad mu (Eq. pbin), central differences
+    const float2 pn = make_float2(ph.x * __frcp_rn(n.x), ph.y * __frcp_rn(n.y));
+    Ft = mul2(mul2(make_float2(-pn.x, -pn.y), sub2(muN, muS)), f2(a.gt));
+    Fp = mul2(mul2(make_float2(-pn.x, -pn.y), sub2(muE, muW)), f2(sco[C_GP * BQ + fr]));
+  }
+
+  const int64_t gidx = (int64_t)q * a.ns + s;  // even
+  {
+    const float2 lo = ld2(sphl + bi);
+    float2 base = ph, base_lo = lo, inc = mul2(Lphi, f2(a.dt));
+    if (F0) {
+      base = ld2(su0 + NPOP * TQ * TS + ui);
+      base_lo = ld2(su0 + (NPOP + 1) * TQ * TS + ui);
+      inc = mul2(f2(a.b), fma2(Lphi, f2(a.dt), add2(sub2(ph, base), sub2(lo, base_lo))));
+    }
+    float2 hi_o, lo_o;
+    df_add(base.x, base_lo.x, inc.x, hi_o.x, lo_o.x);
+    df_add(base.y, base_lo.y, inc.y, hi_o.y, lo_o.y);
+    st2(a.fout + NPOP * stride + gidx, hi_o);
+    st2(a.fout + (NPOP + 1) * stride + gidx, lo_o);
+  }
+
+  float2 g[NPOP];
+#pragma unroll
+  for (int k = 0; k < NPOP; ++k) g[k] = ld2(sf + k * BQ * BS + bi);
+
+  // UW3 theta weights with ct/6 folded in (same row for both lanes)
+  const float ct6 = ct * sixth, cp6 = cp * sixth;
+  const float Jm1 = sco[C_J * BQ + fr - 1], J0 = sco[C_J * BQ + fr], Jp1 = sco[C_J * BQ + fr + 1];
+  const float wp0 = ct6 * sco[C_J * BQ + fr - 2], wp1 = -6.0f * ct6 * Jm1, wp2 = 3.0f * ct6 * J0,
+              wp3 = 2.0f * ct6 * Jp1;
+  const float wn0 = -2.0f * ct6 * Jm1, wn1 = -3.0f * ct6 * J0, wn2 = 6.0f * ct6 * Jp1,
+              wn3 = -ct6 * sco[C_J * BQ + fr + 2];
+
+  const float2 usq = fma2(ut, ut, mul2(up, up));
+  const float2 hu = mul2(f2(-0.5f), usq);
+  const float2 c0 = add2(f2(1.0f), hu);
+  const float2 ntau = mul2(n, f2(a.inv_tau)), dntau = mul2(dn, f2(a.inv_tau));
+  const float Ep = sco[C_EP * BQ + fr], En = sco[C_EN * BQ + fr];
+  float2 cj[4], nFp[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    cj[j] = sub2(f2(gam * vc.v[j] * vc.v[j]), Ft);  // Gamma v_j^2 - F^theta
+    nFp[j] = mul2(f2(a.n0 * vc.v[j]), Fp);           // n0 v_j F^phi
+  }
+
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    // h_m = (-F^phi - Gamma v_i v_m) g_{i m}  (K~ = K diag v, Sec. 2.3)
+    float2 h[4];
+#pragma unroll
+    for (int mm = 0; mm < 4; ++mm) h[mm] = mul2(sub2(f2(-gam * vc.v[i] * vc.v[mm]), Fp), g[4 * i + mm]);
+    const float2 ai = mul2(f2(vc.v[i]), ut);
+    // BGK relaxation and the closed-form reference part share w_i w_j
+    const float2 ci = fma2(f2(a.n0 * vc.v[i]), add2(f2(i >= 2 ? Ep : En), Ft), dntau);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = 4 * i + j;
+      const float* fk = sf + k * BQ * BS + bi;
+      const float2 gk = g[k];
+      float2 Dt;
+      if (i >= 2)
+        Dt = fma2(f2(wp3), ld2(fk + BS), fma2(f2(wp2), gk, fma2(f2(wp1), ld2(fk - BS), mul2(f2(wp0), ld2(fk - 2 * BS)))));
+      else
+        Dt = fma2(f2(wn3), ld2(fk + 2 * BS), fma2(f2(wn2), ld2(fk + BS), fma2(f2(wn1), gk, mul2(f2(wn0), ld2(fk - BS)))));
+      const float2 A = ld2(fk - 2), C = ld2(fk + 2);
+      const float2 M1 = make_float2(A.y, gk.x), M2 = make_float2(gk.y, C.x);
+      float2 Dp;
+      if (j >= 2)
+        Dp = fma2(f2(2.0f), M2, fma2(f2(3.0f), gk, fma2(f2(-6.0f), M1, A)));
+      else
+        Dp = sub2(fma2(f2(6.0f), M2, fma2(f2(-3.0f), gk, mul2(f2(-2.0f), M1))), C);
+      float2 rhs = fma2(f2(-vc.v[j] * cp6), Dp, mul2(f2(-vc.v[i]), Dt));
+      float2 dvt = mul2(f2(vc.K[i][0]), g[j]);
+      float2 dvp = mul2(f2(vc.K[j][0]), h[0]);
+#pragma unroll
+      for (int mm = 1; mm < 4; ++mm) {
+        dvt = fma2(f2(vc.K[i][mm]), g[4 * mm + j], dvt);
+        dvp = fma2(f2(vc.K[j][mm]), h[mm], dvp);
+      }
+      rhs = add2(fma2(cj[j], dvt, rhs), dvp);
+      // BGK towards the third-order Hermite equilibrium (Eq. feq) plus the reference part
+      const float2 xi = fma2(f2(vc.v[j]), up, ai);
+      const float2 pm1 = fma2(xi, fma2(xi, fma2(xi, f2(sixth), f2(0.5f)), c0), hu);
+      const float2 X = fma2(ntau, pm1, add2(ci, nFp[j]));
+      rhs = fma2(f2(-a.inv_tau), gk, fma2(f2(vc.ww[i][j]), X, rhs));
+      float2 o;
+      if (F0) {
+        const float2 g0 = ld2(su0 + k * TQ * TS + ui);
+        o = fma2(f2(a.b), fma2(rhs, f2(a.dt), sub2(gk, g0)), g0);
+      } else {
+        o = fma2(rhs, f2(a.dt), gk);
+      }
+      st2(a.fout + k * stride + gidx, o);
+    }
+  }
 }
 
 // F0: the stage combines with U^n (stages 2 and 3); the first stage writes U_in + dt L(U_in).
-template <typename T, int ADV, int CH, bool F0>
+// PAIR: FP32 UW3 with n_phi % 4 == 0 -- phase 3 runs on packed node pairs.
+template <typename T, int ADV, int CH, bool F0, bool PAIR>
 __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel(StageArgs<T> a, VConst<T> vc) {
   using S = Smem<T, ADV>;
   constexpr bool DF = S::DF;
@@ -202,27 +376,30 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel
 
   const int nt = a.nt, ns = a.ns;
   const int64_t stride = a.stride;
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TS + tx;
+  const int tid = threadIdx.x;
   const int s0 = blockIdx.x * TS, q0 = blockIdx.y * TQ;
 
   stage_loads<T, ADV, F0>(a, sm, tid, q0, s0);
+  cp_async_wait<1>();  // the box; the U^n group may still be in flight
   __syncthreads();
 
   // ---- phase 2: moments (Sec. 2.3) and mu (Eq. mu) on the tile plus a halo of 1 (cross) ----
   {
-    constexpr int PA = TQ * MS;
+    constexpr int MS2 = TS + 2;  // tile columns -1 .. TS in the rows of the tile
+    constexpr int PA = TQ * MS2;
     constexpr int PM = PA + 2 * TS;
     for (int idx = tid; idx < PM; idx += NTHREADS) {
+      // moment-box position (mr, mc) is tile node (mr - 1, mc - 2)
       int mr, mc;
       if (idx < PA) {
-        mr = 1 + idx / MS;
-        mc = idx - (mr - 1) * MS;
+        mr = 1 + idx / MS2;
+        mc = 1 + (idx - (mr - 1) * MS2);
       } else {
         const int j = idx - PA;
         mr = (j < TS) ? 0 : MQ - 1;
-        mc = 1 + (j < TS ? j : j - TS);
+        mc = 2 + (j < TS ? j : j - TS);
       }
-      const int bi = (mr + H - 1) * BS + (mc + HS - 1);  // box index of this position
+      const int bi = (mr + H - 1) * BS + (mc - 2 + HS);  // box index of this position
       const T* fp = sf + bi;
       T row[4] = {T(0), T(0), T(0), T(0)}, col[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
@@ -262,18 +439,23 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel
       smu[mi] = -a.A * cubic - a.kappa * lap;
     }
   }
+  cp_async_wait<0>();
   __syncthreads();
 
   // ---- phase 3: right-hand sides and the Runge-Kutta combination, per node ----
+  if constexpr (PAIR) {
+    phase3_pair<CH, F0>(a, vc, sm, tid, q0, s0);
+    return;
+  }
   const T sixth = T(1) / T(6);
 #pragma unroll 1
   for (int m = 0; m < NQ; ++m) {
-    const int lr = ty + TYT * m, lc = tx;
+    const int lr = tid / TS + TYT * m, lc = tid % TS;
     const int q = q0 + lr, s = s0 + lc;
     if (q >= nt || s >= ns) continue;
     const int fr = lr + H, fc = lc + HS;
     const int bi = fr * BS + fc;
-    const int mi = (lr + 1) * MS + (lc + 1);
+    const int mi = (lr + 1) * MS + (lc + 2);
     const int ui = lr * TS + lc;
 
     const T dn = sn[mi], ut = sut[mi], up = sup[mi], ph = sphi[bi];
@@ -418,7 +600,7 @@ VConst<T> make_vconst() {
   return c;
 }
 
-template <typename T, int ADV, int CH, bool F0>
+template <typename T, int ADV, int CH, bool F0, bool PAIR>
 cudaError_t launch_variant(const StageArgs<T>& a, cudaStream_t st) {
   using S = Smem<T, ADV>;
   static int configured_mask = 0;  // one bit per device id < 32
@@ -426,20 +608,25 @@ cudaError_t launch_variant(const StageArgs<T>& a, cudaStream_t st) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev >= 32 || !(configured_mask & (1 << dev))) {
-    e = cudaFuncSetAttribute(stage_kernel<T, ADV, CH, F0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(stage_kernel<T, ADV, CH, F0, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)S::BYTES);
     if (e != cudaSuccess) return e;
     if (dev < 32) configured_mask |= (1 << dev);
   }
   static const VConst<T> vc = make_vconst<T>();
   dim3 grid((a.ns + TS - 1) / TS, (a.nt + TQ - 1) / TQ);
-  stage_kernel<T, ADV, CH, F0><<<grid, dim3(TS, TYT), S::BYTES, st>>>(a, vc);
+  stage_kernel<T, ADV, CH, F0, PAIR><<<grid, NTHREADS, S::BYTES, st>>>(a, vc);
   return cudaGetLastError();
 }
 
 template <typename T, int ADV, int CH>
 cudaError_t launch_one(const StageArgs<T>& a, cudaStream_t st) {
-  return a.f0 ? launch_variant<T, ADV, CH, true>(a, st) : launch_variant<T, ADV, CH, false>(a, st);
+  using S = Smem<T, ADV>;
+  constexpr bool CAN_PAIR = sizeof(T) == 4 && ADV == VLB_UW3;
+  const bool pair = CAN_PAIR && a.ns % 4 == 0 && a.ns >= S::BS && a.nt >= S::BQ;
+  if (pair)
+    return a.f0 ? launch_variant<T, ADV, CH, true, CAN_PAIR>(a, st) : launch_variant<T, ADV, CH, false, CAN_PAIR>(a, st);
+  return a.f0 ? launch_variant<T, ADV, CH, true, false>(a, st) : launch_variant<T, ADV, CH, false, false>(a, st);
 }
 
 }  // namespace
