@@ -8,26 +8,28 @@
 // are stored as deviations g = f - n0 w_i w_j from the rest equilibrium, and in FP32 mode phi is
 // carried as an unevaluated float pair hi + lo (vlb_internal.cuh explains both).
 //
-// Tiling: a CTA owns a 16 (theta) x 32 (varphi) tile; 256 threads, each thread two nodes.
-// Phase 1 stages, with asynchronous global->shared copies (cp.async, 16-byte chunks when the row
-// length allows it), a box of H rows (2 for UW3, 3 for WENO5) and 4 columns around the tile for
-// the 16 populations and phi, the U^n values of the tile itself, and the row coefficients.
-// Phase 2 computes the moments and mu on the tile plus a halo of 1; phase 3 the right-hand sides
-// and the Runge-Kutta combination.  Periodic wrap-around is resolved on the load addresses, so
-// ragged tiles and tiny grids take the same path (with scalar copies).
+// Work unit: a tile of TQ theta rows x 32 varphi columns.  For a tile the CTA
+//   1. stages, with asynchronous global->shared copies (cp.async), a box of H rows (2 for UW3,
+//      3 for WENO5) and HS columns around the tile for the 16 populations and phi, the tile's
+//      U^n values and the per-row coefficients;
+//   2. computes the moments and mu on the tile plus a halo of 1;
+//   3. computes the right-hand sides and the Runge-Kutta combination and stores the tile.
+// Two kernels share these steps:
+//   - stage_persistent (FP32, UW3, n_phi % 4 == 0 -- the production path): one 384-thread CTA
+//     per SM walks over 24 x 32 tiles; the box of the next tile (double-buffered) and its U^n are
+//     copied in while the current tile computes, and step 3 runs on adjacent node pairs in packed
+//     FP32x2 arithmetic (two lanes of one float2 per thread);
+//   - stage_kernel (every other case: FP64, WENO5, odd or tiny grids): one 256-thread CTA per
+//     16 x 32 tile, scalar arithmetic, two nodes per thread.
+// Periodic wrap-around is resolved on the copy addresses, so ragged tiles need no special case.
 #include "vlb_internal.cuh"
 
 namespace vlb {
 
 namespace {
 
-constexpr int TS = 32;        // tile width along varphi (one warp)
-constexpr int TYT = 8;        // thread rows
-constexpr int NQ = 2;         // nodes per thread along theta
-constexpr int TQ = TYT * NQ;  // tile height along theta
-constexpr int NTHREADS = TS * TYT;
-constexpr int HS = 4;         // box columns on each side (>= stencil reach, keeps 16-byte alignment)
-constexpr int NCT = 11;       // coefficient rows staged in shared memory (C_J .. C_EN)
+constexpr int TS = 32;   // tile width along varphi
+constexpr int NCT = 11;  // coefficient rows staged in shared memory (C_J .. C_EN)
 
 template <typename T>
 struct VConst {
@@ -35,25 +37,38 @@ struct VConst {
   T ww[4][4];  // w_i w_j
 };
 
-template <typename T, int ADV>
-struct Smem {
-  static constexpr bool DF = sizeof(T) == 4;
-  static constexpr int H = (ADV == VLB_UW3) ? 2 : 3;
-  static constexpr int NST = DF ? NARR + 1 : NARR;  // state arrays
-  static constexpr int BQ = TQ + 2 * H, BS = TS + 2 * HS;  // staged box
-  static constexpr int MQ = TQ + 2, MS = TS + 4;           // moment / mu box: halo 1, column origin -2
-  static constexpr int F_OFF = 0;
-  static constexpr int PHI_OFF = F_OFF + NPOP * BQ * BS;
-  static constexpr int PHL_OFF = PHI_OFF + BQ * BS;
-  static constexpr int U0_OFF = PHL_OFF + (DF ? BQ * BS : 0);
+// Shared-memory layout of one CTA.  Offsets are in elements of T.
+template <typename T, int H_, int TQ_, int HS_, int NTH_, int NBUF_>
+struct Lay {
+  static constexpr bool DF = sizeof(T) == 4;       // phi as a float pair
+  static constexpr int H = H_, TQ = TQ_, HS = HS_, NTH = NTH_, NBUF = NBUF_;
+  static constexpr int NST = DF ? NARR + 1 : NARR;  // state arrays (= staged boxes)
+  static constexpr int BQ = TQ + 2 * H, BS = TS + 2 * HS;
+  static constexpr int BOX = NST * BQ * BS;          // populations, phi (, phi lo)
+  static constexpr int MQ = TQ + 2, MS = TS + 4;     // moment / mu box: halo 1, column origin -2
+  static constexpr int CO = (NCT * BQ + 15) / 16 * 16;  // padded: sub-buffers stay 16-byte aligned
+  static constexpr int VEC = 16 / sizeof(T);              // elements per 16-byte chunk
+  // each box row starts HS columns left of the tile: shift the buffers so that the tile columns
+  // (and every 16-byte chunk copied into them) start on a 16-byte boundary
+  static constexpr int BOX_OFF = (VEC - HS % VEC) % VEC;
+  static constexpr int CO_OFF = (BOX_OFF + NBUF * BOX + VEC - 1) / VEC * VEC;
+  static constexpr int U0_OFF = CO_OFF + NBUF * CO;
   static constexpr int N_OFF = U0_OFF + NST * TQ * TS;
   static constexpr int UT_OFF = N_OFF + MQ * MS;
   static constexpr int UP_OFF = UT_OFF + MQ * MS;
   static constexpr int MU_OFF = UP_OFF + MQ * MS;
-  static constexpr int CO_OFF = MU_OFF + MQ * MS;
-  static constexpr int TOTAL = CO_OFF + NCT * BQ;
+  static constexpr int TOTAL = MU_OFF + MQ * MS;
   static constexpr size_t BYTES = sizeof(T) * (size_t)TOTAL;
+  static_assert((BOX * sizeof(T)) % 16 == 0 && (BS * sizeof(T)) % 16 == 0 && (BQ * BS * sizeof(T)) % 16 == 0,
+                "box rows and arrays keep 16-byte alignment");
+  static_assert(((BOX_OFF + HS) * sizeof(T)) % 16 == 0, "tile columns start on a 16-byte boundary");
+  static_assert((BOX_OFF * sizeof(T)) % 8 == 0, "edge chunks are 8-byte aligned");
+  static_assert((CO_OFF * sizeof(T)) % 16 == 0 && (U0_OFF * sizeof(T)) % 16 == 0, "16-byte aligned sub-buffers");
 };
+
+template <typename T, int ADV>
+using GenericLay = Lay<T, (ADV == VLB_UW3 ? 2 : 3), 16, 4, 256, 1>;
+using PersistLay = Lay<float, 2, 24, 2, 384, 2>;
 
 __device__ __forceinline__ int wrap(int x, int n) {
   x %= n;
@@ -67,7 +82,7 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
 }
 
 template <int BYTES>
-__device__ __forceinline__ void cp_async_scalar(void* dst, const void* src) {
+__device__ __forceinline__ void cp_async_small(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_u32(dst)), "l"(src), "n"(BYTES));
 }
 
@@ -107,89 +122,322 @@ __device__ __forceinline__ T weno_diff(const T (&x)[7]) {
   return weno5(x[6], x[5], x[4], x[3], x[2]) - weno5(x[5], x[4], x[3], x[2], x[1]);
 }
 
+// Whether the chunked copy path applies: rows wrap at most once and columns come in aligned
+// 16-byte chunks that never straddle the periodic seam.
+template <typename L>
+__host__ __device__ inline bool chunked(int nt, int ns) {
+  constexpr int VEC = 16 / (L::DF ? 4 : 8);
+  return ns % VEC == 0 && ns >= L::BS && nt >= L::BQ;
+}
+
 // ---------------------------------------------------------------------------------------------
-// Phase 1: asynchronous staging of the box (populations, phi), U^n and the row coefficients.
+// Step 1: asynchronous copies of the box (populations and phi of U_in) with its row coefficients,
+// and of the tile's U^n.
 // ---------------------------------------------------------------------------------------------
-template <typename T, int ADV, bool F0>
-__device__ __forceinline__ void stage_loads(const StageArgs<T>& a, T* sm, int tid, int q0, int s0) {
-  using S = Smem<T, ADV>;
-  constexpr int H = S::H, BQ = S::BQ, BS = S::BS;
-  constexpr int VEC = 16 / sizeof(T);  // elements per 16-byte chunk
-  constexpr int CPR = BS / VEC;        // chunks per box row
-  constexpr int NBOX = NPOP + 1 + (S::DF ? 1 : 0);  // populations, phi (, phi lo): consecutive boxes
-  static_assert(S::PHI_OFF == NPOP * BQ * BS && (!S::DF || S::PHL_OFF == (NPOP + 1) * BQ * BS), "box layout");
+template <typename L, typename T>
+__device__ __forceinline__ void issue_box(const StageArgs<T>& a, T* box, T* co, int q0, int s0, int tid) {
+  constexpr int H = L::H, BQ = L::BQ, BS = L::BS, HS = L::HS;
+  constexpr int VEC = 16 / sizeof(T);
   const int nt = a.nt, ns = a.ns;
   const int64_t stride = a.stride;
-  T* sf = sm + S::F_OFF;
-  T* su0 = sm + S::U0_OFF;
-  const bool fast = (ns % VEC == 0) && ns >= BS && nt >= BQ;
-  if (fast) {
-    // Box rows wrap at most once (nt >= BQ); chunk columns start at multiples of VEC and never
-    // straddle the seam because ns % VEC == 0, so every chunk is one aligned 16-byte copy.  Each
-    // thread owns fixed box positions and walks through the arrays, so the index arithmetic is
-    // done once per position, not once per copy.
-    for (int pos = tid; pos < BQ * CPR; pos += NTHREADS) {
+  if (chunked<L>(nt, ns)) {
+    // chunk c of a box row: with HS % VEC == 0 all chunks are VEC wide; otherwise the two edge
+    // chunks are HS wide (8-byte copies) and the interior ones VEC wide.
+    constexpr bool EDGE = HS % VEC != 0;
+    constexpr int CPR = EDGE ? TS / VEC + 2 : BS / VEC;
+    for (int pos = tid; pos < BQ * CPR; pos += L::NTH) {
       const int r = pos / CPR, ch = pos - r * CPR;
       int gq = q0 + r - H;
       gq += gq < 0 ? nt : (gq >= nt ? -nt : 0);
-      int gs = s0 - HS + ch * VEC;
+      int col, width;
+      if (EDGE) {
+        col = ch == 0 ? 0 : (ch == CPR - 1 ? HS + TS : HS + (ch - 1) * VEC);
+        width = (ch == 0 || ch == CPR - 1) ? HS : VEC;
+      } else {
+        col = ch * VEC;
+        width = VEC;
+      }
+      int gs = s0 - HS + col;
       gs += gs < 0 ? ns : (gs >= ns ? -ns : 0);
       const T* src = a.fin + (int64_t)gq * ns + gs;
-      T* dst = sf + r * BS + ch * VEC;
+      T* dst = box + r * BS + col;
+      if (width == VEC) {
 #pragma unroll
-      for (int k = 0; k < NBOX; ++k) cp_async16(dst + k * BQ * BS, src + k * stride);
-    }
-    cp_async_commit();
-    if (F0) {
-      // the tile's U^n: TQ x TS/VEC chunk positions, the arrays split between thread halves
-      constexpr int CT = TS / VEC, NPOS = TQ * CT;
-      constexpr int GROUPS = NTHREADS / NPOS > 0 ? NTHREADS / NPOS : 1;
-      constexpr int PER = (S::NST + GROUPS - 1) / GROUPS;
-      for (int t = tid; t < NPOS * GROUPS; t += NTHREADS) {
-        const int pos = t % NPOS, grp = t / NPOS;
-        const int r = pos / CT, ch = pos - r * CT;
-        const int gq = q0 + r, gs = s0 + ch * VEC;
-        if (gq < nt && gs < ns) {
-          const T* src = a.f0 + (int64_t)gq * ns + gs;
-          T* dst = su0 + r * TS + ch * VEC;
-          const int k0 = grp * PER, k1 = k0 + PER < S::NST ? k0 + PER : S::NST;
-#pragma unroll 4
-          for (int k = k0; k < k1; ++k) cp_async16(dst + k * TQ * TS, src + k * stride);
-        }
+        for (int k = 0; k < L::NST; ++k) cp_async16(dst + k * BQ * BS, src + k * stride);
+      } else {
+#pragma unroll
+        for (int k = 0; k < L::NST; ++k) cp_async_small<8>(dst + k * BQ * BS, src + k * stride);
       }
     }
   } else {
-    for (int idx = tid; idx < NBOX * BQ * BS; idx += NTHREADS) {
+    for (int idx = tid; idx < L::NST * BQ * BS; idx += L::NTH) {
       const int k = idx / (BQ * BS);
       const int rem = idx - k * (BQ * BS);
       const int r = rem / BS, c = rem - r * BS;
       const int gq = wrap(q0 + r - H, nt), gs = wrap(s0 + c - HS, ns);
-      cp_async_scalar<sizeof(T)>(sf + (k * BQ + r) * BS + c, a.fin + k * stride + (int64_t)gq * ns + gs);
-    }
-    cp_async_commit();
-    if (F0) {
-      for (int idx = tid; idx < S::NST * TQ * TS; idx += NTHREADS) {
-        const int k = idx / (TQ * TS);
-        const int rem = idx - k * (TQ * TS);
-        const int r = rem / TS, c = rem - r * TS;
-        const int gq = q0 + r, gs = s0 + c;
-        if (gq < nt && gs < ns)
-          cp_async_scalar<sizeof(T)>(su0 + (k * TQ + r) * TS + c, a.f0 + k * stride + (int64_t)gq * ns + gs);
-      }
+      cp_async_small<sizeof(T)>(box + (k * BQ + r) * BS + c, a.fin + k * stride + (int64_t)gq * ns + gs);
     }
   }
-  T* sco = sm + S::CO_OFF;
-  for (int idx = tid; idx < NCT * BQ; idx += NTHREADS) {
+  for (int idx = tid; idx < NCT * BQ; idx += L::NTH) {
     const int k = idx / BQ, r = idx - k * BQ;
-    sco[idx] = __ldg(a.coef + (int64_t)k * nt + wrap(q0 + r - H, nt));
+    cp_async_small<sizeof(T)>(co + idx, a.coef + (int64_t)k * nt + wrap(q0 + r - H, nt));
   }
-  cp_async_commit();  // second group: U^n (empty in the first stage)
 }
 
+template <typename L, typename T>
+__device__ __forceinline__ void issue_u0(const StageArgs<T>& a, T* su0, int q0, int s0, int tid) {
+  constexpr int TQ = L::TQ, VEC = 16 / sizeof(T);
+  const int nt = a.nt, ns = a.ns;
+  const int64_t stride = a.stride;
+  if (chunked<L>(nt, ns)) {
+    // TQ x TS/VEC chunk positions; the arrays are split between groups of threads
+    constexpr int CT = TS / VEC, NPOS = TQ * CT;
+    constexpr int GROUPS = L::NTH / NPOS > 0 ? L::NTH / NPOS : 1;
+    constexpr int PER = (L::NST + GROUPS - 1) / GROUPS;
+    for (int t = tid; t < NPOS * GROUPS; t += L::NTH) {
+      const int pos = t % NPOS, grp = t / NPOS;
+      const int r = pos / CT, ch = pos - r * CT;
+      const int gq = q0 + r, gs = s0 + ch * VEC;
+      if (gq < nt && gs < ns) {
+        const T* src = a.f0 + (int64_t)gq * ns + gs;
+        T* dst = su0 + r * TS + ch * VEC;
+        const int k0 = grp * PER, k1 = k0 + PER < L::NST ? k0 + PER : L::NST;
+#pragma unroll 4
+        for (int k = k0; k < k1; ++k) cp_async16(dst + k * TQ * TS, src + k * stride);
+      }
+    }
+  } else {
+    for (int idx = tid; idx < L::NST * TQ * TS; idx += L::NTH) {
+      const int k = idx / (TQ * TS);
+      const int rem = idx - k * (TQ * TS);
+      const int r = rem / TS, c = rem - r * TS;
+      const int gq = q0 + r, gs = s0 + c;
+      if (gq < nt && gs < ns)
+        cp_async_small<sizeof(T)>(su0 + (k * TQ + r) * TS + c, a.f0 + k * stride + (int64_t)gq * ns + gs);
+    }
+  }
+}
 
 // ---------------------------------------------------------------------------------------------
-// Packed FP32 pairs: two horizontally adjacent nodes share one thread, one float2 lane each, so
+// Step 2: moments (Sec. 2.3) and mu (Eq. mu) on the tile plus a halo of 1 (cross-shaped).
+// Moment-box position (mr, mc) is tile node (mr - 1, mc - 2).
+// ---------------------------------------------------------------------------------------------
+template <typename L, typename T>
+__device__ __forceinline__ void phase2(const StageArgs<T>& a, const VConst<T>& vc, const T* box, const T* co,
+                                       T* sm, int tid) {
+  constexpr int H = L::H, BQ = L::BQ, BS = L::BS, HS = L::HS, MQ = L::MQ, MS = L::MS, TQ = L::TQ;
+  const T* sf = box;
+  const T* sphi = box + NPOP * BQ * BS;
+  const T* sphl = box + (NPOP + 1) * BQ * BS;
+  T* sn = sm + L::N_OFF;
+  T* sut = sm + L::UT_OFF;
+  T* sup = sm + L::UP_OFF;
+  T* smu = sm + L::MU_OFF;
+  constexpr int MS2 = TS + 2;  // tile columns -1 .. TS in the rows of the tile
+  constexpr int PA = TQ * MS2;
+  constexpr int PM = PA + 2 * TS;
+  for (int idx = tid; idx < PM; idx += L::NTH) {
+    int mr, mc;
+    if (idx < PA) {
+      mr = 1 + idx / MS2;
+      mc = 1 + (idx - (mr - 1) * MS2);
+    } else {
+      const int j = idx - PA;
+      mr = (j < TS) ? 0 : MQ - 1;
+      mc = 2 + (j < TS ? j : j - TS);
+    }
+    const int bi = (mr + H - 1) * BS + (mc - 2 + HS);  // box index of this position
+    const T* fp = sf + bi;
+    T row[4] = {T(0), T(0), T(0), T(0)}, col[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const T x = fp[(4 * i + j) * BQ * BS];
+        row[i] += x;
+        col[j] += x;
+      }
+    // n = n0 + sum g (the reference part carries no momentum); v_1 = -v_4, v_2 = -v_3
+    const T dn = (row[0] + row[1]) + (row[2] + row[3]);
+    const T mt = vc.v[3] * (row[3] - row[0]) + vc.v[2] * (row[2] - row[1]);
+    const T mp = vc.v[3] * (col[3] - col[0]) + vc.v[2] * (col[2] - col[1]);
+    const int mi = mr * MS + mc;
+    const T inv_n = recip(a.n0 + dn);
+    sn[mi] = dn;
+    sut[mi] = mt * inv_n;
+    sup[mi] = mp * inv_n;
+    const T* pp = sphi + bi;
+    const int cr = mr + H - 1;
+    const T ph = pp[0];
+    // neighbour differences of phi = hi + lo: the hi differences are exact for nearby values
+    T dN = pp[BS] - ph, dS = ph - pp[-BS], dE = pp[1] - ph, dW = ph - pp[-1], lo = T(0);
+    if (L::DF) {
+      const T* pl = sphl + bi;
+      lo = pl[0];
+      dN += pl[BS] - lo;
+      dS += lo - pl[-BS];
+      dE += pl[1] - lo;
+      dW += lo - pl[-1];
+    }
+    const T lap = co[C_LT * BQ + cr] * (co[C_JP * BQ + cr] * dN - co[C_JM * BQ + cr] * dS) +
+                  co[C_LP * BQ + cr] * (dE - dW);
+    // phi (1 - phi^2) at hi + lo, to first order in lo
+    const T cubic = ph * (T(1) - ph * ph) + (T(1) - T(3) * ph * ph) * lo;
+    smu[mi] = -a.A * cubic - a.kappa * lap;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Step 3, scalar: right-hand sides and the Runge-Kutta combination for node (lr, lc) of the tile.
+// ---------------------------------------------------------------------------------------------
+template <typename L, typename T, int ADV, int CH, bool F0>
+__device__ __forceinline__ void phase3_node(const StageArgs<T>& a, const VConst<T>& vc, const T* box, const T* co,
+                                            const T* sm, int lr, int lc, int q, int s) {
+  constexpr bool DF = L::DF;
+  constexpr int H = L::H, BQ = L::BQ, BS = L::BS, HS = L::HS, MS = L::MS, TQ = L::TQ;
+  const T* sf = box;
+  const T* sphi = box + NPOP * BQ * BS;
+  const T* sphl = box + (NPOP + 1) * BQ * BS;
+  const T* su0 = sm + L::U0_OFF;
+  const T* sn = sm + L::N_OFF;
+  const T* sut = sm + L::UT_OFF;
+  const T* sup = sm + L::UP_OFF;
+  const T* smu = sm + L::MU_OFF;
+  const int64_t stride = a.stride;
+  const T sixth = T(1) / T(6);
+  const int fr = lr + H, fc = lc + HS;
+  const int bi = fr * BS + fc;
+  const int mi = (lr + 1) * MS + (lc + 2);
+  const int ui = lr * TS + lc;
+
+  const T dn = sn[mi], ut = sut[mi], up = sup[mi], ph = sphi[bi];
+  const T n = a.n0 + dn;
+  const T ct = co[C_CT * BQ + fr], cp = co[C_CP * BQ + fr], gam = co[C_GAM * BQ + fr];
+  const T mu_c = smu[mi], mu_n = smu[mi + MS], mu_s = smu[mi - MS], mu_e = smu[mi + 1], mu_w = smu[mi - 1];
+
+  // Cahn-Hilliard: M Delta mu - div(u phi) (Eq. CH), flux form with mean face values
+  T Lphi = a.M * (co[C_LT * BQ + fr] * (co[C_JP * BQ + fr] * (mu_n - mu_c) - co[C_JM * BQ + fr] * (mu_c - mu_s)) +
+                  co[C_LP * BQ + fr] * (mu_e - T(2) * mu_c + mu_w));
+  T Ft = T(0), Fp = T(0);
+  if (CH == VLB_HYDRO) {
+    const T Xn = co[C_J * BQ + fr + 1] * sut[mi + MS] * sphi[bi + BS];
+    const T Xs = co[C_J * BQ + fr - 1] * sut[mi - MS] * sphi[bi - BS];
+    const T Ye = sup[mi + 1] * sphi[bi + 1];
+    const T Yw = sup[mi - 1] * sphi[bi - 1];
+    Lphi -= T(0.5) * (ct * (Xn - Xs) + cp * (Ye - Yw));
+    // n F = -phi grad mu (Eq. pbin), central differences
+    const T pn = ph * recip(n);
+    Ft = -pn * (mu_n - mu_s) * a.gt;
+    Fp = -pn * (mu_e - mu_w) * co[C_GP * BQ + fr];
+  }
+
+  const int64_t gidx = (int64_t)q * a.ns + s;
+  {
+    const T lo = DF ? sphl[bi] : T(0);
+    T base = ph, base_lo = lo, inc = Lphi * a.dt;
+    if (F0) {
+      base = su0[NPOP * TQ * TS + ui];
+      base_lo = DF ? su0[(NPOP + 1) * TQ * TS + ui] : T(0);
+      inc = a.b * (((ph - base) + (lo - base_lo)) + inc);
+    }
+    if (DF) {
+      // (hi, lo) <- (base, base_lo) + inc with an error-free sum, then renormalised
+      const T s1 = base + inc;
+      const T bb = s1 - base;
+      const T err = (base - (s1 - bb)) + (inc - bb);
+      const T lo2 = base_lo + err;
+      const T hi_out = s1 + lo2;
+      a.fout[NPOP * stride + gidx] = hi_out;
+      a.fout[(NPOP + 1) * stride + gidx] = lo2 - (hi_out - s1);
+    } else {
+      a.fout[NPOP * stride + gidx] = base + inc;
+    }
+  }
+
+  // population deviations at the node
+  T g[NPOP];
+#pragma unroll
+  for (int k = 0; k < NPOP; ++k) g[k] = sf[k * BQ * BS + bi];
+
+  // UW3 advection weights: the theta flux difference of G = J g with ct/6 folded in, over
+  // d = -2..1 (v > 0) and d = -1..2 (v < 0); the varphi difference is scaled by cp/6.
+  const T ct6 = ct * sixth, cp6 = cp * sixth;
+  const T Jm1 = co[C_J * BQ + fr - 1], J0 = co[C_J * BQ + fr], Jp1 = co[C_J * BQ + fr + 1];
+  const T wp0 = ct6 * co[C_J * BQ + fr - 2], wp1 = T(-6) * ct6 * Jm1, wp2 = T(3) * ct6 * J0, wp3 = T(2) * ct6 * Jp1;
+  const T wn0 = T(-2) * ct6 * Jm1, wn1 = T(-3) * ct6 * J0, wn2 = T(6) * ct6 * Jp1, wn3 = -ct6 * co[C_J * BQ + fr + 2];
+
+  const T usq = ut * ut + up * up;
+  const T c0 = T(1) - T(0.5) * usq;
+  const T hu = T(-0.5) * usq;
+  const T ntau = n * a.inv_tau, dntau = dn * a.inv_tau;
+  const T Ep = co[C_EP * BQ + fr], En = co[C_EN * BQ + fr];
+
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    // varphi-derivative operands h_m = (-F^phi - Gamma v_i v_m) g_{i m}; K~ = K diag(v) (Sec. 2.3)
+    const T gvi = gam * vc.v[i];
+    T h[4];
+#pragma unroll
+    for (int mm = 0; mm < 4; ++mm) h[mm] = (-Fp - gvi * vc.v[mm]) * g[4 * i + mm];
+    const T ai = vc.v[i] * ut;
+    // The BGK relaxation and the closed-form reference part share the factor w_i w_j:
+    //   (f^eq - n0 w w)/tau + n0 w w [v_i (E(q) + F^theta) + v_j F^phi]
+    //   = w_i w_j [ (dn + n (poly - 1))/tau + n0 v_i (E + F^theta) + n0 v_j F^phi ]
+    const T ci = dntau + a.n0 * vc.v[i] * ((i >= 2 ? Ep : En) + Ft);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = 4 * i + j;
+      const T* fk = sf + k * BQ * BS + bi;
+      T rhs;
+      if (ADV == VLB_UW3) {
+        const T Dt = (i >= 2) ? wp0 * fk[-2 * BS] + wp1 * fk[-BS] + wp2 * g[k] + wp3 * fk[BS]
+                              : wn0 * fk[-BS] + wn1 * g[k] + wn2 * fk[BS] + wn3 * fk[2 * BS];
+        const T Dp = (j >= 2) ? (fk[-2] - T(6) * fk[-1] + T(3) * g[k] + T(2) * fk[1])
+                              : (T(-2) * fk[-1] - T(3) * g[k] + T(6) * fk[1] - fk[2]);
+        rhs = -(vc.v[i] * Dt) - (vc.v[j] * cp6) * Dp;
+      } else {
+        // WENO5 is nonlinear: theta reconstruction of the full G = J (g + n0 w_i w_j); along
+        // varphi the reference part is a constant, which the reconstruction passes through.
+        const T fref = a.n0 * vc.ww[i][j];
+        T xt[7], xp[7];
+#pragma unroll
+        for (int d = 0; d < 7; ++d) {
+          xt[d] = co[C_J * BQ + fr + d - 3] * (fk[(d - 3) * BS] + fref);
+          xp[d] = fk[d - 3];
+        }
+        const T Dt = (i >= 2) ? weno_diff<T, true>(xt) : weno_diff<T, false>(xt);
+        const T Dp = (j >= 2) ? weno_diff<T, true>(xp) : weno_diff<T, false>(xp);
+        rhs = -(vc.v[i] * ct) * Dt - (vc.v[j] * cp) * Dp;
+      }
+      // force and inertial terms on the deviation: (Gamma v_j^2 - F^theta) dg/dv_theta + sum_m K_jm h_m
+      T dvt = T(0), dvp = T(0);
+#pragma unroll
+      for (int mm = 0; mm < 4; ++mm) {
+        dvt += vc.K[i][mm] * g[4 * mm + j];
+        dvp += vc.K[j][mm] * h[mm];
+      }
+      rhs += (gam * vc.v[j] * vc.v[j] - Ft) * dvt + dvp;
+      // BGK towards the third-order Hermite equilibrium (Eq. feq) plus the reference part
+      const T xi = ai + vc.v[j] * up;
+      const T pm1 = xi * (c0 + xi * (T(0.5) + xi * sixth)) + hu;
+      const T X = ntau * pm1 + (ci + a.n0 * vc.v[j] * Fp);
+      rhs += vc.ww[i][j] * X - a.inv_tau * g[k];
+      T o;
+      if (F0) {
+        const T g0 = su0[k * TQ * TS + ui];
+        o = g0 + a.b * ((g[k] - g0) + rhs * a.dt);
+      } else {
+        o = rhs * a.dt + g[k];
+      }
+      a.fout[k * stride + gidx] = o;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Step 3, packed FP32 pairs: two horizontally adjacent nodes per thread, one float2 lane each, so
 // the per-population arithmetic issues as FFMA2/FADD2/FMUL2 and shared/global accesses are 8 bytes.
+// Same arithmetic as phase3_node, lane by lane.
 // ---------------------------------------------------------------------------------------------
 __device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
@@ -209,37 +457,31 @@ __device__ __forceinline__ void df_add(float base, float base_lo, float inc, flo
   lo = lo2 - (hi - s1);
 }
 
-// Phase 3 of the FP32 UW3 stage for the node pair (lr, lc), (lr, lc + 1) of the tile; the same
-// arithmetic as the scalar path, lane by lane.
-template <int CH, bool F0>
-__device__ __forceinline__ void phase3_pair(const StageArgs<float>& a, const VConst<float>& vc, float* sm, int tid,
-                                            int q0, int s0) {
-  using S = Smem<float, VLB_UW3>;
-  constexpr int H = S::H, BQ = S::BQ, BS = S::BS, MS = S::MS;
-  const float* sf = sm + S::F_OFF;
-  const float* sphi = sm + S::PHI_OFF;
-  const float* sphl = sm + S::PHL_OFF;
-  const float* su0 = sm + S::U0_OFF;
-  const float* sn = sm + S::N_OFF;
-  const float* sut = sm + S::UT_OFF;
-  const float* sup = sm + S::UP_OFF;
-  const float* smu = sm + S::MU_OFF;
-  const float* sco = sm + S::CO_OFF;
-  const int lr = tid / (TS / 2), lc = 2 * (tid % (TS / 2));
-  const int q = q0 + lr, s = s0 + lc;
-  if (q >= a.nt || s >= a.ns) return;  // n_phi is even here, so s + 1 < n_phi as well
+template <typename L, int CH, bool F0>
+__device__ __forceinline__ void phase3_pair(const StageArgs<float>& a, const VConst<float>& vc, const float* box,
+                                            const float* co, const float* sm, int lr, int lc, int q, int s) {
+  constexpr int H = L::H, BQ = L::BQ, BS = L::BS, HS = L::HS, MS = L::MS, TQ = L::TQ;
+  static_assert(HS % 2 == 0 && BS % 2 == 0 && MS % 2 == 0, "pair alignment");
+  const float* sf = box;
+  const float* sphi = box + NPOP * BQ * BS;
+  const float* sphl = box + (NPOP + 1) * BQ * BS;
+  const float* su0 = sm + L::U0_OFF;
+  const float* sn = sm + L::N_OFF;
+  const float* sut = sm + L::UT_OFF;
+  const float* sup = sm + L::UP_OFF;
+  const float* smu = sm + L::MU_OFF;
   const int64_t stride = a.stride;
   const int fr = lr + H;
-  const int bi = fr * BS + lc + HS;      // even: 8-byte aligned pairs
+  const int bi = fr * BS + lc + HS;       // even: 8-byte aligned pairs
   const int mi = (lr + 1) * MS + lc + 2;  // even
   const int ui = lr * TS + lc;
   const float sixth = 1.0f / 6.0f;
 
   const float2 dn = ld2(sn + mi), ut = ld2(sut + mi), up = ld2(sup + mi), ph = ld2(sphi + bi);
   const float2 n = add2(dn, f2(a.n0));
-  const float ct = sco[C_CT * BQ + fr], cp = sco[C_CP * BQ + fr], gam = sco[C_GAM * BQ + fr];
-  const float lt = sco[C_LT * BQ + fr], lp = sco[C_LP * BQ + fr];
-  const float Jp = sco[C_JP * BQ + fr], Jm = sco[C_JM * BQ + fr];
+  const float ct = co[C_CT * BQ + fr], cp = co[C_CP * BQ + fr], gam = co[C_GAM * BQ + fr];
+  const float lt = co[C_LT * BQ + fr], lp = co[C_LP * BQ + fr];
+  const float Jp = co[C_JP * BQ + fr], Jm = co[C_JM * BQ + fr];
   const float2 muC = ld2(smu + mi), muN = ld2(smu + mi + MS), muS = ld2(smu + mi - MS);
   const float2 muL = ld2(smu + mi - 2), muR = ld2(smu + mi + 2);
   const float2 muE = make_float2(muC.y, muR.x), muW = make_float2(muL.y, muC.x);
@@ -250,17 +492,17 @@ __device__ __forceinline__ void phase3_pair(const StageArgs<float>& a, const VCo
   float2 Lphi = mul2(f2(a.M), lapmu);
   float2 Ft = f2(0.0f), Fp = f2(0.0f);
   if (CH == VLB_HYDRO) {
-    const float2 Xn = mul2(f2(sco[C_J * BQ + fr + 1]), mul2(ld2(sut + mi + MS), ld2(sphi + bi + BS)));
-    const float2 Xs = mul2(f2(sco[C_J * BQ + fr - 1]), mul2(ld2(sut + mi - MS), ld2(sphi + bi - BS)));
+    const float2 Xn = mul2(f2(co[C_J * BQ + fr + 1]), mul2(ld2(sut + mi + MS), ld2(sphi + bi + BS)));
+    const float2 Xs = mul2(f2(co[C_J * BQ + fr - 1]), mul2(ld2(sut + mi - MS), ld2(sphi + bi - BS)));
     const float2 upL = ld2(sup + mi - 2), upR = ld2(sup + mi + 2);
     const float2 phL = ld2(sphi + bi - 2), phR = ld2(sphi + bi + 2);
     const float2 Ye = mul2(make_float2(up.y, upR.x), make_float2(ph.y, phR.x));
     const float2 Yw = mul2(make_float2(upL.y, up.x), make_float2(phL.y, ph.x));
     Lphi = sub2(Lphi, mul2(f2(0.5f), fma2(f2(ct), sub2(Xn, Xs), mul2(f2(cp), sub2(Ye, Yw)))));
     // n F = -phi grad mu (Eq. pbin), central differences
-    const float2 pn = make_float2(ph.x * __frcp_rn(n.x), ph.y * __frcp_rn(n.y));
-    Ft = mul2(mul2(make_float2(-pn.x, -pn.y), sub2(muN, muS)), f2(a.gt));
-    Fp = mul2(mul2(make_float2(-pn.x, -pn.y), sub2(muE, muW)), f2(sco[C_GP * BQ + fr]));
+    const float2 mpn = make_float2(-ph.x * __frcp_rn(n.x), -ph.y * __frcp_rn(n.y));
+    Ft = mul2(mul2(mpn, sub2(muN, muS)), f2(a.gt));
+    Fp = mul2(mul2(mpn, sub2(muE, muW)), f2(co[C_GP * BQ + fr]));
   }
 
   const int64_t gidx = (int64_t)q * a.ns + s;  // even
@@ -285,17 +527,15 @@ __device__ __forceinline__ void phase3_pair(const StageArgs<float>& a, const VCo
 
   // UW3 theta weights with ct/6 folded in (same row for both lanes)
   const float ct6 = ct * sixth, cp6 = cp * sixth;
-  const float Jm1 = sco[C_J * BQ + fr - 1], J0 = sco[C_J * BQ + fr], Jp1 = sco[C_J * BQ + fr + 1];
-  const float wp0 = ct6 * sco[C_J * BQ + fr - 2], wp1 = -6.0f * ct6 * Jm1, wp2 = 3.0f * ct6 * J0,
-              wp3 = 2.0f * ct6 * Jp1;
-  const float wn0 = -2.0f * ct6 * Jm1, wn1 = -3.0f * ct6 * J0, wn2 = 6.0f * ct6 * Jp1,
-              wn3 = -ct6 * sco[C_J * BQ + fr + 2];
+  const float Jm1 = co[C_J * BQ + fr - 1], J0 = co[C_J * BQ + fr], Jp1 = co[C_J * BQ + fr + 1];
+  const float wp0 = ct6 * co[C_J * BQ + fr - 2], wp1 = -6.0f * ct6 * Jm1, wp2 = 3.0f * ct6 * J0, wp3 = 2.0f * ct6 * Jp1;
+  const float wn0 = -2.0f * ct6 * Jm1, wn1 = -3.0f * ct6 * J0, wn2 = 6.0f * ct6 * Jp1, wn3 = -ct6 * co[C_J * BQ + fr + 2];
 
   const float2 usq = fma2(ut, ut, mul2(up, up));
   const float2 hu = mul2(f2(-0.5f), usq);
   const float2 c0 = add2(f2(1.0f), hu);
   const float2 ntau = mul2(n, f2(a.inv_tau)), dntau = mul2(dn, f2(a.inv_tau));
-  const float Ep = sco[C_EP * BQ + fr], En = sco[C_EN * BQ + fr];
+  const float Ep = co[C_EP * BQ + fr], En = co[C_EN * BQ + fr];
   float2 cj[4], nFp[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
@@ -355,234 +595,88 @@ __device__ __forceinline__ void phase3_pair(const StageArgs<float>& a, const VCo
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Kernels
+// ---------------------------------------------------------------------------------------------
+
+// Generic: one CTA per 16 x 32 tile, two nodes per thread (rows lr and lr + 8).
 // F0: the stage combines with U^n (stages 2 and 3); the first stage writes U_in + dt L(U_in).
-// PAIR: FP32 UW3 with n_phi % 4 == 0 -- phase 3 runs on packed node pairs.
-template <typename T, int ADV, int CH, bool F0, bool PAIR>
-__global__ void __launch_bounds__(NTHREADS, sizeof(T) == 4 ? 2 : 1) stage_kernel(StageArgs<T> a, VConst<T> vc) {
-  using S = Smem<T, ADV>;
-  constexpr bool DF = S::DF;
-  constexpr int H = S::H, BQ = S::BQ, BS = S::BS, MQ = S::MQ, MS = S::MS;
+template <typename T, int ADV, int CH, bool F0>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) stage_kernel(StageArgs<T> a, VConst<T> vc) {
+  using L = GenericLay<T, ADV>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
-  T* sf = sm + S::F_OFF;
-  T* sphi = sm + S::PHI_OFF;
-  T* sphl = sm + S::PHL_OFF;
-  T* su0 = sm + S::U0_OFF;
-  T* sn = sm + S::N_OFF;
-  T* sut = sm + S::UT_OFF;
-  T* sup = sm + S::UP_OFF;
-  T* smu = sm + S::MU_OFF;
-  T* sco = sm + S::CO_OFF;
-
-  const int nt = a.nt, ns = a.ns;
-  const int64_t stride = a.stride;
+  T* box = sm + L::BOX_OFF;
+  T* co = sm + L::CO_OFF;
   const int tid = threadIdx.x;
-  const int s0 = blockIdx.x * TS, q0 = blockIdx.y * TQ;
-
-  stage_loads<T, ADV, F0>(a, sm, tid, q0, s0);
-  cp_async_wait<1>();  // the box; the U^n group may still be in flight
+  const int s0 = blockIdx.x * TS, q0 = blockIdx.y * L::TQ;
+  issue_box<L>(a, box, co, q0, s0, tid);
+  cp_async_commit();
+  if (F0) issue_u0<L>(a, sm + L::U0_OFF, q0, s0, tid);
+  cp_async_commit();
+  cp_async_wait<1>();  // the box; U^n may still be in flight
   __syncthreads();
-
-  // ---- phase 2: moments (Sec. 2.3) and mu (Eq. mu) on the tile plus a halo of 1 (cross) ----
-  {
-    constexpr int MS2 = TS + 2;  // tile columns -1 .. TS in the rows of the tile
-    constexpr int PA = TQ * MS2;
-    constexpr int PM = PA + 2 * TS;
-    for (int idx = tid; idx < PM; idx += NTHREADS) {
-      // moment-box position (mr, mc) is tile node (mr - 1, mc - 2)
-      int mr, mc;
-      if (idx < PA) {
-        mr = 1 + idx / MS2;
-        mc = 1 + (idx - (mr - 1) * MS2);
-      } else {
-        const int j = idx - PA;
-        mr = (j < TS) ? 0 : MQ - 1;
-        mc = 2 + (j < TS ? j : j - TS);
-      }
-      const int bi = (mr + H - 1) * BS + (mc - 2 + HS);  // box index of this position
-      const T* fp = sf + bi;
-      T row[4] = {T(0), T(0), T(0), T(0)}, col[4] = {T(0), T(0), T(0), T(0)};
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const T x = fp[(4 * i + j) * BQ * BS];
-          row[i] += x;
-          col[j] += x;
-        }
-      // n = n0 + sum g (the reference part carries no momentum); v_1 = -v_4, v_2 = -v_3
-      const T dn = (row[0] + row[1]) + (row[2] + row[3]);
-      const T mt = vc.v[3] * (row[3] - row[0]) + vc.v[2] * (row[2] - row[1]);
-      const T mp = vc.v[3] * (col[3] - col[0]) + vc.v[2] * (col[2] - col[1]);
-      const int mi = mr * MS + mc;
-      const T inv_n = recip(a.n0 + dn);
-      sn[mi] = dn;
-      sut[mi] = mt * inv_n;
-      sup[mi] = mp * inv_n;
-      const T* pp = sphi + bi;
-      const int cr = mr + H - 1;
-      const T ph = pp[0];
-      // neighbour differences of phi = hi + lo: the hi differences are exact for nearby values
-      T dN = pp[BS] - ph, dS = ph - pp[-BS], dE = pp[1] - ph, dW = ph - pp[-1], lo = T(0);
-      if (DF) {
-        const T* pl = sphl + bi;
-        lo = pl[0];
-        dN += pl[BS] - lo;
-        dS += lo - pl[-BS];
-        dE += pl[1] - lo;
-        dW += lo - pl[-1];
-      }
-      const T lap = sco[C_LT * BQ + cr] * (sco[C_JP * BQ + cr] * dN - sco[C_JM * BQ + cr] * dS) +
-                    sco[C_LP * BQ + cr] * (dE - dW);
-      // phi (1 - phi^2) at hi + lo, to first order in lo
-      const T cubic = ph * (T(1) - ph * ph) + (T(1) - T(3) * ph * ph) * lo;
-      smu[mi] = -a.A * cubic - a.kappa * lap;
-    }
-  }
+  phase2<L>(a, vc, box, co, sm, tid);
   cp_async_wait<0>();
   __syncthreads();
-
-  // ---- phase 3: right-hand sides and the Runge-Kutta combination, per node ----
-  if constexpr (PAIR) {
-    phase3_pair<CH, F0>(a, vc, sm, tid, q0, s0);
-    return;
-  }
-  const T sixth = T(1) / T(6);
 #pragma unroll 1
-  for (int m = 0; m < NQ; ++m) {
-    const int lr = tid / TS + TYT * m, lc = tid % TS;
+  for (int m = 0; m < 2; ++m) {
+    const int lr = tid / TS + 8 * m, lc = tid % TS;
     const int q = q0 + lr, s = s0 + lc;
-    if (q >= nt || s >= ns) continue;
-    const int fr = lr + H, fc = lc + HS;
-    const int bi = fr * BS + fc;
-    const int mi = (lr + 1) * MS + (lc + 2);
-    const int ui = lr * TS + lc;
-
-    const T dn = sn[mi], ut = sut[mi], up = sup[mi], ph = sphi[bi];
-    const T n = a.n0 + dn;
-    const T ct = sco[C_CT * BQ + fr], cp = sco[C_CP * BQ + fr], gam = sco[C_GAM * BQ + fr];
-    const T mu_c = smu[mi], mu_n = smu[mi + MS], mu_s = smu[mi - MS], mu_e = smu[mi + 1], mu_w = smu[mi - 1];
-
-    // Cahn-Hilliard: M Delta mu - div(u phi) (Eq. CH), flux form with mean face values
-    T Lphi = a.M * (sco[C_LT * BQ + fr] * (sco[C_JP * BQ + fr] * (mu_n - mu_c) - sco[C_JM * BQ + fr] * (mu_c - mu_s)) +
-                    sco[C_LP * BQ + fr] * (mu_e - T(2) * mu_c + mu_w));
-    T Ft = T(0), Fp = T(0);
-    if (CH == VLB_HYDRO) {
-      const T Xn = sco[C_J * BQ + fr + 1] * sut[mi + MS] * sphi[bi + BS];
-      const T Xs = sco[C_J * BQ + fr - 1] * sut[mi - MS] * sphi[bi - BS];
-      const T Ye = sup[mi + 1] * sphi[bi + 1];
-      const T Yw = sup[mi - 1] * sphi[bi - 1];
-      Lphi -= T(0.5) * (ct * (Xn - Xs) + cp * (Ye - Yw));
-      // n F = -phi grad mu (Eq. pbin), central differences
-      const T pn = ph * recip(n);
-      Ft = -pn * (mu_n - mu_s) * a.gt;
-      Fp = -pn * (mu_e - mu_w) * sco[C_GP * BQ + fr];
-    }
-
-    const int64_t gidx = (int64_t)q * ns + s;
-    {
-      const T lo = DF ? sphl[bi] : T(0);
-      T base = ph, base_lo = lo, inc = Lphi * a.dt;
-      if (F0) {
-        base = su0[NPOP * TQ * TS + ui];
-        base_lo = DF ? su0[(NPOP + 1) * TQ * TS + ui] : T(0);
-        inc = a.b * (((ph - base) + (lo - base_lo)) + inc);
-      }
-      if (DF) {
-        // (hi, lo) <- (base, base_lo) + inc with an error-free sum, then renormalised
-        const T s1 = base + inc;
-        const T bb = s1 - base;
-        const T err = (base - (s1 - bb)) + (inc - bb);
-        const T lo2 = base_lo + err;
-        const T hi_out = s1 + lo2;
-        a.fout[NPOP * stride + gidx] = hi_out;
-        a.fout[(NPOP + 1) * stride + gidx] = lo2 - (hi_out - s1);
-      } else {
-        a.fout[NPOP * stride + gidx] = base + inc;
-      }
-    }
-
-    // population deviations at the node
-    T g[NPOP];
-#pragma unroll
-    for (int k = 0; k < NPOP; ++k) g[k] = sf[k * BQ * BS + bi];
-
-    // UW3 advection weights: the theta flux difference of G = J g with ct/6 folded in, over
-    // d = -2..1 (v > 0) and d = -1..2 (v < 0); the varphi difference is scaled by cp/6.
-    const T ct6 = ct * sixth, cp6 = cp * sixth;
-    const T Jm1 = sco[C_J * BQ + fr - 1], J0 = sco[C_J * BQ + fr], Jp1 = sco[C_J * BQ + fr + 1];
-    const T wp0 = ct6 * sco[C_J * BQ + fr - 2], wp1 = T(-6) * ct6 * Jm1, wp2 = T(3) * ct6 * J0,
-            wp3 = T(2) * ct6 * Jp1;
-    const T wn0 = T(-2) * ct6 * Jm1, wn1 = T(-3) * ct6 * J0, wn2 = T(6) * ct6 * Jp1,
-            wn3 = -ct6 * sco[C_J * BQ + fr + 2];
-
-    const T usq = ut * ut + up * up;
-    const T c0 = T(1) - T(0.5) * usq;
-    const T hu = T(-0.5) * usq;
-    const T ntau = n * a.inv_tau, dntau = dn * a.inv_tau;
-    const T Ep = sco[C_EP * BQ + fr], En = sco[C_EN * BQ + fr];
-
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      // varphi-derivative operands h_m = (-F^phi - Gamma v_i v_m) g_{i m}; K~ = K diag(v) (Sec. 2.3)
-      const T gvi = gam * vc.v[i];
-      T h[4];
-#pragma unroll
-      for (int mm = 0; mm < 4; ++mm) h[mm] = (-Fp - gvi * vc.v[mm]) * g[4 * i + mm];
-      const T ai = vc.v[i] * ut;
-      // The BGK relaxation and the closed-form reference part share the factor w_i w_j:
-      //   (f^eq - n0 w w)/tau + n0 w w [v_i (E(q) + F^theta) + v_j F^phi]
-      //   = w_i w_j [ (dn + n (poly - 1))/tau + n0 v_i (E + F^theta) + n0 v_j F^phi ]
-      const T ci = dntau + a.n0 * vc.v[i] * ((i >= 2 ? Ep : En) + Ft);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int k = 4 * i + j;
-        const T* fk = sf + k * BQ * BS + bi;
-        T rhs;
-        if (ADV == VLB_UW3) {
-          const T Dt = (i >= 2) ? wp0 * fk[-2 * BS] + wp1 * fk[-BS] + wp2 * g[k] + wp3 * fk[BS]
-                                : wn0 * fk[-BS] + wn1 * g[k] + wn2 * fk[BS] + wn3 * fk[2 * BS];
-          const T Dp = (j >= 2) ? (fk[-2] - T(6) * fk[-1] + T(3) * g[k] + T(2) * fk[1])
-                                : (T(-2) * fk[-1] - T(3) * g[k] + T(6) * fk[1] - fk[2]);
-          rhs = -(vc.v[i] * Dt) - (vc.v[j] * cp6) * Dp;
-        } else {
-          // WENO5 is nonlinear: theta reconstruction of the full G = J (g + n0 w_i w_j); along
-          // varphi the reference part is a constant, which the reconstruction passes through.
-          const T fref = a.n0 * vc.ww[i][j];
-          T xt[7], xp[7];
-#pragma unroll
-          for (int d = 0; d < 7; ++d) {
-            xt[d] = sco[C_J * BQ + fr + d - 3] * (fk[(d - 3) * BS] + fref);
-            xp[d] = fk[d - 3];
-          }
-          const T Dt = (i >= 2) ? weno_diff<T, true>(xt) : weno_diff<T, false>(xt);
-          const T Dp = (j >= 2) ? weno_diff<T, true>(xp) : weno_diff<T, false>(xp);
-          rhs = -(vc.v[i] * ct) * Dt - (vc.v[j] * cp) * Dp;
-        }
-        // force and inertial terms on the deviation: (Gamma v_j^2 - F^theta) dg/dv_theta + sum_m K_jm h_m
-        T dvt = T(0), dvp = T(0);
-#pragma unroll
-        for (int mm = 0; mm < 4; ++mm) {
-          dvt += vc.K[i][mm] * g[4 * mm + j];
-          dvp += vc.K[j][mm] * h[mm];
-        }
-        rhs += (gam * vc.v[j] * vc.v[j] - Ft) * dvt + dvp;
-        // BGK towards the third-order Hermite equilibrium (Eq. feq) plus the reference part
-        const T xi = ai + vc.v[j] * up;
-        const T pm1 = xi * (c0 + xi * (T(0.5) + xi * sixth)) + hu;
-        const T X = ntau * pm1 + (ci + a.n0 * vc.v[j] * Fp);
-        rhs += vc.ww[i][j] * X - a.inv_tau * g[k];
-        T o;
-        if (F0) {
-          const T g0 = su0[k * TQ * TS + ui];
-          o = g0 + a.b * ((g[k] - g0) + rhs * a.dt);
-        } else {
-          o = rhs * a.dt + g[k];
-        }
-        a.fout[k * stride + gidx] = o;
-      }
-    }
+    if (q < a.nt && s < a.ns) phase3_node<L, T, ADV, CH, F0>(a, vc, box, co, sm, lr, lc, q, s);
   }
+}
+
+// Persistent FP32 UW3 kernel: one CTA per SM walks over the tiles t = blockIdx.x, + gridDim.x, ...
+// While tile t computes, the box of tile t + gridDim.x streams into the other buffer and, after
+// tile t's step 3, its U^n into the U^n buffer.  cp.async groups are committed in the order
+// box(t0), U0(t0), box(t1), U0(t1), ..., so "wait until one group is pending" always waits for
+// exactly the buffer that is needed next.
+template <int CH, bool F0>
+__global__ void __launch_bounds__(384, 1) stage_persistent(StageArgs<float> a, VConst<float> vc, int ntiles,
+                                                           int tiles_s) {
+  using L = PersistLay;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* sm = reinterpret_cast<float*>(smem_raw);
+  const int tid = threadIdx.x;
+  int t = blockIdx.x;
+  if (t >= ntiles) return;
+  {
+    const int q0 = (t / tiles_s) * L::TQ, s0 = (t % tiles_s) * TS;
+    issue_box<L>(a, sm + L::BOX_OFF, sm + L::CO_OFF, q0, s0, tid);
+    cp_async_commit();
+    if (F0) issue_u0<L>(a, sm + L::U0_OFF, q0, s0, tid);
+    cp_async_commit();
+  }
+  for (int it = 0; t < ntiles; ++it, t += gridDim.x) {
+    const int b = it & 1;
+    const int q0 = (t / tiles_s) * L::TQ, s0 = (t % tiles_s) * TS;
+    const float* box = sm + L::BOX_OFF + b * L::BOX;
+    const float* co = sm + L::CO_OFF + b * L::CO;
+    cp_async_wait<1>();  // box(t) has landed; U0(t) may be pending
+    __syncthreads();
+    const int tn = t + gridDim.x;
+    if (tn < ntiles) {
+      const int qn = (tn / tiles_s) * L::TQ, sn0 = (tn % tiles_s) * TS;
+      issue_box<L>(a, sm + L::BOX_OFF + (b ^ 1) * L::BOX, sm + L::CO_OFF + (b ^ 1) * L::CO, qn, sn0, tid);
+    }
+    cp_async_commit();
+    phase2<L>(a, vc, box, co, sm, tid);
+    cp_async_wait<1>();  // U0(t) has landed; box(tn) may be pending
+    __syncthreads();
+    {
+      const int lr = tid / (TS / 2), lc = 2 * (tid % (TS / 2));
+      const int q = q0 + lr, s = s0 + lc;
+      if (q < a.nt && s < a.ns) phase3_pair<L, CH, F0>(a, vc, box, co, sm, lr, lc, q, s);
+    }
+    __syncthreads();  // the tile's U^n, moments and box are no longer read
+    if (F0 && tn < ntiles) {
+      const int qn = (tn / tiles_s) * L::TQ, sn0 = (tn % tiles_s) * TS;
+      issue_u0<L>(a, sm + L::U0_OFF, qn, sn0, tid);
+    }
+    cp_async_commit();
+  }
+  cp_async_wait<0>();
 }
 
 template <typename T>
@@ -600,33 +694,55 @@ VConst<T> make_vconst() {
   return c;
 }
 
-template <typename T, int ADV, int CH, bool F0, bool PAIR>
-cudaError_t launch_variant(const StageArgs<T>& a, cudaStream_t st) {
-  using S = Smem<T, ADV>;
-  static int configured_mask = 0;  // one bit per device id < 32
+// Per-device, per-kernel one-time set-up (dynamic shared memory opt-in).
+template <typename K>
+cudaError_t ensure_smem(K kernel, size_t bytes, int& mask) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev >= 32 || !(configured_mask & (1 << dev))) {
-    e = cudaFuncSetAttribute(stage_kernel<T, ADV, CH, F0, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)S::BYTES);
-    if (e != cudaSuccess) return e;
-    if (dev < 32) configured_mask |= (1 << dev);
-  }
+  if (dev < 32 && (mask & (1 << dev))) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess && dev < 32) mask |= (1 << dev);
+  return e;
+}
+
+template <typename T, int ADV, int CH, bool F0>
+cudaError_t launch_generic(const StageArgs<T>& a, cudaStream_t st) {
+  using L = GenericLay<T, ADV>;
+  static int mask = 0;
+  cudaError_t e = ensure_smem(stage_kernel<T, ADV, CH, F0>, L::BYTES, mask);
+  if (e != cudaSuccess) return e;
   static const VConst<T> vc = make_vconst<T>();
-  dim3 grid((a.ns + TS - 1) / TS, (a.nt + TQ - 1) / TQ);
-  stage_kernel<T, ADV, CH, F0, PAIR><<<grid, NTHREADS, S::BYTES, st>>>(a, vc);
+  dim3 grid((a.ns + TS - 1) / TS, (a.nt + L::TQ - 1) / L::TQ);
+  stage_kernel<T, ADV, CH, F0><<<grid, 256, L::BYTES, st>>>(a, vc);
+  return cudaGetLastError();
+}
+
+template <int CH, bool F0>
+cudaError_t launch_persistent(const StageArgs<float>& a, cudaStream_t st) {
+  using L = PersistLay;
+  static int mask = 0;
+  cudaError_t e = ensure_smem(stage_persistent<CH, F0>, L::BYTES, mask);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  static const VConst<float> vc = make_vconst<float>();
+  const int tiles_s = (a.ns + TS - 1) / TS;
+  const int ntiles = tiles_s * ((a.nt + L::TQ - 1) / L::TQ);
+  const int grid = ntiles < sms ? ntiles : sms;
+  stage_persistent<CH, F0><<<grid, L::NTH, L::BYTES, st>>>(a, vc, ntiles, tiles_s);
   return cudaGetLastError();
 }
 
 template <typename T, int ADV, int CH>
 cudaError_t launch_one(const StageArgs<T>& a, cudaStream_t st) {
-  using S = Smem<T, ADV>;
-  constexpr bool CAN_PAIR = sizeof(T) == 4 && ADV == VLB_UW3;
-  const bool pair = CAN_PAIR && a.ns % 4 == 0 && a.ns >= S::BS && a.nt >= S::BQ;
-  if (pair)
-    return a.f0 ? launch_variant<T, ADV, CH, true, CAN_PAIR>(a, st) : launch_variant<T, ADV, CH, false, CAN_PAIR>(a, st);
-  return a.f0 ? launch_variant<T, ADV, CH, true, false>(a, st) : launch_variant<T, ADV, CH, false, false>(a, st);
+  if constexpr (sizeof(T) == 4 && ADV == VLB_UW3) {
+    if (chunked<PersistLay>(a.nt, a.ns))
+      return a.f0 ? launch_persistent<CH, true>(a, st) : launch_persistent<CH, false>(a, st);
+  }
+  return a.f0 ? launch_generic<T, ADV, CH, true>(a, st) : launch_generic<T, ADV, CH, false>(a, st);
 }
 
 }  // namespace
