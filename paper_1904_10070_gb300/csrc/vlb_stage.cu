@@ -14,13 +14,13 @@
 //      U^n values and the per-row coefficients;
 //   2. computes the moments and mu on the tile plus a halo of 1;
 //   3. computes the right-hand sides and the Runge-Kutta combination and stores the tile.
-// Two kernels share these steps:
-//   - stage_persistent (FP32, UW3, n_phi % 4 == 0 -- the production path): one 384-thread CTA
-//     per SM walks over 24 x 32 tiles; the box of the next tile (double-buffered) and its U^n are
-//     copied in while the current tile computes, and step 3 runs on adjacent node pairs in packed
-//     FP32x2 arithmetic (two lanes of one float2 per thread);
-//   - stage_kernel (every other case: FP64, WENO5, odd or tiny grids): one 256-thread CTA per
-//     16 x 32 tile, scalar arithmetic, two nodes per thread.
+// One 256-thread CTA per 16 x 32 tile, two CTAs per SM.  For FP32 UW3 grids with n_phi % 4 == 0 (the
+// production path) step 3 runs on adjacent node pairs in packed FP32x2 arithmetic, two lanes of
+// one float2 per thread; every other case (FP64, WENO5, odd or tiny grids) runs step 3 in scalar
+// arithmetic, two nodes per thread.  A persistent double-buffered variant (next tile copied in
+// while the current one computes, one 384-thread CTA per SM) measured 1.6x slower on GB300: with
+// 12 warps per SM and all warps issuing copies and shared loads in the same phase, the memory-
+// input queue throttled issue to 30%.
 // Periodic wrap-around is resolved on the copy addresses, so ragged tiles need no special case.
 #include "vlb_internal.cuh"
 
@@ -68,7 +68,6 @@ struct Lay {
 
 template <typename T, int ADV>
 using GenericLay = Lay<T, (ADV == VLB_UW3 ? 2 : 3), 16, 4, 256, 1>;
-using PersistLay = Lay<float, 2, 24, 2, 384, 2>;
 
 __device__ __forceinline__ int wrap(int x, int n) {
   x %= n;
@@ -599,9 +598,11 @@ __device__ __forceinline__ void phase3_pair(const StageArgs<float>& a, const VCo
 // Kernels
 // ---------------------------------------------------------------------------------------------
 
-// Generic: one CTA per 16 x 32 tile, two nodes per thread (rows lr and lr + 8).
+// One CTA per 16 x 32 tile.
 // F0: the stage combines with U^n (stages 2 and 3); the first stage writes U_in + dt L(U_in).
-template <typename T, int ADV, int CH, bool F0>
+// PAIR: step 3 on packed node pairs (FP32, UW3, chunked layout); otherwise two scalar nodes per
+// thread (rows lr and lr + 8).
+template <typename T, int ADV, int CH, bool F0, bool PAIR>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) stage_kernel(StageArgs<T> a, VConst<T> vc) {
   using L = GenericLay<T, ADV>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -619,64 +620,18 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) stage_kernel(Stag
   phase2<L>(a, vc, box, co, sm, tid);
   cp_async_wait<0>();
   __syncthreads();
+  if constexpr (PAIR) {
+    const int lr = tid / (TS / 2), lc = 2 * (tid % (TS / 2));
+    const int q = q0 + lr, s = s0 + lc;  // n_phi is even, so s + 1 < n_phi whenever s < n_phi
+    if (q < a.nt && s < a.ns) phase3_pair<L, CH, F0>(a, vc, box, co, sm, lr, lc, q, s);
+  } else {
 #pragma unroll 1
-  for (int m = 0; m < 2; ++m) {
-    const int lr = tid / TS + 8 * m, lc = tid % TS;
-    const int q = q0 + lr, s = s0 + lc;
-    if (q < a.nt && s < a.ns) phase3_node<L, T, ADV, CH, F0>(a, vc, box, co, sm, lr, lc, q, s);
-  }
-}
-
-// Persistent FP32 UW3 kernel: one CTA per SM walks over the tiles t = blockIdx.x, + gridDim.x, ...
-// While tile t computes, the box of tile t + gridDim.x streams into the other buffer and, after
-// tile t's step 3, its U^n into the U^n buffer.  cp.async groups are committed in the order
-// box(t0), U0(t0), box(t1), U0(t1), ..., so "wait until one group is pending" always waits for
-// exactly the buffer that is needed next.
-template <int CH, bool F0>
-__global__ void __launch_bounds__(384, 1) stage_persistent(StageArgs<float> a, VConst<float> vc, int ntiles,
-                                                           int tiles_s) {
-  using L = PersistLay;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* sm = reinterpret_cast<float*>(smem_raw);
-  const int tid = threadIdx.x;
-  int t = blockIdx.x;
-  if (t >= ntiles) return;
-  {
-    const int q0 = (t / tiles_s) * L::TQ, s0 = (t % tiles_s) * TS;
-    issue_box<L>(a, sm + L::BOX_OFF, sm + L::CO_OFF, q0, s0, tid);
-    cp_async_commit();
-    if (F0) issue_u0<L>(a, sm + L::U0_OFF, q0, s0, tid);
-    cp_async_commit();
-  }
-  for (int it = 0; t < ntiles; ++it, t += gridDim.x) {
-    const int b = it & 1;
-    const int q0 = (t / tiles_s) * L::TQ, s0 = (t % tiles_s) * TS;
-    const float* box = sm + L::BOX_OFF + b * L::BOX;
-    const float* co = sm + L::CO_OFF + b * L::CO;
-    cp_async_wait<1>();  // box(t) has landed; U0(t) may be pending
-    __syncthreads();
-    const int tn = t + gridDim.x;
-    if (tn < ntiles) {
-      const int qn = (tn / tiles_s) * L::TQ, sn0 = (tn % tiles_s) * TS;
-      issue_box<L>(a, sm + L::BOX_OFF + (b ^ 1) * L::BOX, sm + L::CO_OFF + (b ^ 1) * L::CO, qn, sn0, tid);
-    }
-    cp_async_commit();
-    phase2<L>(a, vc, box, co, sm, tid);
-    cp_async_wait<1>();  // U0(t) has landed; box(tn) may be pending
-    __syncthreads();
-    {
-      const int lr = tid / (TS / 2), lc = 2 * (tid % (TS / 2));
+    for (int m = 0; m < 2; ++m) {
+      const int lr = tid / TS + 8 * m, lc = tid % TS;
       const int q = q0 + lr, s = s0 + lc;
-      if (q < a.nt && s < a.ns) phase3_pair<L, CH, F0>(a, vc, box, co, sm, lr, lc, q, s);
+      if (q < a.nt && s < a.ns) phase3_node<L, T, ADV, CH, F0>(a, vc, box, co, sm, lr, lc, q, s);
     }
-    __syncthreads();  // the tile's U^n, moments and box are no longer read
-    if (F0 && tn < ntiles) {
-      const int qn = (tn / tiles_s) * L::TQ, sn0 = (tn % tiles_s) * TS;
-      issue_u0<L>(a, sm + L::U0_OFF, qn, sn0, tid);
-    }
-    cp_async_commit();
   }
-  cp_async_wait<0>();
 }
 
 template <typename T>
@@ -706,43 +661,25 @@ cudaError_t ensure_smem(K kernel, size_t bytes, int& mask) {
   return e;
 }
 
-template <typename T, int ADV, int CH, bool F0>
+template <typename T, int ADV, int CH, bool F0, bool PAIR>
 cudaError_t launch_generic(const StageArgs<T>& a, cudaStream_t st) {
   using L = GenericLay<T, ADV>;
   static int mask = 0;
-  cudaError_t e = ensure_smem(stage_kernel<T, ADV, CH, F0>, L::BYTES, mask);
+  cudaError_t e = ensure_smem(stage_kernel<T, ADV, CH, F0, PAIR>, L::BYTES, mask);
   if (e != cudaSuccess) return e;
   static const VConst<T> vc = make_vconst<T>();
   dim3 grid((a.ns + TS - 1) / TS, (a.nt + L::TQ - 1) / L::TQ);
-  stage_kernel<T, ADV, CH, F0><<<grid, 256, L::BYTES, st>>>(a, vc);
-  return cudaGetLastError();
-}
-
-template <int CH, bool F0>
-cudaError_t launch_persistent(const StageArgs<float>& a, cudaStream_t st) {
-  using L = PersistLay;
-  static int mask = 0;
-  cudaError_t e = ensure_smem(stage_persistent<CH, F0>, L::BYTES, mask);
-  if (e != cudaSuccess) return e;
-  int dev = 0, sms = 0;
-  e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e != cudaSuccess) return e;
-  static const VConst<float> vc = make_vconst<float>();
-  const int tiles_s = (a.ns + TS - 1) / TS;
-  const int ntiles = tiles_s * ((a.nt + L::TQ - 1) / L::TQ);
-  const int grid = ntiles < sms ? ntiles : sms;
-  stage_persistent<CH, F0><<<grid, L::NTH, L::BYTES, st>>>(a, vc, ntiles, tiles_s);
+  stage_kernel<T, ADV, CH, F0, PAIR><<<grid, 256, L::BYTES, st>>>(a, vc);
   return cudaGetLastError();
 }
 
 template <typename T, int ADV, int CH>
 cudaError_t launch_one(const StageArgs<T>& a, cudaStream_t st) {
   if constexpr (sizeof(T) == 4 && ADV == VLB_UW3) {
-    if (chunked<PersistLay>(a.nt, a.ns))
-      return a.f0 ? launch_persistent<CH, true>(a, st) : launch_persistent<CH, false>(a, st);
+    if (chunked<GenericLay<T, ADV>>(a.nt, a.ns))  // n_phi % 4 == 0: packed node pairs
+      return a.f0 ? launch_generic<T, ADV, CH, true, true>(a, st) : launch_generic<T, ADV, CH, false, true>(a, st);
   }
-  return a.f0 ? launch_generic<T, ADV, CH, true>(a, st) : launch_generic<T, ADV, CH, false>(a, st);
+  return a.f0 ? launch_generic<T, ADV, CH, true, false>(a, st) : launch_generic<T, ADV, CH, false, false>(a, st);
 }
 
 }  // namespace

@@ -68,7 +68,7 @@ CASES = [
     (64, 1, vlb.TORUS, vlb.UW3, vlb.HYDRO),
     (24, 1, vlb.TORUS, vlb.WENO5, vlb.HYDRO),
     (17, 33, vlb.TORUS, vlb.UW3, vlb.HYDRO),
-    # FP32 UW3 with n_phi % 4 == 0 runs the persistent kernel: ragged 24 x 32 tiles, single wrap
+    # FP32 UW3 with n_phi % 4 == 0 and n_phi >= 40 runs the packed-pair kernel: ragged tiles, single wrap
     (50, 36, vlb.TORUS, vlb.UW3, vlb.HYDRO),
     (28, 44, vlb.FLAT, vlb.UW3, vlb.HYDRO),
     (61, 100, vlb.TORUS, vlb.UW3, vlb.DIFFUSIVE),
