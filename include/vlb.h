@@ -141,6 +141,34 @@ vlb_status vlb_steps_done(const vlb_handle* h, int64_t* out);
  * h is NULL).  Never NULL; empty when there was none. */
 const char* vlb_last_error(const vlb_handle* h);
 
+/* Fixed size, in bytes, of the device scratch that vlb_step_noalloc uses. */
+#define VLB_NOALLOC_SCRATCH_BYTES (24u * 1024u * 1024u)
+
+/* vlb_step without any device allocation.  The paper has no counterpart: this is a deployment
+ * variant for callers that cannot allocate device memory where they step -- code running while a
+ * stream is captured into a CUDA graph, plug-ins that may only use buffers their host application
+ * hands them, loops that cannot afford cudaMalloc's implicit device synchronisation.
+ *
+ * Advances the caller's device state in place by nsteps SSP-RK3 steps on cuda_stream (NULL: the
+ * legacy default stream), asynchronously.  d_state (256-byte aligned) holds arrays spaced stride
+ * elements apart (stride >= n_theta * n_phi, a multiple of 64): 16 population deviations
+ * g_k = f_k - n0 w_i w_j (k = 4 i + j, w the weights of Sec. 2.3), then phi; in FP32 mode phi is
+ * the float pair hi (array 16) + lo (array 17).  Elements are double (FP64) or float (FP32).
+ * n0 > 0 is the caller's reference density (any value near the mean density keeps the FP32
+ * resolution).  diag_every is ignored; nothing is read back.
+ *
+ * The two intermediate Runge-Kutta states and the row coefficients live in one file-scope device
+ * array of VLB_NOALLOC_SCRATCH_BYTES that every device loading the library holds until exit; the
+ * call needs 2 * (17 or 18) * stride * element-size bytes plus the tables, and a larger grid is
+ * rejected with VLB_ERR_ARG (about 170 k nodes in FP32, 90 k in FP64).  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress) with that device current, so
+ * that first call should come before any stream capture.  All calls share the array, which keeps
+ * the previous call's contents: calls whose GPU work overlaps (other streams, other host threads
+ * on the same device) race.  No cudaMalloc, cudaFree or other allocating routine is called.
+ * On failure *error (if not NULL) points to a thread-local message. */
+vlb_status vlb_step_noalloc(const vlb_params* p, void* d_state, int64_t stride, double n0, int64_t nsteps,
+                            void* cuda_stream, const char** error);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,7 +23,10 @@ HYDRO, DIFFUSIVE = 0, 1
 # every entry point declared in include/vlb.h
 EXPORTS = ["vlb_workspace_bytes", "vlb_max_stable_dt", "vlb_create", "vlb_destroy", "vlb_set_fields",
            "vlb_set_state", "vlb_get_state", "vlb_step", "vlb_get_fields", "vlb_get_totals",
-           "vlb_interface_length", "vlb_state_device", "vlb_steps_done", "vlb_last_error"]
+           "vlb_interface_length", "vlb_state_device", "vlb_steps_done", "vlb_last_error",
+           "vlb_step_noalloc"]
+
+NOALLOC_SCRATCH_BYTES = 24 * 1024 * 1024
 
 
 class vlb_params(ctypes.Structure):
@@ -75,6 +78,8 @@ def lib() -> ctypes.CDLL:
     L.vlb_state_device.argtypes, L.vlb_state_device.restype = [P, ctypes.POINTER(P), ctypes.POINTER(I64)], I32
     L.vlb_steps_done.argtypes, L.vlb_steps_done.restype = [P, ctypes.POINTER(I64)], I32
     L.vlb_last_error.argtypes, L.vlb_last_error.restype = [P], ctypes.c_char_p
+    L.vlb_step_noalloc.argtypes = [PP, P, I64, ctypes.c_double, I64, P, ctypes.POINTER(ctypes.c_char_p)]
+    L.vlb_step_noalloc.restype = I32
     _lib = L
     return L
 
@@ -165,6 +170,15 @@ def vlb_steps_done(h) -> int:
     s = ctypes.c_int64()
     _check(lib().vlb_steps_done(h, ctypes.byref(s)), h)
     return s.value
+
+
+def vlb_step_noalloc(p: vlb_params, state_ptr: int, stride: int, n0: float, nsteps: int, stream_ptr: int):
+    """Step a caller-owned device state in place with no device allocation (see include/vlb.h)."""
+    err = ctypes.c_char_p()
+    st = lib().vlb_step_noalloc(ctypes.byref(p), ctypes.c_void_p(state_ptr), stride, n0, nsteps,
+                                ctypes.c_void_p(stream_ptr), ctypes.byref(err))
+    if st != VLB_OK:
+        raise VlbError(st, (err.value or b"").decode())
 
 
 class Solver:
