@@ -134,6 +134,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def reduce_max(values, dist=None, device="cpu"):
+    """Max over ranks of a list of floats (each rank's timings); identity without a process group."""
+    if dist is None:
+        return list(values)
+    import torch
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
+def aggregate_value(world: int, units_per_rank: float, seconds_max: float) -> float:
+    """Whole-job throughput: every rank processed units_per_rank; the job took the slowest rank's time."""
+    return world * units_per_rank / seconds_max
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -259,17 +274,14 @@ def main():
     e2e_s = time.perf_counter() - t0
     barrier()
 
-    if dist is not None:
-        t = torch.tensor([ms, e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, e2e_s = float(t[0]), float(t[1])
+    ms, e2e_s = reduce_max([ms, e2e_s], dist, device="cuda")
     solver.close()
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
 
-    value = world * 16.0 * N * args.steps / (ms * 1e-3)
+    value = aggregate_value(world, 16.0 * N * args.steps, ms * 1e-3)
     peaks, peak_kind = _peaks()
     step_s = ms * 1e-3 / args.steps
     launch_s = step_s / 3.0
@@ -289,7 +301,7 @@ def main():
                      "kernel": "stage_kernel<float,UW3,HYDRO>",
                      "peak_source": f"{peak_kind} hbm_gbs (copy)",
                      "algorithmic_bytes_per_launch": alg_bytes_launch},
-        "e2e": {"value": world * 16.0 * N * args.steps / e2e_s, "unit": UNIT,
+        "e2e": {"value": aggregate_value(world, 16.0 * N * args.steps, e2e_s), "unit": UNIT,
                 "h2d_bytes_per_step": 4 * N * 8 / args.steps, "d2h_bytes_per_step": 5 * N * 8 / args.steps,
                 "what": "vlb_set_fields (host) + vlb_step(K) + vlb_get_fields (host), wall clock"},
         "gpu_launches": 3 * args.steps,
