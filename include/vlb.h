@@ -141,6 +141,35 @@ vlb_status vlb_steps_done(const vlb_handle* h, int64_t* out);
  * h is NULL).  Never NULL; empty when there was none. */
 const char* vlb_last_error(const vlb_handle* h);
 
+/* ---- Ensembles: many tori in one batched launch per Runge-Kutta stage ----
+ * Members are independent problems (own geometry, grid, time step, seed) in FP32 with UW3
+ * advection and one common ch_mode.  Each stage of all members is one launch over a work list of
+ * (member, tile) items; the per-step launch sequence is recorded into CUDA graphs (1 and 32
+ * steps) on the first vlb_ensemble_step and replayed on the caller's stream afterwards.  The tile
+ * height (16 or 8 theta rows) is chosen on that first call by timing both on the ensemble. */
+
+/* Workspace bytes for an ensemble of `count` members p[0..count-1]; 0 if invalid. */
+size_t vlb_ensemble_workspace_bytes(const vlb_params* p, int32_t count);
+
+/* Create an ensemble handle over a caller-owned workspace (see vlb_create for the conventions). */
+vlb_status vlb_ensemble_create(const vlb_params* p, int32_t count, void* d_workspace, size_t bytes,
+                               void* cuda_stream, vlb_handle** out);
+
+/* Advance every member by nsteps steps of its own dt, asynchronously on the stream.  The first
+ * call synchronises once (autotuning and graph recording; it also takes the first step eagerly).
+ * diag_every is not applied: read the totals of members through their views. */
+vlb_status vlb_ensemble_step(vlb_handle* h, int64_t nsteps);
+
+/* A view of member idx, usable with vlb_set_fields, vlb_set_state, vlb_get_state, vlb_get_fields,
+ * vlb_get_totals, vlb_interface_length, vlb_state_device and vlb_step (which then advances that
+ * member alone with per-member launches).  Views are owned by the ensemble: vlb_destroy on a view
+ * is a no-op, vlb_destroy on the ensemble releases them. */
+vlb_status vlb_ensemble_member(vlb_handle* h, int32_t idx, vlb_handle** view);
+
+/* The autotuner's tile height (16 or 8; 0 before the first vlb_ensemble_step) and the measured
+ * time of one first-stage launch for each candidate (ms; either pointer may be NULL). */
+vlb_status vlb_ensemble_tile_rows(const vlb_handle* h, int32_t* rows, float* ms16, float* ms8);
+
 /* Fixed size, in bytes, of the device scratch that vlb_step_noalloc uses. */
 #define VLB_NOALLOC_SCRATCH_BYTES (24u * 1024u * 1024u)
 

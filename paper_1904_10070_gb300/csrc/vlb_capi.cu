@@ -11,8 +11,10 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <new>
+#include <vector>
 
 #include "vlb_internal.cuh"
 
@@ -39,6 +41,19 @@ struct vlb_handle {
   double n0;           // reference density of the stored deviations g = f - n0 w_i w_j
   int64_t steps_done;
   char err[512];
+  // ensembles
+  int kind = 0;                              // 0 solver, 1 ensemble, 2 member view of an ensemble
+  vlb_handle* parent = nullptr;              // view: its ensemble
+  int index = 0;                             // view: member index
+  int count = 0;                             // ensemble: members
+  vlb_handle** views = nullptr;              // ensemble: one view per member
+  vlb::EnsembleMember* d_members = nullptr;  // ensemble: device descriptors
+  int2* d_items[2] = {nullptr, nullptr};     // ensemble: work lists for tile rows 16 and 8
+  int nitems[2] = {0, 0};
+  int tile_rows = 0;                         // ensemble: autotuner's choice, 0 = not tuned yet
+  float tune_ms[2] = {0.0f, 0.0f};
+  cudaStream_t capture_stream = nullptr;
+  cudaGraphExec_t graph_1 = nullptr, graph_32 = nullptr;  // one step, 32 steps
 };
 
 namespace {
@@ -185,6 +200,44 @@ bool reference_density(const vlb_params& p, F n_at, double* out) {
   return true;
 }
 
+// Uploads the FP64 and state-precision row tables of h (synchronous on h's stream).
+vlb_status upload_tables(vlb_handle* h) {
+  const vlb_params* p = &h->p;
+  const int nt = p->n_theta;
+  double* tab = (double*)malloc(sizeof(double) * vlb::NCOEF * nt);
+  void* tabT = malloc(h->esize * vlb::NCOEF * nt);
+  if (!tab || !tabT) {
+    free(tab);
+    free(tabT);
+    return fail(h, VLB_ERR_ARG, "out of host memory");
+  }
+  row_tables(p, tab);
+  for (int i = 0; i < vlb::NCOEF * nt; ++i) {
+    if (h->esize == 8)
+      ((double*)tabT)[i] = tab[i];
+    else
+      ((float*)tabT)[i] = (float)tab[i];
+  }
+  cudaError_t e = cudaMemcpyAsync(h->coefD, tab, sizeof(double) * vlb::NCOEF * nt, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->coefT, tabT, h->esize * vlb::NCOEF * nt, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  free(tab);
+  free(tabT);
+  if (e != cudaSuccess) return fail(h, VLB_ERR_CUDA, "table upload: %s", cudaGetErrorString(e));
+  return VLB_OK;
+}
+
+// A member view's reference density lives in the ensemble's device descriptor too.
+vlb_status sync_member_n0(vlb_handle* h) {
+  if (h->kind != 2) return VLB_OK;
+  const float n0 = (float)h->n0;
+  VLB_CUDA(h, cudaMemcpyAsync(&h->parent->d_members[h->index].n0, &n0, sizeof(float), cudaMemcpyHostToDevice,
+                              h->stream));
+  VLB_CUDA(h, cudaStreamSynchronize(h->stream));
+  return VLB_OK;
+}
+
 template <typename T>
 vlb_status run_steps(vlb_handle* h, int64_t nsteps) {
   const vlb_params& p = h->p;
@@ -231,8 +284,10 @@ vlb_status totals_impl(vlb_handle* h) {
   return VLB_OK;
 }
 
-vlb_status check_handle(vlb_handle* h) {
+vlb_status check_handle(vlb_handle* h, bool ensemble_ok = false) {
   if (!h) return fail(nullptr, VLB_ERR_ARG, "handle is NULL");
+  if (h->kind == 1 && !ensemble_ok)
+    return fail(h, VLB_ERR_ARG, "ensemble handle: use vlb_ensemble_step, or a member view from vlb_ensemble_member");
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(h, VLB_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
@@ -397,6 +452,14 @@ vlb_status vlb_create(const vlb_params* p, void* d_workspace, size_t bytes, void
 }
 
 vlb_status vlb_destroy(vlb_handle* h) {
+  if (!h || h->kind == 2) return VLB_OK;  // member views are owned by their ensemble
+  if (h->kind == 1) {
+    if (h->graph_1) cudaGraphExecDestroy(h->graph_1);
+    if (h->graph_32) cudaGraphExecDestroy(h->graph_32);
+    if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+    for (int i = 0; i < h->count; ++i) delete h->views[i];
+    delete[] h->views;
+  }
   delete h;
   return VLB_OK;
 }
@@ -423,7 +486,7 @@ vlb_status vlb_set_fields(vlb_handle* h, const double* rho, const double* u_th, 
   VLB_CUDA(h, cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
   VLB_CUDA(h, cudaStreamSynchronize(h->stream));
   h->steps_done = 0;
-  return VLB_OK;
+  return sync_member_n0(h);
 }
 
 vlb_status vlb_set_state(vlb_handle* h, const double* f16, const double* phi) {
@@ -449,7 +512,7 @@ vlb_status vlb_set_state(vlb_handle* h, const double* f16, const double* phi) {
   VLB_CUDA(h, cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
   VLB_CUDA(h, cudaStreamSynchronize(h->stream));
   h->steps_done = 0;
-  return VLB_OK;
+  return sync_member_n0(h);
 }
 
 vlb_status vlb_get_state(vlb_handle* h, double* f16, double* phi) {
@@ -533,6 +596,7 @@ vlb_status vlb_interface_length(vlb_handle* h, double* out) {
 
 vlb_status vlb_state_device(vlb_handle* h, void** f, int64_t* stride) {
   if (!h) return fail(nullptr, VLB_ERR_ARG, "handle is NULL");
+  if (h->kind == 1) return fail(h, VLB_ERR_ARG, "ensemble handle: use a member view");
   if (!f || !stride) return fail(h, VLB_ERR_ARG, "NULL output");
   *f = h->U[0];
   *stride = h->stride;
@@ -547,5 +611,299 @@ vlb_status vlb_steps_done(const vlb_handle* h, int64_t* out) {
 }
 
 const char* vlb_last_error(const vlb_handle* h) { return h ? h->err : g_err; }
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------------
+// Ensembles: many tori advanced by one batched launch per Runge-Kutta stage.
+// ------------------------------------------------------------------------------------------------
+namespace {
+
+constexpr int kTileRows[2] = {16, 8};
+
+struct EnsLayout {
+  size_t off_staging, off_partials, off_totals, off_diag, off_flag, off_members, off_items[2];
+  std::vector<size_t> off_member;  // start of member m's region: coefT, coefD, U0, U1, U2
+  std::vector<Layout> member;
+  int nitems[2];
+  size_t total;
+};
+
+bool ensemble_params_ok(const vlb_params* p, int count, char* why, size_t n) {
+  if (!p) return snprintf(why, n, "params is NULL"), false;
+  if (count < 1 || count > 65536) return snprintf(why, n, "count must be in 1..65536"), false;
+  for (int m = 0; m < count; ++m) {
+    char w2[200];
+    if (!params_ok(&p[m], w2, sizeof w2)) return snprintf(why, n, "member %d: %s", m, w2), false;
+    if (p[m].precision != VLB_FP32 || p[m].advection != VLB_UW3)
+      return snprintf(why, n, "member %d: ensembles run FP32 UW3", m), false;
+    if (p[m].ch_mode != p[0].ch_mode) return snprintf(why, n, "member %d: all members share ch_mode", m), false;
+  }
+  return true;
+}
+
+EnsLayout ens_layout(const vlb_params* p, int count) {
+  EnsLayout E;
+  int64_t maxN = 0;
+  E.nitems[0] = E.nitems[1] = 0;
+  for (int m = 0; m < count; ++m) {
+    E.member.push_back(layout(&p[m]));
+    maxN = std::max(maxN, E.member.back().N);
+    const int ts = (p[m].n_phi + 31) / 32;
+    for (int k = 0; k < 2; ++k) E.nitems[k] += ts * ((p[m].n_theta + kTileRows[k] - 1) / kTileRows[k]);
+  }
+  size_t off = 0;
+  E.off_staging = off;
+  off = align_up(off + (size_t)vlb::NARR * maxN * 8, 256);
+  E.off_partials = off;
+  off = align_up(off + (size_t)vlb::totals_blocks() * 8 * 8, 256);
+  E.off_totals = off;
+  off = align_up(off + 64, 256);
+  E.off_diag = off;
+  off = align_up(off + 64, 256);
+  E.off_flag = off;
+  off = align_up(off + 256, 256);
+  E.off_members = off;
+  off = align_up(off + sizeof(vlb::EnsembleMember) * count, 256);
+  for (int k = 0; k < 2; ++k) {
+    E.off_items[k] = off;
+    off = align_up(off + sizeof(int2) * E.nitems[k], 256);
+  }
+  for (int m = 0; m < count; ++m) {
+    const Layout& L = E.member[m];
+    E.off_member.push_back(off);
+    off += L.off_staging - L.off_coefT;  // coefT, coefD and the three state buffers of a solver layout
+    off = align_up(off, 256);
+  }
+  E.total = off;
+  return E;
+}
+
+vlb_status ens_launch_step(vlb_handle* h, int rows_idx, cudaStream_t st) {
+  for (int stage = 0; stage < 3; ++stage)
+    VLB_CUDA(h, vlb::launch_ensemble_stage(h->d_members, h->d_items[rows_idx], h->nitems[rows_idx], stage,
+                                          kTileRows[rows_idx], h->p.ch_mode, st));
+  return VLB_OK;
+}
+
+// Autotuner: times the first Runge-Kutta stage (which writes only the scratch U^(1)) with each tile
+// height and keeps the faster one.
+vlb_status ens_autotune(vlb_handle* h) {
+  cudaEvent_t e0, e1;
+  VLB_CUDA(h, cudaEventCreate(&e0));
+  VLB_CUDA(h, cudaEventCreate(&e1));
+  float best = 1e30f;
+  for (int k = 0; k < 2; ++k) {
+    VLB_CUDA(h, vlb::launch_ensemble_stage(h->d_members, h->d_items[k], h->nitems[k], 0, kTileRows[k],
+                                          h->p.ch_mode, h->stream));  // warm-up
+    VLB_CUDA(h, cudaEventRecord(e0, h->stream));
+    for (int r = 0; r < 3; ++r)
+      VLB_CUDA(h, vlb::launch_ensemble_stage(h->d_members, h->d_items[k], h->nitems[k], 0, kTileRows[k],
+                                            h->p.ch_mode, h->stream));
+    VLB_CUDA(h, cudaEventRecord(e1, h->stream));
+    VLB_CUDA(h, cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    VLB_CUDA(h, cudaEventElapsedTime(&ms, e0, e1));
+    h->tune_ms[k] = ms / 3.0f;
+    if (ms < best) {
+      best = ms;
+      h->tile_rows = kTileRows[k];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return VLB_OK;
+}
+
+vlb_status ens_capture(vlb_handle* h, int rows_idx, int steps, cudaGraphExec_t* out) {
+  cudaGraph_t g = nullptr;
+  VLB_CUDA(h, cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
+  vlb_status st = VLB_OK;
+  for (int n = 0; n < steps && st == VLB_OK; ++n) st = ens_launch_step(h, rows_idx, h->capture_stream);
+  cudaError_t e = cudaStreamEndCapture(h->capture_stream, &g);
+  if (st != VLB_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(h, VLB_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(h, VLB_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  return VLB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t vlb_ensemble_workspace_bytes(const vlb_params* p, int32_t count) {
+  char why[256];
+  if (!ensemble_params_ok(p, count, why, sizeof why)) {
+    fail(nullptr, VLB_ERR_ARG, "%s", why);
+    return 0;
+  }
+  return ens_layout(p, count).total;
+}
+
+vlb_status vlb_ensemble_create(const vlb_params* p, int32_t count, void* d_workspace, size_t bytes, void* cuda_stream,
+                               vlb_handle** out) {
+  char why[256];
+  if (!out) return fail(nullptr, VLB_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!ensemble_params_ok(p, count, why, sizeof why)) return fail(nullptr, VLB_ERR_ARG, "%s", why);
+  const EnsLayout E = ens_layout(p, count);
+  if (!d_workspace) return fail(nullptr, VLB_ERR_WORKSPACE, "workspace is NULL");
+  if (((uintptr_t)d_workspace) % 256 != 0) return fail(nullptr, VLB_ERR_WORKSPACE, "workspace not 256-byte aligned");
+  if (bytes < E.total) return fail(nullptr, VLB_ERR_WORKSPACE, "workspace too small: %zu < %zu bytes", bytes, E.total);
+  unsigned char* ws = (unsigned char*)d_workspace;
+  vlb_handle* h = new (std::nothrow) vlb_handle();
+  if (!h) return fail(nullptr, VLB_ERR_ARG, "out of host memory");
+  h->kind = 1;
+  h->p = p[0];
+  h->stream = (cudaStream_t)cuda_stream;
+  h->ws = ws;
+  h->ws_bytes = bytes;
+  h->esize = 4;
+  h->staging = (double*)(ws + E.off_staging);
+  h->partials = (double*)(ws + E.off_partials);
+  h->totals = (double*)(ws + E.off_totals);
+  h->diag = (double*)(ws + E.off_diag);
+  h->flag = (int*)(ws + E.off_flag);
+  h->d_members = (vlb::EnsembleMember*)(ws + E.off_members);
+  for (int k = 0; k < 2; ++k) {
+    h->d_items[k] = (int2*)(ws + E.off_items[k]);
+    h->nitems[k] = E.nitems[k];
+  }
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e != cudaSuccess) {
+    delete h;
+    return fail(nullptr, VLB_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  }
+  h->count = count;
+  h->views = new (std::nothrow) vlb_handle*[count]();
+  if (!h->views) {
+    delete h;
+    return fail(nullptr, VLB_ERR_ARG, "out of host memory");
+  }
+  std::vector<vlb::EnsembleMember> desc(count);
+  std::vector<int2> items[2];
+  for (int m = 0; m < count; ++m) {
+    vlb_handle* v = new (std::nothrow) vlb_handle();
+    if (!v) {
+      vlb_destroy(h);
+      return fail(nullptr, VLB_ERR_ARG, "out of host memory");
+    }
+    h->views[m] = v;
+    const Layout& L = E.member[m];
+    unsigned char* base = ws + E.off_member[m] - L.off_coefT;  // so that base + L.off_* lands in the region
+    v->kind = 2;
+    v->parent = h;
+    v->index = m;
+    v->p = p[m];
+    v->stream = h->stream;
+    v->device = h->device;
+    v->N = L.N;
+    v->stride = L.stride;
+    v->esize = 4;
+    v->ws = ws;
+    v->ws_bytes = bytes;
+    v->coefT = base + L.off_coefT;
+    v->coefD = (double*)(base + L.off_coefD);
+    for (int k = 0; k < 3; ++k) v->U[k] = base + L.off_U[k];
+    v->staging = h->staging;
+    v->partials = h->partials;
+    v->totals = h->totals;
+    v->diag = h->diag;
+    v->flag = h->flag;
+    v->n0 = 1.0;
+    v->steps_done = 0;
+    vlb_status st = upload_tables(v);
+    if (st == VLB_OK) {
+      e = cudaMemsetAsync(v->U[0], 0, L.off_staging - L.off_U[0], h->stream);
+      if (e != cudaSuccess) st = fail(nullptr, VLB_ERR_CUDA, "memset: %s", cudaGetErrorString(e));
+    } else {
+      fail(nullptr, st, "member %d: %s", m, v->err);
+    }
+    if (st != VLB_OK) {
+      vlb_destroy(h);
+      return st;
+    }
+    vlb::EnsembleMember& d = desc[m];
+    for (int k = 0; k < 3; ++k) d.U[k] = (float*)v->U[k];
+    d.coef = (const float*)v->coefT;
+    d.nt = p[m].n_theta;
+    d.ns = p[m].n_phi;
+    d.stride = L.stride;
+    d.dt = (float)p[m].dt;
+    d.inv_tau = (float)(1.0 / p[m].tau);
+    d.M = (float)p[m].M;
+    d.A = (float)p[m].A;
+    d.kappa = (float)p[m].kappa;
+    d.gt = (float)(1.0 / (2.0 * p[m].r * (2.0 * M_PI / p[m].n_theta)));
+    d.n0 = 1.0f;
+    d.pad = 0;
+    const int ts = (p[m].n_phi + 31) / 32;
+    for (int k = 0; k < 2; ++k) {
+      const int tq = (p[m].n_theta + kTileRows[k] - 1) / kTileRows[k];
+      for (int t = 0; t < ts * tq; ++t) items[k].push_back(make_int2(m, t));
+    }
+  }
+  e = cudaMemcpyAsync(h->d_members, desc.data(), sizeof(vlb::EnsembleMember) * count, cudaMemcpyHostToDevice,
+                      h->stream);
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+    e = cudaMemcpyAsync(h->d_items[k], items[k].data(), sizeof(int2) * items[k].size(), cudaMemcpyHostToDevice,
+                        h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    vlb_destroy(h);
+    return fail(nullptr, VLB_ERR_CUDA, "ensemble set-up: %s", cudaGetErrorString(e));
+  }
+  *out = h;
+  return VLB_OK;
+}
+
+vlb_status vlb_ensemble_step(vlb_handle* h, int64_t nsteps) {
+  vlb_status st = check_handle(h, true);
+  if (st) return st;
+  if (h->kind != 1) return fail(h, VLB_ERR_ARG, "not an ensemble handle");
+  if (nsteps < 0) return fail(h, VLB_ERR_ARG, "nsteps must be >= 0");
+  if (nsteps == 0) return VLB_OK;
+  int64_t left = nsteps;
+  if (!h->graph_1) {
+    // first call: choose the tile height, take one step eagerly (every kernel variant is then set
+    // up outside any capture), and record the 1-step and 32-step graphs
+    if ((st = ens_autotune(h))) return st;
+    const int k = h->tile_rows == kTileRows[0] ? 0 : 1;
+    if ((st = ens_launch_step(h, k, h->stream))) return st;
+    VLB_CUDA(h, cudaStreamSynchronize(h->stream));
+    --left;
+    if ((st = ens_capture(h, k, 1, &h->graph_1))) return st;
+    if ((st = ens_capture(h, k, 32, &h->graph_32))) return st;
+  }
+  for (; left >= 32; left -= 32) VLB_CUDA(h, cudaGraphLaunch(h->graph_32, h->stream));
+  for (; left > 0; --left) VLB_CUDA(h, cudaGraphLaunch(h->graph_1, h->stream));
+  h->steps_done += nsteps;
+  for (int m = 0; m < h->count; ++m) h->views[m]->steps_done += nsteps;
+  return VLB_OK;
+}
+
+vlb_status vlb_ensemble_member(vlb_handle* h, int32_t idx, vlb_handle** view) {
+  if (!h || !view) return fail(h, VLB_ERR_ARG, "NULL argument");
+  if (h->kind != 1) return fail(h, VLB_ERR_ARG, "not an ensemble handle");
+  if (idx < 0 || idx >= h->count) return fail(h, VLB_ERR_ARG, "member index %d out of range", idx);
+  *view = h->views[idx];
+  return VLB_OK;
+}
+
+vlb_status vlb_ensemble_tile_rows(const vlb_handle* h, int32_t* rows, float* ms16, float* ms8) {
+  if (!h || !rows) return fail(const_cast<vlb_handle*>(h), VLB_ERR_ARG, "NULL argument");
+  if (h->kind != 1) return fail(const_cast<vlb_handle*>(h), VLB_ERR_ARG, "not an ensemble handle");
+  *rows = h->tile_rows;
+  if (ms16) *ms16 = h->tune_ms[0];
+  if (ms8) *ms8 = h->tune_ms[1];
+  return VLB_OK;
+}
 
 }  // extern "C"

@@ -70,7 +70,20 @@ struct StageArgs {
   T n0;             // reference density of the stored deviations
 };
 
+// Ensemble member as seen by the batched stage kernel (FP32 state).
+struct EnsembleMember {
+  float* U[3];        // U^n, U^(1), U^(2)
+  const float* coef;  // [NCOEF][n_theta]
+  int nt, ns;
+  int64_t stride;
+  float dt, inv_tau, M, A, kappa, gt, n0;
+  int pad;
+};
+
 // Host launchers (vlb_stage.cu).
+// One stage (0, 1, 2) of every ensemble member; items[b] = (member, tile index), tile_rows 16 or 8.
+cudaError_t launch_ensemble_stage(const EnsembleMember* members, const int2* items, int nitems, int stage,
+                                  int tile_rows, int ch_mode, cudaStream_t s);
 template <typename T>
 cudaError_t launch_stage(const StageArgs<T>& a, int advection, int ch_mode, cudaStream_t s);
 

@@ -598,19 +598,12 @@ __device__ __forceinline__ void phase3_pair(const StageArgs<float>& a, const VCo
 // Kernels
 // ---------------------------------------------------------------------------------------------
 
-// One CTA per 16 x 32 tile.
-// F0: the stage combines with U^n (stages 2 and 3); the first stage writes U_in + dt L(U_in).
-// PAIR: step 3 on packed node pairs (FP32, UW3, chunked layout); otherwise two scalar nodes per
-// thread (rows lr and lr + 8).
-template <typename T, int ADV, int CH, bool F0, bool PAIR>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) stage_kernel(StageArgs<T> a, VConst<T> vc) {
-  using L = GenericLay<T, ADV>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);
+// Steps 1-3 for one tile.  PM: 0 = scalar step 3 (two or more nodes per thread), 1 = packed node
+// pairs, 2 = decided at run time from the grid (pairs when the chunked layout applies, FP32 UW3).
+template <typename L, typename T, int ADV, int CH, bool F0, int PM>
+__device__ __forceinline__ void tile_body(const StageArgs<T>& a, const VConst<T>& vc, T* sm, int tid, int q0, int s0) {
   T* box = sm + L::BOX_OFF;
   T* co = sm + L::CO_OFF;
-  const int tid = threadIdx.x;
-  const int s0 = blockIdx.x * TS, q0 = blockIdx.y * L::TQ;
   issue_box<L>(a, box, co, q0, s0, tid);
   cp_async_commit();
   if (F0) issue_u0<L>(a, sm + L::U0_OFF, q0, s0, tid);
@@ -620,18 +613,73 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) stage_kernel(Stag
   phase2<L>(a, vc, box, co, sm, tid);
   cp_async_wait<0>();
   __syncthreads();
-  if constexpr (PAIR) {
-    const int lr = tid / (TS / 2), lc = 2 * (tid % (TS / 2));
-    const int q = q0 + lr, s = s0 + lc;  // n_phi is even, so s + 1 < n_phi whenever s < n_phi
-    if (q < a.nt && s < a.ns) phase3_pair<L, CH, F0>(a, vc, box, co, sm, lr, lc, q, s);
-  } else {
-#pragma unroll 1
-    for (int m = 0; m < 2; ++m) {
-      const int lr = tid / TS + 8 * m, lc = tid % TS;
-      const int q = q0 + lr, s = s0 + lc;
-      if (q < a.nt && s < a.ns) phase3_node<L, T, ADV, CH, F0>(a, vc, box, co, sm, lr, lc, q, s);
+  bool pair = PM == 1;
+  if constexpr (PM == 2) pair = chunked<L>(a.nt, a.ns);
+  if constexpr (PM != 0 && sizeof(T) == 4 && ADV == VLB_UW3) {
+    if (pair) {
+      static_assert(L::NTH == L::TQ * (TS / 2), "one node pair per thread");
+      const int lr = tid / (TS / 2), lc = 2 * (tid % (TS / 2));
+      const int q = q0 + lr, s = s0 + lc;  // n_phi is even, so s + 1 < n_phi whenever s < n_phi
+      if (q < a.nt && s < a.ns) phase3_pair<L, CH, F0>(a, vc, box, co, sm, lr, lc, q, s);
+      return;
     }
   }
+  constexpr int ROWS = L::NTH / TS;  // thread rows; each thread takes TQ / ROWS nodes of its column
+#pragma unroll 1
+  for (int m = 0; m < L::TQ / ROWS; ++m) {
+    const int lr = tid / TS + ROWS * m, lc = tid % TS;
+    const int q = q0 + lr, s = s0 + lc;
+    if (q < a.nt && s < a.ns) phase3_node<L, T, ADV, CH, F0>(a, vc, box, co, sm, lr, lc, q, s);
+  }
+}
+
+// One CTA per 16 x 32 tile.
+// F0: the stage combines with U^n (stages 2 and 3); the first stage writes U_in + dt L(U_in).
+// PAIR: step 3 on packed node pairs (FP32, UW3, chunked layout); otherwise two scalar nodes per
+// thread (rows lr and lr + 8).
+template <typename T, int ADV, int CH, bool F0, bool PAIR>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) stage_kernel(StageArgs<T> a, VConst<T> vc) {
+  using L = GenericLay<T, ADV>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  tile_body<L, T, ADV, CH, F0, PAIR ? 1 : 0>(a, vc, sm, threadIdx.x, blockIdx.y * L::TQ, blockIdx.x * TS);
+}
+
+// Ensemble: one launch per stage over the tiles of every member (FP32, UW3).  Block b takes work
+// item items[b] = (member, tile index within the member); the member's buffers, grid and scalars
+// come from its descriptor, so members of different sizes, aspect ratios and time steps share the
+// launch.  TQR is the tile height chosen by the autotuner (16 or 8 rows).
+template <int TQR>
+using EnsLay = Lay<float, 2, TQR, 4, TQR * (TS / 2), 1>;
+
+template <int TQR, int CH, bool F0>
+__global__ void __launch_bounds__(TQR * (TS / 2)) ensemble_stage_kernel(const EnsembleMember* members,
+                                                                       const int2* items, int stage,
+                                                                       VConst<float> vc) {
+  using L = EnsLay<TQR>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* sm = reinterpret_cast<float*>(smem_raw);
+  const int2 it = items[blockIdx.x];
+  const EnsembleMember& d = members[it.x];
+  StageArgs<float> a;
+  a.fin = d.U[stage == 0 ? 0 : stage];  // stage 0 reads U^n, 1 reads U^(1), 2 reads U^(2)
+  a.f0 = F0 ? d.U[0] : nullptr;
+  a.fout = d.U[stage == 2 ? 0 : stage + 1];
+  a.coef = d.coef;
+  a.nt = d.nt;
+  a.ns = d.ns;
+  a.stride = d.stride;
+  a.b = stage == 0 ? 1.0f : (stage == 1 ? 0.25f : 2.0f / 3.0f);
+  a.dt = d.dt;
+  a.inv_tau = d.inv_tau;
+  a.M = d.M;
+  a.A = d.A;
+  a.kappa = d.kappa;
+  a.gt = d.gt;
+  a.n0 = d.n0;
+  const int tiles_s = (d.ns + TS - 1) / TS;
+  const int q0 = (it.y / tiles_s) * TQR, s0 = (it.y % tiles_s) * TS;
+  tile_body<L, float, VLB_UW3, CH, F0, 2>(a, vc, sm, threadIdx.x, q0, s0);
 }
 
 template <typename T>
@@ -673,6 +721,27 @@ cudaError_t launch_generic(const StageArgs<T>& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <int TQR, int CH, bool F0>
+cudaError_t launch_ens(const EnsembleMember* members, const int2* items, int nitems, int stage, cudaStream_t st) {
+  using L = EnsLay<TQR>;
+  static int mask = 0;
+  cudaError_t e = ensure_smem(ensemble_stage_kernel<TQR, CH, F0>, L::BYTES, mask);
+  if (e != cudaSuccess) return e;
+  static const VConst<float> vc = make_vconst<float>();
+  ensemble_stage_kernel<TQR, CH, F0><<<nitems, L::NTH, L::BYTES, st>>>(members, items, stage, vc);
+  return cudaGetLastError();
+}
+
+template <int TQR>
+cudaError_t launch_ens_rows(const EnsembleMember* members, const int2* items, int nitems, int stage, int ch_mode,
+                            cudaStream_t st) {
+  if (ch_mode == VLB_HYDRO)
+    return stage == 0 ? launch_ens<TQR, VLB_HYDRO, false>(members, items, nitems, stage, st)
+                      : launch_ens<TQR, VLB_HYDRO, true>(members, items, nitems, stage, st);
+  return stage == 0 ? launch_ens<TQR, VLB_DIFFUSIVE, false>(members, items, nitems, stage, st)
+                    : launch_ens<TQR, VLB_DIFFUSIVE, true>(members, items, nitems, stage, st);
+}
+
 template <typename T, int ADV, int CH>
 cudaError_t launch_one(const StageArgs<T>& a, cudaStream_t st) {
   if constexpr (sizeof(T) == 4 && ADV == VLB_UW3) {
@@ -689,6 +758,13 @@ cudaError_t launch_stage(const StageArgs<T>& a, int advection, int ch_mode, cuda
   if (advection == VLB_UW3)
     return ch_mode == VLB_HYDRO ? launch_one<T, VLB_UW3, VLB_HYDRO>(a, s) : launch_one<T, VLB_UW3, VLB_DIFFUSIVE>(a, s);
   return ch_mode == VLB_HYDRO ? launch_one<T, VLB_WENO5, VLB_HYDRO>(a, s) : launch_one<T, VLB_WENO5, VLB_DIFFUSIVE>(a, s);
+}
+
+cudaError_t launch_ensemble_stage(const EnsembleMember* members, const int2* items, int nitems, int stage,
+                                  int tile_rows, int ch_mode, cudaStream_t s) {
+  if (nitems <= 0) return cudaSuccess;
+  if (tile_rows == 8) return launch_ens_rows<8>(members, items, nitems, stage, ch_mode, s);
+  return launch_ens_rows<16>(members, items, nitems, stage, ch_mode, s);
 }
 
 template cudaError_t launch_stage<float>(const StageArgs<float>&, int, int, cudaStream_t);

@@ -130,3 +130,27 @@ def _stripe(p, width, steps, theta_eq=math.pi, displacement=-math.pi / 20):
     phi = stripe_phi(R, r, p["n_theta"], p["n_phi"], tc, width, xi, offset=off, inside=+1.0)
     z = np.zeros_like(phi)
     return dict(params=p, rho=np.ones_like(phi), ut=z, up=z.copy(), phi=phi, steps=steps)
+
+
+ENSEMBLE_GRIDS = ((64, 128), (128, 256), (256, 512), (512, 1024))
+
+
+def ensemble_workload(count: int = 48, seed: int = 4):
+    """Batched-ensemble workload: `count` tori with r = 1 and R uniformly spaced in [1.3, 5], grids drawn
+    (counter-based, with `seed`) from ENSEMBLE_GRIDS, each with its own noise +-0.01 (seed 1000 + i).
+
+    Fluid parameters are the paper's phase-separation set (tau = M = 2.5e-3, A = 0.5, kappa = 5e-4,
+    Sec. 4) with rho = 1.  dt is left to the caller (each member's own stable step).
+    Returns a list of dicts with `params` (without dt) and the initial fields.
+    """
+    pick = uniform01(seed, count, 1)[:, 0]
+    out = []
+    for i in range(count):
+        nt, ns = ENSEMBLE_GRIDS[int(pick[i] * len(ENSEMBLE_GRIDS))]
+        R = 1.3 + i * (5.0 - 1.3) / max(count - 1, 1)
+        p = dict(geometry=0, R=R, r=1.0, n_theta=nt, n_phi=ns, tau=2.5e-3, M=2.5e-3, A=0.5, kappa=5e-4,
+                 advection=0, ch_mode=0)
+        phi = noise(1000 + i, nt, ns, 0.01)
+        z = np.zeros_like(phi)
+        out.append(dict(params=p, rho=np.ones_like(phi), ut=z, up=z.copy(), phi=phi))
+    return out

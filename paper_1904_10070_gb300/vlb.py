@@ -24,7 +24,8 @@ HYDRO, DIFFUSIVE = 0, 1
 EXPORTS = ["vlb_workspace_bytes", "vlb_max_stable_dt", "vlb_create", "vlb_destroy", "vlb_set_fields",
            "vlb_set_state", "vlb_get_state", "vlb_step", "vlb_get_fields", "vlb_get_totals",
            "vlb_interface_length", "vlb_state_device", "vlb_steps_done", "vlb_last_error",
-           "vlb_step_noalloc"]
+           "vlb_step_noalloc", "vlb_ensemble_workspace_bytes", "vlb_ensemble_create", "vlb_ensemble_step",
+           "vlb_ensemble_member", "vlb_ensemble_tile_rows"]
 
 NOALLOC_SCRATCH_BYTES = 24 * 1024 * 1024
 
@@ -80,6 +81,13 @@ def lib() -> ctypes.CDLL:
     L.vlb_last_error.argtypes, L.vlb_last_error.restype = [P], ctypes.c_char_p
     L.vlb_step_noalloc.argtypes = [PP, P, I64, ctypes.c_double, I64, P, ctypes.POINTER(ctypes.c_char_p)]
     L.vlb_step_noalloc.restype = I32
+    L.vlb_ensemble_workspace_bytes.argtypes, L.vlb_ensemble_workspace_bytes.restype = [PP, I32], S
+    L.vlb_ensemble_create.argtypes, L.vlb_ensemble_create.restype = [PP, I32, P, S, P, ctypes.POINTER(P)], I32
+    L.vlb_ensemble_step.argtypes, L.vlb_ensemble_step.restype = [P, I64], I32
+    L.vlb_ensemble_member.argtypes, L.vlb_ensemble_member.restype = [P, I32, ctypes.POINTER(P)], I32
+    F = ctypes.POINTER(ctypes.c_float)
+    L.vlb_ensemble_tile_rows.argtypes = [P, ctypes.POINTER(I32), F, F]
+    L.vlb_ensemble_tile_rows.restype = I32
     _lib = L
     return L
 
@@ -179,6 +187,61 @@ def vlb_step_noalloc(p: vlb_params, state_ptr: int, stride: int, n0: float, nste
                                 ctypes.c_void_p(stream_ptr), ctypes.byref(err))
     if st != VLB_OK:
         raise VlbError(st, (err.value or b"").decode())
+
+
+def _param_array(members):
+    arr = (vlb_params * len(members))()
+    for i, m in enumerate(members):
+        arr[i] = m
+    return arr
+
+
+def vlb_ensemble_workspace_bytes(members) -> int:
+    return lib().vlb_ensemble_workspace_bytes(_param_array(members), len(members))
+
+
+class Ensemble:
+    """An ensemble handle, its torch-allocated workspace and one view per member."""
+
+    def __init__(self, members, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("vlb.Ensemble needs a CUDA device")
+        arr = _param_array(members)
+        self.params = list(members)
+        self.nbytes = lib().vlb_ensemble_workspace_bytes(arr, len(members))
+        if self.nbytes == 0:
+            _check(VLB_ERR_ARG)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.workspace = torch.empty(self.nbytes, dtype=torch.uint8, device="cuda")
+        self.h = ctypes.c_void_p()
+        _check(lib().vlb_ensemble_create(arr, len(members), ctypes.c_void_p(self.workspace.data_ptr()), self.nbytes,
+                                         ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self.h)))
+        self.views = []
+        for i in range(len(members)):
+            v = ctypes.c_void_p()
+            _check(lib().vlb_ensemble_member(self.h, i, ctypes.byref(v)), self.h)
+            self.views.append(v)
+
+    def step(self, n: int):
+        _check(lib().vlb_ensemble_step(self.h, n), self.h)
+
+    def tile_rows(self):
+        rows = ctypes.c_int32()
+        a, b = ctypes.c_float(), ctypes.c_float()
+        _check(lib().vlb_ensemble_tile_rows(self.h, ctypes.byref(rows), ctypes.byref(a), ctypes.byref(b)), self.h)
+        return rows.value, a.value, b.value
+
+    def close(self):
+        if self.h is not None:
+            vlb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Solver:
