@@ -170,6 +170,60 @@ vlb_status vlb_ensemble_member(vlb_handle* h, int32_t idx, vlb_handle** view);
  * time of one first-stage launch for each candidate (ms; either pointer may be NULL). */
 vlb_status vlb_ensemble_tile_rows(const vlb_handle* h, int32_t* rows, float* ms16, float* ms8);
 
+/* ---- Snapshots: device FP32 [N][4] = (phi, n, u_theta, u_phi), node-major ----
+ * vlb_get_snapshot: moments of the state (Sec. 2.3) and phi; asynchronous on the handle's stream.
+ * vlb_set_snapshot: f := f^eq(n, u) (Eq. feq) and phi := phi (the restart after a surrogate window,
+ * which drops the non-equilibrium part of f); if conserve != NULL, uniform shifts of n and phi then
+ * restore sum n sqrt(g) dtheta dvarphi = conserve[0] and sum phi sqrt(g) dtheta dvarphi = conserve[1].
+ * Synchronous. */
+vlb_status vlb_get_snapshot(vlb_handle* h, float* d_snap);
+vlb_status vlb_set_snapshot(vlb_handle* h, const float* d_snap, const double* conserve);
+
+/* ---- Surrogate network kernels (not in the paper) ----
+ * A periodic-padding CNN that stands in for blocks of solver steps.  Tensors are device NHWC
+ * [H][W][C] (H = N_theta rows, W = N_phi columns, W a multiple of 128), bf16 unless named f32;
+ * weights [C_out][3][3][C_in] bf16, biases f32.  Supported (C_in, C_out): (16, 64), (64, 64),
+ * (64, 16).  All calls are asynchronous on cuda_stream and accumulate in FP32 on the tensor cores.
+ *
+ * y = act(conv3x3(x, w) + bias): tap t = 3 (dy + 1) + (dx + 1) reads x at (y + dy, x + dx) mod
+ * (H, W); bias may be NULL; relu != 0 clamps at 0; if mask != NULL (same shape as y) outputs where
+ * mask <= 0 are zeroed; y_bf16 and/or y_f32 receive the result.
+ * Backward data of a layer is this call on dY with the flipped weights of vlb_conv3x3_flip
+ * (w'[ci][8 - t][co] = w[co][t][ci]) and mask = the layer's input activation (ReLU derivative). */
+vlb_status vlb_conv3x3_fwd(int32_t H, int32_t W, int32_t cin, int32_t cout, const void* x, const void* w,
+                           const float* bias, const void* mask, int32_t relu, void* y_bf16, float* y_f32,
+                           void* cuda_stream);
+vlb_status vlb_conv3x3_flip(int32_t cin, int32_t cout, const void* w, void* w_flipped, void* cuda_stream);
+/* dw[co][t][ci] = sum_p dy[p][co] x[p + d_t][ci] and db[co] = sum_p dy[p][co] (db may be NULL), in
+ * FP32, with partial sums reduced in a fixed order; workspace of vlb_conv3x3_wgrad_workspace_bytes. */
+size_t vlb_conv3x3_wgrad_workspace_bytes(int32_t H, int32_t W, int32_t cin, int32_t cout);
+vlb_status vlb_conv3x3_bwd_weight(int32_t H, int32_t W, int32_t cin, int32_t cout, const void* x, const void* dy,
+                                  float* dw, float* db, void* workspace, size_t bytes, void* cuda_stream);
+/* Scratch (bytes) that vlb_channel_sums and vlb_mse_loss need in d_work. */
+size_t vlb_reduce_workspace_bytes(void);
+/* Network input from a snapshot: 16 bf16 channels per node -- phi, (n - 1)/s_n, u_theta/s_u,
+ * u_phi/s_u, J = 1 + a cos theta (sqrt(g)/(r R)), R Gamma = sin theta / J, sin theta, cos theta, 1/J,
+ * a = r/R, then zeros (App. A geometry; row q has theta = 2 pi q / H). */
+vlb_status vlb_surrogate_features(int32_t H, int32_t W, double r_over_R, const float* snap, float s_n, float s_u,
+                                  void* out_bf16, void* cuda_stream);
+/* target[p][c] = (after[p][c] - before[p][c]) / scale[c] for the 4 snapshot channels. */
+vlb_status vlb_surrogate_targets(int64_t npix, const float* before, const float* after, const float scale[4],
+                                 float* target, void* cuda_stream);
+/* after[p][c] = before[p][c] + scale[c] * pred16[p][c] (first 4 of 16 f32 channels). */
+vlb_status vlb_surrogate_apply(int64_t npix, const float* before, const float* pred16, const float scale[4],
+                               float* after, void* cuda_stream);
+/* d_out[c] = sum_p x[p][c], d_out[C + c] = sum_p x[p][c]^2 in FP64 (C <= 16). */
+vlb_status vlb_channel_sums(int64_t npix, int32_t C, const float* x, double* d_work, double* d_out, void* cuda_stream);
+/* *d_loss = mean over p and c < 4 of (pred16[p][c] - target4[p][c])^2 (FP64); if grad16_bf16 != NULL
+ * it receives d loss / d pred (zero in channels 4..15). */
+vlb_status vlb_mse_loss(int64_t npix, const float* pred16, const float* target4, void* grad16_bf16, double* d_work,
+                        double* d_loss, void* cuda_stream);
+/* One Adam step (Kingma & Ba 2015, step t >= 1) on FP32 parameters; p_bf16 (may be NULL) receives
+ * the updated parameters rounded to bf16. */
+vlb_status vlb_adam_step(int64_t n, float* p, const float* g, float* m, float* v, int64_t t, float lr, float b1,
+                         float b2, float eps, void* p_bf16, void* cuda_stream);
+vlb_status vlb_to_bf16(int64_t n, const float* x, void* y, void* cuda_stream);
+
 /* Fixed size, in bytes, of the device scratch that vlb_step_noalloc uses. */
 #define VLB_NOALLOC_SCRATCH_BYTES (24u * 1024u * 1024u)
 

@@ -195,6 +195,47 @@ __global__ void totals_final_kernel(const double* partials, int nb, double* out)
   out[k] = x;
 }
 
+// (phi, n, u_theta, u_phi) per node, from the state, in FP32.
+template <typename T>
+__global__ void snapshot_out_kernel(const T* state, int64_t stride, int64_t n, double n0, float* snap, VD vd) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    double nn, a, b;
+    node_moments(state, stride, idx, vd, n0, nn, a, b);
+    reinterpret_cast<float4*>(snap)[idx] =
+        make_float4((float)load_phi(state, stride, idx), (float)nn, (float)a, (float)b);
+  }
+}
+
+// f := f^eq(n, u) (Eq. feq), phi := phi from a snapshot (the surrogate restart).
+template <typename T>
+__global__ void snapshot_in_kernel(T* state, int64_t stride, int64_t n, double n0, const float* snap, VD vd) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    const float4 s = reinterpret_cast<const float4*>(snap)[idx];
+    const double nn = s.y, a = s.z, b = s.w;
+    const double usq = a * a + b * b;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const double xi = vd.v[i] * a + vd.v[j] * b;
+        const double pm1 = xi + 0.5 * (xi * xi - usq) + xi * (xi * xi - 3.0 * usq) / 6.0;
+        state[(4 * i + j) * stride + idx] = (T)(vd.w[i] * vd.w[j] * ((nn - n0) + nn * pm1));
+      }
+    store_phi(state, stride, idx, (double)s.x);
+  }
+}
+
+// Uniform shifts: n += dn at rest (f_k += w_i w_j dn), phi += dphi.
+template <typename T>
+__global__ void shift_kernel(T* state, int64_t stride, int64_t n, double dn, double dphi, VD vd) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < NPOP; ++k) state[k * stride + idx] = (T)((double)state[k * stride + idx] +
+                                                                  vd.w[k >> 2] * vd.w[k & 3] * dn);
+    store_phi(state, stride, idx, load_phi(state, stride, idx) + dphi);
+  }
+}
+
 int grid_for(int64_t n) {
   int64_t g = (n + 255) / 256;
   if (g > 152 * 16) g = 152 * 16;
@@ -250,6 +291,24 @@ cudaError_t launch_totals(const T* state, int64_t stride, const double* coefd, i
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_snapshot_out(const T* state, int64_t stride, int64_t n, double n0, float* snap, cudaStream_t s) {
+  snapshot_out_kernel<T><<<grid_for(n), 256, 0, s>>>(state, stride, n, n0, snap, make_vd());
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_snapshot_in(T* state, int64_t stride, int64_t n, double n0, const float* snap, cudaStream_t s) {
+  snapshot_in_kernel<T><<<grid_for(n), 256, 0, s>>>(state, stride, n, n0, snap, make_vd());
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_shift(T* state, int64_t stride, int64_t n, double dn, double dphi, cudaStream_t s) {
+  shift_kernel<T><<<grid_for(n), 256, 0, s>>>(state, stride, n, dn, dphi, make_vd());
+  return cudaGetLastError();
+}
+
 #define VLB_INST(T)                                                                                              \
   template cudaError_t launch_init_feq<T>(T*, int64_t, const double*, const double*, const double*,              \
                                           const double*, int64_t, double, cudaStream_t);                          \
@@ -258,7 +317,10 @@ cudaError_t launch_totals(const T* state, int64_t stride, const double* coefd, i
   template cudaError_t launch_fields<T>(const T*, int64_t, const double*, int, int, double, double, double,     \
                                         double*, double*, double*, double*, double*, cudaStream_t);               \
   template cudaError_t launch_totals<T>(const T*, int64_t, const double*, int, int, double, double, double,      \
-                                        double, double, int, double*, int, double*, cudaStream_t);
+                                        double, double, int, double*, int, double*, cudaStream_t);               \
+  template cudaError_t launch_snapshot_out<T>(const T*, int64_t, int64_t, double, float*, cudaStream_t);        \
+  template cudaError_t launch_snapshot_in<T>(T*, int64_t, int64_t, double, const float*, cudaStream_t);         \
+  template cudaError_t launch_shift<T>(T*, int64_t, int64_t, double, double, cudaStream_t);
 VLB_INST(float)
 VLB_INST(double)
 #undef VLB_INST

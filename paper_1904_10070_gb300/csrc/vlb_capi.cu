@@ -907,3 +907,132 @@ vlb_status vlb_ensemble_tile_rows(const vlb_handle* h, int32_t* rows, float* ms1
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------------------
+// Snapshots (device FP32 (phi, n, u_theta, u_phi)) and the surrogate network's kernels.
+// ------------------------------------------------------------------------------------------------
+extern "C" {
+
+vlb_status vlb_get_snapshot(vlb_handle* h, float* d_snap) {
+  vlb_status st = check_handle(h);
+  if (st) return st;
+  if (!d_snap) return fail(h, VLB_ERR_ARG, "snapshot pointer is NULL");
+  if (h->esize == 8)
+    VLB_CUDA(h, vlb::launch_snapshot_out<double>((const double*)h->U[0], h->stride, h->N, h->n0, d_snap, h->stream));
+  else
+    VLB_CUDA(h, vlb::launch_snapshot_out<float>((const float*)h->U[0], h->stride, h->N, h->n0, d_snap, h->stream));
+  return VLB_OK;
+}
+
+vlb_status vlb_set_snapshot(vlb_handle* h, const float* d_snap, const double* conserve) {
+  vlb_status st = check_handle(h);
+  if (st) return st;
+  if (!d_snap) return fail(h, VLB_ERR_ARG, "snapshot pointer is NULL");
+  if (h->esize == 8)
+    VLB_CUDA(h, vlb::launch_snapshot_in<double>((double*)h->U[0], h->stride, h->N, h->n0, d_snap, h->stream));
+  else
+    VLB_CUDA(h, vlb::launch_snapshot_in<float>((float*)h->U[0], h->stride, h->N, h->n0, d_snap, h->stream));
+  if (conserve) {
+    double t[4];
+    if ((st = vlb_get_totals(h, t))) return st;
+    const vlb_params& p = h->p;
+    const double area = p.geometry == VLB_TORUS ? 4.0 * M_PI * M_PI * p.r * p.R : 4.0 * M_PI * M_PI * p.r * p.R;
+    const double dn = (conserve[0] - t[0]) / area, dphi = (conserve[1] - t[1]) / area;
+    if (h->esize == 8)
+      VLB_CUDA(h, vlb::launch_shift<double>((double*)h->U[0], h->stride, h->N, dn, dphi, h->stream));
+    else
+      VLB_CUDA(h, vlb::launch_shift<float>((float*)h->U[0], h->stride, h->N, dn, dphi, h->stream));
+  }
+  VLB_CUDA(h, cudaStreamSynchronize(h->stream));
+  return VLB_OK;
+}
+
+vlb_status vlb_conv3x3_fwd(int32_t H, int32_t W, int32_t cin, int32_t cout, const void* x, const void* w,
+                           const float* bias, const void* mask, int32_t relu, void* y_bf16, float* y_f32,
+                           void* cuda_stream) {
+  const char* why = nullptr;
+  if (!vlb::conv_shape_ok(H, W, cin, cout, &why)) return fail(nullptr, VLB_ERR_ARG, "vlb_conv3x3_fwd: %s", why);
+  if (!x || !w || (!y_bf16 && !y_f32)) return fail(nullptr, VLB_ERR_ARG, "vlb_conv3x3_fwd: NULL tensor");
+  VLB_CUDA(nullptr, vlb::conv_fwd(H, W, cin, cout, x, w, bias, mask, relu, y_bf16, y_f32, (cudaStream_t)cuda_stream));
+  return VLB_OK;
+}
+
+vlb_status vlb_conv3x3_flip(int32_t cin, int32_t cout, const void* w, void* w_flipped, void* cuda_stream) {
+  if (!w || !w_flipped || cin < 1 || cout < 1) return fail(nullptr, VLB_ERR_ARG, "vlb_conv3x3_flip: bad argument");
+  VLB_CUDA(nullptr, vlb::conv_flip(cin, cout, w, w_flipped, (cudaStream_t)cuda_stream));
+  return VLB_OK;
+}
+
+size_t vlb_conv3x3_wgrad_workspace_bytes(int32_t H, int32_t W, int32_t cin, int32_t cout) {
+  const char* why = nullptr;
+  if (!vlb::conv_shape_ok(H, W, cin, cout, &why)) return 0;
+  return vlb::conv_wgrad_workspace_bytes(H, W, cin, cout);
+}
+
+vlb_status vlb_conv3x3_bwd_weight(int32_t H, int32_t W, int32_t cin, int32_t cout, const void* x, const void* dy,
+                                  float* dw, float* db, void* workspace, size_t bytes, void* cuda_stream) {
+  const char* why = nullptr;
+  if (!vlb::conv_shape_ok(H, W, cin, cout, &why)) return fail(nullptr, VLB_ERR_ARG, "vlb_conv3x3_bwd_weight: %s", why);
+  if (!x || !dy || !dw || !workspace) return fail(nullptr, VLB_ERR_ARG, "vlb_conv3x3_bwd_weight: NULL tensor");
+  if (bytes < vlb::conv_wgrad_workspace_bytes(H, W, cin, cout))
+    return fail(nullptr, VLB_ERR_WORKSPACE, "vlb_conv3x3_bwd_weight: workspace too small");
+  VLB_CUDA(nullptr, vlb::conv_wgrad(H, W, cin, cout, x, dy, dw, db, (float*)workspace, (cudaStream_t)cuda_stream));
+  return VLB_OK;
+}
+
+size_t vlb_reduce_workspace_bytes(void) { return sizeof(double) * vlb::sur_reduce_doubles(); }
+
+vlb_status vlb_surrogate_features(int32_t H, int32_t W, double r_over_R, const float* snap, float s_n, float s_u,
+                                  void* out_bf16, void* cuda_stream) {
+  if (H < 1 || W < 1 || !snap || !out_bf16 || !(s_n > 0.0f) || !(s_u > 0.0f))
+    return fail(nullptr, VLB_ERR_ARG, "vlb_surrogate_features: bad argument");
+  VLB_CUDA(nullptr, vlb::sur_features(H, W, r_over_R, snap, s_n, s_u, out_bf16, (cudaStream_t)cuda_stream));
+  return VLB_OK;
+}
+
+vlb_status vlb_surrogate_targets(int64_t npix, const float* before, const float* after, const float scale[4],
+                                 float* target, void* cuda_stream) {
+  if (npix < 1 || !before || !after || !scale || !target)
+    return fail(nullptr, VLB_ERR_ARG, "vlb_surrogate_targets: bad argument");
+  VLB_CUDA(nullptr, vlb::sur_targets(npix, before, after, scale, target, (cudaStream_t)cuda_stream));
+  return VLB_OK;
+}
+
+vlb_status vlb_surrogate_apply(int64_t npix, const float* before, const float* pred16, const float scale[4],
+                               float* after, void* cuda_stream) {
+  if (npix < 1 || !before || !pred16 || !scale || !after)
+    return fail(nullptr, VLB_ERR_ARG, "vlb_surrogate_apply: bad argument");
+  VLB_CUDA(nullptr, vlb::sur_apply(npix, before, pred16, scale, after, (cudaStream_t)cuda_stream));
+  return VLB_OK;
+}
+
+vlb_status vlb_channel_sums(int64_t npix, int32_t C, const float* x, double* d_work, double* d_out,
+                            void* cuda_stream) {
+  if (npix < 1 || C < 1 || C > 16 || !x || !d_work || !d_out)
+    return fail(nullptr, VLB_ERR_ARG, "vlb_channel_sums: bad argument");
+  VLB_CUDA(nullptr, vlb::sur_stats(npix, C, x, d_work, d_out, (cudaStream_t)cuda_stream));
+  return VLB_OK;
+}
+
+vlb_status vlb_mse_loss(int64_t npix, const float* pred16, const float* target4, void* grad16_bf16, double* d_work,
+                        double* d_loss, void* cuda_stream) {
+  if (npix < 1 || !pred16 || !target4 || !d_work || !d_loss)
+    return fail(nullptr, VLB_ERR_ARG, "vlb_mse_loss: bad argument");
+  VLB_CUDA(nullptr, vlb::sur_mse(npix, pred16, target4, grad16_bf16, d_work, d_loss, (cudaStream_t)cuda_stream));
+  return VLB_OK;
+}
+
+vlb_status vlb_adam_step(int64_t n, float* p, const float* g, float* m, float* v, int64_t t, float lr, float b1,
+                         float b2, float eps, void* p_bf16, void* cuda_stream) {
+  if (n < 1 || !p || !g || !m || !v || t < 1) return fail(nullptr, VLB_ERR_ARG, "vlb_adam_step: bad argument");
+  VLB_CUDA(nullptr, vlb::sur_adam(n, p, g, m, v, t, lr, b1, b2, eps, p_bf16, (cudaStream_t)cuda_stream));
+  return VLB_OK;
+}
+
+vlb_status vlb_to_bf16(int64_t n, const float* x, void* y, void* cuda_stream) {
+  if (n < 1 || !x || !y) return fail(nullptr, VLB_ERR_ARG, "vlb_to_bf16: bad argument");
+  VLB_CUDA(nullptr, vlb::sur_to_bf16(n, x, y, (cudaStream_t)cuda_stream));
+  return VLB_OK;
+}
+
+}  // extern "C"

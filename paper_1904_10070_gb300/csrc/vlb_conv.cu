@@ -1,0 +1,341 @@
+// 3x3 periodic convolutions on BF16 NHWC tensors with FP32 accumulation on the tensor cores
+// (mma.sync m16n8k16), for the learned surrogate that stands in for blocks of solver steps.
+//
+// Layouts: activations [H][W][C] (C contiguous), weights [C_out][3][3][C_in], both bf16; the torus
+// is periodic in both directions, so the padding wraps.  Tap t = 3 (dy + 1) + (dx + 1) reads the
+// input at (y + dy, x + dx).
+//
+//   forward        Y[p][co] = act( sum_{t,ci} X[p + d_t][ci] W[co][t][ci] + b[co] )
+//   backward data  dX[p][ci] = mask(p, ci) * sum_{t,co} dY[p - d_t][co] W[co][t][ci]
+//                  = a forward convolution of dY with W'[ci][8 - t][co] (vlb_conv3x3_flip)
+//   backward wts   dW[co][t][ci] = sum_p dY[p][co] X[p + d_t][ci],  db[co] = sum_p dY[p][co]
+//
+// Forward tiling: a CTA (4 warps) owns 128 consecutive pixels of one row; the 3 x 130 x C_in input
+// patch is staged in shared memory with cp.async (pixel stride C_in + 8 elements, so the eight
+// 16-byte rows of an ldmatrix land in different bank groups); each warp computes 32 pixels x C_out.
+// Weight fragments are read from global memory (all weights of a layer fit in L1).
+// Weight gradient: a CTA (4 warps) owns one tap and a group of row segments; per segment it stages
+// the shifted input row and dY in shared memory and accumulates dY^T X_t with both operands loaded
+// by ldmatrix.trans; per-group partial sums are reduced in a fixed order by a second kernel.
+#include <cuda_bf16.h>
+
+#include "vlb_internal.cuh"
+
+namespace vlb {
+
+namespace {
+
+constexpr int CPX = 128;  // pixels per CTA (one row segment)
+constexpr int NWARP = 4;
+constexpr int NTHR = NWARP * 32;
+constexpr int WG_SEGS = 16;  // row segments per weight-gradient CTA
+
+using bf16 = __nv_bfloat16;
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void cp16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(src));
+}
+
+__device__ __forceinline__ void cp_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::);
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void ldsm4(uint32_t (&r)[4], const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(smem_addr(p)));
+}
+
+__device__ __forceinline__ void ldsm4t(uint32_t (&r)[4], const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(smem_addr(p)));
+}
+
+__device__ __forceinline__ uint32_t ldg32(const bf16* p) { return __ldg(reinterpret_cast<const unsigned int*>(p)); }
+
+template <int CIN>
+constexpr size_t fwd_smem() {
+  return sizeof(bf16) * 3 * (CPX + 2) * (CIN + 8);
+}
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(NTHR) conv_fwd_kernel(int H, int W, const bf16* __restrict__ x,
+                                                        const bf16* __restrict__ w, const float* __restrict__ bias,
+                                                        const bf16* __restrict__ mask, int relu, bf16* y, float* yf) {
+  constexpr int PS = CIN + 8, PW = CPX + 2, CH = CIN / 8, NT = COUT / 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  bf16* patch = reinterpret_cast<bf16*>(smem_raw);
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  const int segs = W / CPX;
+  const int row = blockIdx.x / segs, x0 = (blockIdx.x % segs) * CPX;
+  for (int idx = tid; idx < 3 * PW * CH; idx += NTHR) {
+    const int pr = idx / (PW * CH), rem = idx - pr * (PW * CH);
+    const int pc = rem / CH, ch = rem - pc * CH;
+    int gy = row + pr - 1;
+    gy += gy < 0 ? H : (gy >= H ? -H : 0);
+    int gx = x0 + pc - 1;
+    gx += gx < 0 ? W : (gx >= W ? -W : 0);
+    cp16(patch + (pr * PW + pc) * PS + ch * 8, x + ((size_t)gy * W + gx) * CIN + ch * 8);
+  }
+  cp_wait_all();
+  __syncthreads();
+
+  const int g = lane / 4, t4 = lane % 4;
+  const int px0 = warp * 32;
+  float acc[2][NT][4];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.0f;
+  // ldmatrix row address of this lane: matrix j = lane / 8 covers A rows 8 (j % 2).. and k 8 (j / 2)..
+  const int arow = (lane % 8) + 8 * ((lane / 8) % 2), akof = 8 * (lane / 16);
+#pragma unroll 1
+  for (int tap = 0; tap < 9; ++tap) {
+    const int dy = tap / 3, dx = tap % 3;
+#pragma unroll
+    for (int c0 = 0; c0 < CIN; c0 += 16) {
+      uint32_t a[2][4];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+        ldsm4(a[mt], patch + (dy * PW + px0 + mt * 16 + arow + dx) * PS + c0 + akof);
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt) {
+        const bf16* wp = w + ((size_t)(nt * 8 + g) * 9 + tap) * CIN + c0 + 2 * t4;
+        const uint32_t b0 = ldg32(wp), b1 = ldg32(wp + 8);
+        mma16816(acc[0][nt], a[0], b0, b1);
+        mma16816(acc[1][nt], a[1], b0, b1);
+      }
+    }
+  }
+  // epilogue: acc[mt][nt][2h + e] is pixel px0 + 16 mt + g + 8 h, channel 8 nt + 2 t4 + e
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const size_t p = (size_t)row * W + x0 + px0 + mt * 16 + g + 8 * h;
+        const int co = nt * 8 + 2 * t4;
+        float v0 = acc[mt][nt][2 * h], v1 = acc[mt][nt][2 * h + 1];
+        if (bias) {
+          v0 += bias[co];
+          v1 += bias[co + 1];
+        }
+        if (relu) {
+          v0 = fmaxf(v0, 0.0f);
+          v1 = fmaxf(v1, 0.0f);
+        }
+        if (mask) {
+          const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162*>(mask + p * COUT + co);
+          if (!(__bfloat162float(m.x) > 0.0f)) v0 = 0.0f;
+          if (!(__bfloat162float(m.y) > 0.0f)) v1 = 0.0f;
+        }
+        if (y) *reinterpret_cast<__nv_bfloat162*>(y + p * COUT + co) = __floats2bfloat162_rn(v0, v1);
+        if (yf) *reinterpret_cast<float2*>(yf + p * COUT + co) = make_float2(v0, v1);
+      }
+}
+
+// W'[ci][8 - t][co] = W[co][t][ci]
+__global__ void flip_kernel(int cin, int cout, const bf16* w, bf16* wf) {
+  const int n = cout * 9 * cin;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int co = i / (9 * cin), rem = i - co * 9 * cin, t = rem / cin, ci = rem - t * cin;
+    wf[((size_t)ci * 9 + (8 - t)) * cout + co] = w[i];
+  }
+}
+
+template <int CIN, int COUT>
+constexpr size_t wg_smem() {
+  return sizeof(bf16) * CPX * ((CIN + 8) + (COUT + 8));
+}
+
+// Partial weight gradients of tap blockIdx.y over the row segments of group blockIdx.x.
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(NTHR) conv_wgrad_kernel(int H, int W, const bf16* __restrict__ x,
+                                                          const bf16* __restrict__ dy, float* partial) {
+  constexpr int XS = CIN + 8, DS = COUT + 8, MT = COUT / 16, NT8 = CIN / 8;
+  // warps split the (m-tile, n-tile pair) grid: MT m-tiles x NT8/2 n-pairs
+  constexpr int WORK = MT * (NT8 / 2);
+  constexpr int PER = (WORK + NWARP - 1) / NWARP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  bf16* xs = reinterpret_cast<bf16*>(smem_raw);
+  bf16* ds = xs + CPX * XS;
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  const int tap = blockIdx.y, ddy = tap / 3 - 1, ddx = tap % 3 - 1;
+  const int segs_row = W / CPX, nseg = H * segs_row;
+  float acc[PER][2][4];
+#pragma unroll
+  for (int u = 0; u < PER; ++u)
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[u][h][e] = 0.0f;
+  const int j = lane / 8, i8 = lane % 8;
+#pragma unroll 1
+  for (int sg = blockIdx.x * WG_SEGS; sg < (blockIdx.x + 1) * WG_SEGS && sg < nseg; ++sg) {
+    const int row = sg / segs_row, x0 = (sg % segs_row) * CPX;
+    int gy = row + ddy;
+    gy += gy < 0 ? H : (gy >= H ? -H : 0);
+    __syncthreads();  // the previous segment's tiles are consumed
+    for (int idx = tid; idx < CPX * (CIN / 8); idx += NTHR) {
+      const int pc = idx / (CIN / 8), ch = idx - pc * (CIN / 8);
+      int gx = x0 + pc + ddx;
+      gx += gx < 0 ? W : (gx >= W ? -W : 0);
+      cp16(xs + pc * XS + ch * 8, x + ((size_t)gy * W + gx) * CIN + ch * 8);
+    }
+    for (int idx = tid; idx < CPX * (COUT / 8); idx += NTHR) {
+      const int pc = idx / (COUT / 8), ch = idx - pc * (COUT / 8);
+      cp16(ds + pc * DS + ch * 8, dy + ((size_t)row * W + x0 + pc) * COUT + ch * 8);
+    }
+    cp_wait_all();
+    __syncthreads();
+#pragma unroll 1
+    for (int kb = 0; kb < CPX; kb += 16) {
+#pragma unroll
+      for (int u = 0; u < PER; ++u) {
+        const int wi = warp + NWARP * u;
+        if (wi < WORK) {
+          const int mt = wi % MT, np = wi / MT;
+          uint32_t a[4], b[4];
+          // A = dY^T (m = co, k = pixel) from ds[pixel][co]: blocks (k 0-7|8-15, m 0-7|8-15)
+          ldsm4t(a, ds + (kb + i8 + 8 * (j / 2)) * DS + mt * 16 + 8 * (j % 2));
+          // B = X_t (k = pixel, n = ci) from xs[pixel][ci]: blocks (k 0-7|8-15, n 0-7|8-15)
+          ldsm4t(b, xs + (kb + i8 + 8 * (j % 2)) * XS + np * 16 + 8 * (j / 2));
+          mma16816(acc[u][0], a, b[0], b[1]);
+          mma16816(acc[u][1], a, b[2], b[3]);
+        }
+      }
+    }
+  }
+  // partial[group][tap][co][ci]
+  const int g = lane / 4, t4 = lane % 4;
+  float* out = partial + ((size_t)blockIdx.x * 9 + tap) * COUT * CIN;
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int wi = warp + NWARP * u;
+    if (wi < WORK) {
+      const int mt = wi % MT, np = wi / MT;
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const int co = mt * 16 + g + 8 * r, ci = np * 16 + 8 * h + 2 * t4;
+          out[co * CIN + ci] = acc[u][h][2 * r];
+          out[co * CIN + ci + 1] = acc[u][h][2 * r + 1];
+        }
+    }
+  }
+}
+
+// dW[co][t][ci] = sum over groups (fixed order) of partial[group][t][co][ci]
+__global__ void wgrad_reduce_kernel(int groups, int cin, int cout, const float* partial, float* dw) {
+  const int n = 9 * cout * cin;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int t = i / (cout * cin), rem = i - t * cout * cin, co = rem / cin, ci = rem - co * cin;
+    float s = 0.0f;
+    for (int gp = 0; gp < groups; ++gp) s += partial[(size_t)gp * n + i];
+    dw[((size_t)co * 9 + t) * cin + ci] = s;
+  }
+}
+
+// db[co] = sum_p dY[p][co]: one block per channel, fixed-order tree
+__global__ void bias_grad_kernel(int npix, int cout, const bf16* dy, float* db) {
+  __shared__ float red[256];
+  const int co = blockIdx.x;
+  float s = 0.0f;
+  for (int p = threadIdx.x; p < npix; p += blockDim.x) s += __bfloat162float(dy[(size_t)p * cout + co]);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) db[co] = red[0];
+}
+
+template <typename K>
+cudaError_t allow_smem(K kernel, size_t bytes) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int CIN, int COUT>
+cudaError_t fwd_launch(int H, int W, const void* x, const void* w, const float* b, const void* mask, int relu, void* y,
+                       float* yf, cudaStream_t st) {
+  constexpr size_t S = fwd_smem<CIN>();
+  cudaError_t e = allow_smem(conv_fwd_kernel<CIN, COUT>, S);
+  if (e != cudaSuccess) return e;
+  conv_fwd_kernel<CIN, COUT><<<H * (W / CPX), NTHR, S, st>>>(H, W, (const bf16*)x, (const bf16*)w, b,
+                                                             (const bf16*)mask, relu, (bf16*)y, yf);
+  return cudaGetLastError();
+}
+
+template <int CIN, int COUT>
+cudaError_t wg_launch(int H, int W, const void* x, const void* dy, float* partial, float* dw, cudaStream_t st) {
+  constexpr size_t S = wg_smem<CIN, COUT>();
+  cudaError_t e = allow_smem(conv_wgrad_kernel<CIN, COUT>, S);
+  if (e != cudaSuccess) return e;
+  const int groups = (H * (W / CPX) + WG_SEGS - 1) / WG_SEGS;
+  conv_wgrad_kernel<CIN, COUT><<<dim3(groups, 9), NTHR, S, st>>>(H, W, (const bf16*)x, (const bf16*)dy, partial);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  wgrad_reduce_kernel<<<(9 * CIN * COUT + 255) / 256, 256, 0, st>>>(groups, CIN, COUT, partial, dw);
+  return cudaGetLastError();
+}
+
+bool shape_ok(int H, int W, int cin, int cout, const char** why) {
+  if (H < 1 || W < CPX || W % CPX != 0) return *why = "W must be a positive multiple of 128", false;
+  if (!((cin == 16 && cout == 64) || (cin == 64 && cout == 64) || (cin == 64 && cout == 16)))
+    return *why = "(c_in, c_out) must be (16, 64), (64, 64) or (64, 16)", false;
+  return true;
+}
+
+}  // namespace
+
+size_t conv_wgrad_workspace_bytes(int H, int W, int cin, int cout) {
+  const int groups = (H * (W / CPX) + WG_SEGS - 1) / WG_SEGS;
+  return sizeof(float) * (size_t)groups * 9 * cin * cout;
+}
+
+cudaError_t conv_fwd(int H, int W, int cin, int cout, const void* x, const void* w, const float* b, const void* mask,
+                     int relu, void* y, float* yf, cudaStream_t st) {
+  if (cin == 16) return fwd_launch<16, 64>(H, W, x, w, b, mask, relu, y, yf, st);
+  if (cout == 64) return fwd_launch<64, 64>(H, W, x, w, b, mask, relu, y, yf, st);
+  return fwd_launch<64, 16>(H, W, x, w, b, mask, relu, y, yf, st);
+}
+
+cudaError_t conv_flip(int cin, int cout, const void* w, void* wf, cudaStream_t st) {
+  flip_kernel<<<(9 * cin * cout + 255) / 256, 256, 0, st>>>(cin, cout, (const bf16*)w, (bf16*)wf);
+  return cudaGetLastError();
+}
+
+cudaError_t conv_wgrad(int H, int W, int cin, int cout, const void* x, const void* dy, float* dw, float* db,
+                       float* partial, cudaStream_t st) {
+  cudaError_t e;
+  if (cin == 16)
+    e = wg_launch<16, 64>(H, W, x, dy, partial, dw, st);
+  else if (cout == 64)
+    e = wg_launch<64, 64>(H, W, x, dy, partial, dw, st);
+  else
+    e = wg_launch<64, 16>(H, W, x, dy, partial, dw, st);
+  if (e != cudaSuccess || !db) return e;
+  bias_grad_kernel<<<cout, 256, 0, st>>>(H * W, cout, (const bf16*)dy, db);
+  return cudaGetLastError();
+}
+
+bool conv_shape_ok(int H, int W, int cin, int cout, const char** why) { return shape_ok(H, W, cin, cout, why); }
+
+}  // namespace vlb

@@ -107,4 +107,33 @@ cudaError_t launch_totals(const T* state, int64_t stride, const double* coefd, i
                           int n_blocks, double* out, cudaStream_t s);
 int totals_blocks();
 
+// Solver snapshots (vlb_aux.cu): FP32 [N][4] = (phi, n, u_theta, u_phi) on the device.
+template <typename T>
+cudaError_t launch_snapshot_out(const T* state, int64_t stride, int64_t n, double n0, float* snap, cudaStream_t s);
+template <typename T>
+cudaError_t launch_snapshot_in(T* state, int64_t stride, int64_t n, double n0, const float* snap, cudaStream_t s);
+template <typename T>
+cudaError_t launch_shift(T* state, int64_t stride, int64_t n, double dn, double dphi, cudaStream_t s);
+
+// Surrogate network kernels (vlb_conv.cu, vlb_surrogate.cu).
+bool conv_shape_ok(int H, int W, int cin, int cout, const char** why);
+size_t conv_wgrad_workspace_bytes(int H, int W, int cin, int cout);
+cudaError_t conv_fwd(int H, int W, int cin, int cout, const void* x, const void* w, const float* b, const void* mask,
+                     int relu, void* y, float* yf, cudaStream_t st);
+cudaError_t conv_flip(int cin, int cout, const void* w, void* wf, cudaStream_t st);
+cudaError_t conv_wgrad(int H, int W, int cin, int cout, const void* x, const void* dy, float* dw, float* db,
+                       float* partial, cudaStream_t st);
+cudaError_t sur_features(int H, int W, double a, const float* snap, float s_n, float s_u, void* out, cudaStream_t st);
+cudaError_t sur_targets(int64_t n, const float* before, const float* after, const float* scale4, float* target,
+                        cudaStream_t st);
+cudaError_t sur_apply(int64_t n, const float* before, const float* pred, const float* scale4, float* after,
+                      cudaStream_t st);
+cudaError_t sur_stats(int64_t n, int C, const float* x, double* part, double* out, cudaStream_t st);
+cudaError_t sur_mse(int64_t n, const float* pred, const float* target, void* grad, double* part, double* loss,
+                    cudaStream_t st);
+cudaError_t sur_adam(int64_t n, float* p, const float* g, float* m, float* v, int64_t t, float lr, float b1, float b2,
+                     float eps, void* pb, cudaStream_t st);
+cudaError_t sur_to_bf16(int64_t n, const float* x, void* y, cudaStream_t st);
+size_t sur_reduce_doubles();
+
 }  // namespace vlb

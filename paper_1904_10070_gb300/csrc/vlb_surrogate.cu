@@ -1,0 +1,198 @@
+// Kernels of the learned surrogate other than the convolutions: input features, training targets,
+// channel statistics, the MSE loss and its gradient, and the Adam update.  Snapshots are FP32
+// [H][W][4] arrays (phi, n, u_theta, u_phi) on the device; network tensors are NHWC.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include "vlb_internal.cuh"
+
+namespace vlb {
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+// Input channels: 0 phi, 1 (n - 1)/s_n, 2 u_theta/s_u, 3 u_phi/s_u, then the geometry of the row
+// (App. A): 4 J = 1 + a cos theta (sqrt(g)/(r R)), 5 R Gamma = sin theta / J (Eq. conn_torus),
+// 6 sin theta, 7 cos theta, 8 1/J, 9 a = r/R; 10-15 zero.
+__global__ void features_kernel(int H, int W, double a, const float* snap, float s_n, float s_u, bf16* out) {
+  const int64_t n = (int64_t)H * W;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(p / W);
+    const double th = 2.0 * 3.14159265358979323846 * q / H;
+    const double J = 1.0 + a * cos(th);
+    const float4 s = reinterpret_cast<const float4*>(snap)[p];
+    float c[16] = {s.x, (s.y - 1.0f) / s_n, s.z / s_u, s.w / s_u, (float)J, (float)(sin(th) / J), (float)sin(th),
+                   (float)cos(th), (float)(1.0 / J), (float)a, 0, 0, 0, 0, 0, 0};
+    __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(out + p * 16);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) o[k] = __floats2bfloat162_rn(c[2 * k], c[2 * k + 1]);
+  }
+}
+
+// target[p][c] = (after[p][c] - before[p][c]) / scale[c]
+__global__ void targets_kernel(int64_t n, const float* before, const float* after, float4 scale, float* target) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const float4 b = reinterpret_cast<const float4*>(before)[p], f = reinterpret_cast<const float4*>(after)[p];
+    reinterpret_cast<float4*>(target)[p] =
+        make_float4((f.x - b.x) / scale.x, (f.y - b.y) / scale.y, (f.z - b.z) / scale.z, (f.w - b.w) / scale.w);
+  }
+}
+
+// after[p][c] = before[p][c] + scale[c] * pred[p][c]  (pred: the first 4 of 16 FP32 channels)
+__global__ void apply_kernel(int64_t n, const float* before, const float* pred, float4 scale, float* after) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const float4 b = reinterpret_cast<const float4*>(before)[p];
+    const float4 d = *reinterpret_cast<const float4*>(pred + p * 16);
+    reinterpret_cast<float4*>(after)[p] =
+        make_float4(b.x + scale.x * d.x, b.y + scale.y * d.y, b.z + scale.z * d.z, b.w + scale.w * d.w);
+  }
+}
+
+constexpr int RED_BLOCKS = 256;
+
+// per-block FP64 sums of x[p][c] and x[p][c]^2 for c < C (C <= 16)
+__global__ void stats_kernel(int64_t n, int C, const float* x, double* part) {
+  double s[16], s2[16];
+  for (int c = 0; c < 16; ++c) s[c] = s2[c] = 0.0;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
+    for (int c = 0; c < C; ++c) {
+      const double v = x[p * C + c];
+      s[c] += v;
+      s2[c] += v * v;
+    }
+  __shared__ double red[256];
+  for (int c = 0; c < 2 * C; ++c) {
+    red[threadIdx.x] = c < C ? s[c] : s2[c - C];
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x * 32 + c] = red[0];
+    __syncthreads();
+  }
+}
+
+__global__ void stats_final_kernel(int nb, int C, const double* part, double* out) {
+  const int c = threadIdx.x;
+  if (c >= 2 * C) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += part[b * 32 + c];
+  out[c] = s;
+}
+
+// loss partials of (pred[p][c] - target[p][c])^2 over c < 4; grad[p][c] = 2 (pred - target) / (4 n)
+__global__ void mse_kernel(int64_t n, const float* pred, const float* target, bf16* grad, double* part) {
+  double s = 0.0;
+  const float inv = 2.0f / (4.0f * (float)n);
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const float4 y = *reinterpret_cast<const float4*>(pred + p * 16);
+    const float4 t = reinterpret_cast<const float4*>(target)[p];
+    const float d0 = y.x - t.x, d1 = y.y - t.y, d2 = y.z - t.z, d3 = y.w - t.w;
+    s += (double)d0 * d0 + (double)d1 * d1 + (double)d2 * d2 + (double)d3 * d3;
+    if (grad) {
+      __nv_bfloat162* g = reinterpret_cast<__nv_bfloat162*>(grad + p * 16);
+      g[0] = __floats2bfloat162_rn(inv * d0, inv * d1);
+      g[1] = __floats2bfloat162_rn(inv * d2, inv * d3);
+#pragma unroll
+      for (int k = 2; k < 8; ++k) g[k] = __floats2bfloat162_rn(0.0f, 0.0f);
+    }
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void sum_final_kernel(int nb, const double* part, double scale, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[b];
+    *out = s * scale;
+  }
+}
+
+// Adam (Kingma & Ba 2015) on FP32 master parameters; optionally refreshes a BF16 copy.
+__global__ void adam_kernel(int64_t n, float* p, const float* g, float* m, float* v, float lr, float b1, float b2,
+                            float eps, float c1, float c2, bf16* pb) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float upd = lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    const float pi = p[i] - upd;
+    p[i] = pi;
+    if (pb) pb[i] = __float2bfloat16_rn(pi);
+  }
+}
+
+__global__ void to_bf16_kernel(int64_t n, const float* x, bf16* y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = __float2bfloat16_rn(x[i]);
+}
+
+int blocks_for(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  return (int)(b < 1 ? 1 : (b > 2048 ? 2048 : b));
+}
+
+}  // namespace
+
+cudaError_t sur_features(int H, int W, double a, const float* snap, float s_n, float s_u, void* out, cudaStream_t st) {
+  features_kernel<<<blocks_for((int64_t)H * W), 256, 0, st>>>(H, W, a, snap, s_n, s_u, (bf16*)out);
+  return cudaGetLastError();
+}
+
+cudaError_t sur_targets(int64_t n, const float* before, const float* after, const float* scale4, float* target,
+                        cudaStream_t st) {
+  targets_kernel<<<blocks_for(n), 256, 0, st>>>(n, before, after,
+                                                 make_float4(scale4[0], scale4[1], scale4[2], scale4[3]), target);
+  return cudaGetLastError();
+}
+
+cudaError_t sur_apply(int64_t n, const float* before, const float* pred, const float* scale4, float* after,
+                      cudaStream_t st) {
+  apply_kernel<<<blocks_for(n), 256, 0, st>>>(n, before, pred, make_float4(scale4[0], scale4[1], scale4[2], scale4[3]),
+                                               after);
+  return cudaGetLastError();
+}
+
+cudaError_t sur_stats(int64_t n, int C, const float* x, double* part, double* out, cudaStream_t st) {
+  stats_kernel<<<RED_BLOCKS, 256, 0, st>>>(n, C, x, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  stats_final_kernel<<<1, 32, 0, st>>>(RED_BLOCKS, C, part, out);
+  return cudaGetLastError();
+}
+
+cudaError_t sur_mse(int64_t n, const float* pred, const float* target, void* grad, double* part, double* loss,
+                    cudaStream_t st) {
+  mse_kernel<<<RED_BLOCKS, 256, 0, st>>>(n, pred, target, (bf16*)grad, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  sum_final_kernel<<<1, 32, 0, st>>>(RED_BLOCKS, part, 1.0 / (4.0 * (double)n), loss);
+  return cudaGetLastError();
+}
+
+cudaError_t sur_adam(int64_t n, float* p, const float* g, float* m, float* v, int64_t t, float lr, float b1, float b2,
+                     float eps, void* pb, cudaStream_t st) {
+  const float c1 = 1.0f - powf(b1, (float)t), c2 = 1.0f - powf(b2, (float)t);
+  adam_kernel<<<blocks_for(n), 256, 0, st>>>(n, p, g, m, v, lr, b1, b2, eps, c1, c2, (bf16*)pb);
+  return cudaGetLastError();
+}
+
+cudaError_t sur_to_bf16(int64_t n, const float* x, void* y, cudaStream_t st) {
+  to_bf16_kernel<<<blocks_for(n), 256, 0, st>>>(n, x, (bf16*)y);
+  return cudaGetLastError();
+}
+
+size_t sur_reduce_doubles() { return RED_BLOCKS * 32; }
+
+}  // namespace vlb

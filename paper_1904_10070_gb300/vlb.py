@@ -25,7 +25,10 @@ EXPORTS = ["vlb_workspace_bytes", "vlb_max_stable_dt", "vlb_create", "vlb_destro
            "vlb_set_state", "vlb_get_state", "vlb_step", "vlb_get_fields", "vlb_get_totals",
            "vlb_interface_length", "vlb_state_device", "vlb_steps_done", "vlb_last_error",
            "vlb_step_noalloc", "vlb_ensemble_workspace_bytes", "vlb_ensemble_create", "vlb_ensemble_step",
-           "vlb_ensemble_member", "vlb_ensemble_tile_rows"]
+           "vlb_ensemble_member", "vlb_ensemble_tile_rows", "vlb_get_snapshot", "vlb_set_snapshot",
+           "vlb_conv3x3_fwd", "vlb_conv3x3_flip", "vlb_conv3x3_wgrad_workspace_bytes", "vlb_conv3x3_bwd_weight",
+           "vlb_reduce_workspace_bytes", "vlb_surrogate_features", "vlb_surrogate_targets", "vlb_surrogate_apply",
+           "vlb_channel_sums", "vlb_mse_loss", "vlb_adam_step", "vlb_to_bf16"]
 
 NOALLOC_SCRATCH_BYTES = 24 * 1024 * 1024
 
@@ -88,6 +91,28 @@ def lib() -> ctypes.CDLL:
     F = ctypes.POINTER(ctypes.c_float)
     L.vlb_ensemble_tile_rows.argtypes = [P, ctypes.POINTER(I32), F, F]
     L.vlb_ensemble_tile_rows.restype = I32
+    FP = ctypes.POINTER(ctypes.c_float)
+    DP = ctypes.POINTER(ctypes.c_double)
+    L.vlb_get_snapshot.argtypes, L.vlb_get_snapshot.restype = [P, P], I32
+    L.vlb_set_snapshot.argtypes, L.vlb_set_snapshot.restype = [P, P, DP], I32
+    L.vlb_conv3x3_fwd.argtypes = [I32, I32, I32, I32, P, P, P, P, I32, P, P, P]
+    L.vlb_conv3x3_flip.argtypes = [I32, I32, P, P, P]
+    L.vlb_conv3x3_wgrad_workspace_bytes.argtypes = [I32, I32, I32, I32]
+    L.vlb_conv3x3_wgrad_workspace_bytes.restype = S
+    L.vlb_conv3x3_bwd_weight.argtypes = [I32, I32, I32, I32, P, P, P, P, P, S, P]
+    L.vlb_reduce_workspace_bytes.argtypes, L.vlb_reduce_workspace_bytes.restype = [], S
+    L.vlb_surrogate_features.argtypes = [I32, I32, ctypes.c_double, P, ctypes.c_float, ctypes.c_float, P, P]
+    L.vlb_surrogate_targets.argtypes = [I64, P, P, FP, P, P]
+    L.vlb_surrogate_apply.argtypes = [I64, P, P, FP, P, P]
+    L.vlb_channel_sums.argtypes = [I64, I32, P, P, P, P]
+    L.vlb_mse_loss.argtypes = [I64, P, P, P, P, P, P]
+    L.vlb_adam_step.argtypes = [I64, P, P, P, P, I64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                ctypes.c_float, P, P]
+    L.vlb_to_bf16.argtypes = [I64, P, P, P]
+    for name in ("vlb_conv3x3_fwd", "vlb_conv3x3_flip", "vlb_conv3x3_bwd_weight", "vlb_surrogate_features",
+                 "vlb_surrogate_targets", "vlb_surrogate_apply", "vlb_channel_sums", "vlb_mse_loss", "vlb_adam_step",
+                 "vlb_to_bf16"):
+        getattr(L, name).restype = I32
     _lib = L
     return L
 
@@ -187,6 +212,78 @@ def vlb_step_noalloc(p: vlb_params, state_ptr: int, stride: int, n0: float, nste
                                 ctypes.c_void_p(stream_ptr), ctypes.byref(err))
     if st != VLB_OK:
         raise VlbError(st, (err.value or b"").decode())
+
+
+def _ptr(t):
+    """Device address of a torch tensor (or None)."""
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _scale4(scale):
+    return (ctypes.c_float * 4)(*[float(x) for x in scale])
+
+
+def vlb_get_snapshot(h, snap):
+    _check(lib().vlb_get_snapshot(h, _ptr(snap)), h)
+
+
+def vlb_set_snapshot(h, snap, conserve=None):
+    c = None if conserve is None else (ctypes.c_double * 2)(*conserve)
+    _check(lib().vlb_set_snapshot(h, _ptr(snap), c), h)
+
+
+def vlb_conv3x3_fwd(H, W, cin, cout, x, w, bias, mask, relu, y_bf16, y_f32, stream):
+    _check(lib().vlb_conv3x3_fwd(H, W, cin, cout, _ptr(x), _ptr(w), _ptr(bias), _ptr(mask), int(relu), _ptr(y_bf16),
+                                 _ptr(y_f32), ctypes.c_void_p(stream)))
+
+
+def vlb_conv3x3_flip(cin, cout, w, w_flipped, stream):
+    _check(lib().vlb_conv3x3_flip(cin, cout, _ptr(w), _ptr(w_flipped), ctypes.c_void_p(stream)))
+
+
+def vlb_conv3x3_wgrad_workspace_bytes(H, W, cin, cout) -> int:
+    return lib().vlb_conv3x3_wgrad_workspace_bytes(H, W, cin, cout)
+
+
+def vlb_conv3x3_bwd_weight(H, W, cin, cout, x, dy, dw, db, workspace, stream):
+    _check(lib().vlb_conv3x3_bwd_weight(H, W, cin, cout, _ptr(x), _ptr(dy), _ptr(dw), _ptr(db), _ptr(workspace),
+                                        workspace.numel() * workspace.element_size(), ctypes.c_void_p(stream)))
+
+
+def vlb_reduce_workspace_bytes() -> int:
+    return lib().vlb_reduce_workspace_bytes()
+
+
+def vlb_surrogate_features(H, W, r_over_R, snap, s_n, s_u, out, stream):
+    _check(lib().vlb_surrogate_features(H, W, r_over_R, _ptr(snap), s_n, s_u, _ptr(out), ctypes.c_void_p(stream)))
+
+
+def vlb_surrogate_targets(npix, before, after, scale, target, stream):
+    _check(lib().vlb_surrogate_targets(npix, _ptr(before), _ptr(after), _scale4(scale), _ptr(target),
+                                       ctypes.c_void_p(stream)))
+
+
+def vlb_surrogate_apply(npix, before, pred16, scale, after, stream):
+    _check(lib().vlb_surrogate_apply(npix, _ptr(before), _ptr(pred16), _scale4(scale), _ptr(after),
+                                     ctypes.c_void_p(stream)))
+
+
+def vlb_channel_sums(npix, C, x, work, out, stream):
+    _check(lib().vlb_channel_sums(npix, C, _ptr(x), _ptr(work), _ptr(out), ctypes.c_void_p(stream)))
+
+
+def vlb_mse_loss(npix, pred16, target4, grad16, work, loss, stream):
+    _check(lib().vlb_mse_loss(npix, _ptr(pred16), _ptr(target4), _ptr(grad16), _ptr(work), _ptr(loss),
+                              ctypes.c_void_p(stream)))
+
+
+def vlb_adam_step(n, p, g, m, v, t, lr, b1, b2, eps, p_bf16, stream):
+    _check(lib().vlb_adam_step(n, _ptr(p), _ptr(g), _ptr(m), _ptr(v), t, lr, b1, b2, eps, _ptr(p_bf16),
+                               ctypes.c_void_p(stream)))
+
+
+def vlb_to_bf16(n, x, y, stream):
+    _check(lib().vlb_to_bf16(n, _ptr(x), _ptr(y), ctypes.c_void_p(stream)))
 
 
 def _param_array(members):
