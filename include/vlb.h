@@ -201,10 +201,11 @@ vlb_status vlb_conv3x3_bwd_weight(int32_t H, int32_t W, int32_t cin, int32_t cou
                                   float* dw, float* db, void* workspace, size_t bytes, void* cuda_stream);
 /* Scratch (bytes) that vlb_channel_sums and vlb_mse_loss need in d_work. */
 size_t vlb_reduce_workspace_bytes(void);
-/* Network input from a snapshot: 16 bf16 channels per node -- phi, (n - 1)/s_n, u_theta/s_u,
- * u_phi/s_u, J = 1 + a cos theta (sqrt(g)/(r R)), R Gamma = sin theta / J, sin theta, cos theta, 1/J,
- * a = r/R, then zeros (App. A geometry; row q has theta = 2 pi q / H). */
-vlb_status vlb_surrogate_features(int32_t H, int32_t W, double r_over_R, const float* snap, float s_n, float s_u,
+/* Network input from a snapshot: 16 bf16 channels per node -- phi/s_phi, (n - n_mean)/s_n,
+ * u_theta/s_u, u_phi/s_u with norm = {n_mean, s_phi, s_n, s_u}, then J = 1 + a cos theta
+ * (sqrt(g)/(r R)), R Gamma = sin theta / J, sin theta, cos theta, 1/J, a = r/R, then zeros
+ * (App. A geometry; row q has theta = 2 pi q / H). */
+vlb_status vlb_surrogate_features(int32_t H, int32_t W, double r_over_R, const float* snap, const float norm[4],
                                   void* out_bf16, void* cuda_stream);
 /* target[p][c] = (after[p][c] - before[p][c]) / scale[c] for the 4 snapshot channels. */
 vlb_status vlb_surrogate_targets(int64_t npix, const float* before, const float* after, const float scale[4],

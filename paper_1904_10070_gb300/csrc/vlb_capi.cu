@@ -982,11 +982,11 @@ vlb_status vlb_conv3x3_bwd_weight(int32_t H, int32_t W, int32_t cin, int32_t cou
 
 size_t vlb_reduce_workspace_bytes(void) { return sizeof(double) * vlb::sur_reduce_doubles(); }
 
-vlb_status vlb_surrogate_features(int32_t H, int32_t W, double r_over_R, const float* snap, float s_n, float s_u,
+vlb_status vlb_surrogate_features(int32_t H, int32_t W, double r_over_R, const float* snap, const float norm[4],
                                   void* out_bf16, void* cuda_stream) {
-  if (H < 1 || W < 1 || !snap || !out_bf16 || !(s_n > 0.0f) || !(s_u > 0.0f))
+  if (H < 1 || W < 1 || !snap || !out_bf16 || !norm || !(norm[1] > 0.0f) || !(norm[2] > 0.0f) || !(norm[3] > 0.0f))
     return fail(nullptr, VLB_ERR_ARG, "vlb_surrogate_features: bad argument");
-  VLB_CUDA(nullptr, vlb::sur_features(H, W, r_over_R, snap, s_n, s_u, out_bf16, (cudaStream_t)cuda_stream));
+  VLB_CUDA(nullptr, vlb::sur_features(H, W, r_over_R, snap, norm, out_bf16, (cudaStream_t)cuda_stream));
   return VLB_OK;
 }
 

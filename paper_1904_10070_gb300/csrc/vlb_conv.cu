@@ -10,10 +10,10 @@
 //                  = a forward convolution of dY with W'[ci][8 - t][co] (vlb_conv3x3_flip)
 //   backward wts   dW[co][t][ci] = sum_p dY[p][co] X[p + d_t][ci],  db[co] = sum_p dY[p][co]
 //
-// Forward tiling: a CTA (4 warps) owns 128 consecutive pixels of one row; the 3 x 130 x C_in input
-// patch is staged in shared memory with cp.async (pixel stride C_in + 8 elements, so the eight
-// 16-byte rows of an ldmatrix land in different bank groups); each warp computes 32 pixels x C_out.
-// Weight fragments are read from global memory (all weights of a layer fit in L1).
+// Forward tiling: a CTA (8 warps) owns 128 consecutive pixels of two rows; the 4 x 130 x C_in input
+// patch and the layer's weights are staged in shared memory with cp.async (row strides padded by 8
+// elements, so the eight 16-byte rows of an ldmatrix land in different bank groups); each warp
+// computes 32 pixels x C_out with both operands loaded by ldmatrix.
 // Weight gradient: a CTA (4 warps) owns one tap and a group of row segments; per segment it stages
 // the shifted input row and dY in shared memory and accumulates dY^T X_t with both operands loaded
 // by ldmatrix.trans; per-group partial sums are reduced in a fixed order by a second kernel.
@@ -65,35 +65,45 @@ __device__ __forceinline__ void ldsm4t(uint32_t (&r)[4], const void* p) {
 
 __device__ __forceinline__ uint32_t ldg32(const bf16* p) { return __ldg(reinterpret_cast<const unsigned int*>(p)); }
 
-template <int CIN>
+constexpr int FROWS = 2;              // pixel rows per forward CTA
+constexpr int FTHR = FROWS * NTHR;     // 8 warps: 4 per row, 32 pixels each
+
+template <int CIN, int COUT>
 constexpr size_t fwd_smem() {
-  return sizeof(bf16) * 3 * (CPX + 2) * (CIN + 8);
+  return sizeof(bf16) * ((FROWS + 2) * (CPX + 2) * (CIN + 8) + COUT * 9 * (CIN + 8));
 }
 
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(NTHR) conv_fwd_kernel(int H, int W, const bf16* __restrict__ x,
+__global__ void __launch_bounds__(FTHR) conv_fwd_kernel(int H, int W, const bf16* __restrict__ x,
                                                         const bf16* __restrict__ w, const float* __restrict__ bias,
                                                         const bf16* __restrict__ mask, int relu, bf16* y, float* yf) {
   constexpr int PS = CIN + 8, PW = CPX + 2, CH = CIN / 8, NT = COUT / 8;
+  constexpr int PR = FROWS + 2;                // patch rows
+  constexpr int WS = 9 * PS;                   // weight row stride (one output channel), elements
   extern __shared__ __align__(16) unsigned char smem_raw[];
   bf16* patch = reinterpret_cast<bf16*>(smem_raw);
+  bf16* ws = patch + PR * PW * PS;
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int segs = W / CPX;
-  const int row = blockIdx.x / segs, x0 = (blockIdx.x % segs) * CPX;
-  for (int idx = tid; idx < 3 * PW * CH; idx += NTHR) {
+  const int row0 = (blockIdx.x / segs) * FROWS, x0 = (blockIdx.x % segs) * CPX;
+  for (int idx = tid; idx < PR * PW * CH; idx += FTHR) {
     const int pr = idx / (PW * CH), rem = idx - pr * (PW * CH);
     const int pc = rem / CH, ch = rem - pc * CH;
-    int gy = row + pr - 1;
-    gy += gy < 0 ? H : (gy >= H ? -H : 0);
+    int gy = (row0 + pr - 1) % H;
+    gy += gy < 0 ? H : 0;
     int gx = x0 + pc - 1;
     gx += gx < 0 ? W : (gx >= W ? -W : 0);
     cp16(patch + (pr * PW + pc) * PS + ch * 8, x + ((size_t)gy * W + gx) * CIN + ch * 8);
+  }
+  for (int idx = tid; idx < COUT * 9 * CH; idx += FTHR) {
+    const int co = idx / (9 * CH), rem = idx - co * 9 * CH, t = rem / CH, ch = rem - t * CH;
+    cp16(ws + co * WS + t * PS + ch * 8, w + ((size_t)co * 9 + t) * CIN + ch * 8);
   }
   cp_wait_all();
   __syncthreads();
 
   const int g = lane / 4, t4 = lane % 4;
-  const int px0 = warp * 32;
+  const int wr = warp / NWARP, px0 = (warp % NWARP) * 32;  // this warp's row within the CTA and first pixel
   float acc[2][NT][4];
 #pragma unroll
   for (int mt = 0; mt < 2; ++mt)
@@ -101,8 +111,9 @@ __global__ void __launch_bounds__(NTHR) conv_fwd_kernel(int H, int W, const bf16
     for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
       for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.0f;
-  // ldmatrix row address of this lane: matrix j = lane / 8 covers A rows 8 (j % 2).. and k 8 (j / 2)..
+  // ldmatrix lane roles: A matrices (rows 0-7|8-15, k 0-7|8-15); B matrices (n-tile a|b, k 0-7|8-15)
   const int arow = (lane % 8) + 8 * ((lane / 8) % 2), akof = 8 * (lane / 16);
+  const int brow = (lane % 8) + 8 * (lane / 16), bkof = 8 * ((lane / 8) % 2);
 #pragma unroll 1
   for (int tap = 0; tap < 9; ++tap) {
     const int dy = tap / 3, dx = tap % 3;
@@ -111,17 +122,20 @@ __global__ void __launch_bounds__(NTHR) conv_fwd_kernel(int H, int W, const bf16
       uint32_t a[2][4];
 #pragma unroll
       for (int mt = 0; mt < 2; ++mt)
-        ldsm4(a[mt], patch + (dy * PW + px0 + mt * 16 + arow + dx) * PS + c0 + akof);
+        ldsm4(a[mt], patch + ((wr + dy) * PW + px0 + mt * 16 + arow + dx) * PS + c0 + akof);
 #pragma unroll
-      for (int nt = 0; nt < NT; ++nt) {
-        const bf16* wp = w + ((size_t)(nt * 8 + g) * 9 + tap) * CIN + c0 + 2 * t4;
-        const uint32_t b0 = ldg32(wp), b1 = ldg32(wp + 8);
-        mma16816(acc[0][nt], a[0], b0, b1);
-        mma16816(acc[1][nt], a[1], b0, b1);
+      for (int np = 0; np < NT / 2; ++np) {
+        uint32_t b[4];
+        ldsm4(b, ws + (np * 16 + brow) * WS + tap * PS + c0 + bkof);
+        mma16816(acc[0][2 * np], a[0], b[0], b[1]);
+        mma16816(acc[1][2 * np], a[1], b[0], b[1]);
+        mma16816(acc[0][2 * np + 1], a[0], b[2], b[3]);
+        mma16816(acc[1][2 * np + 1], a[1], b[2], b[3]);
       }
     }
   }
   // epilogue: acc[mt][nt][2h + e] is pixel px0 + 16 mt + g + 8 h, channel 8 nt + 2 t4 + e
+  const int row = row0 + wr;
 #pragma unroll
   for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
@@ -275,11 +289,11 @@ cudaError_t allow_smem(K kernel, size_t bytes) {
 template <int CIN, int COUT>
 cudaError_t fwd_launch(int H, int W, const void* x, const void* w, const float* b, const void* mask, int relu, void* y,
                        float* yf, cudaStream_t st) {
-  constexpr size_t S = fwd_smem<CIN>();
+  constexpr size_t S = fwd_smem<CIN, COUT>();
   cudaError_t e = allow_smem(conv_fwd_kernel<CIN, COUT>, S);
   if (e != cudaSuccess) return e;
-  conv_fwd_kernel<CIN, COUT><<<H * (W / CPX), NTHR, S, st>>>(H, W, (const bf16*)x, (const bf16*)w, b,
-                                                             (const bf16*)mask, relu, (bf16*)y, yf);
+  conv_fwd_kernel<CIN, COUT><<<(H / FROWS) * (W / CPX), FTHR, S, st>>>(H, W, (const bf16*)x, (const bf16*)w, b,
+                                                                       (const bf16*)mask, relu, (bf16*)y, yf);
   return cudaGetLastError();
 }
 
@@ -297,7 +311,8 @@ cudaError_t wg_launch(int H, int W, const void* x, const void* dy, float* partia
 }
 
 bool shape_ok(int H, int W, int cin, int cout, const char** why) {
-  if (H < 1 || W < CPX || W % CPX != 0) return *why = "W must be a positive multiple of 128", false;
+  if (H < FROWS || H % FROWS != 0) return *why = "H must be a positive multiple of 2", false;
+  if (W < CPX || W % CPX != 0) return *why = "W must be a positive multiple of 128", false;
   if (!((cin == 16 && cout == 64) || (cin == 64 && cout == 64) || (cin == 64 && cout == 16)))
     return *why = "(c_in, c_out) must be (16, 64), (64, 64) or (64, 16)", false;
   return true;

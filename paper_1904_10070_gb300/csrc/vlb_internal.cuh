@@ -123,7 +123,7 @@ cudaError_t conv_fwd(int H, int W, int cin, int cout, const void* x, const void*
 cudaError_t conv_flip(int cin, int cout, const void* w, void* wf, cudaStream_t st);
 cudaError_t conv_wgrad(int H, int W, int cin, int cout, const void* x, const void* dy, float* dw, float* db,
                        float* partial, cudaStream_t st);
-cudaError_t sur_features(int H, int W, double a, const float* snap, float s_n, float s_u, void* out, cudaStream_t st);
+cudaError_t sur_features(int H, int W, double a, const float* snap, const float* norm4, void* out, cudaStream_t st);
 cudaError_t sur_targets(int64_t n, const float* before, const float* after, const float* scale4, float* target,
                         cudaStream_t st);
 cudaError_t sur_apply(int64_t n, const float* before, const float* pred, const float* scale4, float* after,

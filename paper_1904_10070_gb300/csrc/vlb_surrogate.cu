@@ -12,17 +12,18 @@ namespace {
 
 using bf16 = __nv_bfloat16;
 
-// Input channels: 0 phi, 1 (n - 1)/s_n, 2 u_theta/s_u, 3 u_phi/s_u, then the geometry of the row
-// (App. A): 4 J = 1 + a cos theta (sqrt(g)/(r R)), 5 R Gamma = sin theta / J (Eq. conn_torus),
-// 6 sin theta, 7 cos theta, 8 1/J, 9 a = r/R; 10-15 zero.
-__global__ void features_kernel(int H, int W, double a, const float* snap, float s_n, float s_u, bf16* out) {
+// Input channels: 0 phi/s_phi, 1 (n - n_mean)/s_n, 2 u_theta/s_u, 3 u_phi/s_u, then the geometry of
+// the row (App. A): 4 J = 1 + a cos theta (sqrt(g)/(r R)), 5 R Gamma = sin theta / J
+// (Eq. conn_torus), 6 sin theta, 7 cos theta, 8 1/J, 9 a = r/R; 10-15 zero.
+__global__ void features_kernel(int H, int W, double a, const float* snap, float n_mean, float s_phi, float s_n,
+                                float s_u, bf16* out) {
   const int64_t n = (int64_t)H * W;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
     const int q = (int)(p / W);
     const double th = 2.0 * 3.14159265358979323846 * q / H;
     const double J = 1.0 + a * cos(th);
     const float4 s = reinterpret_cast<const float4*>(snap)[p];
-    float c[16] = {s.x, (s.y - 1.0f) / s_n, s.z / s_u, s.w / s_u, (float)J, (float)(sin(th) / J), (float)sin(th),
+    float c[16] = {s.x / s_phi, (s.y - n_mean) / s_n, s.z / s_u, s.w / s_u, (float)J, (float)(sin(th) / J), (float)sin(th),
                    (float)cos(th), (float)(1.0 / J), (float)a, 0, 0, 0, 0, 0, 0};
     __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(out + p * 16);
 #pragma unroll
@@ -145,8 +146,9 @@ int blocks_for(int64_t n) {
 
 }  // namespace
 
-cudaError_t sur_features(int H, int W, double a, const float* snap, float s_n, float s_u, void* out, cudaStream_t st) {
-  features_kernel<<<blocks_for((int64_t)H * W), 256, 0, st>>>(H, W, a, snap, s_n, s_u, (bf16*)out);
+cudaError_t sur_features(int H, int W, double a, const float* snap, const float* norm4, void* out, cudaStream_t st) {
+  features_kernel<<<blocks_for((int64_t)H * W), 256, 0, st>>>(H, W, a, snap, norm4[0], norm4[1], norm4[2], norm4[3],
+                                                              (bf16*)out);
   return cudaGetLastError();
 }
 

@@ -125,13 +125,33 @@ def radius_for(seed: int) -> float:
 
 
 class Dataset:
-    """Pairs (snapshot at t, snapshot at t + window) from solver trajectories, kept on the device."""
+    """Pairs (snapshot at t, snapshot at t + window) from solver trajectories, kept on the device,
+    with the per-sample input normalisation (n_mean, s_phi, s_n, s_u) of each `before` snapshot."""
 
-    def __init__(self, before, after, radii):
-        self.before, self.after, self.radii = before, after, radii
+    def __init__(self, before, after, radii, norms):
+        self.before, self.after, self.radii, self.norms = before, after, radii, norms
 
     def __len__(self):
         return len(self.radii)
+
+
+class Normaliser:
+    """Per-snapshot scales from FP64 channel sums (one small device reduction and read-back)."""
+
+    def __init__(self):
+        import torch
+        self.work = torch.empty(vlb.vlb_reduce_workspace_bytes(), dtype=torch.uint8, device="cuda")
+        self.sums = torch.empty(8, dtype=torch.float64, device="cuda")
+
+    def __call__(self, snap):
+        N = snap.shape[0]
+        vlb.vlb_channel_sums(N, 4, snap, self.work, self.sums, _stream())
+        s = self.sums.cpu().numpy()
+        mean, sq = s[:4] / N, s[4:] / N
+        s_phi = math.sqrt(max(sq[0], 0.0))
+        s_n = math.sqrt(max(sq[1] - mean[1] ** 2, 0.0))
+        s_u = math.sqrt(max(0.5 * (sq[2] + sq[3]), 0.0))
+        return (float(mean[1]), max(s_phi, 1e-12), max(s_n, 1e-12), max(s_u, 1e-12))
 
 
 def generate(seeds, H=256, W=512, window=50, pairs=5, spacing=100, batch=48, noise=0.01):
@@ -139,7 +159,8 @@ def generate(seeds, H=256, W=512, window=50, pairs=5, spacing=100, batch=48, noi
     each: snapshots at steps k * spacing and k * spacing + window, k = 0 .. pairs - 1."""
     import torch
     N = H * W
-    before, after, radii = [], [], []
+    norm = Normaliser()
+    before, after, radii, norms = [], [], [], []
     for i0 in range(0, len(seeds), batch):
         sel = seeds[i0:i0 + batch]
         ps = [member_params(radius_for(s), H, W) for s in sel]
@@ -164,50 +185,46 @@ def generate(seeds, H=256, W=512, window=50, pairs=5, spacing=100, batch=48, noi
                 before.append(snaps[k * spacing][j])
                 after.append(snaps[k * spacing + window][j])
                 radii.append(ps[j]["R"])
+                norms.append(norm(before[-1]))
         ens.close()
         del snaps
-    return Dataset(before, after, radii)
+    return Dataset(before, after, radii, norms)
 
 
-def channel_scales(ds: Dataset, sample: int = 64):
-    """Input scales (s_n, s_u) and target scales (per channel) from a sample of the dataset."""
+def target_ratios(ds: Dataset, sample: int = 64):
+    """g_c = mean over a sample of rms(change of channel c) / (its input scale): targets are then O(1)."""
     import torch
-    st = _stream()
     N = ds.before[0].shape[0]
-    work = torch.empty(vlb.vlb_reduce_workspace_bytes(), dtype=torch.uint8, device="cuda")
-    sums = torch.empty(8, dtype=torch.float64, device="cuda")
     tgt = torch.empty((N, 4), dtype=torch.float32, device="cuda")
-    acc_in, acc_t = np.zeros(8), np.zeros(8)
+    norm = Normaliser()
     idx = np.linspace(0, len(ds) - 1, min(sample, len(ds))).astype(int)
-    ones = [1.0, 1.0, 1.0, 1.0]
+    acc = np.zeros(4)
     for i in idx:
-        vlb.vlb_channel_sums(N, 4, ds.before[i], work, sums, st)
-        acc_in += sums.cpu().numpy()
-        vlb.vlb_surrogate_targets(N, ds.before[i], ds.after[i], ones, tgt, st)
-        vlb.vlb_channel_sums(N, 4, tgt, work, sums, st)
-        acc_t += sums.cpu().numpy()
-    cnt = len(idx) * N
-    mean_in, var_in = acc_in[:4] / cnt, acc_in[4:] / cnt - (acc_in[:4] / cnt) ** 2
-    mean_t, var_t = acc_t[:4] / cnt, acc_t[4:] / cnt - (acc_t[:4] / cnt) ** 2
-    s_n = float(max(math.sqrt(max(var_in[1], 0.0)), 1e-8))
-    s_u = float(max(math.sqrt(max(0.5 * (var_in[2] + var_in[3]), 0.0)), 1e-8))
-    s_t = [float(max(math.sqrt(max(v, 0.0) + m * m), 1e-12)) for v, m in zip(var_t, mean_t)]
-    return s_n, s_u, s_t
+        _, s_phi, s_n, s_u = ds.norms[i]
+        vlb.vlb_surrogate_targets(N, ds.before[i], ds.after[i], [s_phi, s_n, s_u, s_u], tgt, _stream())
+        vlb.vlb_channel_sums(N, 4, tgt, norm.work, norm.sums, _stream())
+        sq = norm.sums.cpu().numpy()[4:] / N
+        acc += np.sqrt(np.maximum(sq, 0.0))
+    return [float(max(x / len(idx), 1e-6)) for x in acc]
 
 
 class Trainer:
-    def __init__(self, net: SurrogateNet, scales):
+    def __init__(self, net: SurrogateNet, ratios):
         import torch
         self.net = net
-        self.s_n, self.s_u, self.s_t = scales
+        self.g = list(ratios)
         N = net.H * net.W
         self.target = torch.empty((N, 4), dtype=torch.float32, device="cuda")
 
-    def sample_loss(self, before, after, R, train: bool, lr: float = 1e-3):
+    def out_scale(self, norm):
+        _, s_phi, s_n, s_u = norm
+        return [self.g[0] * s_phi, self.g[1] * s_n, self.g[2] * s_u, self.g[3] * s_u]
+
+    def sample_loss(self, before, after, R, norm, train: bool, lr: float = 1e-3):
         net, st = self.net, _stream()
         N = net.H * net.W
-        vlb.vlb_surrogate_features(net.H, net.W, 1.0 / R, before, self.s_n, self.s_u, net.acts[0], st)
-        vlb.vlb_surrogate_targets(N, before, after, self.s_t, self.target, st)
+        vlb.vlb_surrogate_features(net.H, net.W, 1.0 / R, before, norm, net.acts[0], st)
+        vlb.vlb_surrogate_targets(N, before, after, self.out_scale(norm), self.target, st)
         net.forward()
         net.loss_and_grad(self.target)
         if train:
@@ -225,7 +242,7 @@ class Trainer:
         for ep in range(epochs):
             for i in rng.permutation(len(ds)):
                 lr_t = lr * 0.5 * (1.0 + math.cos(math.pi * it / n_it))  # cosine schedule
-                loss = self.sample_loss(ds.before[i], ds.after[i], ds.radii[i], True, lr_t)
+                loss = self.sample_loss(ds.before[i], ds.after[i], ds.radii[i], ds.norms[i], True, lr_t)
                 it += 1
                 if log_every and it % log_every == 0:
                     hist.append((it, float(loss.cpu())))
@@ -233,7 +250,8 @@ class Trainer:
         return hist, time.perf_counter() - t0
 
     def evaluate(self, ds: Dataset):
-        vals = [float(self.sample_loss(ds.before[i], ds.after[i], ds.radii[i], False).cpu()) for i in range(len(ds))]
+        vals = [float(self.sample_loss(ds.before[i], ds.after[i], ds.radii[i], ds.norms[i], False).cpu())
+                for i in range(len(ds))]
         return float(np.mean(vals))
 
 
@@ -260,6 +278,7 @@ class Advancer:
         self.snap = torch.empty((N, 4), dtype=torch.float32, device="cuda")
         self.pred = torch.empty((N, 4), dtype=torch.float32, device="cuda")
         self.check = torch.empty((N, 4), dtype=torch.float32, device="cuda")
+        self.normaliser = Normaliser()
         self.fallbacks = 0
         self.checks = 0
         self.max_check_err = 0.0
@@ -268,9 +287,10 @@ class Advancer:
         """pred := the network's estimate of the state one window ahead of the solver's state."""
         net, st = self.tr.net, _stream()
         vlb.vlb_get_snapshot(self.s.h, self.snap)
-        vlb.vlb_surrogate_features(net.H, net.W, 1.0 / self.R, self.snap, self.tr.s_n, self.tr.s_u, net.acts[0], st)
+        norm = self.normaliser(self.snap)
+        vlb.vlb_surrogate_features(net.H, net.W, 1.0 / self.R, self.snap, norm, net.acts[0], st)
         net.forward()
-        vlb.vlb_surrogate_apply(net.H * net.W, self.snap, net.out, self.tr.s_t, self.pred, st)
+        vlb.vlb_surrogate_apply(net.H * net.W, self.snap, net.out, self.tr.out_scale(norm), self.pred, st)
 
     def window_step(self, k: int, check_every: int, phi_tol: float) -> str:
         s = self.s

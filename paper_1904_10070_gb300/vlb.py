@@ -101,7 +101,7 @@ def lib() -> ctypes.CDLL:
     L.vlb_conv3x3_wgrad_workspace_bytes.restype = S
     L.vlb_conv3x3_bwd_weight.argtypes = [I32, I32, I32, I32, P, P, P, P, P, S, P]
     L.vlb_reduce_workspace_bytes.argtypes, L.vlb_reduce_workspace_bytes.restype = [], S
-    L.vlb_surrogate_features.argtypes = [I32, I32, ctypes.c_double, P, ctypes.c_float, ctypes.c_float, P, P]
+    L.vlb_surrogate_features.argtypes = [I32, I32, ctypes.c_double, P, FP, P, P]
     L.vlb_surrogate_targets.argtypes = [I64, P, P, FP, P, P]
     L.vlb_surrogate_apply.argtypes = [I64, P, P, FP, P, P]
     L.vlb_channel_sums.argtypes = [I64, I32, P, P, P, P]
@@ -254,8 +254,9 @@ def vlb_reduce_workspace_bytes() -> int:
     return lib().vlb_reduce_workspace_bytes()
 
 
-def vlb_surrogate_features(H, W, r_over_R, snap, s_n, s_u, out, stream):
-    _check(lib().vlb_surrogate_features(H, W, r_over_R, _ptr(snap), s_n, s_u, _ptr(out), ctypes.c_void_p(stream)))
+def vlb_surrogate_features(H, W, r_over_R, snap, norm, out, stream):
+    """norm = (n_mean, s_phi, s_n, s_u)."""
+    _check(lib().vlb_surrogate_features(H, W, r_over_R, _ptr(snap), _scale4(norm), _ptr(out), ctypes.c_void_p(stream)))
 
 
 def vlb_surrogate_targets(npix, before, after, scale, target, stream):
