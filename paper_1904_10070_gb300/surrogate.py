@@ -151,6 +151,8 @@ class Normaliser:
         s_phi = math.sqrt(max(sq[0], 0.0))
         s_n = math.sqrt(max(sq[1] - mean[1] ** 2, 0.0))
         s_u = math.sqrt(max(0.5 * (sq[2] + sq[3]), 0.0))
+        if not np.all(np.isfinite(s)):
+            return (float("nan"),) * 4
         return (float(mean[1]), max(s_phi, 1e-12), max(s_n, 1e-12), max(s_u, 1e-12))
 
 
@@ -296,6 +298,10 @@ class Advancer:
         s = self.s
         tot = s.totals()
         self.predict()
+        if not all(math.isfinite(x) for x in self.normaliser(self.pred)):  # unusable prediction
+            self.fallbacks += 1
+            s.step(self.window)
+            return "fallback"
         if check_every > 0 and (k + 1) % check_every == 0:
             s.step(self.window)  # the judge: the solver over the same window from the same state
             vlb.vlb_get_snapshot(s.h, self.check)
