@@ -172,12 +172,16 @@ vlb_status vlb_ensemble_tile_rows(const vlb_handle* h, int32_t* rows, float* ms1
 
 /* ---- Snapshots: device FP32 [N][4] = (phi, n, u_theta, u_phi), node-major ----
  * vlb_get_snapshot: moments of the state (Sec. 2.3) and phi; asynchronous on the handle's stream.
- * vlb_set_snapshot: f := f^eq(n, u) (Eq. feq) and phi := phi (the restart after a surrogate window,
- * which drops the non-equilibrium part of f); if conserve != NULL, uniform shifts of n and phi then
- * restore sum n sqrt(g) dtheta dvarphi = conserve[0] and sum phi sqrt(g) dtheta dvarphi = conserve[1].
- * Synchronous. */
+ * vlb_set_snapshot: restart from a snapshot (n', u', phi').  phi := phi'; keep_nonequilibrium == 0:
+ * f := f^eq(n', u') (Eq. feq), which drops the non-equilibrium part of f; keep_nonequilibrium != 0:
+ * f := f + f^eq(n', u') - f^eq(n, u) with (n, u) the moments of the current f, which keeps
+ * f - f^eq(n, u) (it relaxes on the time scale tau, longer than a surrogate window when tau >> dt).
+ * If conserve != NULL, n' and phi' are first shifted uniformly so that sum n' sqrt(g) dtheta dvarphi =
+ * conserve[0] and sum phi' sqrt(g) dtheta dvarphi = conserve[1] (reduced on the device).
+ * Arithmetic in the state's precision.  Asynchronous on the handle's stream; d_snap is read in that
+ * stream's order. */
 vlb_status vlb_get_snapshot(vlb_handle* h, float* d_snap);
-vlb_status vlb_set_snapshot(vlb_handle* h, const float* d_snap, const double* conserve);
+vlb_status vlb_set_snapshot(vlb_handle* h, const float* d_snap, const double* conserve, int32_t keep_nonequilibrium);
 
 /* ---- Surrogate network kernels (not in the paper) ----
  * A periodic-padding CNN that stands in for blocks of solver steps.  Tensors are device NHWC
@@ -201,18 +205,33 @@ vlb_status vlb_conv3x3_bwd_weight(int32_t H, int32_t W, int32_t cin, int32_t cou
                                   float* dw, float* db, void* workspace, size_t bytes, void* cuda_stream);
 /* Scratch (bytes) that vlb_channel_sums and vlb_mse_loss need in d_work. */
 size_t vlb_reduce_workspace_bytes(void);
+/* Snapshot statistics for the network, on the device, without a host read-back:
+ * d_norm8[0..3] = {n_mean, s_phi, s_n, s_u} with n_mean the mean of n, s_phi = rms(phi),
+ * s_n = rms(n - n_mean) and s_u = rms(|u|) / sqrt 2 unless the fixed values s_n_fixed / s_u_fixed are
+ * > 0 (each scale floored at 1e-12; a non-finite snapshot gives NaNs), and
+ * d_norm8[4..7] = {g[0] s_phi, g[1] s_n, g[2] s_u, g[3] s_u}, the output scales (g NULL: all 1).
+ * d_work: vlb_reduce_workspace_bytes of scratch; d_sums: 8 doubles of scratch. */
+vlb_status vlb_surrogate_norm(int64_t npix, const float* snap, float s_n_fixed, float s_u_fixed, const float g[4],
+                              double* d_work, double* d_sums, float* d_norm8, void* cuda_stream);
 /* Network input from a snapshot: 16 bf16 channels per node -- phi/s_phi, (n - n_mean)/s_n,
- * u_theta/s_u, u_phi/s_u with norm = {n_mean, s_phi, s_n, s_u}, then J = 1 + a cos theta
- * (sqrt(g)/(r R)), R Gamma = sin theta / J, sin theta, cos theta, 1/J, a = r/R, then zeros
- * (App. A geometry; row q has theta = 2 pi q / H). */
-vlb_status vlb_surrogate_features(int32_t H, int32_t W, double r_over_R, const float* snap, const float norm[4],
+ * u_theta/s_u, u_phi/s_u with d_norm = {n_mean, s_phi, s_n, s_u} (a device array), then
+ * J = 1 + a cos theta (sqrt(g)/(r R)), R Gamma = sin theta / J, sin theta, cos theta, 1/J, a = r/R,
+ * then zeros (App. A geometry; row q has theta = 2 pi q / H). */
+vlb_status vlb_surrogate_features(int32_t H, int32_t W, double r_over_R, const float* snap, const float* d_norm,
                                   void* out_bf16, void* cuda_stream);
-/* target[p][c] = (after[p][c] - before[p][c]) / scale[c] for the 4 snapshot channels. */
-vlb_status vlb_surrogate_targets(int64_t npix, const float* before, const float* after, const float scale[4],
+/* target[p][c] = (after[p][c] - before[p][c]) / d_scale[c] for the 4 snapshot channels (d_scale on
+ * the device). */
+vlb_status vlb_surrogate_targets(int64_t npix, const float* before, const float* after, const float* d_scale,
                                  float* target, void* cuda_stream);
-/* after[p][c] = before[p][c] + scale[c] * pred16[p][c] (first 4 of 16 f32 channels). */
-vlb_status vlb_surrogate_apply(int64_t npix, const float* before, const float* pred16, const float scale[4],
+/* after[p][c] = before[p][c] + d_scale[c] * pred16[p][c] (first 4 of 16 f32 channels; d_scale on the
+ * device). */
+vlb_status vlb_surrogate_apply(int64_t npix, const float* before, const float* pred16, const float* d_scale,
                                float* after, void* cuda_stream);
+/* Error of a predicted snapshot a against a reference b in phi: d_out4 = {max_p |a.phi - b.phi|,
+ * max_p |b.phi|, sum_p (a.phi - b.phi)^2, sum_p b.phi^2} (FP64; sums in a fixed order, maxima exact).
+ * A non-finite value in a or b makes d_out4[0] and d_out4[2] +inf.  d_work: vlb_reduce_workspace_bytes. */
+vlb_status vlb_snapshot_compare(int64_t npix, const float* a, const float* b, double* d_work, double* d_out4,
+                                void* cuda_stream);
 /* d_out[c] = sum_p x[p][c], d_out[C + c] = sum_p x[p][c]^2 in FP64 (C <= 16). */
 vlb_status vlb_channel_sums(int64_t npix, int32_t C, const float* x, double* d_work, double* d_out, void* cuda_stream);
 /* *d_loss = mean over p and c < 4 of (pred16[p][c] - target4[p][c])^2 (FP64); if grad16_bf16 != NULL

@@ -195,44 +195,115 @@ __global__ void totals_final_kernel(const double* partials, int nb, double* out)
   out[k] = x;
 }
 
-// (phi, n, u_theta, u_phi) per node, from the state, in FP32.
+__device__ __forceinline__ float mul_rn(float x, float y) { return __fmul_rn(x, y); }
+__device__ __forceinline__ double mul_rn(double x, double y) { return __dmul_rn(x, y); }
+
+// The surrogate's snapshot kernels work in the state's own precision T (they run once per window).
 template <typename T>
-__global__ void snapshot_out_kernel(const T* state, int64_t stride, int64_t n, double n0, float* snap, VD vd) {
+__device__ __forceinline__ void node_moments_t(const T* state, int64_t stride, int64_t idx, const VD& vd, T n0, T& n,
+                                               T& ut, T& up) {
+  T row[4] = {0, 0, 0, 0}, col[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const T x = state[(4 * i + j) * stride + idx];
+      row[i] += x;
+      col[j] += x;
+    }
+  n = n0 + ((row[0] + row[1]) + (row[2] + row[3]));
+  ut = ((T)vd.v[0] * row[0] + (T)vd.v[1] * row[1] + (T)vd.v[2] * row[2] + (T)vd.v[3] * row[3]) / n;
+  up = ((T)vd.v[0] * col[0] + (T)vd.v[1] * col[1] + (T)vd.v[2] * col[2] + (T)vd.v[3] * col[3]) / n;
+}
+
+// (phi, n, u_theta, u_phi) per node, from the state, as FP32.
+template <typename T>
+__global__ void snapshot_out_kernel(const T* state, int64_t stride, int64_t n, T n0, float* snap, VD vd) {
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
-    double nn, a, b;
-    node_moments(state, stride, idx, vd, n0, nn, a, b);
+    T nn, a, b;
+    node_moments_t(state, stride, idx, vd, n0, nn, a, b);
     reinterpret_cast<float4*>(snap)[idx] =
         make_float4((float)load_phi(state, stride, idx), (float)nn, (float)a, (float)b);
   }
 }
 
-// f := f^eq(n, u) (Eq. feq), phi := phi from a snapshot (the surrogate restart).
+// Per-block FP64 partial sums of n dA and phi dA over a snapshot (dA the row's area element).
+__global__ void __launch_bounds__(TOTAL_THREADS) snapshot_sums_kernel(const float* snap, const double* coefd, int nt,
+                                                                      int ns, double* partials) {
+  const int64_t n = (int64_t)nt * ns;
+  double sn = 0.0, sp = 0.0;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    const float4 v = reinterpret_cast<const float4*>(snap)[idx];
+    const double dA = coefd[C_DA * nt + (int)(idx / ns)];
+    sn += (double)v.y * dA;
+    sp += (double)v.x * dA;
+  }
+  __shared__ double red[2][TOTAL_THREADS];
+  red[0][threadIdx.x] = sn;
+  red[1][threadIdx.x] = sp;
+  __syncthreads();
+  for (int o = TOTAL_THREADS / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + o];
+      red[1][threadIdx.x] += red[1][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x * NSUM] = red[0][0];
+    partials[blockIdx.x * NSUM + 1] = red[1][0];
+  }
+}
+
+// shift[0] = (mass - sum n dA) / area, shift[1] = (phi_total - sum phi dA) / area (Sec. 2.5 totals).
+__global__ void snapshot_shift_kernel(const double* partials, int nb, double mass, double phi_total, double inv_area,
+                                      double* shift) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double sn = 0.0, sp = 0.0;
+  for (int b = 0; b < nb; ++b) {
+    sn += partials[b * NSUM];
+    sp += partials[b * NSUM + 1];
+  }
+  shift[0] = (mass - sn) * inv_area;
+  shift[1] = (phi_total - sp) * inv_area;
+}
+
+// The surrogate restart from a snapshot (n', u', phi'), with n' += shift[0] and phi' += shift[1] when
+// shift != NULL.  keep_neq == 0: f := f^eq(n', u') (Eq. feq).  keep_neq != 0: f := f + f^eq(n', u') -
+// f^eq(n, u) with (n, u) the moments of the current f, which keeps the non-equilibrium part f - f^eq
+// of the state and gives f the moments (n', u').  In the deviation storage g = f - n0 w_i w_j:
+// f^eq - n0 w_i w_j = w_i w_j ((n - n0) + n P(u)), P(u) = xi + (xi^2 - u^2)/2 + xi (xi^2 - 3 u^2)/6.
 template <typename T>
-__global__ void snapshot_in_kernel(T* state, int64_t stride, int64_t n, double n0, const float* snap, VD vd) {
+__global__ void snapshot_in_kernel(T* state, int64_t stride, int64_t n, T n0, const float* snap, const double* shift,
+                                   int keep_neq, VD vd) {
+  const T dn = shift ? (T)shift[0] : (T)0, dphi = shift ? (T)shift[1] : (T)0;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
     const float4 s = reinterpret_cast<const float4*>(snap)[idx];
-    const double nn = s.y, a = s.z, b = s.w;
-    const double usq = a * a + b * b;
+    const T nn = (T)s.y + dn, a = (T)s.z, b = (T)s.w;
+    const T usq = a * a + b * b;
+    T n1 = 0, a1 = 0, b1 = 0, usq1 = 0;
+    if (keep_neq) {
+      node_moments_t(state, stride, idx, vd, n0, n1, a1, b1);
+      usq1 = a1 * a1 + b1 * b1;
+    }
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const double xi = vd.v[i] * a + vd.v[j] * b;
-        const double pm1 = xi + 0.5 * (xi * xi - usq) + xi * (xi * xi - 3.0 * usq) / 6.0;
-        state[(4 * i + j) * stride + idx] = (T)(vd.w[i] * vd.w[j] * ((nn - n0) + nn * pm1));
+        const T vi = (T)vd.v[i], vj = (T)vd.v[j], ww = (T)(vd.w[i] * vd.w[j]);
+        const T xi = vi * a + vj * b;
+        const T pm = xi + (T)0.5 * (xi * xi - usq) + xi * (xi * xi - (T)3 * usq) / (T)6;
+        T* g = state + (4 * i + j) * stride + idx;
+        if (keep_neq) {
+          const T xi1 = vi * a1 + vj * b1;
+          const T pm1 = xi1 + (T)0.5 * (xi1 * xi1 - usq1) + xi1 * (xi1 * xi1 - (T)3 * usq1) / (T)6;
+          // rounded products (no contraction): the state's own moments give exactly zero change
+          *g = *g + ww * ((nn - n1) + (mul_rn(nn, pm) - mul_rn(n1, pm1)));
+        } else {
+          *g = ww * ((nn - n0) + nn * pm);
+        }
       }
-    store_phi(state, stride, idx, (double)s.x);
-  }
-}
-
-// Uniform shifts: n += dn at rest (f_k += w_i w_j dn), phi += dphi.
-template <typename T>
-__global__ void shift_kernel(T* state, int64_t stride, int64_t n, double dn, double dphi, VD vd) {
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
-#pragma unroll
-    for (int k = 0; k < NPOP; ++k) state[k * stride + idx] = (T)((double)state[k * stride + idx] +
-                                                                  vd.w[k >> 2] * vd.w[k & 3] * dn);
-    store_phi(state, stride, idx, load_phi(state, stride, idx) + dphi);
+    store_phi(state, stride, idx, (double)s.x + (double)dphi);
   }
 }
 
@@ -293,19 +364,23 @@ cudaError_t launch_totals(const T* state, int64_t stride, const double* coefd, i
 
 template <typename T>
 cudaError_t launch_snapshot_out(const T* state, int64_t stride, int64_t n, double n0, float* snap, cudaStream_t s) {
-  snapshot_out_kernel<T><<<grid_for(n), 256, 0, s>>>(state, stride, n, n0, snap, make_vd());
+  snapshot_out_kernel<T><<<grid_for(n), 256, 0, s>>>(state, stride, n, (T)n0, snap, make_vd());
+  return cudaGetLastError();
+}
+
+cudaError_t launch_snapshot_shift(const float* snap, const double* coefd, int nt, int ns, double mass,
+                                  double phi_total, double inv_area, double* partials, double* shift, cudaStream_t s) {
+  snapshot_sums_kernel<<<TOTAL_BLOCKS, TOTAL_THREADS, 0, s>>>(snap, coefd, nt, ns, partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  snapshot_shift_kernel<<<1, 32, 0, s>>>(partials, TOTAL_BLOCKS, mass, phi_total, inv_area, shift);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_snapshot_in(T* state, int64_t stride, int64_t n, double n0, const float* snap, cudaStream_t s) {
-  snapshot_in_kernel<T><<<grid_for(n), 256, 0, s>>>(state, stride, n, n0, snap, make_vd());
-  return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_shift(T* state, int64_t stride, int64_t n, double dn, double dphi, cudaStream_t s) {
-  shift_kernel<T><<<grid_for(n), 256, 0, s>>>(state, stride, n, dn, dphi, make_vd());
+cudaError_t launch_snapshot_in(T* state, int64_t stride, int64_t n, double n0, const float* snap, const double* shift,
+                               int keep_neq, cudaStream_t s) {
+  snapshot_in_kernel<T><<<grid_for(n), 256, 0, s>>>(state, stride, n, (T)n0, snap, shift, keep_neq, make_vd());
   return cudaGetLastError();
 }
 
@@ -319,8 +394,8 @@ cudaError_t launch_shift(T* state, int64_t stride, int64_t n, double dn, double 
   template cudaError_t launch_totals<T>(const T*, int64_t, const double*, int, int, double, double, double,      \
                                         double, double, int, double*, int, double*, cudaStream_t);               \
   template cudaError_t launch_snapshot_out<T>(const T*, int64_t, int64_t, double, float*, cudaStream_t);        \
-  template cudaError_t launch_snapshot_in<T>(T*, int64_t, int64_t, double, const float*, cudaStream_t);         \
-  template cudaError_t launch_shift<T>(T*, int64_t, int64_t, double, double, cudaStream_t);
+  template cudaError_t launch_snapshot_in<T>(T*, int64_t, int64_t, double, const float*, const double*, int,   \
+                                             cudaStream_t);
 VLB_INST(float)
 VLB_INST(double)
 #undef VLB_INST

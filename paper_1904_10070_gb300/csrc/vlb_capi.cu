@@ -924,26 +924,25 @@ vlb_status vlb_get_snapshot(vlb_handle* h, float* d_snap) {
   return VLB_OK;
 }
 
-vlb_status vlb_set_snapshot(vlb_handle* h, const float* d_snap, const double* conserve) {
+vlb_status vlb_set_snapshot(vlb_handle* h, const float* d_snap, const double* conserve, int32_t keep_nonequilibrium) {
   vlb_status st = check_handle(h);
   if (st) return st;
   if (!d_snap) return fail(h, VLB_ERR_ARG, "snapshot pointer is NULL");
-  if (h->esize == 8)
-    VLB_CUDA(h, vlb::launch_snapshot_in<double>((double*)h->U[0], h->stride, h->N, h->n0, d_snap, h->stream));
-  else
-    VLB_CUDA(h, vlb::launch_snapshot_in<float>((float*)h->U[0], h->stride, h->N, h->n0, d_snap, h->stream));
+  const vlb_params& p = h->p;
+  double* shift = nullptr;
   if (conserve) {
-    double t[4];
-    if ((st = vlb_get_totals(h, t))) return st;
-    const vlb_params& p = h->p;
-    const double area = p.geometry == VLB_TORUS ? 4.0 * M_PI * M_PI * p.r * p.R : 4.0 * M_PI * M_PI * p.r * p.R;
-    const double dn = (conserve[0] - t[0]) / area, dphi = (conserve[1] - t[1]) / area;
-    if (h->esize == 8)
-      VLB_CUDA(h, vlb::launch_shift<double>((double*)h->U[0], h->stride, h->N, dn, dphi, h->stream));
-    else
-      VLB_CUDA(h, vlb::launch_shift<float>((float*)h->U[0], h->stride, h->N, dn, dphi, h->stream));
+    shift = h->totals + 6;  // two spare slots of the totals read-out
+    const double inv_area = 1.0 / (4.0 * M_PI * M_PI * p.r * p.R);  // sum of the area elements, torus or flat
+    VLB_CUDA(h, vlb::launch_snapshot_shift(d_snap, h->coefD, p.n_theta, p.n_phi, conserve[0], conserve[1], inv_area,
+                                           h->partials, shift, h->stream));
   }
-  VLB_CUDA(h, cudaStreamSynchronize(h->stream));
+  const int keep = keep_nonequilibrium ? 1 : 0;
+  if (h->esize == 8)
+    VLB_CUDA(h, vlb::launch_snapshot_in<double>((double*)h->U[0], h->stride, h->N, h->n0, d_snap, shift, keep,
+                                                h->stream));
+  else
+    VLB_CUDA(h, vlb::launch_snapshot_in<float>((float*)h->U[0], h->stride, h->N, h->n0, d_snap, shift, keep,
+                                               h->stream));
   return VLB_OK;
 }
 
@@ -982,27 +981,44 @@ vlb_status vlb_conv3x3_bwd_weight(int32_t H, int32_t W, int32_t cin, int32_t cou
 
 size_t vlb_reduce_workspace_bytes(void) { return sizeof(double) * vlb::sur_reduce_doubles(); }
 
-vlb_status vlb_surrogate_features(int32_t H, int32_t W, double r_over_R, const float* snap, const float norm[4],
+vlb_status vlb_surrogate_norm(int64_t npix, const float* snap, float s_n_fixed, float s_u_fixed, const float g[4],
+                              double* d_work, double* d_sums, float* d_norm8, void* cuda_stream) {
+  if (npix < 1 || !snap || !d_work || !d_sums || !d_norm8)
+    return fail(nullptr, VLB_ERR_ARG, "vlb_surrogate_norm: bad argument");
+  const float ones[4] = {1.0f, 1.0f, 1.0f, 1.0f};
+  VLB_CUDA(nullptr, vlb::sur_norm(npix, snap, s_n_fixed, s_u_fixed, g ? g : ones, d_work, d_sums, d_norm8,
+                                  (cudaStream_t)cuda_stream));
+  return VLB_OK;
+}
+
+vlb_status vlb_surrogate_features(int32_t H, int32_t W, double r_over_R, const float* snap, const float* d_norm,
                                   void* out_bf16, void* cuda_stream) {
-  if (H < 1 || W < 1 || !snap || !out_bf16 || !norm || !(norm[1] > 0.0f) || !(norm[2] > 0.0f) || !(norm[3] > 0.0f))
+  if (H < 1 || W < 1 || !snap || !out_bf16 || !d_norm)
     return fail(nullptr, VLB_ERR_ARG, "vlb_surrogate_features: bad argument");
-  VLB_CUDA(nullptr, vlb::sur_features(H, W, r_over_R, snap, norm, out_bf16, (cudaStream_t)cuda_stream));
+  VLB_CUDA(nullptr, vlb::sur_features(H, W, r_over_R, snap, d_norm, out_bf16, (cudaStream_t)cuda_stream));
   return VLB_OK;
 }
 
-vlb_status vlb_surrogate_targets(int64_t npix, const float* before, const float* after, const float scale[4],
+vlb_status vlb_surrogate_targets(int64_t npix, const float* before, const float* after, const float* d_scale,
                                  float* target, void* cuda_stream) {
-  if (npix < 1 || !before || !after || !scale || !target)
+  if (npix < 1 || !before || !after || !d_scale || !target)
     return fail(nullptr, VLB_ERR_ARG, "vlb_surrogate_targets: bad argument");
-  VLB_CUDA(nullptr, vlb::sur_targets(npix, before, after, scale, target, (cudaStream_t)cuda_stream));
+  VLB_CUDA(nullptr, vlb::sur_targets(npix, before, after, d_scale, target, (cudaStream_t)cuda_stream));
   return VLB_OK;
 }
 
-vlb_status vlb_surrogate_apply(int64_t npix, const float* before, const float* pred16, const float scale[4],
+vlb_status vlb_surrogate_apply(int64_t npix, const float* before, const float* pred16, const float* d_scale,
                                float* after, void* cuda_stream) {
-  if (npix < 1 || !before || !pred16 || !scale || !after)
+  if (npix < 1 || !before || !pred16 || !d_scale || !after)
     return fail(nullptr, VLB_ERR_ARG, "vlb_surrogate_apply: bad argument");
-  VLB_CUDA(nullptr, vlb::sur_apply(npix, before, pred16, scale, after, (cudaStream_t)cuda_stream));
+  VLB_CUDA(nullptr, vlb::sur_apply(npix, before, pred16, d_scale, after, (cudaStream_t)cuda_stream));
+  return VLB_OK;
+}
+
+vlb_status vlb_snapshot_compare(int64_t npix, const float* a, const float* b, double* d_work, double* d_out4,
+                                void* cuda_stream) {
+  if (npix < 1 || !a || !b || !d_work || !d_out4) return fail(nullptr, VLB_ERR_ARG, "vlb_snapshot_compare: bad argument");
+  VLB_CUDA(nullptr, vlb::sur_compare(npix, a, b, d_work, d_out4, (cudaStream_t)cuda_stream));
   return VLB_OK;
 }
 

@@ -111,9 +111,11 @@ int totals_blocks();
 template <typename T>
 cudaError_t launch_snapshot_out(const T* state, int64_t stride, int64_t n, double n0, float* snap, cudaStream_t s);
 template <typename T>
-cudaError_t launch_snapshot_in(T* state, int64_t stride, int64_t n, double n0, const float* snap, cudaStream_t s);
-template <typename T>
-cudaError_t launch_shift(T* state, int64_t stride, int64_t n, double dn, double dphi, cudaStream_t s);
+cudaError_t launch_snapshot_in(T* state, int64_t stride, int64_t n, double n0, const float* snap, const double* shift,
+                               int keep_neq, cudaStream_t s);
+// shift[0..1] := the uniform shifts of n and phi that give the snapshot the totals (mass, phi_total)
+cudaError_t launch_snapshot_shift(const float* snap, const double* coefd, int nt, int ns, double mass,
+                                  double phi_total, double inv_area, double* partials, double* shift, cudaStream_t s);
 
 // Surrogate network kernels (vlb_conv.cu, vlb_surrogate.cu).
 bool conv_shape_ok(int H, int W, int cin, int cout, const char** why);
@@ -123,7 +125,10 @@ cudaError_t conv_fwd(int H, int W, int cin, int cout, const void* x, const void*
 cudaError_t conv_flip(int cin, int cout, const void* w, void* wf, cudaStream_t st);
 cudaError_t conv_wgrad(int H, int W, int cin, int cout, const void* x, const void* dy, float* dw, float* db,
                        float* partial, cudaStream_t st);
+cudaError_t sur_norm(int64_t n, const float* snap, float s_n, float s_u, const float* g4, double* part, double* sums,
+                     float* norm8, cudaStream_t st);
 cudaError_t sur_features(int H, int W, double a, const float* snap, const float* norm4, void* out, cudaStream_t st);
+cudaError_t sur_compare(int64_t n, const float* a, const float* b, double* part, double* out4, cudaStream_t st);
 cudaError_t sur_targets(int64_t n, const float* before, const float* after, const float* scale4, float* target,
                         cudaStream_t st);
 cudaError_t sur_apply(int64_t n, const float* before, const float* pred, const float* scale4, float* after,

@@ -46,6 +46,19 @@ def noise(seed: int, n_theta: int, n_phi: int, amplitude: float) -> np.ndarray:
     return amplitude * (2.0 * uniform01(seed, n_theta, n_phi) - 1.0)
 
 
+def quenched_noise(seed: int, n_theta: int, n_phi: int, corr: float, width: float) -> np.ndarray:
+    """Seeded noise quenched into domains: uniform noise (seed) smoothed by a periodic Gaussian filter
+    of `corr` grid cells (applied in Fourier space), scaled to zero mean and unit variance, then
+    phi = tanh(G corr / width), so that domains a few `corr` across are separated by tanh walls about
+    `width` cells wide.  A start in the coarsening regime of the phase-separation runs (Sec. 4)."""
+    u = noise(seed, n_theta, n_phi, 1.0)
+    fq = np.fft.fftfreq(n_theta)[:, None]
+    fs = np.fft.fftfreq(n_phi)[None, :]
+    g = np.fft.ifft2(np.fft.fft2(u) * np.exp(-2.0 * (math.pi * corr) ** 2 * (fq ** 2 + fs ** 2))).real
+    g = (g - g.mean()) / g.std()
+    return np.tanh(g * corr / width)
+
+
 def grid(n_theta: int, n_phi: int):
     """Node angles theta_q = q dtheta, varphi_s = s dvarphi on the periodic grid."""
     th = np.arange(n_theta) * (2.0 * math.pi / n_theta)

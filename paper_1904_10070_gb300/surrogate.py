@@ -78,11 +78,15 @@ class SurrogateNet:
     def loss_and_grad(self, target):
         vlb.vlb_mse_loss(self.H * self.W, self.out, target, self.grad_out, self.red_ws, self.loss, _stream())
 
-    def backward(self):
+    def backward(self, trace=None):
+        """Weight and bias gradients of every layer; `trace` (a list) receives a copy of the gradient
+        entering each layer, last layer first."""
         st = _stream()
         dz = self.grad_out
         for li in range(len(LAYERS) - 1, -1, -1):
             cin, cout = LAYERS[li]
+            if trace is not None:
+                trace.append(dz.clone())
             vlb.vlb_conv3x3_bwd_weight(self.H, self.W, cin, cout, self.acts[li], dz, self.dw[li], self.db[li],
                                        self.wg_ws, st)
             if li > 0:
@@ -124,55 +128,71 @@ def radius_for(seed: int) -> float:
     return 1.5 + 2.5 * float(inputs.uniform01(seed, 1, 1)[0, 0])
 
 
-class Dataset:
-    """Pairs (snapshot at t, snapshot at t + window) from solver trajectories, kept on the device,
-    with the per-sample input normalisation (n_mean, s_phi, s_n, s_u) of each `before` snapshot."""
+CORR_CELLS, WALL_CELLS = 4.0, 1.8
 
-    def __init__(self, before, after, radii, norms):
-        self.before, self.after, self.radii, self.norms = before, after, radii, norms
+
+def initial_phi(seed: int, H: int, W: int) -> np.ndarray:
+    """Start of a surrogate trajectory: seeded noise quenched into domains of a few cells
+    (inputs.quenched_noise), i.e. a torus early in coarsening."""
+    return inputs.quenched_noise(seed, H, W, CORR_CELLS, WALL_CELLS)
+
+
+class Normaliser:
+    """Input statistics of a snapshot on the device (vlb_surrogate_norm): fills an 8-float device
+    array (n_mean, s_phi, s_n, s_u, then the output scales g_c s_c) without a host read-back."""
+
+    def __init__(self, s_n: float = 0.0, s_u: float = 0.0, g=None):
+        import torch
+        self.work = torch.empty(vlb.vlb_reduce_workspace_bytes(), dtype=torch.uint8, device="cuda")
+        self.sums = torch.empty(8, dtype=torch.float64, device="cuda")
+        self.s_n, self.s_u, self.g = s_n, s_u, g
+
+    def __call__(self, snap, out8):
+        vlb.vlb_surrogate_norm(snap.shape[0], snap, self.s_n, self.s_u, self.g, self.work, self.sums, out8, _stream())
+
+    def host(self, snap):
+        """(n_mean, s_phi, s_n, s_u) of one snapshot, read back."""
+        import torch
+        out = torch.empty(8, dtype=torch.float32, device="cuda")
+        self(snap, out)
+        return tuple(float(x) for x in out[:4].cpu())
+
+
+class Dataset:
+    """Pairs (snapshot at t, snapshot at t + window) from solver trajectories, kept on the device.
+    stats[i] = (n_mean, s_phi, rms(n - n_mean), rms|u|/sqrt2) of before[i]; s_n and s_u, the medians of
+    the last two over the set, are the fixed input scales of n and u (per-snapshot values vanish at
+    rest)."""
+
+    def __init__(self, before, after, radii, stats):
+        self.before, self.after, self.radii, self.stats = before, after, radii, stats
+        self.s_n = float(np.median([t[2] for t in stats]))
+        self.s_u = float(np.median([t[3] for t in stats]))
+        self.norm8 = None  # per-pair device normalisation, filled by a Trainer
 
     def __len__(self):
         return len(self.radii)
 
 
-class Normaliser:
-    """Per-snapshot scales from FP64 channel sums (one small device reduction and read-back)."""
-
-    def __init__(self):
-        import torch
-        self.work = torch.empty(vlb.vlb_reduce_workspace_bytes(), dtype=torch.uint8, device="cuda")
-        self.sums = torch.empty(8, dtype=torch.float64, device="cuda")
-
-    def __call__(self, snap):
-        N = snap.shape[0]
-        vlb.vlb_channel_sums(N, 4, snap, self.work, self.sums, _stream())
-        s = self.sums.cpu().numpy()
-        mean, sq = s[:4] / N, s[4:] / N
-        s_phi = math.sqrt(max(sq[0], 0.0))
-        s_n = math.sqrt(max(sq[1] - mean[1] ** 2, 0.0))
-        s_u = math.sqrt(max(0.5 * (sq[2] + sq[3]), 0.0))
-        if not np.all(np.isfinite(s)):
-            return (float("nan"),) * 4
-        return (float(mean[1]), max(s_phi, 1e-12), max(s_n, 1e-12), max(s_u, 1e-12))
-
-
-def generate(seeds, H=256, W=512, window=50, pairs=5, spacing=100, batch=48, noise=0.01):
-    """Runs one trajectory per seed (batched through the ensemble path) and keeps `pairs` windows of
-    each: snapshots at steps k * spacing and k * spacing + window, k = 0 .. pairs - 1."""
+def generate(seeds, H=256, W=512, window=50, pairs=8, spacing=100, start=100, batch=48):
+    """Runs one trajectory per seed from initial_phi(seed) at rest (batched through the ensemble path)
+    and keeps `pairs` windows of each: snapshots at steps start + k spacing and start + k spacing +
+    window, k = 0 .. pairs - 1."""
     import torch
     N = H * W
-    norm = Normaliser()
-    before, after, radii, norms = [], [], [], []
+    stat = Normaliser()
+    before, after, radii, stats = [], [], [], []
     for i0 in range(0, len(seeds), batch):
         sel = seeds[i0:i0 + batch]
         ps = [member_params(radius_for(s), H, W) for s in sel]
         ens = vlb.Ensemble([vlb.make_params(**p, precision=vlb.FP32) for p in ps])
         for v, s in zip(ens.views, sel):
-            phi = inputs.noise(s, H, W, noise)
+            phi = initial_phi(s, H, W)
             z = np.zeros_like(phi)
             vlb.vlb_set_fields(v, np.ones_like(phi), z, z, phi)
         snaps = {}
-        marks = sorted({k * spacing for k in range(pairs)} | {k * spacing + window for k in range(pairs)})
+        firsts = [start + k * spacing for k in range(pairs)]
+        marks = sorted(set(firsts) | {m + window for m in firsts})
         done = 0
         for m in marks:
             if m > done:
@@ -181,52 +201,63 @@ def generate(seeds, H=256, W=512, window=50, pairs=5, spacing=100, batch=48, noi
             snaps[m] = [torch.empty((N, 4), dtype=torch.float32, device="cuda") for _ in sel]
             for v, buf in zip(ens.views, snaps[m]):
                 vlb.vlb_get_snapshot(v, buf)
-        torch.cuda.synchronize()
         for j, s in enumerate(sel):
-            for k in range(pairs):
-                before.append(snaps[k * spacing][j])
-                after.append(snaps[k * spacing + window][j])
+            for m in firsts:
+                before.append(snaps[m][j])
+                after.append(snaps[m + window][j])
                 radii.append(ps[j]["R"])
-                norms.append(norm(before[-1]))
+                stats.append(stat.host(before[-1]))
         ens.close()
         del snaps
-    return Dataset(before, after, radii, norms)
+    return Dataset(before, after, radii, stats)
 
 
 def target_ratios(ds: Dataset, sample: int = 64):
-    """g_c = mean over a sample of rms(change of channel c) / (its input scale): targets are then O(1)."""
+    """g_c = mean over a sample of rms(change of channel c over the window) / (input scale of c), so
+    that the targets are O(1)."""
     import torch
     N = ds.before[0].shape[0]
     tgt = torch.empty((N, 4), dtype=torch.float32, device="cuda")
-    norm = Normaliser()
+    norm = Normaliser(ds.s_n, ds.s_u)
+    n8 = torch.empty(8, dtype=torch.float32, device="cuda")
+    sums = torch.empty(8, dtype=torch.float64, device="cuda")
     idx = np.linspace(0, len(ds) - 1, min(sample, len(ds))).astype(int)
     acc = np.zeros(4)
     for i in idx:
-        _, s_phi, s_n, s_u = ds.norms[i]
-        vlb.vlb_surrogate_targets(N, ds.before[i], ds.after[i], [s_phi, s_n, s_u, s_u], tgt, _stream())
-        vlb.vlb_channel_sums(N, 4, tgt, norm.work, norm.sums, _stream())
-        sq = norm.sums.cpu().numpy()[4:] / N
+        norm(ds.before[i], n8)
+        vlb.vlb_surrogate_targets(N, ds.before[i], ds.after[i], n8[4:], tgt, _stream())
+        vlb.vlb_channel_sums(N, 4, tgt, norm.work, sums, _stream())
+        sq = sums.cpu().numpy()[4:] / N
         acc += np.sqrt(np.maximum(sq, 0.0))
     return [float(max(x / len(idx), 1e-6)) for x in acc]
 
 
 class Trainer:
-    def __init__(self, net: SurrogateNet, ratios):
+    """Fits the network to a Dataset.  Inputs are the snapshot scaled by (n_mean, s_phi, s_n, s_u);
+    targets are the window's change divided by g_c times the input scale of channel c."""
+
+    def __init__(self, net: SurrogateNet, ratios, s_n: float, s_u: float, weights=(1.0, 1.0, 1.0, 1.0)):
         import torch
         self.net = net
-        self.g = list(ratios)
-        N = net.H * net.W
-        self.target = torch.empty((N, 4), dtype=torch.float32, device="cuda")
+        # a loss weight w_c on channel c is a target scaled by w_c: g_c -> g_c / w_c
+        self.g = [float(x) / float(w) for x, w in zip(ratios, weights)]
+        self.s_n, self.s_u = float(s_n), float(s_u)
+        self.normaliser = Normaliser(self.s_n, self.s_u, self.g)
+        self.target = torch.empty((net.H * net.W, 4), dtype=torch.float32, device="cuda")
 
-    def out_scale(self, norm):
-        _, s_phi, s_n, s_u = norm
-        return [self.g[0] * s_phi, self.g[1] * s_n, self.g[2] * s_u, self.g[3] * s_u]
+    def prepare(self, ds: Dataset):
+        import torch
+        if ds.norm8 is None or getattr(ds, "norm_key", None) != (self.s_n, self.s_u, tuple(self.g)):
+            ds.norm8 = torch.empty((len(ds), 8), dtype=torch.float32, device="cuda")
+            for i in range(len(ds)):
+                self.normaliser(ds.before[i], ds.norm8[i])
+            ds.norm_key = (self.s_n, self.s_u, tuple(self.g))
 
-    def sample_loss(self, before, after, R, norm, train: bool, lr: float = 1e-3):
+    def sample_loss(self, ds: Dataset, i: int, train: bool, lr: float = 1e-3):
         net, st = self.net, _stream()
         N = net.H * net.W
-        vlb.vlb_surrogate_features(net.H, net.W, 1.0 / R, before, norm, net.acts[0], st)
-        vlb.vlb_surrogate_targets(N, before, after, self.out_scale(norm), self.target, st)
+        vlb.vlb_surrogate_features(net.H, net.W, 1.0 / ds.radii[i], ds.before[i], ds.norm8[i], net.acts[0], st)
+        vlb.vlb_surrogate_targets(N, ds.before[i], ds.after[i], ds.norm8[i, 4:], self.target, st)
         net.forward()
         net.loss_and_grad(self.target)
         if train:
@@ -235,16 +266,18 @@ class Trainer:
         return net.loss
 
     def fit(self, ds: Dataset, epochs: int, lr: float = 1e-3, seed: int = 0, log_every: int = 0):
+        """Adam over the pairs in seeded random order with a cosine learning-rate schedule."""
         import torch
+        self.prepare(ds)
         rng = np.random.default_rng(seed)
         hist = []
         n_it = epochs * len(ds)
         t0 = time.perf_counter()
         it = 0
-        for ep in range(epochs):
+        for _ in range(epochs):
             for i in rng.permutation(len(ds)):
-                lr_t = lr * 0.5 * (1.0 + math.cos(math.pi * it / n_it))  # cosine schedule
-                loss = self.sample_loss(ds.before[i], ds.after[i], ds.radii[i], ds.norms[i], True, lr_t)
+                lr_t = lr * 0.5 * (1.0 + math.cos(math.pi * it / n_it))
+                loss = self.sample_loss(ds, int(i), True, lr_t)
                 it += 1
                 if log_every and it % log_every == 0:
                     hist.append((it, float(loss.cpu())))
@@ -252,9 +285,16 @@ class Trainer:
         return hist, time.perf_counter() - t0
 
     def evaluate(self, ds: Dataset):
-        vals = [float(self.sample_loss(ds.before[i], ds.after[i], ds.radii[i], ds.norms[i], False).cpu())
-                for i in range(len(ds))]
-        return float(np.mean(vals))
+        self.prepare(ds)
+        return float(np.mean([float(self.sample_loss(ds, i, False).cpu()) for i in range(len(ds))]))
+
+    def predict(self, snap, R: float, norm8, out):
+        """out := the network's estimate of snap one window ahead (all on the device)."""
+        net, st = self.net, _stream()
+        self.normaliser(snap, norm8)
+        vlb.vlb_surrogate_features(net.H, net.W, 1.0 / R, snap, norm8, net.acts[0], st)
+        net.forward()
+        vlb.vlb_surrogate_apply(net.H * net.W, snap, net.out, norm8[4:], out, st)
 
 
 # ------------------------------------------------------------------------------------------------
@@ -262,61 +302,122 @@ class Trainer:
 # ------------------------------------------------------------------------------------------------
 
 class Advancer:
-    """Advances a solver (FP32 handle) by windows of `window` steps with the network.
+    """Advances an FP32 solver by windows of `window` steps, most of them with the network.
 
-    Every `check_every` windows the solver itself runs the window from the unchanged state and its
-    phi is compared with the prediction: a relative L-infinity error above `phi_tol` keeps the
-    solver's result (a fallback), otherwise the prediction is taken.  A prediction whose free energy
-    Psi rises is replaced by a solver window too.  A taken prediction restarts the solver at
-    f = f^eq(n, u) with int n sqrt(g) and int phi sqrt(g) projected back to their values before the
-    window (vlb_set_snapshot).
+    Every `check_every`-th window is a check: the network predicts the window, the solver runs it from
+    the same state, and the two phi fields are compared (vlb_snapshot_compare) by their relative L2
+    error ||phi_net - phi_solver||_2 / ||phi_solver||_2 (norm="l2") or relative L-infinity error
+    (norm="linf").  The solver's result is kept.  A check whose error exceeds `phi_tol` (or a
+    non-finite state) is a fallback: the state returns to the last checked one, the solver redoes the
+    windows since then and runs the next `check_every` windows alone.  A taken prediction (n', u',
+    phi') replaces the state by f + f^eq(n', u') - f^eq(n, u), keeping the non-equilibrium part of f
+    (it relaxes over tau / dt steps, many windows when tau >> dt), with the conserved totals
+    int n sqrt(g) and int phi sqrt(g) restored to their values at the start (vlb_set_snapshot).  Between checks nothing is read back to the host,
+    and a predicted window (snapshot, statistics, features, eight convolutions, restart) replays as
+    one CUDA graph when the solver runs on its own (non-default) stream.
     """
 
-    def __init__(self, trainer: Trainer, solver: vlb.Solver, window: int = 50):
+    def __init__(self, trainer: Trainer, solver: vlb.Solver, window: int = 50, check_every: int = 4,
+                 phi_tol: float = 1e-2, norm: str = "l2", graph: bool = True):
         import torch
+        if solver.p.precision != vlb.FP32:
+            raise ValueError("the surrogate advances FP32 solvers")
+        if norm not in ("l2", "linf"):
+            raise ValueError("norm must be 'l2' or 'linf'")
         self.tr, self.s, self.window = trainer, solver, window
+        self.check_every, self.phi_tol, self.norm = check_every, phi_tol, norm
         self.R = solver.p.R
+        self.stream = solver.stream
+        self.use_graph = graph and self.stream.cuda_stream != 0
+        self.graph = None
         N = solver.p.n_theta * solver.p.n_phi
-        self.snap = torch.empty((N, 4), dtype=torch.float32, device="cuda")
-        self.pred = torch.empty((N, 4), dtype=torch.float32, device="cuda")
-        self.check = torch.empty((N, 4), dtype=torch.float32, device="cuda")
-        self.normaliser = Normaliser()
-        self.fallbacks = 0
-        self.checks = 0
-        self.max_check_err = 0.0
+        dev = "cuda"
+        with torch.cuda.stream(self.stream):
+            self.snap = torch.empty((N, 4), dtype=torch.float32, device=dev)
+            self.pred = torch.empty((N, 4), dtype=torch.float32, device=dev)
+            self.check = torch.empty((N, 4), dtype=torch.float32, device=dev)
+            self.norm8 = torch.empty(8, dtype=torch.float32, device=dev)
+            self.cmp = torch.empty(4, dtype=torch.float64, device=dev)
+            self.work = torch.empty(vlb.vlb_reduce_workspace_bytes(), dtype=torch.uint8, device=dev)
+            ptr, stride = vlb.vlb_state_device(solver.h)
+            off = ptr - solver.workspace.data_ptr()
+            self.state = solver.workspace[off:off + 18 * stride * 4]  # the 18 FP32 state arrays
+            self.good = torch.empty_like(self.state)
+        t = solver.totals()
+        self.conserve = (t[0], t[1])
+        self.solver_only = 0
+        self.since_good = 0
+        self.count = 0
+        self.predicted = 0
+        self.kinds = []
+        self.errors = []
+        self.errors_linf = []
 
-    def predict(self):
-        """pred := the network's estimate of the state one window ahead of the solver's state."""
-        net, st = self.tr.net, _stream()
+    def _save(self):
+        self.good.copy_(self.state)
+        self.since_good = 0
+
+    def _predict_window(self):
         vlb.vlb_get_snapshot(self.s.h, self.snap)
-        norm = self.normaliser(self.snap)
-        vlb.vlb_surrogate_features(net.H, net.W, 1.0 / self.R, self.snap, norm, net.acts[0], st)
-        net.forward()
-        vlb.vlb_surrogate_apply(net.H * net.W, self.snap, net.out, self.tr.out_scale(norm), self.pred, st)
+        self.tr.predict(self.snap, self.R, self.norm8, self.pred)
+        vlb.vlb_set_snapshot(self.s.h, self.pred, self.conserve, keep_neq=True)
 
-    def window_step(self, k: int, check_every: int, phi_tol: float) -> str:
-        s = self.s
-        tot = s.totals()
-        self.predict()
-        if not all(math.isfinite(x) for x in self.normaliser(self.pred)):  # unusable prediction
-            self.fallbacks += 1
-            s.step(self.window)
-            return "fallback"
-        if check_every > 0 and (k + 1) % check_every == 0:
-            s.step(self.window)  # the judge: the solver over the same window from the same state
+    def _surrogate_window(self):
+        import torch
+        self.predicted += 1
+        if not self.use_graph or self.predicted == 1:  # the first one runs eagerly (module loading)
+            self._predict_window()
+            return
+        if self.graph is None:
+            self.graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.graph, stream=self.stream):
+                self._predict_window()
+        self.graph.replay()
+
+    def window_step(self) -> str:
+        import torch
+        with torch.cuda.stream(self.stream):
+            return self._window_step()
+
+    def _window_step(self) -> str:
+        s, w = self.s, self.window
+        if self.count == 0:
+            self._save()
+        self.count += 1
+        if self.solver_only > 0:
+            s.step(w)
+            self.solver_only -= 1
+            self.since_good += 1
+            if self.solver_only == 0:
+                self._save()
+            kind = "solver"
+        elif self.check_every > 0 and self.count % self.check_every == 0:
+            vlb.vlb_get_snapshot(s.h, self.snap)
+            self.tr.predict(self.snap, self.R, self.norm8, self.pred)
+            s.step(w)
             vlb.vlb_get_snapshot(s.h, self.check)
-            pc = self.check[:, 0].cpu().numpy().astype(np.float64)
-            pp = self.pred[:, 0].cpu().numpy().astype(np.float64)
-            err = float(np.max(np.abs(pp - pc)) / max(np.max(np.abs(pc)), 1e-30))
-            self.checks += 1
-            self.max_check_err = max(self.max_check_err, err)
-            if err > phi_tol:
-                self.fallbacks += 1
-                return "fallback"
-        vlb.vlb_set_snapshot(s.h, self.pred, (tot[0], tot[1]))
-        if s.totals()[2] > tot[2] * (1.0 + 1e-3) + 1e-12:  # Psi rose: redo the window with the solver
-            self.fallbacks += 1
-            vlb.vlb_set_snapshot(s.h, self.snap, (tot[0], tot[1]))
-            s.step(self.window)
-            return "fallback"
-        return "surrogate"
+            vlb.vlb_snapshot_compare(self.pred.shape[0], self.pred, self.check, self.work, self.cmp, self.stream.cuda_stream)
+            dmax, bmax, d2, b2 = (float(x) for x in self.cmp.cpu())
+            e_inf = dmax / bmax if bmax > 0 else math.inf
+            e_2 = math.sqrt(d2 / b2) if b2 > 0 else math.inf
+            self.errors.append(e_2)
+            self.errors_linf.append(e_inf)
+            err = e_2 if self.norm == "l2" else e_inf
+            if err <= self.phi_tol:
+                self._save()
+                kind = "checked"
+            else:
+                self.state.copy_(self.good)
+                s.step(w * (self.since_good + 1))
+                self.solver_only = self.check_every
+                self._save()
+                kind = "fallback"
+        else:
+            self._surrogate_window()
+            self.since_good += 1
+            kind = "surrogate"
+        self.kinds.append(kind)
+        return kind
+
+    def advance(self, nwin: int):
+        return [self.window_step() for _ in range(nwin)]

@@ -27,8 +27,8 @@ EXPORTS = ["vlb_workspace_bytes", "vlb_max_stable_dt", "vlb_create", "vlb_destro
            "vlb_step_noalloc", "vlb_ensemble_workspace_bytes", "vlb_ensemble_create", "vlb_ensemble_step",
            "vlb_ensemble_member", "vlb_ensemble_tile_rows", "vlb_get_snapshot", "vlb_set_snapshot",
            "vlb_conv3x3_fwd", "vlb_conv3x3_flip", "vlb_conv3x3_wgrad_workspace_bytes", "vlb_conv3x3_bwd_weight",
-           "vlb_reduce_workspace_bytes", "vlb_surrogate_features", "vlb_surrogate_targets", "vlb_surrogate_apply",
-           "vlb_channel_sums", "vlb_mse_loss", "vlb_adam_step", "vlb_to_bf16"]
+           "vlb_reduce_workspace_bytes", "vlb_surrogate_norm", "vlb_surrogate_features", "vlb_surrogate_targets",
+           "vlb_surrogate_apply", "vlb_snapshot_compare", "vlb_channel_sums", "vlb_mse_loss", "vlb_adam_step", "vlb_to_bf16"]
 
 NOALLOC_SCRATCH_BYTES = 24 * 1024 * 1024
 
@@ -101,15 +101,18 @@ def lib() -> ctypes.CDLL:
     L.vlb_conv3x3_wgrad_workspace_bytes.restype = S
     L.vlb_conv3x3_bwd_weight.argtypes = [I32, I32, I32, I32, P, P, P, P, P, S, P]
     L.vlb_reduce_workspace_bytes.argtypes, L.vlb_reduce_workspace_bytes.restype = [], S
-    L.vlb_surrogate_features.argtypes = [I32, I32, ctypes.c_double, P, FP, P, P]
-    L.vlb_surrogate_targets.argtypes = [I64, P, P, FP, P, P]
-    L.vlb_surrogate_apply.argtypes = [I64, P, P, FP, P, P]
+    L.vlb_surrogate_norm.argtypes = [I64, P, ctypes.c_float, ctypes.c_float, FP, P, P, P, P]
+    L.vlb_surrogate_features.argtypes = [I32, I32, ctypes.c_double, P, P, P, P]
+    L.vlb_surrogate_targets.argtypes = [I64, P, P, P, P, P]
+    L.vlb_surrogate_apply.argtypes = [I64, P, P, P, P, P]
+    L.vlb_snapshot_compare.argtypes = [I64, P, P, P, P, P]
     L.vlb_channel_sums.argtypes = [I64, I32, P, P, P, P]
     L.vlb_mse_loss.argtypes = [I64, P, P, P, P, P, P]
     L.vlb_adam_step.argtypes = [I64, P, P, P, P, I64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                 ctypes.c_float, P, P]
     L.vlb_to_bf16.argtypes = [I64, P, P, P]
-    for name in ("vlb_conv3x3_fwd", "vlb_conv3x3_flip", "vlb_conv3x3_bwd_weight", "vlb_surrogate_features",
+    for name in ("vlb_conv3x3_fwd", "vlb_conv3x3_flip", "vlb_conv3x3_bwd_weight", "vlb_surrogate_norm",
+                 "vlb_surrogate_features", "vlb_snapshot_compare",
                  "vlb_surrogate_targets", "vlb_surrogate_apply", "vlb_channel_sums", "vlb_mse_loss", "vlb_adam_step",
                  "vlb_to_bf16"):
         getattr(L, name).restype = I32
@@ -227,9 +230,9 @@ def vlb_get_snapshot(h, snap):
     _check(lib().vlb_get_snapshot(h, _ptr(snap)), h)
 
 
-def vlb_set_snapshot(h, snap, conserve=None):
+def vlb_set_snapshot(h, snap, conserve=None, keep_neq=False):
     c = None if conserve is None else (ctypes.c_double * 2)(*conserve)
-    _check(lib().vlb_set_snapshot(h, _ptr(snap), c), h)
+    _check(lib().vlb_set_snapshot(h, _ptr(snap), c, 1 if keep_neq else 0), h)
 
 
 def vlb_conv3x3_fwd(H, W, cin, cout, x, w, bias, mask, relu, y_bf16, y_f32, stream):
@@ -254,19 +257,31 @@ def vlb_reduce_workspace_bytes() -> int:
     return lib().vlb_reduce_workspace_bytes()
 
 
-def vlb_surrogate_features(H, W, r_over_R, snap, norm, out, stream):
-    """norm = (n_mean, s_phi, s_n, s_u)."""
-    _check(lib().vlb_surrogate_features(H, W, r_over_R, _ptr(snap), _scale4(norm), _ptr(out), ctypes.c_void_p(stream)))
+def vlb_surrogate_norm(npix, snap, s_n_fixed, s_u_fixed, g, work, sums, norm8, stream):
+    """norm8 (device, 8 floats) := (n_mean, s_phi, s_n, s_u, g0 s_phi, g1 s_n, g2 s_u, g3 s_u)."""
+    gg = None if g is None else _scale4(g)
+    _check(lib().vlb_surrogate_norm(npix, _ptr(snap), float(s_n_fixed), float(s_u_fixed), gg, _ptr(work), _ptr(sums),
+                                    _ptr(norm8), ctypes.c_void_p(stream)))
 
 
-def vlb_surrogate_targets(npix, before, after, scale, target, stream):
-    _check(lib().vlb_surrogate_targets(npix, _ptr(before), _ptr(after), _scale4(scale), _ptr(target),
+def vlb_surrogate_features(H, W, r_over_R, snap, d_norm, out, stream):
+    """d_norm: device (n_mean, s_phi, s_n, s_u)."""
+    _check(lib().vlb_surrogate_features(H, W, r_over_R, _ptr(snap), _ptr(d_norm), _ptr(out), ctypes.c_void_p(stream)))
+
+
+def vlb_surrogate_targets(npix, before, after, d_scale, target, stream):
+    _check(lib().vlb_surrogate_targets(npix, _ptr(before), _ptr(after), _ptr(d_scale), _ptr(target),
                                        ctypes.c_void_p(stream)))
 
 
-def vlb_surrogate_apply(npix, before, pred16, scale, after, stream):
-    _check(lib().vlb_surrogate_apply(npix, _ptr(before), _ptr(pred16), _scale4(scale), _ptr(after),
+def vlb_surrogate_apply(npix, before, pred16, d_scale, after, stream):
+    _check(lib().vlb_surrogate_apply(npix, _ptr(before), _ptr(pred16), _ptr(d_scale), _ptr(after),
                                      ctypes.c_void_p(stream)))
+
+
+def vlb_snapshot_compare(npix, a, b, work, out4, stream):
+    """out4 (device, 4 doubles) := (max |a.phi - b.phi|, max |b.phi|, sum (a.phi - b.phi)^2, sum b.phi^2)."""
+    _check(lib().vlb_snapshot_compare(npix, _ptr(a), _ptr(b), _ptr(work), _ptr(out4), ctypes.c_void_p(stream)))
 
 
 def vlb_channel_sums(npix, C, x, work, out, stream):

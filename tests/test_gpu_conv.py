@@ -158,3 +158,41 @@ def test_snapshot_roundtrip_restarts_at_equilibrium_and_conserves():
     r, a, b, _, _ = s.fields()
     np.testing.assert_allclose(f16.reshape(4, 4, nt, ns), O.feq(r, a, b), rtol=0, atol=2e-6)
     s.close()
+
+
+def test_snapshot_restart_keeps_the_nonequilibrium_part():
+    """keep_neq: f := f + f^eq(n', u') - f^eq(n, u).  The state's own snapshot leaves the populations
+    unchanged bit for bit; a changed one gives f the new moments and keeps f - f^eq."""
+    import torch
+    from oracle import vlb_oracle as O
+    nt, ns = 32, 64
+    p = vlb.make_params(R=2.5, r=1.0, n_theta=nt, n_phi=ns, dt=1e-3, tau=0.5, M=0.05, A=0.3, kappa=0.01,
+                        precision=vlb.FP32)
+    rng = np.random.default_rng(12)
+    rho = 1.0 + 0.05 * rng.uniform(-1, 1, (nt, ns))
+    ut, up = 0.03 * rng.uniform(-1, 1, (nt, ns)), 0.03 * rng.uniform(-1, 1, (nt, ns))
+    s = vlb.Solver(p)
+    s.set_fields(rho, ut, up, np.tanh(2 * rng.uniform(-1, 1, (nt, ns))))
+    s.step(20)  # develops a non-equilibrium part
+    f0, phi0 = s.get_state()
+    snap = torch.empty((nt * ns, 4), dtype=torch.float32, device="cuda")
+    vlb.vlb_get_snapshot(s.h, snap)
+    vlb.vlb_set_snapshot(s.h, snap, None, keep_neq=True)
+    f1, phi1 = s.get_state()
+    np.testing.assert_array_equal(f1, f0)
+    np.testing.assert_allclose(phi1, phi0, rtol=0, atol=1e-7)
+    r0, a0, b0, _, _ = s.fields()
+    neq0 = f0.reshape(4, 4, nt, ns) - O.feq(r0, a0, b0)
+    assert np.max(np.abs(neq0)) > 1e-5  # there is a non-equilibrium part to keep
+    sn = snap.cpu().numpy().astype(np.float64)
+    sn[:, 1] *= 1.002
+    sn[:, 2] += 0.01
+    vlb.vlb_set_snapshot(s.h, torch.tensor(sn, dtype=torch.float32, device="cuda"), None, keep_neq=True)
+    f2, _ = s.get_state()
+    r2, a2, b2, _, _ = s.fields()
+    np.testing.assert_allclose(r2.ravel(), sn[:, 1], rtol=2e-6)
+    np.testing.assert_allclose(a2.ravel(), sn[:, 2], rtol=0, atol=2e-6)
+    np.testing.assert_allclose(b2.ravel(), sn[:, 3], rtol=0, atol=2e-6)
+    neq2 = f2.reshape(4, 4, nt, ns) - O.feq(r2, a2, b2)
+    np.testing.assert_allclose(neq2, neq0, rtol=0, atol=2e-6)
+    s.close()
