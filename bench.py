@@ -177,10 +177,10 @@ def _calibrated_rows(target_s: float, steps: int) -> int:
     O.step(f, ph, geo)
     rate = 32 * ns / (time.perf_counter() - t0)  # node-steps per second
     # larger grids run slower per node (memory-bound numpy temporaries): keep a factor 2 of margin
-    return int(max(1, min(512, 0.5 * target_s * rate / (ns * steps))))
+    return int(max(1, min(1024, 0.5 * target_s * rate / (ns * steps))))
 
 
-def cpu_baseline(steps: int = 2, target_s: float = 15.0):
+def cpu_baseline(steps: int = 2, target_s: float = 20.0):
     """The FP64 oracle as it stands, on a bounded sub-grid of the workload (single-threaded numpy)."""
     rows = _calibrated_rows(target_s, steps)
     O, geo, f, ph, ns = _oracle_sample(rows)

@@ -37,7 +37,8 @@ struct vlb_handle {
   double* partials;    // totals_blocks() * 8
   double* totals;      // 8 doubles (read-out)
   double* diag;        // 8 doubles (last in-step diagnostic)
-  int* flag;           // device flag: diagnostics found an unstable state
+  int* flag;           // device flag: diagnostics found an unstable state (1) or a bulk copy gave up (2)
+  vlb::StageMaps* maps = nullptr;  // FP32 UW3: tensor maps of the three stage inputs (NULL: per-thread copies)
   double n0;           // reference density of the stored deviations g = f - n0 w_i w_j
   int64_t steps_done;
   char err[512];
@@ -253,18 +254,20 @@ vlb_status run_steps(vlb_handle* h, int64_t nsteps) {
   a.kappa = (T)p.kappa;
   a.gt = (T)(1.0 / (2.0 * p.r * (2.0 * M_PI / p.n_theta)));
   a.n0 = (T)h->n0;
+  a.err = h->flag;
   T* U0 = (T*)h->U[0];
   T* U1 = (T*)h->U[1];
   T* U2 = (T*)h->U[2];
   for (int64_t n = 0; n < nsteps; ++n) {
     // SSP-RK3 (Shu & Osher 1988): U1 = U + dt L(U); U2 = 3/4 U + 1/4 (U1 + dt L(U1));
     // U <- 1/3 U + 2/3 (U2 + dt L(U2))
+    const vlb::StageMaps* m = h->maps;
     a.fin = U0; a.f0 = nullptr; a.fout = U1; a.b = (T)1;
-    VLB_CUDA(h, vlb::launch_stage<T>(a, p.advection, p.ch_mode, h->stream));
+    VLB_CUDA(h, vlb::launch_stage<T>(a, p.advection, p.ch_mode, h->stream, m ? m + 0 : nullptr));
     a.fin = U1; a.f0 = U0; a.fout = U2; a.b = (T)0.25;
-    VLB_CUDA(h, vlb::launch_stage<T>(a, p.advection, p.ch_mode, h->stream));
+    VLB_CUDA(h, vlb::launch_stage<T>(a, p.advection, p.ch_mode, h->stream, m ? m + 1 : nullptr));
     a.fin = U2; a.f0 = U0; a.fout = U0; a.b = (T)(2.0 / 3.0);
-    VLB_CUDA(h, vlb::launch_stage<T>(a, p.advection, p.ch_mode, h->stream));
+    VLB_CUDA(h, vlb::launch_stage<T>(a, p.advection, p.ch_mode, h->stream, m ? m + 2 : nullptr));
     h->steps_done++;
     if (p.diag_every > 0 && (h->steps_done % p.diag_every == 0 || n + 1 == nsteps)) {
       VLB_CUDA(h, vlb::launch_totals<T>(U0, h->stride, h->coefD, p.n_theta, p.n_phi, p.R, p.r, p.A, p.kappa,
@@ -447,6 +450,15 @@ vlb_status vlb_create(const vlb_params* p, void* d_workspace, size_t bytes, void
     delete h;
     return fail(nullptr, VLB_ERR_CUDA, "vlb_create upload: %s", cudaGetErrorString(e));
   }
+  if (h->esize == 4 && p->advection == VLB_UW3 && vlb::stage_maps_apply(p->n_theta, p->n_phi)) {
+    h->maps = new (std::nothrow) vlb::StageMaps[3];
+    for (int k = 0; k < 3 && h->maps; ++k)
+      if (vlb::make_stage_maps((const float*)h->U[k], (const float*)h->U[0], p->n_theta, p->n_phi, h->stride,
+                               h->maps + k) != cudaSuccess) {
+        delete[] h->maps;  // the driver has no tensor-map encoder: per-thread copies only
+        h->maps = nullptr;
+      }
+  }
   *out = h;
   return VLB_OK;
 }
@@ -460,6 +472,7 @@ vlb_status vlb_destroy(vlb_handle* h) {
     for (int i = 0; i < h->count; ++i) delete h->views[i];
     delete[] h->views;
   }
+  delete[] h->maps;
   delete h;
   return VLB_OK;
 }

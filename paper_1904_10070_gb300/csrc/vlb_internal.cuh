@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libvlb (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (type only: the encoder is looked up in the driver at run time)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -68,7 +69,20 @@ struct StageArgs {
   T b, dt;         // U_out = U0 + b (U_in - U0 + dt L(U_in)); without U0: U_in + dt L(U_in)
   T inv_tau, M, A, kappa, gt;  // gt = 1 / (2 r dtheta)
   T n0;             // reference density of the stored deviations
+  int* err;         // device flag raised if a bounded wait on a bulk copy gives up (may be NULL)
 };
+
+// Tensor maps of the FP32 UW3 stage kernel over the 18 state arrays: the halo box of the stage
+// input (fin) and the U^n tile (f0).  With them, interior tiles are staged by the tensor-memory-
+// access unit (cp.async.bulk.tensor) instead of per-thread copies.
+struct StageMaps {
+  CUtensorMap box;
+  CUtensorMap tile;
+};
+// Whether a grid takes the tensor-map path (FP32 UW3 with n_phi % 4 == 0 and a grid at least one
+// box large).
+bool stage_maps_apply(int nt, int ns);
+cudaError_t make_stage_maps(const float* fin, const float* f0, int nt, int ns, int64_t stride, StageMaps* out);
 
 // Ensemble member as seen by the batched stage kernel (FP32 state).
 struct EnsembleMember {
@@ -84,8 +98,10 @@ struct EnsembleMember {
 // One stage (0, 1, 2) of every ensemble member; items[b] = (member, tile index), tile_rows 16 or 8.
 cudaError_t launch_ensemble_stage(const EnsembleMember* members, const int2* items, int nitems, int stage,
                                   int tile_rows, int ch_mode, cudaStream_t s);
+// maps: tensor maps for this stage's fin / f0 (FP32 UW3 only), or NULL for per-thread copies.
 template <typename T>
-cudaError_t launch_stage(const StageArgs<T>& a, int advection, int ch_mode, cudaStream_t s);
+cudaError_t launch_stage(const StageArgs<T>& a, int advection, int ch_mode, cudaStream_t s,
+                         const StageMaps* maps = nullptr);
 
 // Auxiliary kernels (vlb_aux.cu).  Staging arrays are FP64 [n_theta][n_phi].
 template <typename T>

@@ -117,6 +117,7 @@ cudaError_t run(const vlb_params* p, T* state, int64_t stride, double n0, int64_
   a.kappa = (T)p->kappa;
   a.gt = (T)(1.0 / (2.0 * p->r * (2.0 * M_PI / nt)));
   a.n0 = (T)n0;
+  a.err = nullptr;
   for (int64_t n = 0; n < nsteps; ++n) {
     a.fin = state; a.f0 = nullptr; a.fout = U1; a.b = (T)1;
     if ((e = vlb::launch_stage<T>(a, p->advection, p->ch_mode, st)) != cudaSuccess) return e;

@@ -57,7 +57,8 @@ struct Lay {
   static constexpr int UT_OFF = N_OFF + MQ * MS;
   static constexpr int UP_OFF = UT_OFF + MQ * MS;
   static constexpr int MU_OFF = UP_OFF + MQ * MS;
-  static constexpr int TOTAL = MU_OFF + MQ * MS;
+  static constexpr int MB_OFF = (MU_OFF + MQ * MS + 1) / 2 * 2;  // two 8-byte mbarriers
+  static constexpr int TOTAL = MB_OFF + 16 / (int)sizeof(T);
   static constexpr size_t BYTES = sizeof(T) * (size_t)TOTAL;
   static_assert((BOX * sizeof(T)) % 16 == 0 && (BS * sizeof(T)) % 16 == 0 && (BQ * BS * sizeof(T)) % 16 == 0,
                 "box rows and arrays keep 16-byte alignment");
@@ -90,6 +91,40 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// mbarrier and bulk tensor copy (TMA) primitives.
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: gives up after 2^22 polls (each poll may suspend the thread for a while), so that a
+// copy that never lands cannot hang the GPU.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  for (int it = 0; it < (1 << 22); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+// Copy the box {x, y, z} .. + box dims of a 3-D tensor map into shared memory (128-byte aligned),
+// completing on bar.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
+      "[%2];\n" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+      : "memory");
 }
 
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
@@ -134,6 +169,14 @@ __host__ __device__ inline bool chunked(int nt, int ns) {
 // and of the tile's U^n.
 // ---------------------------------------------------------------------------------------------
 template <typename L, typename T>
+__device__ __forceinline__ void issue_co(const StageArgs<T>& a, T* co, int q0, int tid) {
+  for (int idx = tid; idx < NCT * L::BQ; idx += L::NTH) {
+    const int k = idx / L::BQ, r = idx - k * L::BQ;
+    cp_async_small<sizeof(T)>(co + idx, a.coef + (int64_t)k * a.nt + wrap(q0 + r - L::H, a.nt));
+  }
+}
+
+template <typename L, typename T>
 __device__ __forceinline__ void issue_box(const StageArgs<T>& a, T* box, T* co, int q0, int s0, int tid) {
   constexpr int H = L::H, BQ = L::BQ, BS = L::BS, HS = L::HS;
   constexpr int VEC = 16 / sizeof(T);
@@ -177,10 +220,7 @@ __device__ __forceinline__ void issue_box(const StageArgs<T>& a, T* box, T* co, 
       cp_async_small<sizeof(T)>(box + (k * BQ + r) * BS + c, a.fin + k * stride + (int64_t)gq * ns + gs);
     }
   }
-  for (int idx = tid; idx < NCT * BQ; idx += L::NTH) {
-    const int k = idx / BQ, r = idx - k * BQ;
-    cp_async_small<sizeof(T)>(co + idx, a.coef + (int64_t)k * nt + wrap(q0 + r - H, nt));
-  }
+  issue_co<L>(a, co, q0, tid);
 }
 
 template <typename L, typename T>
@@ -633,16 +673,80 @@ __device__ __forceinline__ void tile_body(const StageArgs<T>& a, const VConst<T>
   }
 }
 
+// Steps 1-3 for an interior tile (box inside the grid, no wrap-around) of the FP32 UW3 pair path,
+// with the box and the U^n tile staged by two tensor-map copies issued by one thread and
+// completing on two mbarriers.  The layout in shared memory is the one issue_box / issue_u0 produce.
+template <typename L, int CH, bool F0>
+__device__ __forceinline__ void tile_body_tma(const StageArgs<float>& a, const VConst<float>& vc, float* sm, int tid,
+                                              int q0, int s0, const CUtensorMap* tmb, const CUtensorMap* tmu) {
+  constexpr unsigned BOX_BYTES = sizeof(float) * L::NST * L::BQ * L::BS;
+  constexpr unsigned U0_BYTES = sizeof(float) * L::NST * L::TQ * TS;
+  static_assert((L::BOX_OFF * sizeof(float)) % 128 == 0 && (L::U0_OFF * sizeof(float)) % 128 == 0,
+                "tensor-map destinations are 128-byte aligned");
+  static_assert((L::MB_OFF * sizeof(float)) % 8 == 0, "mbarriers are 8-byte aligned");
+  float* box = sm + L::BOX_OFF;
+  float* co = sm + L::CO_OFF;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L::MB_OFF);
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_init(bar + 1, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    mbar_expect_tx(bar, BOX_BYTES);
+    tma_load_3d(box, tmb, bar, s0 - L::HS, q0 - L::H, 0);
+    if (F0) {
+      mbar_expect_tx(bar + 1, U0_BYTES);
+      tma_load_3d(sm + L::U0_OFF, tmu, bar + 1, s0, q0, 0);
+    }
+  }
+  issue_co<L>(a, co, q0, tid);
+  cp_async_commit();
+  cp_async_wait<0>();
+  bool ok = mbar_wait(bar, 0);
+  if (__syncthreads_or(!ok)) {  // a copy did not land: flag it, let the copies settle, skip the tile
+    if (tid == 0) {
+      if (a.err) atomicExch(a.err, 2);
+      mbar_wait(bar, 0);
+      if (F0) mbar_wait(bar + 1, 0);
+    }
+    return;
+  }
+  phase2<L>(a, vc, box, co, sm, tid);
+  ok = F0 ? mbar_wait(bar + 1, 0) : true;
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) {
+      if (a.err) atomicExch(a.err, 2);
+      mbar_wait(bar + 1, 0);
+    }
+    return;
+  }
+  const int lr = tid / (TS / 2), lc = 2 * (tid % (TS / 2));
+  phase3_pair<L, CH, F0>(a, vc, box, co, sm, lr, lc, q0 + lr, s0 + lc);
+}
+
 // One CTA per 16 x 32 tile.
 // F0: the stage combines with U^n (stages 2 and 3); the first stage writes U_in + dt L(U_in).
 // PAIR: step 3 on packed node pairs (FP32, UW3, chunked layout); otherwise two scalar nodes per
 // thread (rows lr and lr + 8).
-template <typename T, int ADV, int CH, bool F0, bool PAIR>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) stage_kernel(StageArgs<T> a, VConst<T> vc) {
+// TMA: interior tiles are staged by tensor-map copies (tmb: the box of fin, tmu: the tile of f0);
+// tiles whose box wraps around the grid take the per-thread copies.
+template <typename T, int ADV, int CH, bool F0, bool PAIR, bool TMA>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
+    stage_kernel(StageArgs<T> a, VConst<T> vc, const __grid_constant__ CUtensorMap tmb,
+                 const __grid_constant__ CUtensorMap tmu) {
   using L = GenericLay<T, ADV>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
-  tile_body<L, T, ADV, CH, F0, PAIR ? 1 : 0>(a, vc, sm, threadIdx.x, blockIdx.y * L::TQ, blockIdx.x * TS);
+  const int q0 = blockIdx.y * L::TQ, s0 = blockIdx.x * TS;
+  if constexpr (TMA && sizeof(T) == 4 && ADV == VLB_UW3 && PAIR) {
+    if (q0 >= L::H && q0 + L::TQ + L::H <= a.nt && s0 >= L::HS && s0 + TS + L::HS <= a.ns) {
+      tile_body_tma<L, CH, F0>(a, vc, sm, threadIdx.x, q0, s0, &tmb, &tmu);
+      return;
+    }
+  }
+  tile_body<L, T, ADV, CH, F0, PAIR ? 1 : 0>(a, vc, sm, threadIdx.x, q0, s0);
 }
 
 // Ensemble: one launch per stage over the tiles of every member (FP32, UW3).  Block b takes work
@@ -657,7 +761,7 @@ __global__ void __launch_bounds__(TQR * (TS / 2)) ensemble_stage_kernel(const En
                                                                        const int2* items, int stage,
                                                                        VConst<float> vc) {
   using L = EnsLay<TQR>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   float* sm = reinterpret_cast<float*>(smem_raw);
   const int2 it = items[blockIdx.x];
   const EnsembleMember& d = members[it.x];
@@ -677,6 +781,7 @@ __global__ void __launch_bounds__(TQR * (TS / 2)) ensemble_stage_kernel(const En
   a.kappa = d.kappa;
   a.gt = d.gt;
   a.n0 = d.n0;
+  a.err = nullptr;
   const int tiles_s = (d.ns + TS - 1) / TS;
   const int q0 = (it.y / tiles_s) * TQR, s0 = (it.y % tiles_s) * TS;
   tile_body<L, float, VLB_UW3, CH, F0, 2>(a, vc, sm, threadIdx.x, q0, s0);
@@ -709,15 +814,17 @@ cudaError_t ensure_smem(K kernel, size_t bytes, int& mask) {
   return e;
 }
 
-template <typename T, int ADV, int CH, bool F0, bool PAIR>
-cudaError_t launch_generic(const StageArgs<T>& a, cudaStream_t st) {
+template <typename T, int ADV, int CH, bool F0, bool PAIR, bool TMA>
+cudaError_t launch_generic(const StageArgs<T>& a, cudaStream_t st, const StageMaps* maps) {
   using L = GenericLay<T, ADV>;
   static int mask = 0;
-  cudaError_t e = ensure_smem(stage_kernel<T, ADV, CH, F0, PAIR>, L::BYTES, mask);
+  cudaError_t e = ensure_smem(stage_kernel<T, ADV, CH, F0, PAIR, TMA>, L::BYTES, mask);
   if (e != cudaSuccess) return e;
   static const VConst<T> vc = make_vconst<T>();
+  static const StageMaps none = {};
+  const StageMaps& m = maps ? *maps : none;
   dim3 grid((a.ns + TS - 1) / TS, (a.nt + L::TQ - 1) / L::TQ);
-  stage_kernel<T, ADV, CH, F0, PAIR><<<grid, 256, L::BYTES, st>>>(a, vc);
+  stage_kernel<T, ADV, CH, F0, PAIR, TMA><<<grid, 256, L::BYTES, st>>>(a, vc, m.box, m.tile);
   return cudaGetLastError();
 }
 
@@ -743,21 +850,72 @@ cudaError_t launch_ens_rows(const EnsembleMember* members, const int2* items, in
 }
 
 template <typename T, int ADV, int CH>
-cudaError_t launch_one(const StageArgs<T>& a, cudaStream_t st) {
+cudaError_t launch_one(const StageArgs<T>& a, cudaStream_t st, const StageMaps* maps) {
   if constexpr (sizeof(T) == 4 && ADV == VLB_UW3) {
-    if (chunked<GenericLay<T, ADV>>(a.nt, a.ns))  // n_phi % 4 == 0: packed node pairs
-      return a.f0 ? launch_generic<T, ADV, CH, true, true>(a, st) : launch_generic<T, ADV, CH, false, true>(a, st);
+    if (chunked<GenericLay<T, ADV>>(a.nt, a.ns)) {  // n_phi % 4 == 0: packed node pairs
+      if (maps)
+        return a.f0 ? launch_generic<T, ADV, CH, true, true, true>(a, st, maps)
+                    : launch_generic<T, ADV, CH, false, true, true>(a, st, maps);
+      return a.f0 ? launch_generic<T, ADV, CH, true, true, false>(a, st, nullptr)
+                  : launch_generic<T, ADV, CH, false, true, false>(a, st, nullptr);
+    }
   }
-  return a.f0 ? launch_generic<T, ADV, CH, true, false>(a, st) : launch_generic<T, ADV, CH, false, false>(a, st);
+  return a.f0 ? launch_generic<T, ADV, CH, true, false, false>(a, st, nullptr)
+              : launch_generic<T, ADV, CH, false, false, false>(a, st, nullptr);
+}
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder() {
+  static EncodeTiled fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(p);
+  }
+  return fn;
+}
+
+// 3-D map over the 18 FP32 state arrays: (varphi, theta, array), box bx x by x 18.
+cudaError_t encode_state_map(CUtensorMap* m, const float* base, int nt, int ns, int64_t stride, int bx, int by) {
+  EncodeTiled fn = encoder();
+  if (!fn) return cudaErrorNotSupported;
+  const cuuint64_t dims[3] = {(cuuint64_t)ns, (cuuint64_t)nt, (cuuint64_t)(NARR + 1)};
+  const cuuint64_t strides[2] = {(cuuint64_t)ns * sizeof(float), (cuuint64_t)stride * sizeof(float)};
+  const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)(NARR + 1)};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 }  // namespace
 
+bool stage_maps_apply(int nt, int ns) { return chunked<GenericLay<float, VLB_UW3>>(nt, ns); }
+
+cudaError_t make_stage_maps(const float* fin, const float* f0, int nt, int ns, int64_t stride, StageMaps* out) {
+  using L = GenericLay<float, VLB_UW3>;
+  if (!stage_maps_apply(nt, ns) || stride % 4 != 0 || ((uintptr_t)fin) % 16 != 0 || ((uintptr_t)f0) % 16 != 0)
+    return cudaErrorInvalidValue;
+  cudaError_t e = encode_state_map(&out->box, fin, nt, ns, stride, L::BS, L::BQ);
+  if (e == cudaSuccess) e = encode_state_map(&out->tile, f0, nt, ns, stride, TS, L::TQ);
+  return e;
+}
+
 template <typename T>
-cudaError_t launch_stage(const StageArgs<T>& a, int advection, int ch_mode, cudaStream_t s) {
+cudaError_t launch_stage(const StageArgs<T>& a, int advection, int ch_mode, cudaStream_t s, const StageMaps* maps) {
   if (advection == VLB_UW3)
-    return ch_mode == VLB_HYDRO ? launch_one<T, VLB_UW3, VLB_HYDRO>(a, s) : launch_one<T, VLB_UW3, VLB_DIFFUSIVE>(a, s);
-  return ch_mode == VLB_HYDRO ? launch_one<T, VLB_WENO5, VLB_HYDRO>(a, s) : launch_one<T, VLB_WENO5, VLB_DIFFUSIVE>(a, s);
+    return ch_mode == VLB_HYDRO ? launch_one<T, VLB_UW3, VLB_HYDRO>(a, s, maps)
+                                : launch_one<T, VLB_UW3, VLB_DIFFUSIVE>(a, s, maps);
+  return ch_mode == VLB_HYDRO ? launch_one<T, VLB_WENO5, VLB_HYDRO>(a, s, nullptr)
+                              : launch_one<T, VLB_WENO5, VLB_DIFFUSIVE>(a, s, nullptr);
 }
 
 cudaError_t launch_ensemble_stage(const EnsembleMember* members, const int2* items, int nitems, int stage,
@@ -767,7 +925,7 @@ cudaError_t launch_ensemble_stage(const EnsembleMember* members, const int2* ite
   return launch_ens_rows<16>(members, items, nitems, stage, ch_mode, s);
 }
 
-template cudaError_t launch_stage<float>(const StageArgs<float>&, int, int, cudaStream_t);
-template cudaError_t launch_stage<double>(const StageArgs<double>&, int, int, cudaStream_t);
+template cudaError_t launch_stage<float>(const StageArgs<float>&, int, int, cudaStream_t, const StageMaps*);
+template cudaError_t launch_stage<double>(const StageArgs<double>&, int, int, cudaStream_t, const StageMaps*);
 
 }  // namespace vlb
