@@ -93,6 +93,14 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// Programmatic dependent launch: a stage may start while the previous kernel in the stream drains.
+// pdl_wait() blocks until that kernel has completed and its writes are visible (a no-op without a
+// programmatic launch); pdl_trigger() lets the next stage's CTAs be scheduled.  Every global
+// access (state buffers and coefficient tables) comes after pdl_wait(); only shared-memory set-up
+// runs before it.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
 // mbarrier and bulk tensor copy (TMA) primitives.
 __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
@@ -220,7 +228,6 @@ __device__ __forceinline__ void issue_box(const StageArgs<T>& a, T* box, T* co, 
       cp_async_small<sizeof(T)>(box + (k * BQ + r) * BS + c, a.fin + k * stride + (int64_t)gq * ns + gs);
     }
   }
-  issue_co<L>(a, co, q0, tid);
 }
 
 template <typename L, typename T>
@@ -644,6 +651,8 @@ template <typename L, typename T, int ADV, int CH, bool F0, int PM>
 __device__ __forceinline__ void tile_body(const StageArgs<T>& a, const VConst<T>& vc, T* sm, int tid, int q0, int s0) {
   T* box = sm + L::BOX_OFF;
   T* co = sm + L::CO_OFF;
+  pdl_wait();  // the coefficients too may come from the previous kernel (the scratch tables of vlb_step_noalloc)
+  issue_co<L>(a, co, q0, tid);
   issue_box<L>(a, box, co, q0, s0, tid);
   cp_async_commit();
   if (F0) issue_u0<L>(a, sm + L::U0_OFF, q0, s0, tid);
@@ -653,6 +662,7 @@ __device__ __forceinline__ void tile_body(const StageArgs<T>& a, const VConst<T>
   phase2<L>(a, vc, box, co, sm, tid);
   cp_async_wait<0>();
   __syncthreads();
+  pdl_trigger();
   bool pair = PM == 1;
   if constexpr (PM == 2) pair = chunked<L>(a.nt, a.ns);
   if constexpr (PM != 0 && sizeof(T) == 4 && ADV == VLB_UW3) {
@@ -693,6 +703,9 @@ __device__ __forceinline__ void tile_body_tma(const StageArgs<float>& a, const V
     fence_mbar_init();
   }
   __syncthreads();
+  pdl_wait();
+  issue_co<L>(a, co, q0, tid);
+  cp_async_commit();
   if (tid == 0) {
     mbar_expect_tx(bar, BOX_BYTES);
     tma_load_3d(box, tmb, bar, s0 - L::HS, q0 - L::H, 0);
@@ -701,8 +714,6 @@ __device__ __forceinline__ void tile_body_tma(const StageArgs<float>& a, const V
       tma_load_3d(sm + L::U0_OFF, tmu, bar + 1, s0, q0, 0);
     }
   }
-  issue_co<L>(a, co, q0, tid);
-  cp_async_commit();
   cp_async_wait<0>();
   bool ok = mbar_wait(bar, 0);
   if (__syncthreads_or(!ok)) {  // a copy did not land: flag it, let the copies settle, skip the tile
@@ -722,6 +733,7 @@ __device__ __forceinline__ void tile_body_tma(const StageArgs<float>& a, const V
     }
     return;
   }
+  pdl_trigger();
   const int lr = tid / (TS / 2), lc = 2 * (tid % (TS / 2));
   phase3_pair<L, CH, F0>(a, vc, box, co, sm, lr, lc, q0 + lr, s0 + lc);
 }
@@ -823,9 +835,17 @@ cudaError_t launch_generic(const StageArgs<T>& a, cudaStream_t st, const StageMa
   static const VConst<T> vc = make_vconst<T>();
   static const StageMaps none = {};
   const StageMaps& m = maps ? *maps : none;
-  dim3 grid((a.ns + TS - 1) / TS, (a.nt + L::TQ - 1) / L::TQ);
-  stage_kernel<T, ADV, CH, F0, PAIR, TMA><<<grid, 256, L::BYTES, st>>>(a, vc, m.box, m.tile);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((a.ns + TS - 1) / TS, (a.nt + L::TQ - 1) / L::TQ);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = L::BYTES;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, stage_kernel<T, ADV, CH, F0, PAIR, TMA>, a, vc, m.box, m.tile);
 }
 
 template <int TQR, int CH, bool F0>
