@@ -70,6 +70,7 @@ struct StageArgs {
   T inv_tau, M, A, kappa, gt;  // gt = 1 / (2 r dtheta)
   T n0;             // reference density of the stored deviations
   int* err;         // device flag raised if a bounded wait on a bulk copy gives up (may be NULL)
+  int ahead;        // tensor-map path: CTAs resident at once; each prefetches the tile this many ahead
 };
 
 // Tensor maps of the FP32 UW3 stage kernel over the 18 state arrays: the halo box of the stage

@@ -135,6 +135,14 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+// Prefetch the box {x, y, z} .. + box dims of a 3-D tensor map into L2 (a hint: no shared memory).
+__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap* map, int x, int y, int z) {
+  asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];\n" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y), "r"(z)
+               : "memory");
+}
+
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
@@ -713,6 +721,15 @@ __device__ __forceinline__ void tile_body_tma(const StageArgs<float>& a, const V
       mbar_expect_tx(bar + 1, U0_BYTES);
       tma_load_3d(sm + L::U0_OFF, tmu, bar + 1, s0, q0, 0);
     }
+    // Software pipelining through L2: the CTA that takes this slot one wave later (linear tile
+    // index + a.ahead) will find its box and U^n tile already on chip.
+    const int tiles_s = (a.ns + TS - 1) / TS;
+    const int nxt = (q0 / L::TQ) * tiles_s + s0 / TS + a.ahead;
+    const int qn = (nxt / tiles_s) * L::TQ, sn = (nxt % tiles_s) * TS;
+    if (a.ahead > 0 && qn >= L::H && qn + L::TQ + L::H <= a.nt && sn >= L::HS && sn + TS + L::HS <= a.ns) {
+      tma_prefetch_3d(tmb, sn - L::HS, qn - L::H, 0);
+      if (F0) tma_prefetch_3d(tmu, sn, qn, 0);
+    }
   }
   cp_async_wait<0>();
   bool ok = mbar_wait(bar, 0);
@@ -794,6 +811,7 @@ __global__ void __launch_bounds__(TQR * (TS / 2)) ensemble_stage_kernel(const En
   a.gt = d.gt;
   a.n0 = d.n0;
   a.err = nullptr;
+  a.ahead = 0;
   const int tiles_s = (d.ns + TS - 1) / TS;
   const int q0 = (it.y / tiles_s) * TQR, s0 = (it.y % tiles_s) * TS;
   tile_body<L, float, VLB_UW3, CH, F0, 2>(a, vc, sm, threadIdx.x, q0, s0);
@@ -835,6 +853,22 @@ cudaError_t launch_generic(const StageArgs<T>& a, cudaStream_t st, const StageMa
   static const VConst<T> vc = make_vconst<T>();
   static const StageMaps none = {};
   const StageMaps& m = maps ? *maps : none;
+  StageArgs<T> args = a;
+  args.ahead = 0;
+  if (TMA) {
+    static int resident[32] = {0};  // CTAs of this kernel resident at once, per device
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if (dev < 32 && resident[dev] == 0) {
+      int per_sm = 0, sms = 0;
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel<T, ADV, CH, F0, PAIR, TMA>, 256,
+                                                             L::BYTES)) != cudaSuccess)
+        return e;
+      if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+      resident[dev] = per_sm * sms;
+    }
+    args.ahead = dev < 32 ? resident[dev] : 0;
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((a.ns + TS - 1) / TS, (a.nt + L::TQ - 1) / L::TQ);
   cfg.blockDim = dim3(256);
@@ -845,7 +879,7 @@ cudaError_t launch_generic(const StageArgs<T>& a, cudaStream_t st, const StageMa
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, stage_kernel<T, ADV, CH, F0, PAIR, TMA>, a, vc, m.box, m.tile);
+  return cudaLaunchKernelEx(&cfg, stage_kernel<T, ADV, CH, F0, PAIR, TMA>, args, vc, m.box, m.tile);
 }
 
 template <int TQR, int CH, bool F0>
