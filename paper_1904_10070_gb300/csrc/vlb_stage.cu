@@ -721,8 +721,8 @@ __device__ __forceinline__ void tile_body_tma(const StageArgs<float>& a, const V
       mbar_expect_tx(bar + 1, U0_BYTES);
       tma_load_3d(sm + L::U0_OFF, tmu, bar + 1, s0, q0, 0);
     }
-    // Software pipelining through L2: the CTA that takes this slot one wave later (linear tile
-    // index + a.ahead) will find its box and U^n tile already on chip.
+    // Software pipelining through L2: the CTA that starts a.ahead tiles later (linear tile index,
+    // about half a wave) will find its box and U^n tile already on chip.
     const int tiles_s = (a.ns + TS - 1) / TS;
     const int nxt = (q0 / L::TQ) * tiles_s + s0 / TS + a.ahead;
     const int qn = (nxt / tiles_s) * L::TQ, sn = (nxt % tiles_s) * TS;
@@ -867,7 +867,9 @@ cudaError_t launch_generic(const StageArgs<T>& a, cudaStream_t st, const StageMa
       if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
       resident[dev] = per_sm * sms;
     }
-    args.ahead = dev < 32 ? resident[dev] : 0;
+    // half a wave ahead (about the next tile started on the same SM) measured best on GB300: 0.237 ms
+    // per step on 1024 x 2048 against 0.244 (one wave), 0.268 (two) and 0.254 (no prefetch)
+    args.ahead = dev < 32 ? resident[dev] / 2 : 0;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((a.ns + TS - 1) / TS, (a.nt + L::TQ - 1) / L::TQ);
