@@ -266,19 +266,38 @@ __global__ void wgrad_reduce_kernel(int groups, int cin, int cout, const float* 
   }
 }
 
-// db[co] = sum_p dY[p][co]: one block per channel, fixed-order tree
-__global__ void bias_grad_kernel(int npix, int cout, const bf16* dy, float* db) {
-  __shared__ float red[256];
-  const int co = blockIdx.x;
-  float s = 0.0f;
-  for (int p = threadIdx.x; p < npix; p += blockDim.x) s += __bfloat162float(dy[(size_t)p * cout + co]);
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
+// db[co] = sum_p dY[p][co] in two passes with a fixed order.  Pass 1: BG_BLOCKS blocks; thread t
+// takes channel pair t % (cout / 2) of every (256 / (cout / 2))-th pixel of its block's share, so a
+// warp reads whole 128-byte rows; the pixel lanes of a block are then summed in shared memory.
+constexpr int BG_BLOCKS = 128;
+
+__global__ void __launch_bounds__(256) bias_partial_kernel(int npix, int cout, const bf16* dy, float* part) {
+  __shared__ float red[256 * 2];
+  const int cpairs = cout / 2, lanes = blockDim.x / cpairs;
+  const int cp = threadIdx.x % cpairs, pl = threadIdx.x / cpairs;
+  float s0 = 0.0f, s1 = 0.0f;
+  for (int p = blockIdx.x * lanes + pl; p < npix; p += gridDim.x * lanes) {
+    const float2 v = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(dy + (size_t)p * cout)[cp]);
+    s0 += v.x;
+    s1 += v.y;
   }
-  if (threadIdx.x == 0) db[co] = red[0];
+  red[pl * cout + 2 * cp] = s0;
+  red[pl * cout + 2 * cp + 1] = s1;
+  __syncthreads();
+  if (threadIdx.x < cout) {
+    float s = 0.0f;
+    for (int l = 0; l < lanes; ++l) s += red[l * cout + threadIdx.x];
+    part[blockIdx.x * cout + threadIdx.x] = s;
+  }
+}
+
+// Pass 2: db[co] = sum over the blocks' partials, in block order.
+__global__ void bias_final_kernel(int nb, int cout, const float* part, float* db) {
+  const int co = threadIdx.x;
+  if (co >= cout) return;
+  float s = 0.0f;
+  for (int b = 0; b < nb; ++b) s += part[b * cout + co];
+  db[co] = s;
 }
 
 template <typename K>
@@ -322,7 +341,8 @@ bool shape_ok(int H, int W, int cin, int cout, const char** why) {
 
 size_t conv_wgrad_workspace_bytes(int H, int W, int cin, int cout) {
   const int groups = (H * (W / CPX) + WG_SEGS - 1) / WG_SEGS;
-  return sizeof(float) * (size_t)groups * 9 * cin * cout;
+  const size_t wg = (size_t)groups * 9 * cin * cout, bg = (size_t)BG_BLOCKS * cout;
+  return sizeof(float) * (wg > bg ? wg : bg);
 }
 
 cudaError_t conv_fwd(int H, int W, int cin, int cout, const void* x, const void* w, const float* b, const void* mask,
@@ -347,7 +367,11 @@ cudaError_t conv_wgrad(int H, int W, int cin, int cout, const void* x, const voi
   else
     e = wg_launch<64, 16>(H, W, x, dy, partial, dw, st);
   if (e != cudaSuccess || !db) return e;
-  bias_grad_kernel<<<cout, 256, 0, st>>>(H * W, cout, (const bf16*)dy, db);
+  // the weight partials are consumed by now: their workspace (>= 9 * 16 * 64 floats) holds the
+  // BG_BLOCKS x cout bias partials
+  bias_partial_kernel<<<BG_BLOCKS, 256, 0, st>>>(H * W, cout, (const bf16*)dy, partial);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  bias_final_kernel<<<1, 64, 0, st>>>(BG_BLOCKS, cout, partial, db);
   return cudaGetLastError();
 }
 
