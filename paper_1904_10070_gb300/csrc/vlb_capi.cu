@@ -965,7 +965,7 @@ vlb_status vlb_conv3x3_fwd(int32_t H, int32_t W, int32_t cin, int32_t cout, cons
   const char* why = nullptr;
   if (!vlb::conv_shape_ok(H, W, cin, cout, &why)) return fail(nullptr, VLB_ERR_ARG, "vlb_conv3x3_fwd: %s", why);
   if (!x || !w || (!y_bf16 && !y_f32)) return fail(nullptr, VLB_ERR_ARG, "vlb_conv3x3_fwd: NULL tensor");
-  VLB_CUDA(nullptr, vlb::conv_fwd(H, W, cin, cout, x, w, bias, mask, relu, y_bf16, y_f32, (cudaStream_t)cuda_stream));
+  VLB_CUDA(nullptr, vlb::conv_fwd_tc(H, W, cin, cout, x, w, bias, mask, relu, y_bf16, y_f32, (cudaStream_t)cuda_stream));
   return VLB_OK;
 }
 

@@ -1,5 +1,7 @@
-// 3x3 periodic convolutions on BF16 NHWC tensors with FP32 accumulation on the tensor cores
-// (mma.sync m16n8k16), for the learned surrogate that stands in for blocks of solver steps.
+// 3x3 periodic convolutions on BF16 NHWC tensors for the learned surrogate: the weight gradient
+// (mma.sync m16n8k16 tensor-core tiles, FP32 accumulation), the bias gradient and the weight flip
+// that turns the backward-data convolution into a forward one.  The forward itself runs on the
+// tcgen05 tensor cores (vlb_conv_tc.cu).
 //
 // Layouts: activations [H][W][C] (C contiguous), weights [C_out][3][3][C_in], both bf16; the torus
 // is periodic in both directions, so the padding wraps.  Tap t = 3 (dy + 1) + (dx + 1) reads the
@@ -10,10 +12,6 @@
 //                  = a forward convolution of dY with W'[ci][8 - t][co] (vlb_conv3x3_flip)
 //   backward wts   dW[co][t][ci] = sum_p dY[p][co] X[p + d_t][ci],  db[co] = sum_p dY[p][co]
 //
-// Forward tiling: a CTA (8 warps) owns 128 consecutive pixels of two rows; the 4 x 130 x C_in input
-// patch and the layer's weights are staged in shared memory with cp.async (row strides padded by 8
-// elements, so the eight 16-byte rows of an ldmatrix land in different bank groups); each warp
-// computes 32 pixels x C_out with both operands loaded by ldmatrix.
 // Weight gradient: a CTA (4 warps) owns one tap and a group of row segments; per segment it stages
 // the shifted input row and dY in shared memory and accumulates dY^T X_t with both operands loaded
 // by ldmatrix.trans; per-group partial sums are reduced in a fixed order by a second kernel.
@@ -51,116 +49,10 @@ __device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ void ldsm4(uint32_t (&r)[4], const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(smem_addr(p)));
-}
-
 __device__ __forceinline__ void ldsm4t(uint32_t (&r)[4], const void* p) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                : "r"(smem_addr(p)));
-}
-
-__device__ __forceinline__ uint32_t ldg32(const bf16* p) { return __ldg(reinterpret_cast<const unsigned int*>(p)); }
-
-constexpr int FROWS = 2;              // pixel rows per forward CTA
-constexpr int FTHR = FROWS * NTHR;     // 8 warps: 4 per row, 32 pixels each
-
-template <int CIN, int COUT>
-constexpr size_t fwd_smem() {
-  return sizeof(bf16) * ((FROWS + 2) * (CPX + 2) * (CIN + 8) + COUT * 9 * (CIN + 8));
-}
-
-template <int CIN, int COUT>
-__global__ void __launch_bounds__(FTHR) conv_fwd_kernel(int H, int W, const bf16* __restrict__ x,
-                                                        const bf16* __restrict__ w, const float* __restrict__ bias,
-                                                        const bf16* __restrict__ mask, int relu, bf16* y, float* yf) {
-  constexpr int PS = CIN + 8, PW = CPX + 2, CH = CIN / 8, NT = COUT / 8;
-  constexpr int PR = FROWS + 2;                // patch rows
-  constexpr int WS = 9 * PS;                   // weight row stride (one output channel), elements
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  bf16* patch = reinterpret_cast<bf16*>(smem_raw);
-  bf16* ws = patch + PR * PW * PS;
-  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-  const int segs = W / CPX;
-  const int row0 = (blockIdx.x / segs) * FROWS, x0 = (blockIdx.x % segs) * CPX;
-  for (int idx = tid; idx < PR * PW * CH; idx += FTHR) {
-    const int pr = idx / (PW * CH), rem = idx - pr * (PW * CH);
-    const int pc = rem / CH, ch = rem - pc * CH;
-    int gy = (row0 + pr - 1) % H;
-    gy += gy < 0 ? H : 0;
-    int gx = x0 + pc - 1;
-    gx += gx < 0 ? W : (gx >= W ? -W : 0);
-    cp16(patch + (pr * PW + pc) * PS + ch * 8, x + ((size_t)gy * W + gx) * CIN + ch * 8);
-  }
-  for (int idx = tid; idx < COUT * 9 * CH; idx += FTHR) {
-    const int co = idx / (9 * CH), rem = idx - co * 9 * CH, t = rem / CH, ch = rem - t * CH;
-    cp16(ws + co * WS + t * PS + ch * 8, w + ((size_t)co * 9 + t) * CIN + ch * 8);
-  }
-  cp_wait_all();
-  __syncthreads();
-
-  const int g = lane / 4, t4 = lane % 4;
-  const int wr = warp / NWARP, px0 = (warp % NWARP) * 32;  // this warp's row within the CTA and first pixel
-  float acc[2][NT][4];
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-    for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.0f;
-  // ldmatrix lane roles: A matrices (rows 0-7|8-15, k 0-7|8-15); B matrices (n-tile a|b, k 0-7|8-15)
-  const int arow = (lane % 8) + 8 * ((lane / 8) % 2), akof = 8 * (lane / 16);
-  const int brow = (lane % 8) + 8 * (lane / 16), bkof = 8 * ((lane / 8) % 2);
-#pragma unroll 1
-  for (int tap = 0; tap < 9; ++tap) {
-    const int dy = tap / 3, dx = tap % 3;
-#pragma unroll
-    for (int c0 = 0; c0 < CIN; c0 += 16) {
-      uint32_t a[2][4];
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt)
-        ldsm4(a[mt], patch + ((wr + dy) * PW + px0 + mt * 16 + arow + dx) * PS + c0 + akof);
-#pragma unroll
-      for (int np = 0; np < NT / 2; ++np) {
-        uint32_t b[4];
-        ldsm4(b, ws + (np * 16 + brow) * WS + tap * PS + c0 + bkof);
-        mma16816(acc[0][2 * np], a[0], b[0], b[1]);
-        mma16816(acc[1][2 * np], a[1], b[0], b[1]);
-        mma16816(acc[0][2 * np + 1], a[0], b[2], b[3]);
-        mma16816(acc[1][2 * np + 1], a[1], b[2], b[3]);
-      }
-    }
-  }
-  // epilogue: acc[mt][nt][2h + e] is pixel px0 + 16 mt + g + 8 h, channel 8 nt + 2 t4 + e
-  const int row = row0 + wr;
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-    for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const size_t p = (size_t)row * W + x0 + px0 + mt * 16 + g + 8 * h;
-        const int co = nt * 8 + 2 * t4;
-        float v0 = acc[mt][nt][2 * h], v1 = acc[mt][nt][2 * h + 1];
-        if (bias) {
-          v0 += bias[co];
-          v1 += bias[co + 1];
-        }
-        if (relu) {
-          v0 = fmaxf(v0, 0.0f);
-          v1 = fmaxf(v1, 0.0f);
-        }
-        if (mask) {
-          const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162*>(mask + p * COUT + co);
-          if (!(__bfloat162float(m.x) > 0.0f)) v0 = 0.0f;
-          if (!(__bfloat162float(m.y) > 0.0f)) v1 = 0.0f;
-        }
-        if (y) *reinterpret_cast<__nv_bfloat162*>(y + p * COUT + co) = __floats2bfloat162_rn(v0, v1);
-        if (yf) *reinterpret_cast<float2*>(yf + p * COUT + co) = make_float2(v0, v1);
-      }
 }
 
 // W'[ci][8 - t][co] = W[co][t][ci]
@@ -306,17 +198,6 @@ cudaError_t allow_smem(K kernel, size_t bytes) {
 }
 
 template <int CIN, int COUT>
-cudaError_t fwd_launch(int H, int W, const void* x, const void* w, const float* b, const void* mask, int relu, void* y,
-                       float* yf, cudaStream_t st) {
-  constexpr size_t S = fwd_smem<CIN, COUT>();
-  cudaError_t e = allow_smem(conv_fwd_kernel<CIN, COUT>, S);
-  if (e != cudaSuccess) return e;
-  conv_fwd_kernel<CIN, COUT><<<(H / FROWS) * (W / CPX), FTHR, S, st>>>(H, W, (const bf16*)x, (const bf16*)w, b,
-                                                                       (const bf16*)mask, relu, (bf16*)y, yf);
-  return cudaGetLastError();
-}
-
-template <int CIN, int COUT>
 cudaError_t wg_launch(int H, int W, const void* x, const void* dy, float* partial, float* dw, cudaStream_t st) {
   constexpr size_t S = wg_smem<CIN, COUT>();
   cudaError_t e = allow_smem(conv_wgrad_kernel<CIN, COUT>, S);
@@ -330,7 +211,7 @@ cudaError_t wg_launch(int H, int W, const void* x, const void* dy, float* partia
 }
 
 bool shape_ok(int H, int W, int cin, int cout, const char** why) {
-  if (H < FROWS || H % FROWS != 0) return *why = "H must be a positive multiple of 2", false;
+  if (H < 2 || H % 2 != 0) return *why = "H must be a positive multiple of 2", false;
   if (W < CPX || W % CPX != 0) return *why = "W must be a positive multiple of 128", false;
   if (!((cin == 16 && cout == 64) || (cin == 64 && cout == 64) || (cin == 64 && cout == 16)))
     return *why = "(c_in, c_out) must be (16, 64), (64, 64) or (64, 16)", false;
@@ -343,13 +224,6 @@ size_t conv_wgrad_workspace_bytes(int H, int W, int cin, int cout) {
   const int groups = (H * (W / CPX) + WG_SEGS - 1) / WG_SEGS;
   const size_t wg = (size_t)groups * 9 * cin * cout, bg = (size_t)BG_BLOCKS * cout;
   return sizeof(float) * (wg > bg ? wg : bg);
-}
-
-cudaError_t conv_fwd(int H, int W, int cin, int cout, const void* x, const void* w, const float* b, const void* mask,
-                     int relu, void* y, float* yf, cudaStream_t st) {
-  if (cin == 16) return fwd_launch<16, 64>(H, W, x, w, b, mask, relu, y, yf, st);
-  if (cout == 64) return fwd_launch<64, 64>(H, W, x, w, b, mask, relu, y, yf, st);
-  return fwd_launch<64, 16>(H, W, x, w, b, mask, relu, y, yf, st);
 }
 
 cudaError_t conv_flip(int cin, int cout, const void* w, void* wf, cudaStream_t st) {

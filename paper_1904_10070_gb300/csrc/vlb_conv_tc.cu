@@ -1,0 +1,467 @@
+// 3x3 periodic convolution forward on the 5th-generation tensor cores (tcgen05.mma, BF16 x BF16 ->
+// FP32 accumulators in tensor memory), for the learned surrogate.  Same contract as the forward of
+// vlb_conv.cu: Y[p][co] = act(sum_{t,ci} X[p + d_t][ci] W[co][t][ci] + b[co]) on NHWC bf16 tensors,
+// periodic in both directions, with the optional bias, ReLU, mask (outputs where mask <= 0 are
+// zeroed) and bf16 / f32 outputs.  The backward-data convolution is this kernel on flipped weights.
+//
+// Implicit GEMM.  A work item is two output rows of 128 pixels; per row, D[m][n] (m = pixel, n =
+// output channel, M = 128, N = C_out) accumulates over K = 9 taps x C_in:
+//   A_t[m][k] = X[pixel m shifted by tap t][k],  B_t[n][k] = W[n][t][k],  D = sum_t A_t B_t^T.
+// Shared-memory operands use the no-swizzle K-major layout of 8 x 16-byte core matrices: element
+// (m, k) of a matrix sits at (k / 8) * LBO + m * 16 + (k % 8) * 2 bytes (the row-group stride SBO is
+// 128 bytes, so rows are simply 16 bytes apart).  The input patch (4 rows x 130 pixels) is stored as
+// [16-byte channel chunk][patch row][patch column]; the A matrix of tap (dy, dx) for output row r is
+// then the same layout starting (r + dy) * 130 + dx pixels in: a shifted window needs no copy.
+// Weights are stored [tap][chunk][c_out] once per CTA (the CTA is persistent over work items).
+//
+// One 128-thread CTA per SM, persistent and pipelined two deep (see the kernel): thread 0 issues the
+// 2 x 9 x C_in / 16 MMAs of an item (M = 128, N = C_out, K = 16 each) and commits them to an
+// mbarrier; the four warps read the accumulators from tensor memory (warp w owns lanes 32w .. 32w + 31,
+// i.e. those pixels) and run the epilogue of the previous item while the next MMAs execute.
+#include <cuda_bf16.h>
+
+#include "vlb_internal.cuh"
+
+namespace vlb {
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int TPX = 128;                 // pixels per accumulator tile (the MMA's M)
+constexpr int TROWS = 2;                 // output rows per work item
+constexpr int TPR = TROWS + 2, TPW = TPX + 2;  // patch rows, patch columns
+// Warp roles: 0-3 epilogue (warp w reads tensor-memory lanes 32w .. 32w + 31), 4 MMA issue and
+// tensor-memory allocation, 5 loads (tensor-map copy of the patch and the periodic fix-ups).
+constexpr int TTHR = 192;
+constexpr int MMA_WARP = 4, LOAD_WARP = 5;
+
+template <int CIN, int COUT>
+struct TcLay {
+  // C_in = 64: 128-byte pixel rows in the 128-byte-swizzled K-major layout (fast row copies);
+  // C_in = 16: the no-swizzle chunk-major layout described above
+  static constexpr bool SW = CIN == 64;
+  static constexpr int CH = CIN / 8;                        // 16-byte channel chunks per pixel
+  static constexpr int WTS = 9 * CH * COUT * 16;             // weight bytes
+  static constexpr int PATCH = CH * TPR * TPW * 16;          // patch bytes
+  static constexpr int W_OFF = 0, P_OFF = WTS, BAR_OFF = WTS + 2 * PATCH;  // two patch buffers
+  static constexpr int NBAR = 10;                            // tma, pfull, pempty, afull, aempty (x 2)
+  static constexpr int TSLOT_OFF = BAR_OFF + 8 * NBAR;       // tensor-memory address
+  static constexpr int BIAS_OFF = TSLOT_OFF + 16;
+  static constexpr int BYTES = BIAS_OFF + 4 * COUT;
+  static constexpr int ACC = TROWS * COUT;                   // accumulator columns of one work item
+  static constexpr int COLS = 2 * ACC <= 32 ? 32 : (2 * ACC <= 64 ? 64 : (2 * ACC <= 128 ? 128 : 256));
+  static constexpr uint32_t LBO_A = TPR * TPW * 16;          // next channel chunk of the patch
+  static constexpr uint32_t LBO_B = COUT * 16;               // next channel chunk of a tap's weights
+  static_assert(SW ? (WTS % 1024 == 0 && PATCH % 1024 == 0) : (WTS % 128 == 0 && PATCH % 128 == 0),
+                "operand buffers stay aligned to the swizzle atom (1024 bytes) or the core matrix (128 bytes)");
+  static_assert(COUT % 16 == 0 && COUT <= 256 && CIN % 16 == 0, "MMA shape M = 128, N = C_out, K = 16");
+};
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void cp16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(su32(dst)), "l"(src));
+}
+// copies written by this thread become visible to the tensor core (the async proxy)
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(su32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(su32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(su32(bar)), "r"(bytes) : "memory");
+}
+// the box at (0, x, y) of a 3-D tensor map into shared memory (1024-byte aligned), completing on bar
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
+      "[%2];\n" ::"r"(su32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(su32(bar)), "r"(0), "r"(x), "r"(y)
+      : "memory");
+}
+// the box at (0, x, y, 0) of a 4-D tensor map into shared memory (128-byte aligned), completing on bar
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, "
+      "%6}], [%2];\n" ::"r"(su32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(su32(bar)), "r"(0), "r"(x), "r"(y), "r"(0)
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 22); ++it) {  // bounded: a commit that never arrives cannot hang the GPU
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(su32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+// Shared-memory matrix descriptor: start, leading (K-direction core-matrix) and stride (M/N-direction
+// core-matrix) byte offsets, each encoded >> 4 in 14 bits; bits 46-47 = 1 (tcgen05 descriptor);
+// base offset 0; layout 0 = no swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+// 128-byte swizzle (layout 2 in bits 61-63): 8-row groups of 128-byte rows 1024 bytes apart, the
+// 16-byte chunk c of row r stored at chunk c ^ (r % 8) counted from the 1024-byte-aligned atom.  The
+// tensor core applies the swizzle to absolute shared-memory address bits, as the tensor-map copy
+// does, so a start address inside an atom (a window shifted by whole pixel rows, or a K step of 32
+// bytes) needs no base offset (bits 49-51 stay 0; measured on GB300).
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B BF16 (bits 7-9, 10-12 = 1), both
+// K-major (bits 15, 16 = 0), N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+template <int N>
+__host__ __device__ constexpr uint32_t idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(TPX >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t id, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(a), "l"(b), "r"(id), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(su32(bar))
+               : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's lane (asynchronous: tmem_wait_ld before use)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+
+// Shared-memory offset of 16-byte chunk c of patch pixel (pr, pc) in a patch buffer.
+template <int CIN>
+__device__ __forceinline__ int patch_off(int c, int pr, int pc) {
+  if constexpr (CIN == 64) {
+    const int j = pr * TPW + pc;  // 128-byte pixel row; buffers are 1024-byte aligned
+    return j * 128 + ((c ^ (j & 7)) << 4);
+  } else {
+    return ((c * TPR + pr) * TPW + pc) * 16;
+  }
+}
+
+// Periodic fix-up of an edge item's patch after its tensor-map copy (which zero-fills out-of-range
+// positions): out-of-range patch rows get whole wrapped rows, out-of-range columns the wrapped pixel.
+// Run by the 32 lanes of the load warp; returns whether anything was copied.
+template <int CIN>
+__device__ __forceinline__ bool fix_patch(unsigned char* dst, const bf16* x, int H, int W, int row0, int x0, int lane) {
+  constexpr int CH = CIN / 8;
+  const bool top = row0 == 0, bottom = row0 + TROWS == H, left = x0 == 0, right = x0 + TPX == W;
+  if (!(top || bottom || left || right)) return false;
+  for (int pr = 0; pr < TPR; ++pr) {
+    const int yy = row0 + pr - 1;
+    const int gy = yy < 0 ? yy + H : (yy >= H ? yy - H : yy);
+    if (gy != yy) {  // a whole wrapped row
+      for (int i = lane; i < TPW * CH; i += 32) {
+        const int c = i % CH, pc = i / CH, xx = x0 + pc - 1;
+        const int gx = xx < 0 ? xx + W : (xx >= W ? xx - W : xx);
+        cp16(dst + patch_off<CIN>(c, pr, pc), x + ((size_t)gy * W + gx) * CIN + c * 8);
+      }
+    } else {  // at most the two edge pixels
+      for (int i = lane; i < 2 * CH; i += 32) {
+        const int c = i % CH, side = i / CH;
+        if ((side == 0 && left) || (side == 1 && right)) {
+          const int pc = side == 0 ? 0 : TPW - 1, gx = side == 0 ? W - 1 : 0;
+          cp16(dst + patch_off<CIN>(c, pr, pc), x + ((size_t)gy * W + gx) * CIN + c * 8);
+        }
+      }
+    }
+  }
+  asm volatile("cp.async.commit_group;\n" ::);
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  return true;
+}
+
+// Epilogue of work item `item` from the accumulators at column `col0`: thread (warp, lane) owns
+// pixel x0 + 32 warp + lane of each row; all C_out columns of a row are read before one wait.
+template <int COUT>
+__device__ __forceinline__ void epilogue(uint32_t tmem, uint32_t col0, int W, int item, int warp, int lane,
+                                         const float* sbias, const bf16* mask, int relu, bf16* y, float* yf) {
+  const int segs = W / TPX, row0 = (item / segs) * TROWS, x0 = (item % segs) * TPX;
+#pragma unroll 1
+  for (int r = 0; r < TROWS; ++r) {
+    const size_t p = (size_t)(row0 + r) * W + x0 + 32 * warp + lane;
+    uint32_t raw[COUT];
+#pragma unroll
+    for (int j = 0; j < COUT / 16; ++j)
+      tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + col0 + (uint32_t)(r * COUT + 16 * j), raw + 16 * j);
+    tmem_wait_ld();
+#pragma unroll
+    for (int j = 0; j < COUT / 16; ++j) {
+      float v[16];
+      const int co = 16 * j;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(raw[co + i]) + sbias[co + i];
+      if (relu) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.0f);
+      }
+      if (mask) {
+        const uint4* mp = reinterpret_cast<const uint4*>(mask + p * COUT + co);
+        const uint4 m0 = mp[0], m1 = mp[1];
+        const __nv_bfloat162* mh = reinterpret_cast<const __nv_bfloat162*>(&m0);
+        const __nv_bfloat162* mh1 = reinterpret_cast<const __nv_bfloat162*>(&m1);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          if (!(__low2float(mh[i]) > 0.0f)) v[2 * i] = 0.0f;
+          if (!(__high2float(mh[i]) > 0.0f)) v[2 * i + 1] = 0.0f;
+          if (!(__low2float(mh1[i]) > 0.0f)) v[8 + 2 * i] = 0.0f;
+          if (!(__high2float(mh1[i]) > 0.0f)) v[8 + 2 * i + 1] = 0.0f;
+        }
+      }
+      if (y) {
+        uint4 o[2];
+        __nv_bfloat162* oh = reinterpret_cast<__nv_bfloat162*>(o);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) oh[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+        uint4* yp = reinterpret_cast<uint4*>(y + p * COUT + co);
+        yp[0] = o[0];
+        yp[1] = o[1];
+      }
+      if (yf) {
+        float4* fp = reinterpret_cast<float4*>(yf + p * COUT + co);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) fp[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+      }
+    }
+  }
+}
+
+// Persistent over work items item_k = blockIdx.x + k gridDim.x with warp-specialised roles and a
+// two-deep pipeline: patch buffer and accumulator k % 2 serve item k.  The load warp copies patch
+// k while the MMA warp works on item k - 1 and the epilogue warps drain item k - 2.  Hand-offs are
+// mbarriers: tma[b] (copy landed), pfull[b] (patch ready, fix-ups included), pempty[b] (its MMAs
+// are done), afull[b] (accumulator ready), aempty[b] (accumulator read, 4 arrivals).
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(TTHR, 1)
+    conv_fwd_tc_kernel(int H, int W, const bf16* __restrict__ x, const bf16* __restrict__ w,
+                       const float* __restrict__ bias, const bf16* __restrict__ mask, int relu, bf16* y, float* yf,
+                       int* err, const __grid_constant__ CUtensorMap xmap) {
+  using L = TcLay<CIN, COUT>;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L::BAR_OFF);
+  uint64_t *tma = bars, *pfull = bars + 2, *pempty = bars + 4, *afull = bars + 6, *aempty = bars + 8;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::TSLOT_OFF);
+  float* sbias = reinterpret_cast<float*>(sm + L::BIAS_OFF);
+  if (warp == MMA_WARP) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(tslot)),
+                 "r"(L::COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tma + b, 1);
+      mbar_init(pfull + b, 1);
+      mbar_init(pempty + b, 1);
+      mbar_init(afull + b, 1);
+      mbar_init(aempty + b, 4);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  for (int i = tid; i < COUT; i += TTHR) sbias[i] = bias ? bias[i] : 0.0f;
+  // weights once: chunk c of W[co][t][:] -> tap t's B matrix (row co): swizzled 128-byte rows for
+  // C_in = 64 ([t][co][128 B], 1024-byte atoms), chunk-major [t][c][co] for C_in = 16
+  for (int i = tid; i < COUT * 9 * L::CH; i += TTHR) {
+    const int c = i % L::CH, t = (i / L::CH) % 9, co = i / (9 * L::CH);
+    const int off = L::SW ? (t * COUT + co) * 128 + ((c ^ (co & 7)) << 4) : ((t * L::CH + c) * COUT + co) * 16;
+    cp16(sm + L::W_OFF + off, w + ((size_t)co * 9 + t) * CIN + c * 8);
+  }
+  asm volatile("cp.async.commit_group;\n" ::);
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const int segs = W / TPX, nitems = (H / TROWS) * segs;
+  const int nmine = blockIdx.x < nitems ? (nitems - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  bool ok = true;
+  if (warp == LOAD_WARP) {
+    for (int k = 0; k < nmine && ok; ++k) {
+      const int b = k & 1, item = blockIdx.x + k * gridDim.x;
+      const int row0 = (item / segs) * TROWS, x0 = (item % segs) * TPX;
+      unsigned char* dst = sm + L::P_OFF + b * L::PATCH;
+      if (k >= 2) ok = mbar_wait(pempty + b, ((k - 2) >> 1) & 1);  // the MMAs of item k - 2 read it
+      if (!ok) break;
+      if (lane == 0) {
+        mbar_expect_tx(tma + b, L::PATCH);
+        if constexpr (L::SW)
+          tma_load_3d(dst, &xmap, tma + b, x0 - 1, row0 - 1);
+        else
+          tma_load_4d(dst, &xmap, tma + b, x0 - 1, row0 - 1);
+      }
+      ok = mbar_wait(tma + b, (k >> 1) & 1);
+      if (!ok) break;
+      if (fix_patch<CIN>(dst, x, H, W, row0, x0, lane)) fence_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(pfull + b);
+    }
+  } else if (warp == MMA_WARP) {
+    if (lane == 0) {
+      constexpr uint32_t ID = idesc<COUT>();
+      const uint64_t bd0 = sdesc(su32(sm + L::W_OFF), L::LBO_B, 128);
+      for (int k = 0; k < nmine && ok; ++k) {
+        const int b = k & 1;
+        ok = mbar_wait(pfull + b, (k >> 1) & 1);
+        if (ok && k >= 2) ok = mbar_wait(aempty + b, ((k - 2) >> 1) & 1);  // epilogue of item k - 2
+        if (!ok) break;
+        tc_fence_after();
+        // descriptors differ only in the start address (low 14 bits, 16-byte units): constant offsets
+        const uint32_t pb = su32(sm + L::P_OFF + b * L::PATCH), wb = su32(sm + L::W_OFF);
+        const uint64_t ad0 = sdesc(pb, L::LBO_A, 128);
+        const uint32_t acc0 = tmem + (uint32_t)(b * L::ACC);
+#pragma unroll
+        for (int r = 0; r < TROWS; ++r)
+#pragma unroll
+          for (int t = 0; t < 9; ++t)
+#pragma unroll
+            for (int s2 = 0; s2 < CIN / 16; ++s2) {
+              uint64_t ad, bdd;
+              if constexpr (L::SW) {  // rows (r + dy) * TPW + dx + m; K step s2 is 32 bytes into the row
+                ad = sdesc_sw128(pb + (uint32_t)(((r + t / 3) * TPW + t % 3) * 128 + 32 * s2));
+                bdd = sdesc_sw128(wb + (uint32_t)(t * COUT * 128 + 32 * s2));
+              } else {
+                ad = ad0 + (uint32_t)(((2 * s2) * TPR + r + t / 3) * TPW + t % 3);
+                bdd = bd0 + (uint32_t)((t * L::CH + 2 * s2) * COUT);
+              }
+              umma(acc0 + r * COUT, ad, bdd, ID, (t | s2) != 0);
+            }
+        umma_commit(pempty + b);
+        umma_commit(afull + b);
+      }
+    }
+    __syncwarp();
+  } else {  // epilogue warps 0-3
+    for (int k = 0; k < nmine && ok; ++k) {
+      const int b = k & 1;
+      ok = mbar_wait(afull + b, (k >> 1) & 1);
+      if (!ok) break;
+      tc_fence_after();
+      epilogue<COUT>(tmem, (uint32_t)(b * L::ACC), W, blockIdx.x + k * gridDim.x, warp, lane, sbias, mask, relu, y,
+                     yf);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(aempty + b);
+    }
+  }
+  if (!ok && lane == 0 && err) atomicExch(err, 1);  // a wait gave up: flagged, the CTA winds down
+  tc_fence_before();
+  __syncthreads();
+  if (warp == MMA_WARP) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(L::COLS) : "memory");
+  }
+}
+
+__device__ int g_conv_tc_err = 0;  // raised if a bounded wait on the tensor cores gives up
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder() {
+  static EncodeTiled fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(p);
+  }
+  return fn;
+}
+
+template <int CIN, int COUT>
+cudaError_t tc_launch(int H, int W, const void* x, const void* w, const float* b, const void* mask, int relu, void* y,
+                      float* yf, cudaStream_t st) {
+  using L = TcLay<CIN, COUT>;
+  static int ready[32] = {0};
+  static int grid_max[32] = {0};
+  static int* err[32] = {nullptr};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 32) return cudaErrorInvalidDevice;
+  if (!ready[dev]) {
+    e = cudaFuncSetAttribute(conv_fwd_tc_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::BYTES);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_fwd_tc_kernel<CIN, COUT>, TTHR, L::BYTES);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    // at most 512 / COLS CTAs of this kernel share an SM's tensor memory
+    const int tmem_cap = 512 / L::COLS;
+    grid_max[dev] = sms * (per_sm < tmem_cap ? per_sm : tmem_cap);
+    if ((e = cudaGetSymbolAddress((void**)&err[dev], g_conv_tc_err)) != cudaSuccess) return e;
+    ready[dev] = 1;
+  }
+  // the input as (8 channels of a chunk, W, H, chunk) so that a 8 x 130 x 4 x CH box lands in the
+  // chunk-major patch layout; out-of-range rows and columns are zero-filled, then fixed up
+  EncodeTiled enc = encoder();
+  if (!enc) return cudaErrorNotSupported;
+  alignas(64) CUtensorMap xmap;
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r;
+  if (L::SW) {  // (64 channels = one 128-byte row, W, H), box 64 x 130 x 4, 128-byte swizzle
+    const cuuint64_t dims[3] = {(cuuint64_t)CIN, (cuuint64_t)W, (cuuint64_t)H};
+    const cuuint64_t strides[2] = {(cuuint64_t)CIN * 2, (cuuint64_t)W * CIN * 2};
+    const cuuint32_t box[3] = {(cuuint32_t)CIN, (cuuint32_t)TPW, (cuuint32_t)TPR};
+    r = enc(&xmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(x), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  } else {  // (8 channels of a chunk, W, H, chunk): the box lands chunk-major
+    const cuuint64_t dims[4] = {8, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)L::CH};
+    const cuuint64_t strides[3] = {(cuuint64_t)CIN * 2, (cuuint64_t)W * CIN * 2, 16};
+    const cuuint32_t box[4] = {8, (cuuint32_t)TPW, (cuuint32_t)TPR, (cuuint32_t)L::CH};
+    r = enc(&xmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(x), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  }
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  const int nitems = (H / TROWS) * (W / TPX);
+  const int grid = nitems < grid_max[dev] ? nitems : grid_max[dev];
+  conv_fwd_tc_kernel<CIN, COUT><<<grid, TTHR, L::BYTES, st>>>(H, W, (const bf16*)x, (const bf16*)w, b,
+                                                               (const bf16*)mask, relu, (bf16*)y, yf, err[dev], xmap);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t conv_fwd_tc(int H, int W, int cin, int cout, const void* x, const void* w, const float* b,
+                        const void* mask, int relu, void* y, float* yf, cudaStream_t st) {
+  if (cin == 16) return tc_launch<16, 64>(H, W, x, w, b, mask, relu, y, yf, st);
+  if (cout == 64) return tc_launch<64, 64>(H, W, x, w, b, mask, relu, y, yf, st);
+  return tc_launch<64, 16>(H, W, x, w, b, mask, relu, y, yf, st);
+}
+
+}  // namespace vlb

@@ -137,8 +137,9 @@ cudaError_t launch_snapshot_shift(const float* snap, const double* coefd, int nt
 // Surrogate network kernels (vlb_conv.cu, vlb_surrogate.cu).
 bool conv_shape_ok(int H, int W, int cin, int cout, const char** why);
 size_t conv_wgrad_workspace_bytes(int H, int W, int cin, int cout);
-cudaError_t conv_fwd(int H, int W, int cin, int cout, const void* x, const void* w, const float* b, const void* mask,
-                     int relu, void* y, float* yf, cudaStream_t st);
+// the forward on the tcgen05 tensor cores (vlb_conv_tc.cu)
+cudaError_t conv_fwd_tc(int H, int W, int cin, int cout, const void* x, const void* w, const float* b,
+                        const void* mask, int relu, void* y, float* yf, cudaStream_t st);
 cudaError_t conv_flip(int cin, int cout, const void* w, void* wf, cudaStream_t st);
 cudaError_t conv_wgrad(int H, int W, int cin, int cout, const void* x, const void* dy, float* dw, float* db,
                        float* partial, cudaStream_t st);

@@ -314,7 +314,9 @@ class Advancer:
     (it relaxes over tau / dt steps, many windows when tau >> dt), with the conserved totals
     int n sqrt(g) and int phi sqrt(g) restored to their values at the start (vlb_set_snapshot).  Between checks nothing is read back to the host,
     and a predicted window (snapshot, statistics, features, eight convolutions, restart) replays as
-    one CUDA graph when the solver runs on its own (non-default) stream.
+    one CUDA graph when the solver runs on its own (non-default) stream.  Advancers that share a
+    Trainer share its network's activation buffers: run them one after another, with the streams
+    synchronised in between.
     """
 
     def __init__(self, trainer: Trainer, solver: vlb.Solver, window: int = 50, check_every: int = 4,

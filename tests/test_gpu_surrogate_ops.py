@@ -161,12 +161,14 @@ def test_advance_accepting_judge_conserves_totals():
 
 def test_graph_replay_matches_eager_prediction():
     """A predicted window replayed from the captured graph gives the same state as an eager one."""
+    import torch
     H, W = 16, 128
     tr = _trainer(H, W)
     a, b = _solver(H, W, 9, own_stream=True), _solver(H, W, 9, own_stream=True)
     ea = S.Advancer(tr, a, window=10, check_every=0, graph=False)
     ga = S.Advancer(tr, b, window=10, check_every=0, graph=True)
     ea.advance(4)
+    torch.cuda.synchronize()  # both advancers share the network's buffers
     ga.advance(4)
     assert ga.graph is not None and ea.graph is None
     fa, pa = a.get_state()
