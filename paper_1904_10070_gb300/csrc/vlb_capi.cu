@@ -39,6 +39,7 @@ struct vlb_handle {
   double* diag;        // 8 doubles (last in-step diagnostic)
   int* flag;           // device flag: diagnostics found an unstable state (1) or a bulk copy gave up (2)
   vlb::StageMaps* maps = nullptr;  // FP32 UW3: tensor maps of the three stage inputs (NULL: per-thread copies)
+  vlb::EnsembleMaps* ens_maps = nullptr;  // ensemble: members' tensor maps, passed to each launch
   double n0;           // reference density of the stored deviations g = f - n0 w_i w_j
   int64_t steps_done;
   char err[512];
@@ -473,6 +474,7 @@ vlb_status vlb_destroy(vlb_handle* h) {
     delete[] h->views;
   }
   delete[] h->maps;
+  delete h->ens_maps;
   delete h;
   return VLB_OK;
 }
@@ -695,7 +697,7 @@ EnsLayout ens_layout(const vlb_params* p, int count) {
 vlb_status ens_launch_step(vlb_handle* h, int rows_idx, cudaStream_t st) {
   for (int stage = 0; stage < 3; ++stage)
     VLB_CUDA(h, vlb::launch_ensemble_stage(h->d_members, h->d_items[rows_idx], h->nitems[rows_idx], stage,
-                                          kTileRows[rows_idx], h->p.ch_mode, st));
+                                          kTileRows[rows_idx], h->p.ch_mode, st, h->ens_maps));
   return VLB_OK;
 }
 
@@ -708,11 +710,11 @@ vlb_status ens_autotune(vlb_handle* h) {
   float best = 1e30f;
   for (int k = 0; k < 2; ++k) {
     VLB_CUDA(h, vlb::launch_ensemble_stage(h->d_members, h->d_items[k], h->nitems[k], 0, kTileRows[k],
-                                          h->p.ch_mode, h->stream));  // warm-up
+                                          h->p.ch_mode, h->stream, h->ens_maps));  // warm-up
     VLB_CUDA(h, cudaEventRecord(e0, h->stream));
     for (int r = 0; r < 3; ++r)
       VLB_CUDA(h, vlb::launch_ensemble_stage(h->d_members, h->d_items[k], h->nitems[k], 0, kTileRows[k],
-                                            h->p.ch_mode, h->stream));
+                                            h->p.ch_mode, h->stream, h->ens_maps));
     VLB_CUDA(h, cudaEventRecord(e1, h->stream));
     VLB_CUDA(h, cudaEventSynchronize(e1));
     float ms = 0.0f;
@@ -799,6 +801,11 @@ vlb_status vlb_ensemble_create(const vlb_params* p, int32_t count, void* d_works
     return fail(nullptr, VLB_ERR_ARG, "out of host memory");
   }
   std::vector<vlb::EnsembleMember> desc(count);
+  h->ens_maps = new (std::nothrow) vlb::EnsembleMaps();
+  if (!h->ens_maps) {
+    vlb_destroy(h);
+    return fail(nullptr, VLB_ERR_ARG, "out of host memory");
+  }
   std::vector<int2> items[2];
   for (int m = 0; m < count; ++m) {
     vlb_handle* v = new (std::nothrow) vlb_handle();
@@ -854,7 +861,18 @@ vlb_status vlb_ensemble_create(const vlb_params* p, int32_t count, void* d_works
     d.kappa = (float)p[m].kappa;
     d.gt = (float)(1.0 / (2.0 * p[m].r * (2.0 * M_PI / p[m].n_theta)));
     d.n0 = 1.0f;
-    d.pad = 0;
+    d.maps = -1;  // members beyond kEnsMapMembers, or without an encoder, take per-thread copies
+    if (m < vlb::kEnsMapMembers && vlb::stage_maps_apply(p[m].n_theta, p[m].n_phi)) {
+      bool ok = true;
+      for (int k = 0; k < 3 && ok; ++k) {
+        vlb::StageMaps sm;
+        ok = vlb::make_stage_maps((const float*)v->U[k], (const float*)v->U[0], p[m].n_theta, p[m].n_phi, L.stride,
+                                  &sm) == cudaSuccess;
+        h->ens_maps->m[4 * m + k] = sm.box;
+        if (k == 0) h->ens_maps->m[4 * m + 3] = sm.tile;
+      }
+      if (ok) d.maps = 4 * m;
+    }
     const int ts = (p[m].n_phi + 31) / 32;
     for (int k = 0; k < 2; ++k) {
       const int tq = (p[m].n_theta + kTileRows[k] - 1) / kTileRows[k];

@@ -159,27 +159,33 @@ __global__ void wgrad_reduce_kernel(int groups, int cin, int cout, const float* 
 }
 
 // db[co] = sum_p dY[p][co] in two passes with a fixed order.  Pass 1: BG_BLOCKS blocks; thread t
-// takes channel pair t % (cout / 2) of every (256 / (cout / 2))-th pixel of its block's share, so a
-// warp reads whole 128-byte rows; the pixel lanes of a block are then summed in shared memory.
-constexpr int BG_BLOCKS = 128;
+// takes the 8-channel chunk t % (cout / 8) of every (256 / (cout / 8))-th pixel of its block's share
+// (16-byte loads, whole 128-byte rows per 8 or 2 lanes); the pixel lanes of a block are then summed
+// in shared memory.
+constexpr int BG_BLOCKS = 256;
 
 __global__ void __launch_bounds__(256) bias_partial_kernel(int npix, int cout, const bf16* dy, float* part) {
-  __shared__ float red[256 * 2];
-  const int cpairs = cout / 2, lanes = blockDim.x / cpairs;
-  const int cp = threadIdx.x % cpairs, pl = threadIdx.x / cpairs;
-  float s0 = 0.0f, s1 = 0.0f;
+  __shared__ float red[256 * 8];
+  const int chunks = cout / 8, lanes = blockDim.x / chunks;
+  const int ch = threadIdx.x % chunks, pl = threadIdx.x / chunks;
+  float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (int p = blockIdx.x * lanes + pl; p < npix; p += gridDim.x * lanes) {
-    const float2 v = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(dy + (size_t)p * cout)[cp]);
-    s0 += v.x;
-    s1 += v.y;
+    const uint4 v = reinterpret_cast<const uint4*>(dy + (size_t)p * cout)[ch];
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float2 f = __bfloat1622float2(h[i]);
+      s[2 * i] += f.x;
+      s[2 * i + 1] += f.y;
+    }
   }
-  red[pl * cout + 2 * cp] = s0;
-  red[pl * cout + 2 * cp + 1] = s1;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) red[pl * cout + 8 * ch + i] = s[i];
   __syncthreads();
   if (threadIdx.x < cout) {
-    float s = 0.0f;
-    for (int l = 0; l < lanes; ++l) s += red[l * cout + threadIdx.x];
-    part[blockIdx.x * cout + threadIdx.x] = s;
+    float t = 0.0f;
+    for (int l = 0; l < lanes; ++l) t += red[l * cout + threadIdx.x];
+    part[blockIdx.x * cout + threadIdx.x] = t;
   }
 }
 
@@ -241,8 +247,8 @@ cudaError_t conv_wgrad(int H, int W, int cin, int cout, const void* x, const voi
   else
     e = wg_launch<64, 16>(H, W, x, dy, partial, dw, st);
   if (e != cudaSuccess || !db) return e;
-  // the weight partials are consumed by now: their workspace (>= 9 * 16 * 64 floats) holds the
-  // BG_BLOCKS x cout bias partials
+  // the weight partials are consumed by now: their workspace (sized for both, see
+  // conv_wgrad_workspace_bytes) holds the BG_BLOCKS x cout bias partials
   bias_partial_kernel<<<BG_BLOCKS, 256, 0, st>>>(H * W, cout, (const bf16*)dy, partial);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   bias_final_kernel<<<1, 64, 0, st>>>(BG_BLOCKS, cout, partial, db);

@@ -92,13 +92,21 @@ struct EnsembleMember {
   int nt, ns;
   int64_t stride;
   float dt, inv_tau, M, A, kappa, gt, n0;
-  int pad;
+  int maps;  // index of the member's first tensor map in EnsembleMaps, or -1 (per-thread copies)
+};
+
+// Tensor maps of the first kEnsMapMembers ensemble members, passed as one __grid_constant__ kernel
+// parameter (coherent for each launch, no proxy fence): per member the boxes of U^n, U^(1), U^(2)
+// and the U^n tile, for 16-row tiles.  28 KB, inside the 32 KB kernel-parameter limit.
+constexpr int kEnsMapMembers = 56;
+struct EnsembleMaps {
+  CUtensorMap m[4 * kEnsMapMembers];
 };
 
 // Host launchers (vlb_stage.cu).
 // One stage (0, 1, 2) of every ensemble member; items[b] = (member, tile index), tile_rows 16 or 8.
 cudaError_t launch_ensemble_stage(const EnsembleMember* members, const int2* items, int nitems, int stage,
-                                  int tile_rows, int ch_mode, cudaStream_t s);
+                                  int tile_rows, int ch_mode, cudaStream_t s, const EnsembleMaps* maps);
 // maps: tensor maps for this stage's fin / f0 (FP32 UW3 only), or NULL for per-thread copies.
 template <typename T>
 cudaError_t launch_stage(const StageArgs<T>& a, int advection, int ch_mode, cudaStream_t s,

@@ -785,10 +785,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
 template <int TQR>
 using EnsLay = Lay<float, 2, TQR, 4, TQR * (TS / 2), 1>;
 
+// With 16-row tiles, interior tiles of members that have tensor maps are staged by the bulk copies
+// of tile_body_tma, and each block prefetches into L2 the work item `ahead` blocks later.
 template <int TQR, int CH, bool F0>
 __global__ void __launch_bounds__(TQR * (TS / 2)) ensemble_stage_kernel(const EnsembleMember* members,
-                                                                       const int2* items, int stage,
-                                                                       VConst<float> vc) {
+                                                                       const int2* items, int nitems, int ahead,
+                                                                       int stage, VConst<float> vc,
+                                                                       const __grid_constant__ EnsembleMaps maps) {
   using L = EnsLay<TQR>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* sm = reinterpret_cast<float*>(smem_raw);
@@ -814,6 +817,21 @@ __global__ void __launch_bounds__(TQR * (TS / 2)) ensemble_stage_kernel(const En
   a.ahead = 0;
   const int tiles_s = (d.ns + TS - 1) / TS;
   const int q0 = (it.y / tiles_s) * TQR, s0 = (it.y % tiles_s) * TS;
+  if constexpr (TQR == 16) {
+    if (threadIdx.x == 0 && ahead > 0 && blockIdx.x + ahead < nitems) {
+      const int2 nx = items[blockIdx.x + ahead];
+      const EnsembleMember& e = members[nx.x];
+      const int ts = (e.ns + TS - 1) / TS, qn = (nx.y / ts) * TQR, sn = (nx.y % ts) * TS;
+      if (e.maps >= 0 && qn >= L::H && qn + TQR + L::H <= e.nt && sn >= L::HS && sn + TS + L::HS <= e.ns) {
+        tma_prefetch_3d(&maps.m[e.maps + stage], sn - L::HS, qn - L::H, 0);
+        if (F0) tma_prefetch_3d(&maps.m[e.maps + 3], sn, qn, 0);
+      }
+    }
+    if (d.maps >= 0 && q0 >= L::H && q0 + TQR + L::H <= d.nt && s0 >= L::HS && s0 + TS + L::HS <= d.ns) {
+      tile_body_tma<L, CH, F0>(a, vc, sm, threadIdx.x, q0, s0, &maps.m[d.maps + stage], &maps.m[d.maps + 3]);
+      return;
+    }
+  }
   tile_body<L, float, VLB_UW3, CH, F0, 2>(a, vc, sm, threadIdx.x, q0, s0);
 }
 
@@ -885,24 +903,37 @@ cudaError_t launch_generic(const StageArgs<T>& a, cudaStream_t st, const StageMa
 }
 
 template <int TQR, int CH, bool F0>
-cudaError_t launch_ens(const EnsembleMember* members, const int2* items, int nitems, int stage, cudaStream_t st) {
+cudaError_t launch_ens(const EnsembleMember* members, const int2* items, int nitems, int stage, cudaStream_t st,
+                       const EnsembleMaps& maps) {
   using L = EnsLay<TQR>;
   static int mask = 0;
   cudaError_t e = ensure_smem(ensemble_stage_kernel<TQR, CH, F0>, L::BYTES, mask);
   if (e != cudaSuccess) return e;
   static const VConst<float> vc = make_vconst<float>();
-  ensemble_stage_kernel<TQR, CH, F0><<<nitems, L::NTH, L::BYTES, st>>>(members, items, stage, vc);
+  static int resident[32] = {0};  // blocks of this kernel resident at once, per device
+  int dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if (dev < 32 && resident[dev] == 0) {
+    int per_sm = 0, sms = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ensemble_stage_kernel<TQR, CH, F0>, L::NTH,
+                                                           L::BYTES)) != cudaSuccess)
+      return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    resident[dev] = per_sm * sms;
+  }
+  const int ahead = dev < 32 ? resident[dev] / 2 : 0;  // half a wave, as for a single torus
+  ensemble_stage_kernel<TQR, CH, F0><<<nitems, L::NTH, L::BYTES, st>>>(members, items, nitems, ahead, stage, vc, maps);
   return cudaGetLastError();
 }
 
 template <int TQR>
 cudaError_t launch_ens_rows(const EnsembleMember* members, const int2* items, int nitems, int stage, int ch_mode,
-                            cudaStream_t st) {
+                            cudaStream_t st, const EnsembleMaps& maps) {
   if (ch_mode == VLB_HYDRO)
-    return stage == 0 ? launch_ens<TQR, VLB_HYDRO, false>(members, items, nitems, stage, st)
-                      : launch_ens<TQR, VLB_HYDRO, true>(members, items, nitems, stage, st);
-  return stage == 0 ? launch_ens<TQR, VLB_DIFFUSIVE, false>(members, items, nitems, stage, st)
-                    : launch_ens<TQR, VLB_DIFFUSIVE, true>(members, items, nitems, stage, st);
+    return stage == 0 ? launch_ens<TQR, VLB_HYDRO, false>(members, items, nitems, stage, st, maps)
+                      : launch_ens<TQR, VLB_HYDRO, true>(members, items, nitems, stage, st, maps);
+  return stage == 0 ? launch_ens<TQR, VLB_DIFFUSIVE, false>(members, items, nitems, stage, st, maps)
+                    : launch_ens<TQR, VLB_DIFFUSIVE, true>(members, items, nitems, stage, st, maps);
 }
 
 template <typename T, int ADV, int CH>
@@ -975,10 +1006,12 @@ cudaError_t launch_stage(const StageArgs<T>& a, int advection, int ch_mode, cuda
 }
 
 cudaError_t launch_ensemble_stage(const EnsembleMember* members, const int2* items, int nitems, int stage,
-                                  int tile_rows, int ch_mode, cudaStream_t s) {
+                                  int tile_rows, int ch_mode, cudaStream_t s, const EnsembleMaps* maps) {
   if (nitems <= 0) return cudaSuccess;
-  if (tile_rows == 8) return launch_ens_rows<8>(members, items, nitems, stage, ch_mode, s);
-  return launch_ens_rows<16>(members, items, nitems, stage, ch_mode, s);
+  static const EnsembleMaps none = {};
+  const EnsembleMaps& m = maps ? *maps : none;
+  if (tile_rows == 8) return launch_ens_rows<8>(members, items, nitems, stage, ch_mode, s, m);
+  return launch_ens_rows<16>(members, items, nitems, stage, ch_mode, s, m);
 }
 
 template cudaError_t launch_stage<float>(const StageArgs<float>&, int, int, cudaStream_t, const StageMaps*);
