@@ -187,12 +187,27 @@ __global__ void __launch_bounds__(TOTAL_THREADS) totals_kernel(const T* state, i
   }
 }
 
-__global__ void totals_final_kernel(const double* partials, int nb, double* out) {
-  const int k = threadIdx.x;
-  if (k >= NSUM) return;
+// Fixed-order sum (or max) of part[b * stride + k] over b < nb by one warp: lane l takes b = l, l + 32,
+// ... in order, then a shuffle tree; the result depends only on nb, not on scheduling.
+__device__ __forceinline__ double warp_fold(const double* part, int nb, int stride, int k, bool is_max) {
+  const int lane = threadIdx.x & 31;
   double x = 0.0;
-  for (int b = 0; b < nb; ++b) x = (k == 3) ? fmax(x, partials[b * NSUM + k]) : x + partials[b * NSUM + k];
-  out[k] = x;
+  for (int b = lane; b < nb; b += 32) {
+    const double v = part[b * stride + k];
+    x = is_max ? fmax(x, v) : x + v;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double y = __shfl_down_sync(0xffffffffu, x, o);
+    x = is_max ? fmax(x, y) : x + y;
+  }
+  return x;
+}
+
+// one warp per output k (blockDim = 32 NSUM)
+__global__ void totals_final_kernel(const double* partials, int nb, double* out) {
+  const int k = threadIdx.x >> 5;
+  const double x = warp_fold(partials, nb, NSUM, k, k == 3);
+  if ((threadIdx.x & 31) == 0) out[k] = x;
 }
 
 __device__ __forceinline__ float mul_rn(float x, float y) { return __fmul_rn(x, y); }
@@ -238,34 +253,31 @@ __global__ void __launch_bounds__(TOTAL_THREADS) snapshot_sums_kernel(const floa
     sn += (double)v.y * dA;
     sp += (double)v.x * dA;
   }
-  __shared__ double red[2][TOTAL_THREADS];
-  red[0][threadIdx.x] = sn;
-  red[1][threadIdx.x] = sp;
-  __syncthreads();
-  for (int o = TOTAL_THREADS / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-      red[0][threadIdx.x] += red[0][threadIdx.x + o];
-      red[1][threadIdx.x] += red[1][threadIdx.x + o];
-    }
-    __syncthreads();
+  for (int o = 16; o > 0; o >>= 1) {
+    sn += __shfl_down_sync(0xffffffffu, sn, o);
+    sp += __shfl_down_sync(0xffffffffu, sp, o);
   }
-  if (threadIdx.x == 0) {
-    partials[blockIdx.x * NSUM] = red[0][0];
-    partials[blockIdx.x * NSUM + 1] = red[1][0];
+  __shared__ double red[2][TOTAL_THREADS / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][wid] = sn;
+    red[1][wid] = sp;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    double x = 0.0;
+    for (int w = 0; w < TOTAL_THREADS / 32; ++w) x += red[threadIdx.x][w];
+    partials[blockIdx.x * NSUM + threadIdx.x] = x;
   }
 }
 
-// shift[0] = (mass - sum n dA) / area, shift[1] = (phi_total - sum phi dA) / area (Sec. 2.5 totals).
+// shift[0] = (mass - sum n dA) / area, shift[1] = (phi_total - sum phi dA) / area (Sec. 2.5 totals);
+// one warp per total (blockDim = 64).
 __global__ void snapshot_shift_kernel(const double* partials, int nb, double mass, double phi_total, double inv_area,
                                       double* shift) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double sn = 0.0, sp = 0.0;
-  for (int b = 0; b < nb; ++b) {
-    sn += partials[b * NSUM];
-    sp += partials[b * NSUM + 1];
-  }
-  shift[0] = (mass - sn) * inv_area;
-  shift[1] = (phi_total - sp) * inv_area;
+  const int k = threadIdx.x >> 5;
+  const double x = warp_fold(partials, nb, NSUM, k, false);
+  if ((threadIdx.x & 31) == 0) shift[k] = ((k == 0 ? mass : phi_total) - x) * inv_area;
 }
 
 // The surrogate restart from a snapshot (n', u', phi'), with n' += shift[0] and phi' += shift[1] when
@@ -358,7 +370,7 @@ cudaError_t launch_totals(const T* state, int64_t stride, const double* coefd, i
                                                       partials, make_vd());
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  totals_final_kernel<<<1, 32, 0, s>>>(partials, n_blocks, out);
+  totals_final_kernel<<<1, 32 * NSUM, 0, s>>>(partials, n_blocks, out);
   return cudaGetLastError();
 }
 
@@ -373,7 +385,7 @@ cudaError_t launch_snapshot_shift(const float* snap, const double* coefd, int nt
   snapshot_sums_kernel<<<TOTAL_BLOCKS, TOTAL_THREADS, 0, s>>>(snap, coefd, nt, ns, partials);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  snapshot_shift_kernel<<<1, 32, 0, s>>>(partials, TOTAL_BLOCKS, mass, phi_total, inv_area, shift);
+  snapshot_shift_kernel<<<1, 64, 0, s>>>(partials, TOTAL_BLOCKS, mass, phi_total, inv_area, shift);
   return cudaGetLastError();
 }
 

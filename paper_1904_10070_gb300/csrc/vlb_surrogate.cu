@@ -74,7 +74,18 @@ __global__ void norm_kernel(int64_t n, const double* sums, float s_n_fixed, floa
 
 constexpr int RED_BLOCKS = 256;
 
-// per-block FP64 sums of x[p][c] and x[p][c]^2 for c < C (C <= 16)
+// Fixed-order fold of part[b * stride + k] over b < nb by one warp (lane l takes b = l, l + 32, ...,
+// then a shuffle tree): the result depends only on nb, not on scheduling.
+__device__ __forceinline__ double warp_sum(const double* part, int nb, int stride, int k) {
+  const int lane = threadIdx.x & 31;
+  double x = 0.0;
+  for (int b = lane; b < nb; b += 32) x += part[b * stride + k];
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// per-block FP64 sums of x[p][c] and x[p][c]^2 for c < C (C <= 16); squares in FP64 too, since a
+// variance sum(x^2)/n - mean^2 of a density near 1 cancels most of its digits
 __global__ void stats_kernel(int64_t n, int C, const float* x, double* part) {
   double s[16], s2[16];
   for (int c = 0; c < 16; ++c) s[c] = s2[c] = 0.0;
@@ -84,16 +95,18 @@ __global__ void stats_kernel(int64_t n, int C, const float* x, double* part) {
       s[c] += v;
       s2[c] += v * v;
     }
-  __shared__ double red[256];
+  __shared__ double red[8][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int c = 0; c < 2 * C; ++c) {
-    red[threadIdx.x] = c < C ? s[c] : s2[c - C];
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-      if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) part[blockIdx.x * 32 + c] = red[0];
-    __syncthreads();
+    double v = c < C ? s[c] : s2[c - C];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[wid][c] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 * C) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w][threadIdx.x];
+    part[blockIdx.x * 32 + threadIdx.x] = v;
   }
 }
 
@@ -139,26 +152,22 @@ __global__ void compare_kernel(int64_t n, const float* a, const float* b, double
   }
 }
 
-// out4 = {max |a - b|, max |b|, sum (a - b)^2, sum b^2} from compare_kernel's results, in a fixed order.
+// out4 = {max |a - b|, max |b|, sum (a - b)^2, sum b^2} from compare_kernel's results, in a fixed order
+// (one warp per sum, blockDim = 64).
 __global__ void compare_final_kernel(int nb, const double* part, const unsigned* max2, double* out4) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double s2 = 0.0, r2 = 0.0;
-  for (int b = 0; b < nb; ++b) {
-    s2 += part[b * 32];
-    r2 += part[b * 32 + 1];
+  const int k = threadIdx.x >> 5;
+  const double v = warp_sum(part, nb, 32, k);
+  if ((threadIdx.x & 31) == 0) out4[2 + k] = v;
+  if (threadIdx.x == 0) {
+    out4[0] = (double)__uint_as_float(max2[0]);
+    out4[1] = (double)__uint_as_float(max2[1]);
   }
-  out4[0] = (double)__uint_as_float(max2[0]);
-  out4[1] = (double)__uint_as_float(max2[1]);
-  out4[2] = s2;
-  out4[3] = r2;
 }
 
 __global__ void stats_final_kernel(int nb, int C, const double* part, double* out) {
-  const int c = threadIdx.x;
-  if (c >= 2 * C) return;
-  double s = 0.0;
-  for (int b = 0; b < nb; ++b) s += part[b * 32 + c];
-  out[c] = s;
+  const int c = threadIdx.x >> 5;
+  const double v = warp_sum(part, nb, 32, c);
+  if ((threadIdx.x & 31) == 0 && c < 2 * C) out[c] = v;
 }
 
 // loss partials of (pred[p][c] - target[p][c])^2 over c < 4; grad[p][c] = 2 (pred - target) / (4 n)
@@ -189,11 +198,8 @@ __global__ void mse_kernel(int64_t n, const float* pred, const float* target, bf
 }
 
 __global__ void sum_final_kernel(int nb, const double* part, double scale, double* out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += part[b];
-    *out = s * scale;
-  }
+  const double v = warp_sum(part, nb, 1, 0);
+  if (threadIdx.x == 0) *out = v * scale;
 }
 
 // Adam (Kingma & Ba 2015) on FP32 master parameters; optionally refreshes a BF16 copy.
@@ -248,7 +254,7 @@ cudaError_t sur_compare(int64_t n, const float* a, const float* b, double* part,
   if (e != cudaSuccess) return e;
   compare_kernel<<<RED_BLOCKS, 256, 0, st>>>(n, a, b, part, max2);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  compare_final_kernel<<<1, 32, 0, st>>>(RED_BLOCKS, part, max2, out4);
+  compare_final_kernel<<<1, 64, 0, st>>>(RED_BLOCKS, part, max2, out4);
   return cudaGetLastError();
 }
 
@@ -256,7 +262,7 @@ cudaError_t sur_stats(int64_t n, int C, const float* x, double* part, double* ou
   stats_kernel<<<RED_BLOCKS, 256, 0, st>>>(n, C, x, part);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  stats_final_kernel<<<1, 32, 0, st>>>(RED_BLOCKS, C, part, out);
+  stats_final_kernel<<<1, 64 * C, 0, st>>>(RED_BLOCKS, C, part, out);
   return cudaGetLastError();
 }
 
