@@ -189,13 +189,16 @@ __global__ void __launch_bounds__(256) bias_partial_kernel(int npix, int cout, c
   }
 }
 
-// Pass 2: db[co] = sum over the blocks' partials, in block order.
+// Pass 2: db[co] = sum over the blocks' partials in a fixed order: warp w folds channels w, w + 8, ...
+// (lane l takes blocks l, l + 32, ..., then a shuffle tree); blockDim = 256.
 __global__ void bias_final_kernel(int nb, int cout, const float* part, float* db) {
-  const int co = threadIdx.x;
-  if (co >= cout) return;
-  float s = 0.0f;
-  for (int b = 0; b < nb; ++b) s += part[b * cout + co];
-  db[co] = s;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int co = warp; co < cout; co += blockDim.x >> 5) {
+    float s = 0.0f;
+    for (int b = lane; b < nb; b += 32) s += part[b * cout + co];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) db[co] = s;
+  }
 }
 
 template <typename K>
@@ -251,7 +254,7 @@ cudaError_t conv_wgrad(int H, int W, int cin, int cout, const void* x, const voi
   // conv_wgrad_workspace_bytes) holds the BG_BLOCKS x cout bias partials
   bias_partial_kernel<<<BG_BLOCKS, 256, 0, st>>>(H * W, cout, (const bf16*)dy, partial);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  bias_final_kernel<<<1, 64, 0, st>>>(BG_BLOCKS, cout, partial, db);
+  bias_final_kernel<<<1, 256, 0, st>>>(BG_BLOCKS, cout, partial, db);
   return cudaGetLastError();
 }
 
