@@ -54,3 +54,23 @@ def band_pressure_jump(p: np.ndarray, theta_c: float, width: float):
         return (1.0 - t) * p[q % n] + t * p[(q + 1) % n]
 
     return at(theta_c) - at(theta_c + math.pi)
+
+
+def equal_area_drop_radius(R, r, xi, theta0, ref_theta0, ref_radius, n_theta=512, n_phi=1280):
+    """R_0 of a drop (Eq. drop_init, phi = -1 inside, Euclidean distance) centred at (theta0, 0) with
+    the same area as the drop (ref_theta0, ref_radius): the root of
+    int (R + r cos theta) [phi_ref - phi(theta0, R_0)] dtheta dvarphi = 0 (Sec. 3.4), by bisection
+    on a n_theta x n_phi midpoint grid."""
+    from paper_1904_10070_gb300 import inputs
+    th, _ = inputs.grid(n_theta, n_phi)
+    wgt = R + r * np.cos(th)
+    target = np.sum(wgt * inputs.drop_phi(R, r, n_theta, n_phi, ref_theta0, ref_radius, xi, inside=-1.0))
+    lo, hi = 0.25 * ref_radius, 4.0 * ref_radius
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        # a larger drop holds more of the phi = -1 phase: the weighted integral falls as R_0 grows
+        if np.sum(wgt * inputs.drop_phi(R, r, n_theta, n_phi, theta0, mid, xi, inside=-1.0)) > target:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)

@@ -78,3 +78,18 @@ def test_stripe_oscillation_frequency():
     assert abs(abs(popt[1]) / omega0 - 1.0) < 0.03, (popt[1], omega0)
     a_nu = C.alpha_nu(R, r, nu)
     assert 0.5 * a_nu < popt[3] < 5.0 * a_nu, (popt[3], a_nu)
+
+
+def test_equal_area_drop_radii_match_the_printed_values():
+    """The drop-drift figure prints R_0 for three drop centres (tests/golden/drop_radii_printed.txt).
+    Solving the equal-area condition with the drop profile of Eq. drop_init (Euclidean distance, the
+    A8 reading) and the torus area element reproduces all three to the printed three decimals."""
+    import os
+    R, r, kappa, A = 2.0, 0.8, 5e-4, 0.5
+    xi = C.xi0(kappa, A)
+    path = os.path.join(os.path.dirname(__file__), "golden", "drop_radii_printed.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 3
+    for t0, r0 in rows:
+        got = AN.equal_area_drop_radius(R, r, xi, float(t0) * math.pi, 0.0, 30.0 * xi)
+        assert abs(got - float(r0)) <= 0.0006, (t0, got, r0)
