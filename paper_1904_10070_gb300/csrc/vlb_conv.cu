@@ -245,8 +245,14 @@ cudaError_t conv_wgrad(int H, int W, int cin, int cout, const void* x, const voi
   cudaError_t e;
   if (cin == 16)
     e = wg_launch<16, 64>(H, W, x, dy, partial, dw, st);
-  else if (cout == 64)
-    e = wg_launch<64, 64>(H, W, x, dy, partial, dw, st);
+  else if (cout == 64) {  // on tcgen05 (vlb_conv_tc.cu), then the same fixed-order reduction
+    e = conv_wgrad_tc64(H, W, x, dy, partial, WG_SEGS, st);
+    if (e == cudaSuccess) {
+      const int groups = (H * (W / CPX) + WG_SEGS - 1) / WG_SEGS;
+      wgrad_reduce_kernel<<<(9 * 64 * 64 + 255) / 256, 256, 0, st>>>(groups, 64, 64, partial, dw);
+      e = cudaGetLastError();
+    }
+  }
   else
     e = wg_launch<64, 16>(H, W, x, dy, partial, dw, st);
   if (e != cudaSuccess || !db) return e;

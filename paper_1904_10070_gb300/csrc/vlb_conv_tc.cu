@@ -380,6 +380,155 @@ __global__ void __launch_bounds__(TTHR, 1)
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Weight gradient of a 64 -> 64 layer: for tap t, D_t[co][ci] = sum_p dY[p][co] X[p + d_t][ci]
+// (M = 64 output channels, N = 64 input channels, K = pixels, 16 per MMA).  Both operands stay
+// pixel-major as they lie in memory: 128-byte pixel rows (64 channels) with the 128-byte swizzle,
+// i.e. the MN-major layout (transpose bits 15 and 16 set; K steps of 16 pixels are 2048 bytes).  An
+// M = 64 accumulator puts row m in tensor-memory lane 32 (m / 16) + m % 16 (measured on GB300).
+// A CTA owns a group of row segments (128 pixels) and a class of taps (0-4 or 5-8, 5 or 4
+// accumulators of 64 columns) and writes its per-group partial sums; a second kernel reduces the
+// groups in a fixed order.  Warps 0-3 read the accumulators at the end, warp 4 issues the MMAs,
+// warp 5 copies the dY segment (one tensor-map box) and the 3-row input patch (another, plus the
+// periodic fix-ups), double-buffered.
+struct WgLay {
+  static constexpr int DY = TPX * 128;                           // dY segment: 128 pixel rows of 128 B
+  static constexpr int XP = ((3 * TPW * 128) + 1023) / 1024 * 1024;  // input patch, 3 x 130 pixel rows
+  static constexpr int STAGE = DY + XP;
+  static constexpr int BAR_OFF = 2 * STAGE;                      // tma[2], full[2], empty[2], done
+  static constexpr int TSLOT_OFF = BAR_OFF + 8 * 8;
+  static constexpr int BYTES = TSLOT_OFF + 16;
+  static_assert(DY % 1024 == 0 && XP % 1024 == 0, "swizzle atoms stay aligned");
+};
+
+// MN-major, 128-byte swizzle: 8-pixel groups of 128-byte rows 1024 bytes apart (one 64-wide atom in MN)
+__device__ __forceinline__ uint64_t sdesc_mn_sw128(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+__global__ void __launch_bounds__(TTHR, 1)
+    conv_wgrad_tc_kernel(int H, int W, int segs_per_group, const bf16* __restrict__ x, float* partial, int* err,
+                         const __grid_constant__ CUtensorMap dymap, const __grid_constant__ CUtensorMap xmap) {
+  using L = WgLay;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L::BAR_OFF);
+  uint64_t *tma = bars, *full = bars + 2, *empty = bars + 4, *done = bars + 6;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::TSLOT_OFF);
+  const int t0 = blockIdx.y == 0 ? 0 : 5, ntap = blockIdx.y == 0 ? 5 : 4;
+  const uint32_t cols = blockIdx.y == 0 ? 512u : 256u;
+  if (warp == MMA_WARP) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(tslot)), "r"(cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tma + b, 1);
+      mbar_init(full + b, 1);
+      mbar_init(empty + b, 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const int segs_row = W / TPX, nseg = H * segs_row;
+  const int seg0 = blockIdx.x * segs_per_group;
+  const int nmine = seg0 < nseg ? min(segs_per_group, nseg - seg0) : 0;
+  bool ok = true;
+  if (warp == LOAD_WARP) {
+    for (int k = 0; k < nmine && ok; ++k) {
+      const int b = k & 1, sg = seg0 + k, row = sg / segs_row, x0 = (sg % segs_row) * TPX;
+      unsigned char* dyb = sm + b * L::STAGE;
+      unsigned char* xb = dyb + L::DY;
+      if (k >= 2) ok = mbar_wait(empty + b, ((k - 2) >> 1) & 1);
+      if (!ok) break;
+      if (lane == 0) {
+        mbar_expect_tx(tma + b, L::DY + 3 * TPW * 128);
+        tma_load_3d(dyb, &dymap, tma + b, x0, row);
+        tma_load_3d(xb, &xmap, tma + b, x0 - 1, row - 1);
+      }
+      ok = mbar_wait(tma + b, (k >> 1) & 1);
+      if (!ok) break;
+      // periodic fix-ups of the 3-row patch (pixel row j = pr * TPW + pc, chunk c at c ^ (j % 8))
+      const bool top = row == 0, bottom = row == H - 1, left = x0 == 0, right = x0 + TPX == W;
+      if (top || bottom || left || right) {
+        for (int pr = 0; pr < 3; ++pr) {
+          const int yy = row + pr - 1, gy = yy < 0 ? yy + H : (yy >= H ? yy - H : yy);
+          for (int i = lane; i < TPW * 8; i += 32) {
+            const int c = i % 8, pc = i / 8, xx = x0 + pc - 1;
+            const int gx = xx < 0 ? xx + W : (xx >= W ? xx - W : xx);
+            if (gy != yy || gx != xx) {
+              const int j = pr * TPW + pc;
+              cp16(xb + j * 128 + ((c ^ (j & 7)) << 4), x + ((size_t)gy * W + gx) * 64 + c * 8);
+            }
+          }
+        }
+        asm volatile("cp.async.commit_group;\n" ::);
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        fence_async_smem();
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(full + b);
+    }
+  } else if (warp == MMA_WARP) {
+    if (lane == 0) {
+      constexpr uint32_t ID = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((64u >> 3) << 17) |
+                              ((64u >> 4) << 24);
+      for (int k = 0; k < nmine && ok; ++k) {
+        const int b = k & 1;
+        ok = mbar_wait(full + b, (k >> 1) & 1);
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t dyb = su32(sm + b * L::STAGE), xb = dyb + L::DY;
+        for (int j = 0; j < ntap; ++j) {
+          const int t = t0 + j, dy = t / 3, dx = t % 3;
+#pragma unroll
+          for (int s2 = 0; s2 < TPX / 16; ++s2) {
+            const uint64_t ad = sdesc_mn_sw128(dyb + 2048u * s2);
+            const uint64_t bd = sdesc_mn_sw128(xb + (uint32_t)((dy * TPW + dx) * 128) + 2048u * s2);
+            umma(tmem + 64u * j, ad, bd, ID, (k | s2) != 0);
+          }
+        }
+        umma_commit(empty + b);
+      }
+      if (ok) umma_commit(done);
+    }
+    __syncwarp();
+  } else {  // warps 0-3: the partial sums of this group, once every segment is in
+    ok = nmine == 0 || mbar_wait(done, 0);
+    if (ok && nmine > 0) {
+      tc_fence_after();
+      for (int j = 0; j < ntap; ++j) {
+        uint32_t raw[64];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + 64u * j + 16u * q, raw + 16 * q);
+        tmem_wait_ld();
+        if (lane < 16) {  // lanes 0-15 of warp w hold output channels 16 w .. 16 w + 15
+          const int co = 16 * warp + lane;
+          float4* dst = reinterpret_cast<float4*>(partial + (((size_t)blockIdx.x * 9 + t0 + j) * 64 + co) * 64);
+#pragma unroll
+          for (int q = 0; q < 16; ++q)
+            dst[q] = make_float4(__uint_as_float(raw[4 * q]), __uint_as_float(raw[4 * q + 1]),
+                                 __uint_as_float(raw[4 * q + 2]), __uint_as_float(raw[4 * q + 3]));
+        }
+      }
+    }
+  }
+  if (!ok && lane == 0 && err) atomicExch(err, 1);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == MMA_WARP) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(cols) : "memory");
+  }
+}
+
 __device__ int g_conv_tc_err = 0;  // raised if a bounded wait on the tensor cores gives up
 
 using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -455,6 +604,40 @@ cudaError_t tc_launch(int H, int W, const void* x, const void* w, const float* b
   return cudaGetLastError();
 }
 
+cudaError_t wg64_launch(int H, int W, const void* x, const void* dy, float* partial, int segs_per_group,
+                        cudaStream_t st) {
+  static int ready[32] = {0};
+  static int* err[32] = {nullptr};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 32) return cudaErrorInvalidDevice;
+  if (!ready[dev]) {
+    e = cudaFuncSetAttribute(conv_wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, WgLay::BYTES);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaGetSymbolAddress((void**)&err[dev], g_conv_tc_err)) != cudaSuccess) return e;
+    ready[dev] = 1;
+  }
+  EncodeTiled enc = encoder();
+  if (!enc) return cudaErrorNotSupported;
+  alignas(64) CUtensorMap dymap, xmap;
+  const cuuint64_t dims[3] = {64, (cuuint64_t)W, (cuuint64_t)H};
+  const cuuint64_t strides[2] = {128, (cuuint64_t)W * 128};
+  const cuuint32_t box_dy[3] = {64, (cuuint32_t)TPX, 1}, box_x[3] = {64, (cuuint32_t)TPW, 3};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  if (enc(&dymap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(dy), dims, strides, box_dy, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+      enc(&xmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(x), dims, strides, box_x, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  const int nseg = H * (W / TPX), groups = (nseg + segs_per_group - 1) / segs_per_group;
+  conv_wgrad_tc_kernel<<<dim3(groups, 2), TTHR, WgLay::BYTES, st>>>(H, W, segs_per_group, (const bf16*)x, partial,
+                                                                  err[dev], dymap, xmap);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t conv_fwd_tc(int H, int W, int cin, int cout, const void* x, const void* w, const float* b,
@@ -462,6 +645,11 @@ cudaError_t conv_fwd_tc(int H, int W, int cin, int cout, const void* x, const vo
   if (cin == 16) return tc_launch<16, 64>(H, W, x, w, b, mask, relu, y, yf, st);
   if (cout == 64) return tc_launch<64, 64>(H, W, x, w, b, mask, relu, y, yf, st);
   return tc_launch<64, 16>(H, W, x, w, b, mask, relu, y, yf, st);
+}
+
+cudaError_t conv_wgrad_tc64(int H, int W, const void* x, const void* dy, float* partial, int segs_per_group,
+                            cudaStream_t st) {
+  return wg64_launch(H, W, x, dy, partial, segs_per_group, st);
 }
 
 }  // namespace vlb

@@ -148,6 +148,10 @@ size_t conv_wgrad_workspace_bytes(int H, int W, int cin, int cout);
 // the forward on the tcgen05 tensor cores (vlb_conv_tc.cu)
 cudaError_t conv_fwd_tc(int H, int W, int cin, int cout, const void* x, const void* w, const float* b,
                         const void* mask, int relu, void* y, float* yf, cudaStream_t st);
+// partial[group][tap][co][ci] of a 64 -> 64 weight gradient on tcgen05 (vlb_conv_tc.cu); group g
+// covers row segments (128 pixels) g * segs_per_group ..
+cudaError_t conv_wgrad_tc64(int H, int W, const void* x, const void* dy, float* partial, int segs_per_group,
+                            cudaStream_t st);
 cudaError_t conv_flip(int cin, int cout, const void* w, void* wf, cudaStream_t st);
 cudaError_t conv_wgrad(int H, int W, int cin, int cout, const void* x, const void* dy, float* dw, float* db,
                        float* partial, cudaStream_t st);
