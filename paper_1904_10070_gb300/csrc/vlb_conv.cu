@@ -147,14 +147,35 @@ __global__ void __launch_bounds__(NTHR) conv_wgrad_kernel(int H, int W, const bf
   }
 }
 
-// dW[co][t][ci] = sum over groups (fixed order) of partial[group][t][co][ci]
-__global__ void wgrad_reduce_kernel(int groups, int cin, int cout, const float* partial, float* dw) {
-  const int n = 9 * cout * cin;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int t = i / (cout * cin), rem = i - t * cout * cin, co = rem / cin, ci = rem - co * cin;
-    float s = 0.0f;
-    for (int gp = 0; gp < groups; ++gp) s += partial[(size_t)gp * n + i];
-    dw[((size_t)co * 9 + t) * cin + ci] = s;
+// dW[co][t][ci] = sum over groups of partial[group][t][co][ci] in a fixed order. A 256-thread block
+// takes 32 consecutive weights: warp j adds groups j, j + 8, ... (each load 128 contiguous bytes), and
+// the eight warp sums are folded in warp order through shared memory.
+__global__ void __launch_bounds__(256) wgrad_reduce_kernel(int groups, int cin, int cout, const float* partial,
+                                                           float* dw) {
+  __shared__ float part[8][32];
+  const int n = 9 * cout * cin, j = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 32 + lane;
+  float s = 0.0f;
+  if (i < n) {
+    int gp = j;
+    for (; gp + 24 < groups; gp += 32) {
+      const float a0 = partial[(size_t)gp * n + i], a1 = partial[(size_t)(gp + 8) * n + i];
+      const float a2 = partial[(size_t)(gp + 16) * n + i], a3 = partial[(size_t)(gp + 24) * n + i];
+      s += a0;
+      s += a1;
+      s += a2;
+      s += a3;
+    }
+    for (; gp < groups; gp += 8) s += partial[(size_t)gp * n + i];
+  }
+  part[j][lane] = s;
+  __syncthreads();
+  if (j == 0 && i < n) {
+    float t = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += part[k][lane];
+    const int tap = i / (cout * cin), rem = i - tap * cout * cin, co = rem / cin, ci = rem - co * cin;
+    dw[((size_t)co * 9 + tap) * cin + ci] = t;
   }
 }
 
@@ -189,16 +210,19 @@ __global__ void __launch_bounds__(256) bias_partial_kernel(int npix, int cout, c
   }
 }
 
-// Pass 2: db[co] = sum over the blocks' partials in a fixed order: warp w folds channels w, w + 8, ...
-// (lane l takes blocks l, l + 32, ..., then a shuffle tree); blockDim = 256.
-__global__ void bias_final_kernel(int nb, int cout, const float* part, float* db) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int co = warp; co < cout; co += blockDim.x >> 5) {
-    float s = 0.0f;
-    for (int b = lane; b < nb; b += 32) s += part[b * cout + co];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) db[co] = s;
-  }
+// Pass 2: db[co] = sum over the blocks' partials in a fixed order, one warp per channel (lane l adds
+// blocks l, l + 32, ... in order, then a shuffle tree); all loads of a channel are in flight together.
+__global__ void bias_final_kernel(int cout, const float* part, float* db) {
+  const int co = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (co >= cout) return;
+  float v[BG_BLOCKS / 32];
+#pragma unroll
+  for (int i = 0; i < BG_BLOCKS / 32; ++i) v[i] = part[(lane + 32 * i) * cout + co];
+  float s = 0.0f;
+#pragma unroll
+  for (int i = 0; i < BG_BLOCKS / 32; ++i) s += v[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) db[co] = s;
 }
 
 template <typename K>
@@ -215,7 +239,7 @@ cudaError_t wg_launch(int H, int W, const void* x, const void* dy, float* partia
   conv_wgrad_kernel<CIN, COUT><<<dim3(groups, 9), NTHR, S, st>>>(H, W, (const bf16*)x, (const bf16*)dy, partial);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  wgrad_reduce_kernel<<<(9 * CIN * COUT + 255) / 256, 256, 0, st>>>(groups, CIN, COUT, partial, dw);
+  wgrad_reduce_kernel<<<(9 * CIN * COUT + 31) / 32, 256, 0, st>>>(groups, CIN, COUT, partial, dw);
   return cudaGetLastError();
 }
 
@@ -249,7 +273,7 @@ cudaError_t conv_wgrad(int H, int W, int cin, int cout, const void* x, const voi
     e = conv_wgrad_tc64(H, W, x, dy, partial, WG_SEGS, st);
     if (e == cudaSuccess) {
       const int groups = (H * (W / CPX) + WG_SEGS - 1) / WG_SEGS;
-      wgrad_reduce_kernel<<<(9 * 64 * 64 + 255) / 256, 256, 0, st>>>(groups, 64, 64, partial, dw);
+      wgrad_reduce_kernel<<<(9 * 64 * 64 + 31) / 32, 256, 0, st>>>(groups, 64, 64, partial, dw);
       e = cudaGetLastError();
     }
   }
@@ -260,7 +284,7 @@ cudaError_t conv_wgrad(int H, int W, int cin, int cout, const void* x, const voi
   // conv_wgrad_workspace_bytes) holds the BG_BLOCKS x cout bias partials
   bias_partial_kernel<<<BG_BLOCKS, 256, 0, st>>>(H * W, cout, (const bf16*)dy, partial);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  bias_final_kernel<<<1, 256, 0, st>>>(BG_BLOCKS, cout, partial, db);
+  bias_final_kernel<<<(cout + 7) / 8, 256, 0, st>>>(cout, partial, db);
   return cudaGetLastError();
 }
 

@@ -386,19 +386,20 @@ __global__ void __launch_bounds__(TTHR, 1)
 // pixel-major as they lie in memory: 128-byte pixel rows (64 channels) with the 128-byte swizzle,
 // i.e. the MN-major layout (transpose bits 15 and 16 set; K steps of 16 pixels are 2048 bytes).  An
 // M = 64 accumulator puts row m in tensor-memory lane 32 (m / 16) + m % 16 (measured on GB300).
-// A CTA owns a group of row segments (128 pixels) and a class of taps (0-4 or 5-8, 5 or 4
-// accumulators of 64 columns) and writes its per-group partial sums; a second kernel reduces the
-// groups in a fixed order.  Warps 0-3 read the accumulators at the end, warp 4 issues the MMAs,
-// warp 5 copies the dY segment (one tensor-map box) and the 3-row input patch (another, plus the
-// periodic fix-ups), double-buffered.
+// A CTA owns a group of row segments (128 pixels) and one tap row dy (taps 3 dy .. 3 dy + 2): the
+// K window of each of its taps lies in the single input row y + dy - 1, so a step copies the dY
+// segment and that one 130-pixel row (two tensor-map boxes, plus the periodic fix-ups), three deep.
+// Warps 0-3 read the three accumulators at the end and write the group's partial sums (reduced over
+// groups in a fixed order by a second kernel); warp 4 issues the MMAs; warp 5 copies.
 struct WgLay {
-  static constexpr int DY = TPX * 128;                           // dY segment: 128 pixel rows of 128 B
-  static constexpr int XP = ((3 * TPW * 128) + 1023) / 1024 * 1024;  // input patch, 3 x 130 pixel rows
-  static constexpr int STAGE = DY + XP;
-  static constexpr int BAR_OFF = 2 * STAGE;                      // tma[2], full[2], empty[2], done
-  static constexpr int TSLOT_OFF = BAR_OFF + 8 * 8;
+  static constexpr int NSTAGE = 3;
+  static constexpr int DY = TPX * 128;                        // dY segment: 128 pixel rows of 128 B
+  static constexpr int XR = (TPW * 128 + 1023) / 1024 * 1024;  // one input row of 130 pixels
+  static constexpr int STAGE = DY + XR;
+  static constexpr int BAR_OFF = NSTAGE * STAGE;              // tma, full, empty (x NSTAGE), done
+  static constexpr int TSLOT_OFF = BAR_OFF + 8 * (3 * NSTAGE + 1);
   static constexpr int BYTES = TSLOT_OFF + 16;
-  static_assert(DY % 1024 == 0 && XP % 1024 == 0, "swizzle atoms stay aligned");
+  static_assert(DY % 1024 == 0 && XR % 1024 == 0, "swizzle atoms stay aligned");
 };
 
 // MN-major, 128-byte swizzle: 8-pixel groups of 128-byte rows 1024 bytes apart (one 64-wide atom in MN)
@@ -407,24 +408,25 @@ __device__ __forceinline__ uint64_t sdesc_mn_sw128(uint32_t addr) {
          ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
-__global__ void __launch_bounds__(TTHR, 1)
+__global__ void __launch_bounds__(TTHR)
     conv_wgrad_tc_kernel(int H, int W, int segs_per_group, const bf16* __restrict__ x, float* partial, int* err,
                          const __grid_constant__ CUtensorMap dymap, const __grid_constant__ CUtensorMap xmap) {
   using L = WgLay;
+  constexpr int NS = L::NSTAGE;
+  constexpr uint32_t COLS = 256;  // three 64-column accumulators
   extern __shared__ __align__(1024) unsigned char sm[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L::BAR_OFF);
-  uint64_t *tma = bars, *full = bars + 2, *empty = bars + 4, *done = bars + 6;
+  uint64_t *tma = bars, *full = bars + NS, *empty = bars + 2 * NS, *done = bars + 3 * NS;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::TSLOT_OFF);
-  const int t0 = blockIdx.y == 0 ? 0 : 5, ntap = blockIdx.y == 0 ? 5 : 4;
-  const uint32_t cols = blockIdx.y == 0 ? 512u : 256u;
+  const int dyr = blockIdx.y;  // tap row: taps 3 dyr + dx
   if (warp == MMA_WARP) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(tslot)), "r"(cols)
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(tslot)), "r"(COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
   if (tid == 0) {
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NS; ++b) {
       mbar_init(tma + b, 1);
       mbar_init(full + b, 1);
       mbar_init(empty + b, 1);
@@ -442,30 +444,27 @@ __global__ void __launch_bounds__(TTHR, 1)
   bool ok = true;
   if (warp == LOAD_WARP) {
     for (int k = 0; k < nmine && ok; ++k) {
-      const int b = k & 1, sg = seg0 + k, row = sg / segs_row, x0 = (sg % segs_row) * TPX;
+      const int b = k % NS, use = k / NS, sg = seg0 + k, row = sg / segs_row, x0 = (sg % segs_row) * TPX;
       unsigned char* dyb = sm + b * L::STAGE;
       unsigned char* xb = dyb + L::DY;
-      if (k >= 2) ok = mbar_wait(empty + b, ((k - 2) >> 1) & 1);
+      if (k >= NS) ok = mbar_wait(empty + b, (use - 1) & 1);  // the MMAs of step k - NS read it
       if (!ok) break;
+      const int yy = row + dyr - 1, gy = yy < 0 ? yy + H : (yy >= H ? yy - H : yy);
       if (lane == 0) {
-        mbar_expect_tx(tma + b, L::DY + 3 * TPW * 128);
+        mbar_expect_tx(tma + b, L::DY + TPW * 128);
         tma_load_3d(dyb, &dymap, tma + b, x0, row);
-        tma_load_3d(xb, &xmap, tma + b, x0 - 1, row - 1);
+        tma_load_3d(xb, &xmap, tma + b, x0 - 1, gy);  // the row index is wrapped here already
       }
-      ok = mbar_wait(tma + b, (k >> 1) & 1);
+      ok = mbar_wait(tma + b, use & 1);
       if (!ok) break;
-      // periodic fix-ups of the 3-row patch (pixel row j = pr * TPW + pc, chunk c at c ^ (j % 8))
-      const bool top = row == 0, bottom = row == H - 1, left = x0 == 0, right = x0 + TPX == W;
-      if (top || bottom || left || right) {
-        for (int pr = 0; pr < 3; ++pr) {
-          const int yy = row + pr - 1, gy = yy < 0 ? yy + H : (yy >= H ? yy - H : yy);
-          for (int i = lane; i < TPW * 8; i += 32) {
-            const int c = i % 8, pc = i / 8, xx = x0 + pc - 1;
-            const int gx = xx < 0 ? xx + W : (xx >= W ? xx - W : xx);
-            if (gy != yy || gx != xx) {
-              const int j = pr * TPW + pc;
-              cp16(xb + j * 128 + ((c ^ (j & 7)) << 4), x + ((size_t)gy * W + gx) * 64 + c * 8);
-            }
+      // the two edge pixels of a wrapped segment (pixel j, chunk c at c ^ (j % 8))
+      const bool left = x0 == 0, right = x0 + TPX == W;
+      if (left || right) {
+        if (lane < 16) {
+          const int c = lane % 8, side = lane / 8;
+          if ((side == 0 && left) || (side == 1 && right)) {
+            const int j = side == 0 ? 0 : TPW - 1, gx = side == 0 ? W - 1 : 0;
+            cp16(xb + j * 128 + ((c ^ (j & 7)) << 4), x + ((size_t)gy * W + gx) * 64 + c * 8);
           }
         }
         asm volatile("cp.async.commit_group;\n" ::);
@@ -480,20 +479,17 @@ __global__ void __launch_bounds__(TTHR, 1)
       constexpr uint32_t ID = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((64u >> 3) << 17) |
                               ((64u >> 4) << 24);
       for (int k = 0; k < nmine && ok; ++k) {
-        const int b = k & 1;
-        ok = mbar_wait(full + b, (k >> 1) & 1);
+        const int b = k % NS;
+        ok = mbar_wait(full + b, (k / NS) & 1);
         if (!ok) break;
         tc_fence_after();
         const uint32_t dyb = su32(sm + b * L::STAGE), xb = dyb + L::DY;
-        for (int j = 0; j < ntap; ++j) {
-          const int t = t0 + j, dy = t / 3, dx = t % 3;
 #pragma unroll
-          for (int s2 = 0; s2 < TPX / 16; ++s2) {
-            const uint64_t ad = sdesc_mn_sw128(dyb + 2048u * s2);
-            const uint64_t bd = sdesc_mn_sw128(xb + (uint32_t)((dy * TPW + dx) * 128) + 2048u * s2);
-            umma(tmem + 64u * j, ad, bd, ID, (k | s2) != 0);
-          }
-        }
+        for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+          for (int s2 = 0; s2 < TPX / 16; ++s2)
+            umma(tmem + 64u * dx, sdesc_mn_sw128(dyb + 2048u * s2), sdesc_mn_sw128(xb + 128u * dx + 2048u * s2), ID,
+                 (k | s2) != 0);
         umma_commit(empty + b);
       }
       if (ok) umma_commit(done);
@@ -503,15 +499,16 @@ __global__ void __launch_bounds__(TTHR, 1)
     ok = nmine == 0 || mbar_wait(done, 0);
     if (ok && nmine > 0) {
       tc_fence_after();
-      for (int j = 0; j < ntap; ++j) {
+      for (int dx = 0; dx < 3; ++dx) {
         uint32_t raw[64];
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-          tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + 64u * j + 16u * q, raw + 16 * q);
+          tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + 64u * dx + 16u * q, raw + 16 * q);
         tmem_wait_ld();
         if (lane < 16) {  // lanes 0-15 of warp w hold output channels 16 w .. 16 w + 15
           const int co = 16 * warp + lane;
-          float4* dst = reinterpret_cast<float4*>(partial + (((size_t)blockIdx.x * 9 + t0 + j) * 64 + co) * 64);
+          float4* dst =
+              reinterpret_cast<float4*>(partial + (((size_t)blockIdx.x * 9 + 3 * dyr + dx) * 64 + co) * 64);
 #pragma unroll
           for (int q = 0; q < 16; ++q)
             dst[q] = make_float4(__uint_as_float(raw[4 * q]), __uint_as_float(raw[4 * q + 1]),
@@ -525,7 +522,7 @@ __global__ void __launch_bounds__(TTHR, 1)
   __syncthreads();
   if (warp == MMA_WARP) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(cols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(COLS) : "memory");
   }
 }
 
@@ -623,7 +620,7 @@ cudaError_t wg64_launch(int H, int W, const void* x, const void* dy, float* part
   alignas(64) CUtensorMap dymap, xmap;
   const cuuint64_t dims[3] = {64, (cuuint64_t)W, (cuuint64_t)H};
   const cuuint64_t strides[2] = {128, (cuuint64_t)W * 128};
-  const cuuint32_t box_dy[3] = {64, (cuuint32_t)TPX, 1}, box_x[3] = {64, (cuuint32_t)TPW, 3};
+  const cuuint32_t box_dy[3] = {64, (cuuint32_t)TPX, 1}, box_x[3] = {64, (cuuint32_t)TPW, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   if (enc(&dymap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(dy), dims, strides, box_dy, estr,
           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -633,7 +630,7 @@ cudaError_t wg64_launch(int H, int W, const void* x, const void* dy, float* part
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
   const int nseg = H * (W / TPX), groups = (nseg + segs_per_group - 1) / segs_per_group;
-  conv_wgrad_tc_kernel<<<dim3(groups, 2), TTHR, WgLay::BYTES, st>>>(H, W, segs_per_group, (const bf16*)x, partial,
+  conv_wgrad_tc_kernel<<<dim3(groups, 3), TTHR, WgLay::BYTES, st>>>(H, W, segs_per_group, (const bf16*)x, partial,
                                                                   err[dev], dymap, xmap);
   return cudaGetLastError();
 }
