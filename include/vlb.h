@@ -80,7 +80,13 @@ size_t vlb_workspace_bytes(const vlb_params* p);
  * min over (a) advection  dt <= 1 / (v_max (1/h_theta + 1/h_phi,min)), v_max = sqrt(3 + sqrt 6);
  *          (b) BGK        dt <= 2.5 tau  (SSP-RK3 reaches -2.51 on the real axis);
  *          (c) Cahn-Hilliard  dt <= 2.5 / (M lambda (kappa lambda + 2 A)),
- *              lambda = 4/h_theta^2 + 4/h_phi,min^2, h_phi,min = (R - r) dvarphi on the torus.
+ *              lambda = 4/h_theta^2 + 4/h_phi,min^2, h_phi,min = (R - r) dvarphi on the torus;
+ *          (d) relaxation and advection together: the largest dt at which one SSP-RK3 step of
+ *              dg/dt = -(v_i/h_theta) D(k_theta) g - (v_j/h_phi,min) D(k_phi) g - g/tau has
+ *              |1 + z + z^2/2 + z^3/6| <= 1 on a 64 x 64 grid of Fourier modes and all velocity
+ *              pairs (D: the symbol of the UW3 difference, or of the fifth-order linear scheme
+ *              for WENO5).  It binds when dt/tau approaches 2 and advection is not negligible.
+ * The paper leaves the time integrator to its supplement; these are properties of SSP-RK3.
  * Returns VLB_ERR_ARG for invalid parameters (dt itself is not checked). */
 vlb_status vlb_max_stable_dt(const vlb_params* p, double* dt_out);
 

@@ -368,6 +368,68 @@ size_t vlb_workspace_bytes(const vlb_params* p) {
   return layout(p).total;
 }
 
+namespace {
+
+// Largest dt for which one SSP-RK3 step of the linearised per-population model
+//   dg/dt = -(v_i / h_theta) D(k_theta) g - (v_j / h_phi) D(k_phi) g - g / tau
+// has amplification |R(z)| = |1 + z + z^2/2 + z^3/6| <= 1 on every Fourier mode of a 64 x 64 grid
+// over [-pi, pi)^2 and every velocity pair.  D is the symbol of the upwind difference per unit
+// spacing (UW3, or the fifth-order linear scheme WENO5 reduces to on smooth data).  A velocity of
+// the opposite sign has the symbol of mode -k, so |v| in {v_2, v_3} covers all 16 pairs.  With
+// dt / tau near 2 the relaxation shifts the advective eigenvalues to where the stability region of
+// RK3 is narrow, which the separate limits on advection and relaxation miss.
+double combined_rk3_dt(double ht, double hp, double tau, int advection, bool phi_dir, double vmax) {
+  constexpr int NK = 64;
+  double re[NK], im[NK];
+  for (int n = 0; n < NK; ++n) {
+    const double k = -M_PI + 2.0 * M_PI * n / NK;
+    if (advection == VLB_WENO5) {  // (-2 e^{-3ik} + 15 e^{-2ik} - 60 e^{-ik} + 20 + 30 e^{ik} - 3 e^{2ik}) / 60
+      re[n] = (-2.0 * cos(3 * k) + 15.0 * cos(2 * k) - 60.0 * cos(k) + 20.0 + 30.0 * cos(k) - 3.0 * cos(2 * k)) / 60.0;
+      im[n] = (2.0 * sin(3 * k) - 15.0 * sin(2 * k) + 60.0 * sin(k) + 30.0 * sin(k) - 3.0 * sin(2 * k)) / 60.0;
+    } else {  // (2 e^{ik} + 3 - 6 e^{-ik} + e^{-2ik}) / 6
+      re[n] = (2.0 * cos(k) + 3.0 - 6.0 * cos(k) + cos(2 * k)) / 6.0;
+      im[n] = (2.0 * sin(k) + 6.0 * sin(k) - sin(2 * k)) / 6.0;
+    }
+  }
+  const double s6 = sqrt(6.0), va[2] = {sqrt(3.0 - s6), sqrt(3.0 + s6)};
+  const double rel = isfinite(tau) ? 1.0 / tau : 0.0;
+  auto stable = [&](double dt) {
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < (phi_dir ? 2 : 1); ++b)
+        for (int m = 0; m < NK; ++m)
+          for (int n = 0; n < (phi_dir ? NK : 1); ++n) {
+            double zr = -va[a] / ht * re[m] - rel, zi = -va[a] / ht * im[m];
+            if (phi_dir) {
+              zr -= va[b] / hp * re[n];
+              zi -= va[b] / hp * im[n];
+            }
+            zr *= dt;
+            zi *= dt;
+            // R(z) = 1 + z (1 + z (1/2 + z / 6)) in complex arithmetic
+            double tr = 0.5 + zr / 6.0, ti = zi / 6.0;
+            double ur = 1.0 + (zr * tr - zi * ti), ui = zr * ti + zi * tr;
+            const double rr = 1.0 + (zr * ur - zi * ui), ri = zr * ui + zi * ur;
+            if (rr * rr + ri * ri > 1.0 + 1e-12) return false;
+          }
+    return true;
+  };
+  // bracket: the advective CFL limit of RK3 is below 3 / (v_max (1/h_theta + 1/h_phi)) and the
+  // real-axis limit below 2.52 tau
+  double hi = 3.0 / (vmax * (1.0 / ht + (phi_dir ? 1.0 / hp : 0.0)));
+  if (isfinite(tau)) hi = fmin(hi, 2.52 * tau);
+  double lo = 0.0;
+  for (int it = 0; it < 60; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (stable(mid))
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+}  // namespace
+
 vlb_status vlb_max_stable_dt(const vlb_params* p, double* dt_out) {
   char why[256];
   if (!dt_out) return fail(nullptr, VLB_ERR_ARG, "dt_out is NULL");
@@ -380,6 +442,7 @@ vlb_status vlb_max_stable_dt(const vlb_params* p, double* dt_out) {
   const double vmax = sqrt(3.0 + sqrt(6.0));
   double dt = 1.0 / (vmax * (1.0 / ht + (p->n_phi > 1 ? 1.0 / hp : 0.0)));
   if (isfinite(p->tau)) dt = fmin(dt, 2.5 * p->tau);
+  dt = fmin(dt, combined_rk3_dt(ht, hp, p->tau, p->advection, p->n_phi > 1, vmax));
   const double lam = 4.0 / (ht * ht) + (p->n_phi > 1 ? 4.0 / (hp * hp) : 0.0);
   const double ch = p->M * lam * (p->kappa * lam + 2.0 * p->A);
   if (ch > 0.0) dt = fmin(dt, 2.5 / ch);

@@ -118,7 +118,8 @@ def workload(name: str) -> dict:
         return dict(params=p, rho=rho, ut=np.zeros_like(phi), up=np.zeros_like(phi), phi=phi, steps=500)
     if name == "stripe_torus_128x384":
         # stripe oscillation, R=3, r=1; xi = 0.05, nu = M = 2.5e-3; +1 band of width 0.6 rad
-        p = dict(geometry=0, R=3.0, r=1.0, n_theta=128, n_phi=384, dt=5e-3, tau=2.5e-3, M=2.5e-3,
+        # dt = 0.89 of the SSP-RK3 limit of relaxation and varphi advection together (4.5e-3)
+        p = dict(geometry=0, R=3.0, r=1.0, n_theta=128, n_phi=384, dt=4e-3, tau=2.5e-3, M=2.5e-3,
                  A=0.5, kappa=0.5 * 0.05 ** 2, advection=0, ch_mode=0)
         return _stripe(p, width=0.6, steps=20000)
     if name in ("coarsen_torus_1024x2048", "coarsen_flat_1024x2048"):

@@ -70,6 +70,41 @@ def test_create_rejects_missing_or_small_workspace(L):
     assert L.vlb_destroy(None) == vlb.VLB_OK
 
 
+def _rk3_amplification(dt, ht, hp, tau, n=128):
+    """max |1 + z + z^2/2 + z^3/6| over n x n Fourier modes and |v| pairs for the UW3 difference
+    (stencil weights 1, -6, 3, 2 over offsets -2 .. 1, divided by 6) with relaxation 1/tau."""
+    import numpy as np
+    k = -np.pi + 2 * np.pi * np.arange(n) / n
+    offsets, weights = np.array([-2, -1, 0, 1]), np.array([1.0, -6.0, 3.0, 2.0]) / 6.0
+    D = (weights[None, :] * np.exp(1j * k[:, None] * offsets[None, :])).sum(axis=1)
+    worst = 0.0
+    for vi in (math.sqrt(3 - math.sqrt(6)), math.sqrt(3 + math.sqrt(6))):
+        for vj in (math.sqrt(3 - math.sqrt(6)), math.sqrt(3 + math.sqrt(6))):
+            z = dt * (-vi / ht * D[:, None] - vj / hp * D[None, :] - 1.0 / tau)
+            worst = max(worst, float(np.abs(1 + z + z * z / 2 + z ** 3 / 6).max()))
+    return worst
+
+
+def test_max_stable_dt_relaxation_and_advection_together(L):
+    # stripe regime: dt / tau near 2 with advection in both directions; the separate limits give
+    # 2.5 tau = 6.25e-3, at which RK3 amplifies some modes; the combined limit is the largest
+    # stable dt of the linear model, checked here on a finer mode grid
+    p = _p(R=3.0, r=1.0, n_theta=128, n_phi=384, tau=2.5e-3, M=2.5e-3, A=0.5, kappa=1.25e-3)
+    dt = vlb.vlb_max_stable_dt(p)
+    ht, hp = 2 * math.pi / 128, 2.0 * 2 * math.pi / 384
+    assert dt < 2.5 * 2.5e-3
+    assert _rk3_amplification(0.995 * dt, ht, hp, 2.5e-3) <= 1.0 + 1e-9
+    assert _rk3_amplification(1.02 * dt, ht, hp, 2.5e-3) > 1.0
+    assert _rk3_amplification(2.5 * 2.5e-3, ht, hp, 2.5e-3) > 1.3
+
+
+def test_named_workloads_step_below_the_stable_limit(L):
+    from paper_1904_10070_gb300 import inputs
+    for name in ("drop_torus_32x64", "stripe_torus_128x384", "coarsen_torus_1024x2048", "coarsen_flat_1024x2048"):
+        w = inputs.workload(name)["params"]
+        assert w["dt"] <= vlb.vlb_max_stable_dt(vlb.make_params(**w)), name
+
+
 def test_max_stable_dt_limits(L):
     # BGK limit 2.5 tau dominates with a tiny tau
     p = _p(tau=1e-4, M=0.0)
