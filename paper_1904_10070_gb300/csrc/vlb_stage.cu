@@ -276,17 +276,58 @@ __device__ __forceinline__ void issue_u0(const StageArgs<T>& a, T* su0, int q0, 
 // Step 2: moments (Sec. 2.3) and mu (Eq. mu) on the tile plus a halo of 1 (cross-shaped).
 // Moment-box position (mr, mc) is tile node (mr - 1, mc - 2).
 // ---------------------------------------------------------------------------------------------
+// Moments and mu at moment-box position (mr, mc).
 template <typename L, typename T>
-__device__ __forceinline__ void phase2(const StageArgs<T>& a, const VConst<T>& vc, const T* box, const T* co,
-                                       T* sm, int tid) {
-  constexpr int H = L::H, BQ = L::BQ, BS = L::BS, HS = L::HS, MQ = L::MQ, MS = L::MS, TQ = L::TQ;
+__device__ __forceinline__ void moment_point(const StageArgs<T>& a, const VConst<T>& vc, const T* box, const T* co,
+                                             T* sm, int mr, int mc) {
+  constexpr int H = L::H, BQ = L::BQ, BS = L::BS, HS = L::HS, MS = L::MS;
   const T* sf = box;
   const T* sphi = box + NPOP * BQ * BS;
   const T* sphl = box + (NPOP + 1) * BQ * BS;
-  T* sn = sm + L::N_OFF;
-  T* sut = sm + L::UT_OFF;
-  T* sup = sm + L::UP_OFF;
-  T* smu = sm + L::MU_OFF;
+  const int bi = (mr + H - 1) * BS + (mc - 2 + HS);  // box index of this position
+  const T* fp = sf + bi;
+  T row[4] = {T(0), T(0), T(0), T(0)}, col[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const T x = fp[(4 * i + j) * BQ * BS];
+      row[i] += x;
+      col[j] += x;
+    }
+  // n = n0 + sum g (the reference part carries no momentum); v_1 = -v_4, v_2 = -v_3
+  const T dn = (row[0] + row[1]) + (row[2] + row[3]);
+  const T mt = vc.v[3] * (row[3] - row[0]) + vc.v[2] * (row[2] - row[1]);
+  const T mp = vc.v[3] * (col[3] - col[0]) + vc.v[2] * (col[2] - col[1]);
+  const int mi = mr * MS + mc;
+  const T inv_n = recip(a.n0 + dn);
+  sm[L::N_OFF + mi] = dn;
+  sm[L::UT_OFF + mi] = mt * inv_n;
+  sm[L::UP_OFF + mi] = mp * inv_n;
+  const T* pp = sphi + bi;
+  const int cr = mr + H - 1;
+  const T ph = pp[0];
+  // neighbour differences of phi = hi + lo: the hi differences are exact for nearby values
+  T dN = pp[BS] - ph, dS = ph - pp[-BS], dE = pp[1] - ph, dW = ph - pp[-1], lo = T(0);
+  if (L::DF) {
+    const T* pl = sphl + bi;
+    lo = pl[0];
+    dN += pl[BS] - lo;
+    dS += lo - pl[-BS];
+    dE += pl[1] - lo;
+    dW += lo - pl[-1];
+  }
+  const T lap = co[C_LT * BQ + cr] * (co[C_JP * BQ + cr] * dN - co[C_JM * BQ + cr] * dS) +
+                co[C_LP * BQ + cr] * (dE - dW);
+  // phi (1 - phi^2) at hi + lo, to first order in lo
+  const T cubic = ph * (T(1) - ph * ph) + (T(1) - T(3) * ph * ph) * lo;
+  sm[L::MU_OFF + mi] = -a.A * cubic - a.kappa * lap;
+}
+
+template <typename L, typename T>
+__device__ __forceinline__ void phase2(const StageArgs<T>& a, const VConst<T>& vc, const T* box, const T* co,
+                                       T* sm, int tid) {
+  constexpr int MQ = L::MQ, TQ = L::TQ;
   constexpr int MS2 = TS + 2;  // tile columns -1 .. TS in the rows of the tile
   constexpr int PA = TQ * MS2;
   constexpr int PM = PA + 2 * TS;
@@ -300,44 +341,7 @@ __device__ __forceinline__ void phase2(const StageArgs<T>& a, const VConst<T>& v
       mr = (j < TS) ? 0 : MQ - 1;
       mc = 2 + (j < TS ? j : j - TS);
     }
-    const int bi = (mr + H - 1) * BS + (mc - 2 + HS);  // box index of this position
-    const T* fp = sf + bi;
-    T row[4] = {T(0), T(0), T(0), T(0)}, col[4] = {T(0), T(0), T(0), T(0)};
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const T x = fp[(4 * i + j) * BQ * BS];
-        row[i] += x;
-        col[j] += x;
-      }
-    // n = n0 + sum g (the reference part carries no momentum); v_1 = -v_4, v_2 = -v_3
-    const T dn = (row[0] + row[1]) + (row[2] + row[3]);
-    const T mt = vc.v[3] * (row[3] - row[0]) + vc.v[2] * (row[2] - row[1]);
-    const T mp = vc.v[3] * (col[3] - col[0]) + vc.v[2] * (col[2] - col[1]);
-    const int mi = mr * MS + mc;
-    const T inv_n = recip(a.n0 + dn);
-    sn[mi] = dn;
-    sut[mi] = mt * inv_n;
-    sup[mi] = mp * inv_n;
-    const T* pp = sphi + bi;
-    const int cr = mr + H - 1;
-    const T ph = pp[0];
-    // neighbour differences of phi = hi + lo: the hi differences are exact for nearby values
-    T dN = pp[BS] - ph, dS = ph - pp[-BS], dE = pp[1] - ph, dW = ph - pp[-1], lo = T(0);
-    if (L::DF) {
-      const T* pl = sphl + bi;
-      lo = pl[0];
-      dN += pl[BS] - lo;
-      dS += lo - pl[-BS];
-      dE += pl[1] - lo;
-      dW += lo - pl[-1];
-    }
-    const T lap = co[C_LT * BQ + cr] * (co[C_JP * BQ + cr] * dN - co[C_JM * BQ + cr] * dS) +
-                  co[C_LP * BQ + cr] * (dE - dW);
-    // phi (1 - phi^2) at hi + lo, to first order in lo
-    const T cubic = ph * (T(1) - ph * ph) + (T(1) - T(3) * ph * ph) * lo;
-    smu[mi] = -a.A * cubic - a.kappa * lap;
+    moment_point<L>(a, vc, box, co, sm, mr, mc);
   }
 }
 
@@ -511,6 +515,92 @@ __device__ __forceinline__ void df_add(float base, float base_lo, float inc, flo
   lo = lo2 - (hi - s1);
 }
 
+// Step 2 on packed node pairs (FP32): moment-box positions (mr, mc) and (mr, mc + 1), mc even, in
+// FP32x2 arithmetic; lanes: bit 0 stores the first, bit 1 the second.
+template <typename L>
+__device__ __forceinline__ void pair_point(const StageArgs<float>& a, const VConst<float>& vc, const float* box,
+                                           const float* co, float* sm, int mr, int mc, int lanes) {
+  constexpr int H = L::H, BQ = L::BQ, BS = L::BS, HS = L::HS, MS = L::MS;
+  static_assert(HS % 2 == 0 && BS % 2 == 0 && MS % 2 == 0 && L::N_OFF % 2 == 0 && L::UT_OFF % 2 == 0 &&
+                    L::UP_OFF % 2 == 0 && L::MU_OFF % 2 == 0,
+                "pair alignment");
+  const int bi = (mr + H - 1) * BS + (mc - 2 + HS);  // even
+  const float* fp = box + bi;
+  float2 row[4] = {f2(0.0f), f2(0.0f), f2(0.0f), f2(0.0f)}, col[4] = {f2(0.0f), f2(0.0f), f2(0.0f), f2(0.0f)};
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float2 x = ld2(fp + (4 * i + j) * BQ * BS);
+      row[i] = add2(row[i], x);
+      col[j] = add2(col[j], x);
+    }
+  // n = n0 + sum g (the reference part carries no momentum); v_1 = -v_4, v_2 = -v_3
+  const float2 dn = add2(add2(row[0], row[1]), add2(row[2], row[3]));
+  const float2 mt = fma2(f2(vc.v[3]), sub2(row[3], row[0]), mul2(f2(vc.v[2]), sub2(row[2], row[1])));
+  const float2 mp = fma2(f2(vc.v[3]), sub2(col[3], col[0]), mul2(f2(vc.v[2]), sub2(col[2], col[1])));
+  const float2 nn = add2(f2(a.n0), dn);
+  const float2 inv_n = make_float2(__frcp_rn(nn.x), __frcp_rn(nn.y));
+  const float2 ut = mul2(mt, inv_n), up = mul2(mp, inv_n);
+  const int cr = mr + H - 1;
+  const float* pp = box + NPOP * BQ * BS + bi;
+  const float* pl = box + (NPOP + 1) * BQ * BS + bi;
+  const float2 ph = ld2(pp), lo = ld2(pl);
+  const float2 phW = ld2(pp - 2), phE = ld2(pp + 2), loW = ld2(pl - 2), loE = ld2(pl + 2);
+  // neighbour differences of phi = hi + lo: the hi differences are exact for nearby values
+  float2 dN = sub2(ld2(pp + BS), ph), dS = sub2(ph, ld2(pp - BS));
+  float2 dE = sub2(make_float2(ph.y, phE.x), ph), dW = sub2(ph, make_float2(phW.y, ph.x));
+  dN = add2(dN, sub2(ld2(pl + BS), lo));
+  dS = add2(dS, sub2(lo, ld2(pl - BS)));
+  dE = add2(dE, sub2(make_float2(lo.y, loE.x), lo));
+  dW = add2(dW, sub2(lo, make_float2(loW.y, lo.x)));
+  const float2 lap = fma2(f2(co[C_LP * BQ + cr]), sub2(dE, dW),
+                          mul2(f2(co[C_LT * BQ + cr]),
+                               sub2(mul2(f2(co[C_JP * BQ + cr]), dN), mul2(f2(co[C_JM * BQ + cr]), dS))));
+  // phi (1 - phi^2) at hi + lo, to first order in lo
+  const float2 ph2 = mul2(ph, ph);
+  const float2 cubic = fma2(sub2(f2(1.0f), mul2(f2(3.0f), ph2)), lo, mul2(ph, sub2(f2(1.0f), ph2)));
+  const float2 mu = sub2(mul2(f2(-a.A), cubic), mul2(f2(a.kappa), lap));
+  const int mi = mr * MS + mc;  // even
+  if (lanes == 3) {
+    st2(sm + L::N_OFF + mi, dn);
+    st2(sm + L::UT_OFF + mi, ut);
+    st2(sm + L::UP_OFF + mi, up);
+    st2(sm + L::MU_OFF + mi, mu);
+  } else {
+    const int o = lanes == 1 ? 0 : 1;
+    sm[L::N_OFF + mi + o] = o ? dn.y : dn.x;
+    sm[L::UT_OFF + mi + o] = o ? ut.y : ut.x;
+    sm[L::UP_OFF + mi + o] = o ? up.y : up.x;
+    sm[L::MU_OFF + mi + o] = o ? mu.y : mu.x;
+  }
+}
+
+// Step 2 on packed node pairs: tile columns 0 .. TS-1 of every moment row two at a time; the halo
+// columns -1 and TS of the tile rows inside the aligned pairs (-2, -1) and (TS, TS + 1), keeping
+// one lane, so that every column takes the same sequence of FP32 operations (an axisymmetric
+// state stays bitwise axisymmetric).  The pairs' other lanes read box columns -4 .. TS + 3, inside
+// the HS = 4 halo.
+template <typename L>
+__device__ __forceinline__ void phase2_pair(const StageArgs<float>& a, const VConst<float>& vc, const float* box,
+                                            const float* co, float* sm, int tid) {
+  constexpr int MQ = L::MQ, TQ = L::TQ, NP = MQ * (TS / 2), NSGL = 2 * TQ;
+  static_assert(L::HS >= 4, "the halo pairs read two columns beyond the halo column");
+  for (int idx = tid; idx < NP + NSGL; idx += L::NTH) {
+    int mr, mc, lanes = 3;
+    if (idx < NP) {
+      mr = idx / (TS / 2);
+      mc = 2 + 2 * (idx - mr * (TS / 2));
+    } else {  // column TS: first lane of (TS, TS + 1); column -1: second lane of (-2, -1)
+      const int j = idx - NP;
+      mr = 1 + (j >> 1);
+      mc = (j & 1) ? TS + 2 : 0;
+      lanes = (j & 1) ? 1 : 2;
+    }
+    pair_point<L>(a, vc, box, co, sm, mr, mc, lanes);
+  }
+}
+
 template <typename L, int CH, bool F0>
 __device__ __forceinline__ void phase3_pair(const StageArgs<float>& a, const VConst<float>& vc, const float* box,
                                             const float* co, const float* sm, int lr, int lc, int q, int s) {
@@ -667,12 +757,19 @@ __device__ __forceinline__ void tile_body(const StageArgs<T>& a, const VConst<T>
   cp_async_commit();
   cp_async_wait<1>();  // the box; U^n may still be in flight
   __syncthreads();
-  phase2<L>(a, vc, box, co, sm, tid);
+  bool pair = PM == 1;
+  if constexpr (PM == 2) pair = chunked<L>(a.nt, a.ns);
+  if constexpr (PM != 0 && sizeof(T) == 4 && ADV == VLB_UW3) {
+    if (pair)
+      phase2_pair<L>(a, vc, box, co, sm, tid);
+    else
+      phase2<L>(a, vc, box, co, sm, tid);
+  } else {
+    phase2<L>(a, vc, box, co, sm, tid);
+  }
   cp_async_wait<0>();
   __syncthreads();
   pdl_trigger();
-  bool pair = PM == 1;
-  if constexpr (PM == 2) pair = chunked<L>(a.nt, a.ns);
   if constexpr (PM != 0 && sizeof(T) == 4 && ADV == VLB_UW3) {
     if (pair) {
       static_assert(L::NTH == L::TQ * (TS / 2), "one node pair per thread");
@@ -741,7 +838,7 @@ __device__ __forceinline__ void tile_body_tma(const StageArgs<float>& a, const V
     }
     return;
   }
-  phase2<L>(a, vc, box, co, sm, tid);
+  phase2_pair<L>(a, vc, box, co, sm, tid);
   ok = F0 ? mbar_wait(bar + 1, 0) : true;
   if (__syncthreads_or(!ok)) {
     if (tid == 0) {
