@@ -259,6 +259,23 @@ vlb_status run_steps(vlb_handle* h, int64_t nsteps) {
   T* U0 = (T*)h->U[0];
   T* U1 = (T*)h->U[1];
   T* U2 = (T*)h->U[2];
+  if (p.n_phi == 1 && p.n_theta <= vlb::kAxiMaxRows) {
+    // axisymmetric grid: up to 256 steps per single-CTA launch, cut at the diagnostic steps
+    int64_t n = 0;
+    while (n < nsteps) {
+      int64_t chunk = std::min<int64_t>(nsteps - n, 256);
+      if (p.diag_every > 0) chunk = std::min<int64_t>(chunk, p.diag_every - h->steps_done % p.diag_every);
+      VLB_CUDA(h, vlb::launch_axi<T>(a, p.advection, p.ch_mode, U0, U1, U2, (int)chunk, h->stream));
+      h->steps_done += chunk;
+      n += chunk;
+      if (p.diag_every > 0 && (h->steps_done % p.diag_every == 0 || n == nsteps)) {
+        VLB_CUDA(h, vlb::launch_totals<T>(U0, h->stride, h->coefD, p.n_theta, p.n_phi, p.R, p.r, p.A, p.kappa,
+                                          h->n0, p.geometry, h->partials, vlb::totals_blocks(), h->diag, h->stream));
+        VLB_CUDA(h, vlb_internal_flag(h->diag, h->flag, h->stream));
+      }
+    }
+    return VLB_OK;
+  }
   for (int64_t n = 0; n < nsteps; ++n) {
     // SSP-RK3 (Shu & Osher 1988): U1 = U + dt L(U); U2 = 3/4 U + 1/4 (U1 + dt L(U1));
     // U <- 1/3 U + 2/3 (U2 + dt L(U2))

@@ -111,6 +111,13 @@ cudaError_t launch_ensemble_stage(const EnsembleMember* members, const int2* ite
 template <typename T>
 cudaError_t launch_stage(const StageArgs<T>& a, int advection, int ch_mode, cudaStream_t s,
                          const StageMaps* maps = nullptr);
+// Axisymmetric grids (n_phi = 1, n_theta <= kAxiMaxRows): `steps` whole SSP-RK3 steps of the
+// column in one single-CTA launch, on the buffers U0 (U^n, updated in place), U1, U2.  a.fin, a.f0,
+// a.fout and a.b are set per stage inside the kernel.
+constexpr int kAxiMaxRows = 4096;
+template <typename T>
+cudaError_t launch_axi(const StageArgs<T>& a, int advection, int ch_mode, T* U0, T* U1, T* U2, int steps,
+                       cudaStream_t s);
 
 // Auxiliary kernels (vlb_aux.cu).  Staging arrays are FP64 [n_theta][n_phi].
 template <typename T>

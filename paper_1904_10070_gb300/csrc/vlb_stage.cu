@@ -932,6 +932,196 @@ __global__ void __launch_bounds__(TQR * (TS / 2)) ensemble_stage_kernel(const En
   tile_body<L, float, VLB_UW3, CH, F0, 2>(a, vc, sm, threadIdx.x, q0, s0);
 }
 
+// ---------------------------------------------------------------------------------------------
+// Axisymmetric special case, n_phi = 1.  With one varphi column every varphi difference is zero:
+// the varphi flux of f and of u^phi phi, the varphi part of the Laplace-Beltrami operator and the
+// force component F^phi all vanish, while u^phi itself (a swirl) and the inertial terms through
+// Gamma and K~ remain.  One CTA holds the column: per Runge-Kutta stage it computes the moments
+// and mu of every node into shared memory, synchronises, then computes the right-hand sides and
+// the stage update of every node, and synchronises again, for `steps` steps per launch.  The
+// arithmetic is that of the tile kernels (steps 2 and 3) with the varphi terms removed; nodes are
+// strided over the threads.
+// ---------------------------------------------------------------------------------------------
+// threads of the CTA: FP64 keeps 256 so that a thread's node fits in registers
+template <typename T>
+constexpr int axi_threads() { return sizeof(T) == 8 ? 256 : 512; }
+
+template <typename T>
+__device__ __forceinline__ T axi_co(const StageArgs<T>& a, int c, int q) {
+  return a.coef[(int64_t)c * a.nt + wrap(q, a.nt)];
+}
+template <typename T>
+__device__ __forceinline__ T axi_f(const StageArgs<T>& a, const T* f, int k, int q) {
+  return f[k * a.stride + wrap(q, a.nt)];
+}
+
+// Moments and mu of node q of fin into mom = [dn | u^theta | u^phi | mu], each nt long.
+template <typename T>
+__device__ __forceinline__ void axi_moments(const StageArgs<T>& a, const VConst<T>& vc, const T* fin, T* mom, int q) {
+  constexpr bool DF = sizeof(T) == 4;  // phi as a float pair in FP32 storage
+  const int nt = a.nt;
+  T row[4] = {T(0), T(0), T(0), T(0)}, col[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const T x = fin[(4 * i + j) * a.stride + q];
+      row[i] += x;
+      col[j] += x;
+    }
+  const T dn = (row[0] + row[1]) + (row[2] + row[3]);
+  const T mt = vc.v[3] * (row[3] - row[0]) + vc.v[2] * (row[2] - row[1]);
+  const T mp = vc.v[3] * (col[3] - col[0]) + vc.v[2] * (col[2] - col[1]);
+  const T inv_n = recip(a.n0 + dn);
+  mom[q] = dn;
+  mom[nt + q] = mt * inv_n;
+  mom[2 * nt + q] = mp * inv_n;
+  const T ph = fin[NPOP * a.stride + q];
+  T dN = axi_f(a, fin, NPOP, q + 1) - ph, dS = ph - axi_f(a, fin, NPOP, q - 1), lo = T(0);
+  if (DF) {
+    lo = fin[(NPOP + 1) * a.stride + q];
+    dN += axi_f(a, fin, NPOP + 1, q + 1) - lo;
+    dS += lo - axi_f(a, fin, NPOP + 1, q - 1);
+  }
+  const T lap = axi_co(a, C_LT, q) * (axi_co(a, C_JP, q) * dN - axi_co(a, C_JM, q) * dS);
+  const T cubic = ph * (T(1) - ph * ph) + (T(1) - T(3) * ph * ph) * lo;
+  mom[3 * nt + q] = -a.A * cubic - a.kappa * lap;
+}
+
+// Right-hand side and Runge-Kutta combination of node q: fout = f0 + b (fin - f0 + dt L(fin)), or
+// fin + dt L(fin) without f0 (first stage).
+template <typename T, int ADV, int CH, bool F0>
+__device__ __forceinline__ void axi_node(const StageArgs<T>& a, const VConst<T>& vc, const T* fin, const T* f0,
+                                         T* fout, const T* mom, int q) {
+  constexpr bool DF = sizeof(T) == 4;
+  const int nt = a.nt;
+  const int64_t stride = a.stride;
+  const T sixth = T(1) / T(6);
+  const int qn = q + 1 < nt ? q + 1 : q + 1 - nt, qs = q > 0 ? q - 1 : nt - 1;
+  const T dn = mom[q], ut = mom[nt + q], up = mom[2 * nt + q];
+  const T mu_c = mom[3 * nt + q], mu_n = mom[3 * nt + qn], mu_s = mom[3 * nt + qs];
+  const T ph = fin[NPOP * stride + q];
+  const T n = a.n0 + dn;
+  const T ct = axi_co(a, C_CT, q), gam = axi_co(a, C_GAM, q);
+
+  // Cahn-Hilliard (Eq. CH): M Delta mu - div(u phi), theta parts only
+  T Lphi = a.M * (axi_co(a, C_LT, q) * (axi_co(a, C_JP, q) * (mu_n - mu_c) - axi_co(a, C_JM, q) * (mu_c - mu_s)));
+  T Ft = T(0);
+  if (CH == VLB_HYDRO) {
+    const T Xn = axi_co(a, C_J, q + 1) * mom[nt + qn] * fin[NPOP * stride + qn];
+    const T Xs = axi_co(a, C_J, q - 1) * mom[nt + qs] * fin[NPOP * stride + qs];
+    Lphi -= T(0.5) * (ct * (Xn - Xs));
+    Ft = -(ph * recip(n)) * (mu_n - mu_s) * a.gt;  // n F^theta = -phi d_theta mu (Eq. pbin)
+  }
+  {
+    const T lo = DF ? fin[(NPOP + 1) * stride + q] : T(0);
+    T base = ph, base_lo = lo, inc = Lphi * a.dt;
+    if (F0) {
+      base = f0[NPOP * stride + q];
+      base_lo = DF ? f0[(NPOP + 1) * stride + q] : T(0);
+      inc = a.b * (((ph - base) + (lo - base_lo)) + inc);
+    }
+    if (DF) {  // (hi, lo) <- (base, base_lo) + inc, error-free sum, renormalised
+      const T s1 = base + inc;
+      const T bb = s1 - base;
+      const T err = (base - (s1 - bb)) + (inc - bb);
+      const T lo2 = base_lo + err;
+      const T hi_out = s1 + lo2;
+      fout[NPOP * stride + q] = hi_out;
+      fout[(NPOP + 1) * stride + q] = lo2 - (hi_out - s1);
+    } else {
+      fout[NPOP * stride + q] = base + inc;
+    }
+  }
+
+  T g[NPOP];
+#pragma unroll
+  for (int k = 0; k < NPOP; ++k) g[k] = fin[k * stride + q];
+  const T ct6 = ct * sixth;
+  const T Jm1 = axi_co(a, C_J, q - 1), J0 = axi_co(a, C_J, q), Jp1 = axi_co(a, C_J, q + 1);
+  const T wp0 = ct6 * axi_co(a, C_J, q - 2), wp1 = T(-6) * ct6 * Jm1, wp2 = T(3) * ct6 * J0, wp3 = T(2) * ct6 * Jp1;
+  const T wn0 = T(-2) * ct6 * Jm1, wn1 = T(-3) * ct6 * J0, wn2 = T(6) * ct6 * Jp1, wn3 = -ct6 * axi_co(a, C_J, q + 2);
+  const T usq = ut * ut + up * up;
+  const T c0 = T(1) - T(0.5) * usq, hu = T(-0.5) * usq;
+  const T ntau = n * a.inv_tau, dntau = dn * a.inv_tau;
+  const T Ep = axi_co(a, C_EP, q), En = axi_co(a, C_EN, q);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const T gvi = gam * vc.v[i];
+    T h[4];  // (-F^phi - Gamma v_i v_m) g_{im} with F^phi = 0
+#pragma unroll
+    for (int mm = 0; mm < 4; ++mm) h[mm] = (-gvi * vc.v[mm]) * g[4 * i + mm];
+    const T ai = vc.v[i] * ut;
+    const T ci = dntau + a.n0 * vc.v[i] * ((i >= 2 ? Ep : En) + Ft);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = 4 * i + j;
+      T rhs;
+      if (ADV == VLB_UW3) {
+        const T Dt = (i >= 2) ? wp0 * axi_f(a, fin, k, q - 2) + wp1 * axi_f(a, fin, k, q - 1) + wp2 * g[k] +
+                                    wp3 * axi_f(a, fin, k, q + 1)
+                              : wn0 * axi_f(a, fin, k, q - 1) + wn1 * g[k] + wn2 * axi_f(a, fin, k, q + 1) +
+                                    wn3 * axi_f(a, fin, k, q + 2);
+        rhs = -(vc.v[i] * Dt);
+      } else {
+        const T fref = a.n0 * vc.ww[i][j];
+        T xt[7];
+#pragma unroll
+        for (int d = 0; d < 7; ++d) xt[d] = axi_co(a, C_J, q + d - 3) * (axi_f(a, fin, k, q + d - 3) + fref);
+        const T Dt = (i >= 2) ? weno_diff<T, true>(xt) : weno_diff<T, false>(xt);
+        rhs = -(vc.v[i] * ct) * Dt;
+      }
+      T dvt = T(0), dvp = T(0);
+#pragma unroll
+      for (int mm = 0; mm < 4; ++mm) {
+        dvt += vc.K[i][mm] * g[4 * mm + j];
+        dvp += vc.K[j][mm] * h[mm];
+      }
+      rhs += (gam * vc.v[j] * vc.v[j] - Ft) * dvt + dvp;
+      const T xi = ai + vc.v[j] * up;
+      const T pm1 = xi * (c0 + xi * (T(0.5) + xi * sixth)) + hu;
+      rhs += vc.ww[i][j] * (ntau * pm1 + ci) - a.inv_tau * g[k];
+      T o;
+      if (F0) {
+        const T g0 = f0[k * stride + q];
+        o = g0 + a.b * ((g[k] - g0) + rhs * a.dt);
+      } else {
+        o = rhs * a.dt + g[k];
+      }
+      fout[k * stride + q] = o;
+    }
+  }
+}
+
+// `steps` SSP-RK3 steps of the whole column in one CTA, in the Shu-Osher form of run_steps:
+// U1 = U + dt L(U); U2 = U + 1/4 (U1 - U + dt L(U1)); U <- U + 2/3 (U2 - U + dt L(U2)).  The third
+// stage writes U in place: each node's U is read by its own thread before it is overwritten, and no
+// thread reads another node's U in that stage.
+template <typename T, int ADV, int CH>
+__global__ void __launch_bounds__(axi_threads<T>()) axi_kernel(StageArgs<T> a, VConst<T> vc, T* U0, T* U1, T* U2,
+                                                          int steps) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* mom = reinterpret_cast<T*>(smem_raw);  // 4 x nt
+  const int nt = a.nt;
+  for (int n = 0; n < steps; ++n) {
+#pragma unroll 1
+    for (int st = 0; st < 3; ++st) {
+      const T* fin = st == 0 ? U0 : (st == 1 ? U1 : U2);
+      T* fout = st == 0 ? U1 : (st == 1 ? U2 : U0);
+      a.b = st == 0 ? T(1) : (st == 1 ? T(0.25) : T(2.0 / 3.0));
+      for (int q = threadIdx.x; q < nt; q += blockDim.x) axi_moments(a, vc, fin, mom, q);
+      __syncthreads();
+      for (int q = threadIdx.x; q < nt; q += blockDim.x) {
+        if (st == 0)
+          axi_node<T, ADV, CH, false>(a, vc, fin, nullptr, fout, mom, q);
+        else
+          axi_node<T, ADV, CH, true>(a, vc, fin, U0, fout, mom, q);
+      }
+      __syncthreads();
+    }
+  }
+}
+
 template <typename T>
 VConst<T> make_vconst() {
   const VelocityConsts d = velocity_consts();
@@ -1033,6 +1223,17 @@ cudaError_t launch_ens_rows(const EnsembleMember* members, const int2* items, in
                     : launch_ens<TQR, VLB_DIFFUSIVE, true>(members, items, nitems, stage, st, maps);
 }
 
+
+template <typename T, int ADV, int CH>
+cudaError_t launch_axi_t(const StageArgs<T>& a, T* U0, T* U1, T* U2, int steps, cudaStream_t st) {
+  static int mask = 0;
+  cudaError_t e = ensure_smem(axi_kernel<T, ADV, CH>, sizeof(T) * 4 * (size_t)kAxiMaxRows, mask);
+  if (e != cudaSuccess) return e;
+  static const VConst<T> vc = make_vconst<T>();
+  axi_kernel<T, ADV, CH><<<1, axi_threads<T>(), sizeof(T) * 4 * (size_t)a.nt, st>>>(a, vc, U0, U1, U2, steps);
+  return cudaGetLastError();
+}
+
 template <typename T, int ADV, int CH>
 cudaError_t launch_one(const StageArgs<T>& a, cudaStream_t st, const StageMaps* maps) {
   if constexpr (sizeof(T) == 4 && ADV == VLB_UW3) {
@@ -1111,7 +1312,22 @@ cudaError_t launch_ensemble_stage(const EnsembleMember* members, const int2* ite
   return launch_ens_rows<16>(members, items, nitems, stage, ch_mode, s, m);
 }
 
+template <typename T>
+cudaError_t launch_axi(const StageArgs<T>& a, int advection, int ch_mode, T* U0, T* U1, T* U2, int steps,
+                       cudaStream_t s) {
+  if (a.ns != 1 || a.nt < 1 || a.nt > kAxiMaxRows || steps < 0) return cudaErrorInvalidValue;
+  if (steps == 0) return cudaSuccess;
+  if (advection == VLB_UW3)
+    return ch_mode == VLB_HYDRO ? launch_axi_t<T, VLB_UW3, VLB_HYDRO>(a, U0, U1, U2, steps, s)
+                                : launch_axi_t<T, VLB_UW3, VLB_DIFFUSIVE>(a, U0, U1, U2, steps, s);
+  return ch_mode == VLB_HYDRO ? launch_axi_t<T, VLB_WENO5, VLB_HYDRO>(a, U0, U1, U2, steps, s)
+                              : launch_axi_t<T, VLB_WENO5, VLB_DIFFUSIVE>(a, U0, U1, U2, steps, s);
+}
+
 template cudaError_t launch_stage<float>(const StageArgs<float>&, int, int, cudaStream_t, const StageMaps*);
 template cudaError_t launch_stage<double>(const StageArgs<double>&, int, int, cudaStream_t, const StageMaps*);
+template cudaError_t launch_axi<float>(const StageArgs<float>&, int, int, float*, float*, float*, int, cudaStream_t);
+template cudaError_t launch_axi<double>(const StageArgs<double>&, int, int, double*, double*, double*, int,
+                                        cudaStream_t);
 
 }  // namespace vlb

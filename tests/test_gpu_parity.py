@@ -57,7 +57,8 @@ def test_drop_torus_32x64_fp32_500_steps():
 
 
 CASES = [
-    # (n_theta, n_phi, geometry, advection, ch_mode): ragged tiles, tiny grids, N_phi = 1, both schemes
+    # (n_theta, n_phi, geometry, advection, ch_mode): ragged tiles, tiny grids, N_phi = 1 (the
+    # single-CTA axisymmetric kernel), both schemes
     (37, 45, vlb.TORUS, vlb.UW3, vlb.HYDRO),
     (37, 45, vlb.TORUS, vlb.WENO5, vlb.HYDRO),
     (40, 70, vlb.FLAT, vlb.UW3, vlb.HYDRO),
@@ -67,6 +68,8 @@ CASES = [
     (4, 5, vlb.TORUS, vlb.UW3, vlb.HYDRO),
     (64, 1, vlb.TORUS, vlb.UW3, vlb.HYDRO),
     (24, 1, vlb.TORUS, vlb.WENO5, vlb.HYDRO),
+    (40, 1, vlb.TORUS, vlb.UW3, vlb.DIFFUSIVE),
+    (32, 1, vlb.FLAT, vlb.UW3, vlb.HYDRO),
     (17, 33, vlb.TORUS, vlb.UW3, vlb.HYDRO),
     # FP32 UW3 with n_phi % 4 == 0 and n_phi >= 40 runs the packed-pair kernel: ragged tiles, single wrap
     (50, 36, vlb.TORUS, vlb.UW3, vlb.HYDRO),
@@ -151,3 +154,27 @@ def test_axisymmetric_state_stays_bitwise_axisymmetric(nt, ns, precision):
     for name, x in zip(("rho", "u_theta", "u_phi", "phi", "mu"), fields):
         assert np.all(np.isfinite(x)), name
         assert np.array_equal(x, np.repeat(x[:, :1], ns, axis=1)), name
+
+
+@pytest.mark.parametrize("precision", [vlb.FP64, vlb.FP32])
+def test_axisymmetric_kernel_is_independent_of_how_steps_are_grouped(precision):
+    """N_phi = 1 runs up to 256 steps per launch, cut at the diagnostic steps; the state after 300
+    steps is the same bit for bit whether they come in one call or several, with or without
+    diagnostics."""
+    nt = 96
+    p = dict(geometry=vlb.TORUS, R=2.2, r=1.0, n_theta=nt, n_phi=1, dt=1.0, tau=0.4, M=0.05, A=0.3, kappa=0.01,
+             advection=vlb.UW3, ch_mode=vlb.HYDRO)
+    p["dt"] = 0.5 * vlb.vlb_max_stable_dt(vlb.make_params(**p))
+    rho, ut, up, phi = _random_fields(nt, 1, seed=17)
+    states = []
+    for diag, calls in ((0, [300]), (7, [3, 100, 197]), (50, [1] * 20 + [280])):
+        s = vlb.Solver(vlb.make_params(**p, precision=precision, diag_every=diag))
+        s.set_fields(rho, ut, up, phi)
+        for c in calls:
+            s.step(c)
+        states.append(s.fields())
+        assert np.all(np.isfinite(s.totals()))
+        s.close()
+    for other in states[1:]:
+        for x, y in zip(states[0], other):
+            assert np.array_equal(x, y)

@@ -1,6 +1,8 @@
 """Stripe suite on the CUDA path (FP32, the production precision) against the paper's closed forms
-for stripes on a torus (Sec. 3): R = 3, r = 1, A = 0.5, xi = 0.05, M = 2.5e-3, grid 512 x 4 (grid
-spacing xi / 4, azimuthally symmetric stripes).
+for stripes on a torus (Sec. 3): R = 3, r = 1, A = 0.5, xi = 0.05, M = 2.5e-3, 512 theta rows (grid
+spacing xi / 4).  The stripes are azimuthally symmetric: the oscillation fits run on one varphi column
+(the single-CTA axisymmetric kernel), the Laplace pressures on one and on four columns (the tile
+kernel).
 
   * Laplace pressure at equilibrium on both branches: a wide sub-critical stripe at theta = pi and a
     super-critical one at its off-pi equilibrium (Eqs. stripe_laplace_gen, stripe_thceq);
@@ -20,12 +22,12 @@ from paper_1904_10070_gb300 import inputs, vlb
 pytestmark = pytest.mark.gpu
 
 R, r, A, KAPPA, M = 3.0, 1.0, 0.5, 1.25e-3, 2.5e-3
-NT, NS = 512, 4
+NT = 512
 XI = math.sqrt(KAPPA / A)
 
 
-def _params(tau, minor=r):
-    p = dict(geometry=0, R=R, r=minor, n_theta=NT, n_phi=NS, dt=1.0, tau=tau, M=M, A=A, kappa=KAPPA, advection=0,
+def _params(tau, minor=r, ns=1):
+    p = dict(geometry=0, R=R, r=minor, n_theta=NT, n_phi=ns, dt=1.0, tau=tau, M=M, A=A, kappa=KAPPA, advection=0,
              ch_mode=0)
     p["dt"] = 0.5 * vlb.vlb_max_stable_dt(vlb.make_params(**p))
     return p
@@ -35,7 +37,7 @@ def _stripe(p, theta_c, width):
     """A phi = -1 band (the paper's convention) with the offset of Eq. stripe_phi0, at rest."""
     s = vlb.Solver(vlb.make_params(**p, precision=vlb.FP32))
     off = C.stripe_offset(R, p["r"], KAPPA, A, theta_c, width)
-    phi = inputs.stripe_phi(R, p["r"], NT, NS, theta_c, width, XI, offset=off, inside=-1.0)
+    phi = inputs.stripe_phi(R, p["r"], NT, p["n_phi"], theta_c, width, XI, offset=off, inside=-1.0)
     z = np.zeros_like(phi)
     s.set_fields(np.ones_like(phi), z, z, phi)
     return s
@@ -68,12 +70,13 @@ def _oscillation(p, area, tc_eq, tc0, omega, periods):
     return abs(popt[1]), popt[3]
 
 
+@pytest.mark.parametrize("ns", [1, 4])
 @pytest.mark.parametrize("branch", ["subcritical", "supercritical"])
-def test_laplace_pressure_at_equilibrium(branch):
+def test_laplace_pressure_at_equilibrium(branch, ns):
     area = C.stripe_area(R, r, math.pi, 1.2 if branch == "subcritical" else 3.4)
     assert (area > C.critical_area(R, r)) == (branch == "supercritical")
     tc_eq, w_eq = C.equilibrium(R, r, area)
-    p = _params(0.1)
+    p = _params(0.1, ns=ns)
     s = _stripe(p, tc_eq, w_eq)
     s.step(int(30.0 / p["dt"]))
     tc, w, rho, phi = _measure(s)
