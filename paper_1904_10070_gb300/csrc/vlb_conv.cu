@@ -183,15 +183,14 @@ __global__ void __launch_bounds__(256) wgrad_reduce_kernel(int groups, int cin, 
 // takes the 8-channel chunk t % (cout / 8) of every (256 / (cout / 8))-th pixel of its block's share
 // (16-byte loads, whole 128-byte rows per 8 or 2 lanes); the pixel lanes of a block are then summed
 // in shared memory.
-constexpr int BG_BLOCKS = 256;
+constexpr int BG_BLOCKS = 608;  // 4 per SM of GB300; a multiple of 32 for the final warp fold
 
 __global__ void __launch_bounds__(256) bias_partial_kernel(int npix, int cout, const bf16* dy, float* part) {
   __shared__ float red[256 * 8];
   const int chunks = cout / 8, lanes = blockDim.x / chunks;
   const int ch = threadIdx.x % chunks, pl = threadIdx.x / chunks;
   float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int p = blockIdx.x * lanes + pl; p < npix; p += gridDim.x * lanes) {
-    const uint4 v = reinterpret_cast<const uint4*>(dy + (size_t)p * cout)[ch];
+  auto add = [&](const uint4& v) {
     const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -199,7 +198,20 @@ __global__ void __launch_bounds__(256) bias_partial_kernel(int npix, int cout, c
       s[2 * i] += f.x;
       s[2 * i + 1] += f.y;
     }
+  };
+  const int step = gridDim.x * lanes;
+  int p = blockIdx.x * lanes + pl;
+  for (; p + 3 * step < npix; p += 4 * step) {  // four loads in flight, added in pixel order
+    const uint4 v0 = reinterpret_cast<const uint4*>(dy + (size_t)p * cout)[ch];
+    const uint4 v1 = reinterpret_cast<const uint4*>(dy + (size_t)(p + step) * cout)[ch];
+    const uint4 v2 = reinterpret_cast<const uint4*>(dy + (size_t)(p + 2 * step) * cout)[ch];
+    const uint4 v3 = reinterpret_cast<const uint4*>(dy + (size_t)(p + 3 * step) * cout)[ch];
+    add(v0);
+    add(v1);
+    add(v2);
+    add(v3);
   }
+  for (; p < npix; p += step) add(reinterpret_cast<const uint4*>(dy + (size_t)p * cout)[ch]);
 #pragma unroll
   for (int i = 0; i < 8; ++i) red[pl * cout + 8 * ch + i] = s[i];
   __syncthreads();
