@@ -111,6 +111,8 @@ vlb_status vlb_set_state(vlb_handle* h, const double* f16, const double* phi);
 vlb_status vlb_get_state(vlb_handle* h, double* f16, double* phi);
 
 /* Advance nsteps SSP-RK3 steps (3 fused-stage launches per step), asynchronously on the stream.
+ * Axisymmetric grids (N_phi = 1, N_theta <= 4096) run up to 256 whole steps per launch of a
+ * single-CTA kernel instead; the result does not depend on how the steps are grouped.
  * With diag_every > 0 the totals are checked every diag_every steps and at the end, the
  * stream is synchronised, and VLB_ERR_UNSTABLE is returned if a value was non-finite or
  * max |u| exceeded 2. */
