@@ -70,12 +70,18 @@ def test_create_rejects_missing_or_small_workspace(L):
     assert L.vlb_destroy(None) == vlb.VLB_OK
 
 
-def _rk3_amplification(dt, ht, hp, tau, n=128):
-    """max |1 + z + z^2/2 + z^3/6| over n x n Fourier modes and |v| pairs for the UW3 difference
-    (stencil weights 1, -6, 3, 2 over offsets -2 .. 1, divided by 6) with relaxation 1/tau."""
+UW3_STENCIL = ([-2, -1, 0, 1], [1.0, -6.0, 3.0, 2.0], 6.0)
+# the fifth-order upwind difference that WENO5 reduces to with its linear weights
+WENO5_STENCIL = ([-3, -2, -1, 0, 1, 2], [-2.0, 15.0, -60.0, 20.0, 30.0, -3.0], 60.0)
+
+
+def _rk3_amplification(dt, ht, hp, tau, n=128, stencil=UW3_STENCIL):
+    """max |1 + z + z^2/2 + z^3/6| over n x n Fourier modes and |v| pairs for an upwind difference
+    (stencil offsets, weights, divisor) with relaxation 1/tau."""
     import numpy as np
     k = -np.pi + 2 * np.pi * np.arange(n) / n
-    offsets, weights = np.array([-2, -1, 0, 1]), np.array([1.0, -6.0, 3.0, 2.0]) / 6.0
+    offsets, weights = np.array(stencil[0]), np.array(stencil[1]) / stencil[2]
+    assert abs(weights.sum()) < 1e-15 and abs((weights * offsets).sum() - 1.0) < 1e-15  # consistent first derivative
     D = (weights[None, :] * np.exp(1j * k[:, None] * offsets[None, :])).sum(axis=1)
     worst = 0.0
     for vi in (math.sqrt(3 - math.sqrt(6)), math.sqrt(3 + math.sqrt(6))):
@@ -96,6 +102,19 @@ def test_max_stable_dt_relaxation_and_advection_together(L):
     assert _rk3_amplification(0.995 * dt, ht, hp, 2.5e-3) <= 1.0 + 1e-9
     assert _rk3_amplification(1.02 * dt, ht, hp, 2.5e-3) > 1.0
     assert _rk3_amplification(2.5 * 2.5e-3, ht, hp, 2.5e-3) > 1.3
+
+
+@pytest.mark.parametrize("geometry,adv", [(vlb.TORUS, vlb.WENO5), (vlb.FLAT, vlb.UW3)])
+def test_max_stable_dt_combined_bound_other_scheme_and_geometry(L, geometry, adv):
+    p = _p(R=3.0, r=1.0, n_theta=128, n_phi=384, tau=2.5e-3, M=2.5e-3, A=0.5, kappa=1.25e-3)
+    p.geometry, p.advection = geometry, adv
+    dt = vlb.vlb_max_stable_dt(p)
+    ht = 2 * math.pi / 128
+    hp = (2.0 if geometry == vlb.TORUS else 3.0) * 2 * math.pi / 384  # inner equator, or R dvarphi flat
+    stencil = WENO5_STENCIL if adv == vlb.WENO5 else UW3_STENCIL
+    assert dt < 2.5 * 2.5e-3
+    assert _rk3_amplification(0.995 * dt, ht, hp, 2.5e-3, stencil=stencil) <= 1.0 + 1e-9
+    assert _rk3_amplification(1.02 * dt, ht, hp, 2.5e-3, stencil=stencil) > 1.0
 
 
 def test_named_workloads_step_below_the_stable_limit(L):
