@@ -93,3 +93,17 @@ def test_equal_area_drop_radii_match_the_printed_values():
     for t0, r0 in rows:
         got = AN.equal_area_drop_radius(R, r, xi, float(t0) * math.pi, 0.0, 30.0 * xi)
         assert abs(got - float(r0)) <= 0.0006, (t0, got, r0)
+
+
+def test_stripe_area_ratios_printed_with_the_equilibrium_figure():
+    """The stripe-equilibrium subsection prints Delta A / Delta A_crit for its four stripes
+    (tests/golden/stripe_fork_area_ratios_printed.txt).  The stripe area at theta_c = pi/2 over
+    Eq. stripe_dA_crit reproduces all four to the printed two decimals."""
+    import os
+    R, r = 2.0, 0.8
+    path = os.path.join(os.path.dirname(__file__), "golden", "stripe_fork_area_ratios_printed.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 4
+    for w, ratio in rows:
+        got = C.stripe_area(R, r, math.pi / 2, float(w) * math.pi) / C.critical_area(R, r)
+        assert abs(got - float(ratio)) <= 0.006, (w, got, ratio)
