@@ -121,3 +121,21 @@ def test_vectorised_oracle_equals_node_loops(nq, ns, adv, geom, mode):
         fb, pb = _step_loops(fb, pb, p)
     np.testing.assert_allclose(fa, fb, rtol=0, atol=1e-13 * np.max(np.abs(fb)))
     np.testing.assert_allclose(pa, pb, rtol=0, atol=1e-13 * np.max(np.abs(pb)))
+
+
+@pytest.mark.parametrize("adv", [O.UW3, O.WENO5])
+def test_step_window_equals_full_grid_step(adv):
+    """The node-by-node evaluation used at full size (a periodic window cut out around the node)
+    gives the full-grid step at that node, including nodes on the wrap-around seams."""
+    nq, ns = 31, 29
+    p = O.Params(R=2.2, r=0.9, n_theta=nq, n_phi=ns, dt=2e-3, tau=0.3, M=0.07, A=0.4, kappa=0.03,
+                 advection=adv)
+    rng = np.random.default_rng(13)
+    n = 1.0 + 0.1 * rng.uniform(-1, 1, (nq, ns))
+    f = O.feq(n, 0.05 * rng.uniform(-1, 1, (nq, ns)), 0.05 * rng.uniform(-1, 1, (nq, ns)))
+    phi = np.tanh(2 * rng.uniform(-1, 1, (nq, ns)))
+    f1, p1 = O.step(f, phi, O.Geometry(p))
+    for q, s in [(0, 0), (nq - 1, ns - 1), (15, 0), (0, 14), (7, 22)]:
+        fw, pw = O.step_window(f, phi, p, q, s)
+        np.testing.assert_allclose(fw, f1[:, :, q, s], rtol=0, atol=1e-14 * np.max(np.abs(f1)))
+        assert abs(pw - p1[q, s]) <= 1e-14
