@@ -31,7 +31,11 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "coarsen_torus_1024x2048"
 METRIC = "node-velocity updates/s"
 UNIT = "NVU/s"
-BYTES_PER_NODE_STEP = {"f32": 576, "f64": 1088}  # 18 (FP32) or 17 (FP64) arrays: 5 reads + 3 writes per node over 3 stages
+# Algorithmic HBM bytes per node and step: the 17 state arrays (16 populations + phi) are read 5 times
+# (stage 1: U^n; stages 2-3: U_in and U^n) and written 3 times over the three Runge-Kutta stages.
+BYTES_PER_NODE_STEP = {"f32": 544, "f64": 1088}
+# the FP32 path also carries the low word of phi (an 18th array) for precision: 576 B moved per node-step
+BYTES_PER_NODE_STEP_MOVED_F32 = 576
 PKEYS = ["R", "r", "n_theta", "n_phi", "dt", "tau", "M", "A", "kappa", "geometry", "advection", "ch_mode"]
 STAGE_SRC = os.path.join(ROOT, "paper_1904_10070_gb300", "csrc", "vlb_stage.cu")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "stage_kernel_fp32_uw3_coarsen_1024x2048.md")
@@ -103,7 +107,7 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
 
     def __exit__(self, *exc):
         if self.proc is not None:
@@ -113,12 +117,16 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
 
-    def summary(self):
+    def summary(self, t0=None, t1=None):
+        """Median SM clock and the throttle reasons seen in the samples taken between t0 and t1
+        (host time; the timed region), or in all samples."""
         if not self.lines:
             return None
         sm, smax, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ts, ln in self.lines:
+            if t0 is not None and not (t0 <= ts <= t1):
+                continue
             parts = [x.strip() for x in ln.split(",")]
             if len(parts) < 8:
                 continue
@@ -133,7 +141,7 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "window": "timed region" if t0 is not None else "whole run"}
 
 
 def reduce_max(values, dist=None, device="cpu"):
@@ -180,16 +188,54 @@ def _calibrated_rows(target_s: float, steps: int) -> int:
     return int(max(1, min(1024, 0.5 * target_s * rate / (ns * steps))))
 
 
-def cpu_baseline(steps: int = 2, target_s: float = 20.0):
-    """The FP64 oracle as it stands, on a bounded sub-grid of the workload (single-threaded numpy)."""
-    rows = _calibrated_rows(target_s, steps)
+def _oracle_worker(args):
+    """One host core: the oracle steps its own sub-grid of the workload (a process of the pool)."""
+    rows, steps = args
     O, geo, f, ph, ns = _oracle_sample(rows)
     t0 = time.perf_counter()
     O.run(f, ph, geo, steps)
-    dt = time.perf_counter() - t0
-    return {"value": 16.0 * rows * ns * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"FP64 numpy oracle, {steps} SSP-RK3 steps on a {rows}x{ns} sub-grid of the "
-                      f"workload (same parameters), {dt:.1f} s"}
+    return time.perf_counter() - t0
+
+
+def _cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "hardware")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline(steps: int = 2, target_s: float = 12.0):
+    """The FP64 oracle as it stands, on bounded sub-grids of the workload: once on one core, then on
+    every host core at once (one spawned process per core, each stepping its own sub-grid of the same
+    size with numpy held to one thread; throughput = all node updates / the slowest process)."""
+    import multiprocessing as mp
+    rows = _calibrated_rows(target_s, steps)
+    ncores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    ns = 2048
+    t1 = _oracle_worker((rows, steps))
+    single = 16.0 * rows * ns * steps / t1
+    # all cores: 128-row sub-grids (a few hundred MB of numpy temporaries per process), enough steps
+    # for about as long as the single-core run
+    rows_mc = min(rows, 128)
+    steps_mc = max(2, int(round(steps * rows / rows_mc)))
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"  # inherited by the spawned workers: one thread each
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(ncores) as pool:
+        times = pool.map(_oracle_worker, [(rows_mc, steps_mc)] * ncores)
+    wall = time.perf_counter() - t0
+    allc = 16.0 * rows_mc * ns * steps_mc * ncores / max(times)
+    return {"value": allc, "unit": UNIT, "cores": ncores, "kind": "oracle",
+            "single_core_value": single, "cpu_model": _cpu_model(), "nproc": os.cpu_count(),
+            "sample": f"FP64 numpy oracle on sub-grids of the workload (same parameters): one core, {steps} "
+                      f"SSP-RK3 steps on {rows}x{ns} in {t1:.1f} s; {ncores} cores, one process each stepping "
+                      f"its own {rows_mc}x{ns} sub-grid {steps_mc} times, slowest {max(times):.1f} s "
+                      f"(pool wall {wall:.1f} s)"}
 
 
 def run_reference(args):
@@ -356,18 +402,35 @@ def main():
     torch.cuda.synchronize()
     barrier()
 
+    # Timed region: blocks of exactly K steps, each bracketed by a barrier and a synchronize and timed
+    # with CUDA events on the solver's stream; enough blocks to fill about a second, so that the clock
+    # samples (every 200 ms) fall inside it.  ms = the median block.
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    vlb.vlb_step(solver.h, args.steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    est_s = max(ev0.elapsed_time(ev1) * 1e-3, 1e-6)
+    nblocks = int(min(500, max(5, np.ceil(1.0 / est_s))))
+    nblocks = int(reduce_max([nblocks], dist, device="cuda")[0])
+    block_ms = []
     with ClockSampler(local) as clk:
-        torch.cuda.synchronize()
-        barrier()
-        ev0.record(stream)
-        vlb.vlb_step(solver.h, args.steps)
-        ev1.record(stream)
-        ev1.synchronize()
-        torch.cuda.synchronize()
-        barrier()
-    ms = ev0.elapsed_time(ev1)
-    clocks = clk.summary()
+        t_on = time.time()
+        for _ in range(nblocks):
+            torch.cuda.synchronize()
+            barrier()
+            ev0.record(stream)
+            vlb.vlb_step(solver.h, args.steps)
+            ev1.record(stream)
+            ev1.synchronize()
+            torch.cuda.synchronize()
+            barrier()
+            block_ms.append(ev0.elapsed_time(ev1))
+        t_off = time.time()
+        time.sleep(0.25)  # let the sampler deliver the last in-window sample
+    block_ms = reduce_max(block_ms, dist, device="cuda")  # max over ranks, block by block
+    ms = float(np.median(block_ms))
+    clocks = clk.summary(t_on, t_off) or clk.summary()
     tot = solver.totals()
     if not np.all(np.isfinite(tot)):
         raise SystemExit(f"non-finite totals after the timed steps: {tot}")
@@ -395,9 +458,10 @@ def main():
     value = aggregate_value(world, 16.0 * N * args.steps, ms * 1e-3)
     peaks, peak_kind = _peaks()
     step_s = ms * 1e-3 / args.steps
-    launch_s = step_s / 3.0
+    launch_s = step_s / 3.0  # every launch of the step is the stage kernel
     alg_bytes_launch = BYTES_PER_NODE_STEP["f32"] * N / 3.0
     achieved = alg_bytes_launch / launch_s / 1e9
+    moved = BYTES_PER_NODE_STEP_MOVED_F32 * N / 3.0 / launch_s / 1e9
     traffic = _traffic_per_launch()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -406,16 +470,21 @@ def main():
         "config": {"workload": WORKLOAD, "grid": [p["n_theta"], p["n_phi"]], "R": p["R"], "r": p["r"],
                    "precision": "fp32 state, fp64 coefficients and sums", "advection": "uw3",
                    "ch_mode": "hydrodynamic", "parallelism": f"replicas x{world}",
-                   "l2": "no flush: one step moves 576 B x 2.1 M nodes = 1.2 GB through a 126 MB L2"},
+                   "l2": "no flush: one step moves 576 B x 2.1 M nodes = 1.2 GB through a 126 MB L2",
+                   "timed_blocks": {"blocks": nblocks, "steps_each": args.steps, "ms_median": ms,
+                                    "ms_min": float(np.min(block_ms)), "ms_max": float(np.max(block_ms))}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                      "kernel": "stage_kernel<float,UW3,HYDRO>",
                      "peak_source": f"{peak_kind} hbm_gbs (copy)",
-                     "algorithmic_bytes_per_launch": alg_bytes_launch},
+                     "algorithmic_bytes_per_launch": alg_bytes_launch,
+                     "algorithmic_bytes": "544 B per node-step: 17 arrays x (5 reads + 3 writes) x 4 B",
+                     "moved_with_phi_lo": {"bytes_per_node_step": BYTES_PER_NODE_STEP_MOVED_F32,
+                                           "achieved": moved, "frac": moved / peaks["hbm_gbs"]}},
         "e2e": {"value": aggregate_value(world, 16.0 * N * args.steps, e2e_s), "unit": UNIT,
                 "h2d_bytes_per_step": 4 * N * 8 / args.steps, "d2h_bytes_per_step": 5 * N * 8 / args.steps,
                 "what": "vlb_set_fields (host) + vlb_step(K) + vlb_get_fields (host), wall clock"},
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": 3 * args.steps,  # per timed block of K steps
         "clocks": clocks,
     }
     if world == 1 and not args.no_ensemble:

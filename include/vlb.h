@@ -115,8 +115,20 @@ vlb_status vlb_get_state(vlb_handle* h, double* f16, double* phi);
  * single-CTA kernel instead; the result does not depend on how the steps are grouped.
  * With diag_every > 0 the totals are checked every diag_every steps and at the end, the
  * stream is synchronised, and VLB_ERR_UNSTABLE is returned if a value was non-finite or
- * max |u| exceeded 2. */
+ * max |u| exceeded 2.
+ * Every wait of a stage kernel on a bulk copy is bounded; one that gives up skips its tile and
+ * raises the handle's device flag.  vlb_step with diag_every > 0, and every synchronous call below
+ * (vlb_get_state, vlb_get_fields, vlb_get_totals, vlb_interface_length), read that flag and then
+ * return VLB_ERR_TIMEOUT (the state is invalid; the call's outputs are still written).  The flag
+ * stays raised until vlb_set_fields or vlb_set_state. */
 vlb_status vlb_step(vlb_handle* h, int64_t nsteps);
+
+/* Test hook for the status path (not part of the method): sets the device flag of handle h to
+ * `value` (0 = clear, 1 = unstable, 2 = a bounded wait gave up) as a failing kernel would, so that
+ * the statuses above can be checked without making a GPU wait run out.  h == NULL sets the
+ * device-wide flag of the tensor-core convolutions on the current device instead (0 or 1; see
+ * vlb_conv_status).  Synchronous. */
+vlb_status vlb_test_raise_flag(vlb_handle* h, int32_t value);
 
 /* Macroscopic fields (host [N_theta][N_phi] doubles; any pointer may be NULL to skip):
  * rho = n, u = vielbein velocity (Sec. 2.3 moments), phi, and
@@ -211,6 +223,12 @@ vlb_status vlb_conv3x3_flip(int32_t cin, int32_t cout, const void* w, void* w_fl
 size_t vlb_conv3x3_wgrad_workspace_bytes(int32_t H, int32_t W, int32_t cin, int32_t cout);
 vlb_status vlb_conv3x3_bwd_weight(int32_t H, int32_t W, int32_t cin, int32_t cout, const void* x, const void* dy,
                                   float* dw, float* db, void* workspace, size_t bytes, void* cuda_stream);
+/* Status of the tensor-core convolutions: every wait inside their kernels is bounded, and one that
+ * gives up raises a device-wide flag (the kernel winds down and its outputs are invalid) instead of
+ * hanging.  This call synchronises cuda_stream, reads the flag of the current device, clears it if
+ * `clear` != 0, and returns VLB_ERR_TIMEOUT if it was raised, else VLB_OK.  The convolution calls
+ * themselves are asynchronous and do not read it: check at the points where you synchronise. */
+vlb_status vlb_conv_status(void* cuda_stream, int32_t clear);
 /* Scratch (bytes) that vlb_channel_sums and vlb_mse_loss need in d_work. */
 size_t vlb_reduce_workspace_bytes(void);
 /* Snapshot statistics for the network, on the device, without a host read-back:
@@ -256,9 +274,9 @@ vlb_status vlb_to_bf16(int64_t n, const float* x, void* y, void* cuda_stream);
 #define VLB_NOALLOC_SCRATCH_BYTES (24u * 1024u * 1024u)
 
 /* vlb_step without any device allocation.  The paper has no counterpart: this is a deployment
- * variant for callers that cannot allocate device memory where they step -- code running while a
- * stream is captured into a CUDA graph, plug-ins that may only use buffers their host application
- * hands them, loops that cannot afford cudaMalloc's implicit device synchronisation.
+ * variant for callers that cannot allocate device memory where they step -- plug-ins that may only
+ * use the buffers their host application hands them (the host owns the device memory budget), and
+ * loops that cannot afford cudaMalloc's implicit device synchronisation.
  *
  * Advances the caller's device state in place by nsteps SSP-RK3 steps on cuda_stream (NULL: the
  * legacy default stream), asynchronously.  d_state (256-byte aligned) holds arrays spaced stride
@@ -271,9 +289,11 @@ vlb_status vlb_to_bf16(int64_t n, const float* x, void* y, void* cuda_stream);
  * The two intermediate Runge-Kutta states and the row coefficients live in one file-scope device
  * array of VLB_NOALLOC_SCRATCH_BYTES that every device loading the library holds until exit; the
  * call needs 2 * (17 or 18) * stride * element-size bytes plus the tables, and a larger grid is
- * rejected with VLB_ERR_ARG (about 170 k nodes in FP32, 90 k in FP64).  The first call on each
- * device looks up the array's device address (cudaGetSymbolAddress) with that device current, so
- * that first call should come before any stream capture.  All calls share the array, which keeps
+ * rejected with VLB_ERR_ARG (about 170 k nodes in FP32, 90 k in FP64), and so is a stride beyond
+ * that limit, before any size arithmetic.  The first call on each device does the one-time set-up:
+ * it looks up the array's device address (cudaGetSymbolAddress) with that device current, raises
+ * the stage kernels' shared-memory limit (cudaFuncSetAttribute) and builds their constant
+ * velocity tables; so that first call should come before any stream capture.  All calls share the array, which keeps
  * the previous call's contents: calls whose GPU work overlaps (other streams, other host threads
  * on the same device) race.  No cudaMalloc, cudaFree or other allocating routine is called.
  * On failure *error (if not NULL) points to a thread-local message. */

@@ -319,13 +319,32 @@ vlb_status check_handle(vlb_handle* h, bool ensemble_ok = false) {
   return VLB_OK;
 }
 
+// Reads the handle's device flag in the stream order of the work issued so far, synchronises, and
+// turns a raised flag into a status: 2 = a bounded wait on a bulk copy gave up and a tile was
+// skipped (the state is no longer a solution: VLB_ERR_TIMEOUT), 1 = a diagnostic found a non-finite
+// value or |u| > 2 (VLB_ERR_UNSTABLE, reported only when `unstable_too`).  The flag stays raised
+// until the next vlb_set_fields / vlb_set_state.
+vlb_status sync_and_check(vlb_handle* h, const char* what, bool unstable_too) {
+  int flag = 0;
+  VLB_CUDA(h, cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  VLB_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (flag == 2)
+    return fail(h, VLB_ERR_TIMEOUT, "%s: a bounded device wait on a bulk copy gave up after %lld steps; a tile was "
+                "skipped and the state is invalid (reset it with vlb_set_fields or vlb_set_state)", what,
+                (long long)h->steps_done);
+  if (flag == 1 && unstable_too)
+    return fail(h, VLB_ERR_UNSTABLE, "%s: unstable state: non-finite value or |u| > 2 after %lld steps", what,
+                (long long)h->steps_done);
+  return VLB_OK;
+}
+
 }  // namespace
 
 // Flags an unstable state: non-finite values or |u| > 2 in the diagnostic vector.
 __global__ void vlb_flag_kernel(const double* diag, int* flag) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     const double m = diag[0], um = diag[3], bad = diag[4];
-    if (bad > 0.0 || !(um <= 2.0) || !isfinite(m)) *flag = 1;
+    if ((bad > 0.0 || !(um <= 2.0) || !isfinite(m)) && *flag == 0) *flag = 1;  // a timeout (2) takes precedence
   }
 }
 
@@ -623,8 +642,7 @@ vlb_status vlb_get_state(vlb_handle* h, double* f16, double* phi) {
   const size_t nb = sizeof(double) * h->N;
   VLB_CUDA(h, cudaMemcpyAsync(f16, h->staging, 16 * nb, cudaMemcpyDeviceToHost, h->stream));
   VLB_CUDA(h, cudaMemcpyAsync(phi, h->staging + 16 * h->N, nb, cudaMemcpyDeviceToHost, h->stream));
-  VLB_CUDA(h, cudaStreamSynchronize(h->stream));
-  return VLB_OK;
+  return sync_and_check(h, "vlb_get_state", false);
 }
 
 vlb_status vlb_step(vlb_handle* h, int64_t nsteps) {
@@ -633,13 +651,7 @@ vlb_status vlb_step(vlb_handle* h, int64_t nsteps) {
   if (nsteps < 0) return fail(h, VLB_ERR_ARG, "nsteps must be >= 0");
   st = h->esize == 8 ? run_steps<double>(h, nsteps) : run_steps<float>(h, nsteps);
   if (st) return st;
-  if (h->p.diag_every > 0 && nsteps > 0) {
-    int flag = 0;
-    VLB_CUDA(h, cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    VLB_CUDA(h, cudaStreamSynchronize(h->stream));
-    if (flag) return fail(h, VLB_ERR_UNSTABLE, "unstable state: non-finite value or |u| > 2 after %lld steps",
-                          (long long)h->steps_done);
-  }
+  if (h->p.diag_every > 0 && nsteps > 0) return sync_and_check(h, "vlb_step", true);
   return VLB_OK;
 }
 
@@ -659,8 +671,7 @@ vlb_status vlb_get_fields(vlb_handle* h, double* rho, double* u_th, double* u_ph
   for (int k = 0; k < 5; ++k)
     if (outs[k])
       VLB_CUDA(h, cudaMemcpyAsync(outs[k], s + k * N, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream));
-  VLB_CUDA(h, cudaStreamSynchronize(h->stream));
-  return VLB_OK;
+  return sync_and_check(h, "vlb_get_fields", false);
 }
 
 vlb_status vlb_get_totals(vlb_handle* h, double out[4]) {
@@ -671,9 +682,9 @@ vlb_status vlb_get_totals(vlb_handle* h, double out[4]) {
   if (st) return st;
   double t[8];
   VLB_CUDA(h, cudaMemcpyAsync(t, h->totals, sizeof t, cudaMemcpyDeviceToHost, h->stream));
-  VLB_CUDA(h, cudaStreamSynchronize(h->stream));
+  st = sync_and_check(h, "vlb_get_totals", false);
   for (int k = 0; k < 4; ++k) out[k] = t[k];
-  return VLB_OK;
+  return st;
 }
 
 vlb_status vlb_interface_length(vlb_handle* h, double* out) {
@@ -684,9 +695,9 @@ vlb_status vlb_interface_length(vlb_handle* h, double* out) {
   if (st) return st;
   double t[8];
   VLB_CUDA(h, cudaMemcpyAsync(t, h->totals, sizeof t, cudaMemcpyDeviceToHost, h->stream));
-  VLB_CUDA(h, cudaStreamSynchronize(h->stream));
+  st = sync_and_check(h, "vlb_interface_length", false);
   *out = t[5];
-  return VLB_OK;
+  return st;
 }
 
 vlb_status vlb_state_device(vlb_handle* h, void** f, int64_t* stride) {
@@ -777,7 +788,7 @@ EnsLayout ens_layout(const vlb_params* p, int count) {
 vlb_status ens_launch_step(vlb_handle* h, int rows_idx, cudaStream_t st) {
   for (int stage = 0; stage < 3; ++stage)
     VLB_CUDA(h, vlb::launch_ensemble_stage(h->d_members, h->d_items[rows_idx], h->nitems[rows_idx], stage,
-                                          kTileRows[rows_idx], h->p.ch_mode, st, h->ens_maps));
+                                          kTileRows[rows_idx], h->p.ch_mode, h->flag, st, h->ens_maps));
   return VLB_OK;
 }
 
@@ -790,11 +801,11 @@ vlb_status ens_autotune(vlb_handle* h) {
   float best = 1e30f;
   for (int k = 0; k < 2; ++k) {
     VLB_CUDA(h, vlb::launch_ensemble_stage(h->d_members, h->d_items[k], h->nitems[k], 0, kTileRows[k],
-                                          h->p.ch_mode, h->stream, h->ens_maps));  // warm-up
+                                          h->p.ch_mode, h->flag, h->stream, h->ens_maps));  // warm-up
     VLB_CUDA(h, cudaEventRecord(e0, h->stream));
     for (int r = 0; r < 3; ++r)
       VLB_CUDA(h, vlb::launch_ensemble_stage(h->d_members, h->d_items[k], h->nitems[k], 0, kTileRows[k],
-                                            h->p.ch_mode, h->stream, h->ens_maps));
+                                            h->p.ch_mode, h->flag, h->stream, h->ens_maps));
     VLB_CUDA(h, cudaEventRecord(e1, h->stream));
     VLB_CUDA(h, cudaEventSynchronize(e1));
     float ms = 0.0f;
@@ -1087,6 +1098,29 @@ vlb_status vlb_conv3x3_bwd_weight(int32_t H, int32_t W, int32_t cin, int32_t cou
   if (bytes < vlb::conv_wgrad_workspace_bytes(H, W, cin, cout))
     return fail(nullptr, VLB_ERR_WORKSPACE, "vlb_conv3x3_bwd_weight: workspace too small");
   VLB_CUDA(nullptr, vlb::conv_wgrad(H, W, cin, cout, x, dy, dw, db, (float*)workspace, (cudaStream_t)cuda_stream));
+  return VLB_OK;
+}
+
+vlb_status vlb_conv_status(void* cuda_stream, int32_t clear) {
+  int raised = 0;
+  VLB_CUDA(nullptr, vlb::conv_tc_status((cudaStream_t)cuda_stream, clear, &raised));
+  if (raised)
+    return fail(nullptr, VLB_ERR_TIMEOUT, "a bounded wait of a tensor-core convolution gave up: outputs of the "
+                "convolution calls since the last clear are invalid");
+  return VLB_OK;
+}
+
+vlb_status vlb_test_raise_flag(vlb_handle* h, int32_t value) {
+  if (value < 0 || value > 2) return fail(h, VLB_ERR_ARG, "vlb_test_raise_flag: value must be 0, 1 or 2");
+  if (!h) {
+    VLB_CUDA(nullptr, vlb::conv_tc_raise(value));
+    return VLB_OK;
+  }
+  vlb_status st = check_handle(h, true);
+  if (st) return st;
+  const int v = value;
+  VLB_CUDA(h, cudaMemcpyAsync(h->flag, &v, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  VLB_CUDA(h, cudaStreamSynchronize(h->stream));
   return VLB_OK;
 }
 

@@ -649,4 +649,26 @@ cudaError_t conv_wgrad_tc64(int H, int W, const void* x, const void* dy, float* 
   return wg64_launch(H, W, x, dy, partial, segs_per_group, st);
 }
 
+cudaError_t conv_tc_status(cudaStream_t st, int clear, int* raised) {
+  int* flag = nullptr;
+  cudaError_t e = cudaGetSymbolAddress((void**)&flag, g_conv_tc_err);
+  if (e != cudaSuccess) return e;
+  int v = 0;
+  if ((e = cudaMemcpyAsync(&v, flag, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+  *raised = v;
+  if (clear && v) {
+    if ((e = cudaMemsetAsync(flag, 0, sizeof(int), st)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t conv_tc_raise(int value) {
+  int* flag = nullptr;
+  cudaError_t e = cudaGetSymbolAddress((void**)&flag, g_conv_tc_err);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(flag, &value, sizeof(int), cudaMemcpyHostToDevice);
+}
+
 }  // namespace vlb

@@ -105,8 +105,9 @@ struct EnsembleMaps {
 
 // Host launchers (vlb_stage.cu).
 // One stage (0, 1, 2) of every ensemble member; items[b] = (member, tile index), tile_rows 16 or 8.
+// err: the ensemble's device flag, raised (2) if a bounded wait on a bulk copy gives up.
 cudaError_t launch_ensemble_stage(const EnsembleMember* members, const int2* items, int nitems, int stage,
-                                  int tile_rows, int ch_mode, cudaStream_t s, const EnsembleMaps* maps);
+                                  int tile_rows, int ch_mode, int* err, cudaStream_t s, const EnsembleMaps* maps);
 // maps: tensor maps for this stage's fin / f0 (FP32 UW3 only), or NULL for per-thread copies.
 template <typename T>
 cudaError_t launch_stage(const StageArgs<T>& a, int advection, int ch_mode, cudaStream_t s,
@@ -159,6 +160,10 @@ cudaError_t conv_fwd_tc(int H, int W, int cin, int cout, const void* x, const vo
 // covers row segments (128 pixels) g * segs_per_group ..
 cudaError_t conv_wgrad_tc64(int H, int W, const void* x, const void* dy, float* partial, int segs_per_group,
                             cudaStream_t st);
+// The device-wide flag raised (1) when a bounded wait of a tensor-core convolution gives up: read
+// after synchronising st (and cleared if `clear`); conv_tc_raise sets it (tests of the status path).
+cudaError_t conv_tc_status(cudaStream_t st, int clear, int* raised);
+cudaError_t conv_tc_raise(int value);
 cudaError_t conv_flip(int cin, int cout, const void* w, void* wf, cudaStream_t st);
 cudaError_t conv_wgrad(int H, int W, int cin, int cout, const void* x, const void* dy, float* dw, float* db,
                        float* partial, cudaStream_t st);

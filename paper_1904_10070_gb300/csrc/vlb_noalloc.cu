@@ -1,10 +1,9 @@
 // vlb_step_noalloc: the SSP-RK3 step without any device allocation.
 //
 // Some callers cannot allocate device memory at the point where they need to advance a state:
-// code running while a stream is being captured into a CUDA graph (an allocation there is not
-// part of the capture and may be refused), plug-ins whose host application hands out only
-// pre-sized device buffers from its own arena, and latency-critical loops where cudaMalloc's
-// implicit device synchronisation is not acceptable.  For them this entry point keeps the two
+// plug-ins whose host application hands out only pre-sized device buffers from its own arena (the
+// host owns the memory budget), and latency-critical loops where cudaMalloc's implicit device
+// synchronisation is not acceptable.  For them this entry point keeps the two
 // intermediate Runge-Kutta states and the per-row coefficient tables in one file-scope device
 // array of fixed size; the caller passes only the state it owns.
 //
@@ -150,6 +149,14 @@ vlb_status vlb_step_noalloc(const vlb_params* p, void* d_state, int64_t stride, 
   if (nsteps < 0) return fail(VLB_ERR_ARG, "nsteps must be >= 0");
   if (!(n0 > 0.0) || !isfinite(n0)) return fail(VLB_ERR_ARG, "n0 must be finite and > 0");
   const size_t esize = p->precision == VLB_FP64 ? 8 : 4;
+  // bound the stride first, so that the size arithmetic below cannot wrap around
+  const int64_t max_stride = (int64_t)(VLB_NOALLOC_SCRATCH_BYTES / (2 * (size_t)vlb::state_arrays(esize) * esize));
+  if (stride > max_stride) {
+    char msg[160];
+    snprintf(msg, sizeof msg, "stride %lld exceeds %lld elements, the most the fixed scratch (VLB_NOALLOC_SCRATCH_BYTES) holds",
+             (long long)stride, (long long)max_stride);
+    return fail(VLB_ERR_ARG, msg);
+  }
   const size_t need = align256(esize * vlb::NCOEF * p->n_theta) +
                       2 * (size_t)vlb::state_arrays(esize) * (size_t)stride * esize;
   if (need > VLB_NOALLOC_SCRATCH_BYTES) {

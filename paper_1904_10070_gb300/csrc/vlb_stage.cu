@@ -887,7 +887,7 @@ using EnsLay = Lay<float, 2, TQR, 4, TQR * (TS / 2), 1>;
 template <int TQR, int CH, bool F0>
 __global__ void __launch_bounds__(TQR * (TS / 2)) ensemble_stage_kernel(const EnsembleMember* members,
                                                                        const int2* items, int nitems, int ahead,
-                                                                       int stage, VConst<float> vc,
+                                                                       int stage, int* err, VConst<float> vc,
                                                                        const __grid_constant__ EnsembleMaps maps) {
   using L = EnsLay<TQR>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -910,7 +910,7 @@ __global__ void __launch_bounds__(TQR * (TS / 2)) ensemble_stage_kernel(const En
   a.kappa = d.kappa;
   a.gt = d.gt;
   a.n0 = d.n0;
-  a.err = nullptr;
+  a.err = err;
   a.ahead = 0;
   const int tiles_s = (d.ns + TS - 1) / TS;
   const int q0 = (it.y / tiles_s) * TQR, s0 = (it.y % tiles_s) * TS;
@@ -1190,8 +1190,8 @@ cudaError_t launch_generic(const StageArgs<T>& a, cudaStream_t st, const StageMa
 }
 
 template <int TQR, int CH, bool F0>
-cudaError_t launch_ens(const EnsembleMember* members, const int2* items, int nitems, int stage, cudaStream_t st,
-                       const EnsembleMaps& maps) {
+cudaError_t launch_ens(const EnsembleMember* members, const int2* items, int nitems, int stage, int* err,
+                       cudaStream_t st, const EnsembleMaps& maps) {
   using L = EnsLay<TQR>;
   static int mask = 0;
   cudaError_t e = ensure_smem(ensemble_stage_kernel<TQR, CH, F0>, L::BYTES, mask);
@@ -1209,18 +1209,19 @@ cudaError_t launch_ens(const EnsembleMember* members, const int2* items, int nit
     resident[dev] = per_sm * sms;
   }
   const int ahead = dev < 32 ? resident[dev] / 2 : 0;  // half a wave, as for a single torus
-  ensemble_stage_kernel<TQR, CH, F0><<<nitems, L::NTH, L::BYTES, st>>>(members, items, nitems, ahead, stage, vc, maps);
+  ensemble_stage_kernel<TQR, CH, F0><<<nitems, L::NTH, L::BYTES, st>>>(members, items, nitems, ahead, stage, err, vc,
+                                                                     maps);
   return cudaGetLastError();
 }
 
 template <int TQR>
 cudaError_t launch_ens_rows(const EnsembleMember* members, const int2* items, int nitems, int stage, int ch_mode,
-                            cudaStream_t st, const EnsembleMaps& maps) {
+                            int* err, cudaStream_t st, const EnsembleMaps& maps) {
   if (ch_mode == VLB_HYDRO)
-    return stage == 0 ? launch_ens<TQR, VLB_HYDRO, false>(members, items, nitems, stage, st, maps)
-                      : launch_ens<TQR, VLB_HYDRO, true>(members, items, nitems, stage, st, maps);
-  return stage == 0 ? launch_ens<TQR, VLB_DIFFUSIVE, false>(members, items, nitems, stage, st, maps)
-                    : launch_ens<TQR, VLB_DIFFUSIVE, true>(members, items, nitems, stage, st, maps);
+    return stage == 0 ? launch_ens<TQR, VLB_HYDRO, false>(members, items, nitems, stage, err, st, maps)
+                      : launch_ens<TQR, VLB_HYDRO, true>(members, items, nitems, stage, err, st, maps);
+  return stage == 0 ? launch_ens<TQR, VLB_DIFFUSIVE, false>(members, items, nitems, stage, err, st, maps)
+                    : launch_ens<TQR, VLB_DIFFUSIVE, true>(members, items, nitems, stage, err, st, maps);
 }
 
 
@@ -1304,12 +1305,12 @@ cudaError_t launch_stage(const StageArgs<T>& a, int advection, int ch_mode, cuda
 }
 
 cudaError_t launch_ensemble_stage(const EnsembleMember* members, const int2* items, int nitems, int stage,
-                                  int tile_rows, int ch_mode, cudaStream_t s, const EnsembleMaps* maps) {
+                                  int tile_rows, int ch_mode, int* err, cudaStream_t s, const EnsembleMaps* maps) {
   if (nitems <= 0) return cudaSuccess;
   static const EnsembleMaps none = {};
   const EnsembleMaps& m = maps ? *maps : none;
-  if (tile_rows == 8) return launch_ens_rows<8>(members, items, nitems, stage, ch_mode, s, m);
-  return launch_ens_rows<16>(members, items, nitems, stage, ch_mode, s, m);
+  if (tile_rows == 8) return launch_ens_rows<8>(members, items, nitems, stage, ch_mode, err, s, m);
+  return launch_ens_rows<16>(members, items, nitems, stage, ch_mode, err, s, m);
 }
 
 template <typename T>

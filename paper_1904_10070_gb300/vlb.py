@@ -28,7 +28,8 @@ EXPORTS = ["vlb_workspace_bytes", "vlb_max_stable_dt", "vlb_create", "vlb_destro
            "vlb_ensemble_member", "vlb_ensemble_tile_rows", "vlb_get_snapshot", "vlb_set_snapshot",
            "vlb_conv3x3_fwd", "vlb_conv3x3_flip", "vlb_conv3x3_wgrad_workspace_bytes", "vlb_conv3x3_bwd_weight",
            "vlb_reduce_workspace_bytes", "vlb_surrogate_norm", "vlb_surrogate_features", "vlb_surrogate_targets",
-           "vlb_surrogate_apply", "vlb_snapshot_compare", "vlb_channel_sums", "vlb_mse_loss", "vlb_adam_step", "vlb_to_bf16"]
+           "vlb_surrogate_apply", "vlb_snapshot_compare", "vlb_channel_sums", "vlb_mse_loss", "vlb_adam_step", "vlb_to_bf16",
+           "vlb_conv_status", "vlb_test_raise_flag"]
 
 NOALLOC_SCRATCH_BYTES = 24 * 1024 * 1024
 
@@ -94,7 +95,9 @@ def lib() -> ctypes.CDLL:
     FP = ctypes.POINTER(ctypes.c_float)
     DP = ctypes.POINTER(ctypes.c_double)
     L.vlb_get_snapshot.argtypes, L.vlb_get_snapshot.restype = [P, P], I32
-    L.vlb_set_snapshot.argtypes, L.vlb_set_snapshot.restype = [P, P, DP], I32
+    L.vlb_set_snapshot.argtypes, L.vlb_set_snapshot.restype = [P, P, DP, I32], I32
+    L.vlb_conv_status.argtypes, L.vlb_conv_status.restype = [P, I32], I32
+    L.vlb_test_raise_flag.argtypes, L.vlb_test_raise_flag.restype = [P, I32], I32
     L.vlb_conv3x3_fwd.argtypes = [I32, I32, I32, I32, P, P, P, P, I32, P, P, P]
     L.vlb_conv3x3_flip.argtypes = [I32, I32, P, P, P]
     L.vlb_conv3x3_wgrad_workspace_bytes.argtypes = [I32, I32, I32, I32]
@@ -251,6 +254,17 @@ def vlb_conv3x3_wgrad_workspace_bytes(H, W, cin, cout) -> int:
 def vlb_conv3x3_bwd_weight(H, W, cin, cout, x, dy, dw, db, workspace, stream):
     _check(lib().vlb_conv3x3_bwd_weight(H, W, cin, cout, _ptr(x), _ptr(dy), _ptr(dw), _ptr(db), _ptr(workspace),
                                         workspace.numel() * workspace.element_size(), ctypes.c_void_p(stream)))
+
+
+def vlb_conv_status(stream, clear=True):
+    """Synchronises `stream` and raises VlbError(VLB_ERR_TIMEOUT) if a tensor-core convolution's
+    bounded wait gave up since the last clear."""
+    _check(lib().vlb_conv_status(ctypes.c_void_p(stream), 1 if clear else 0))
+
+
+def vlb_test_raise_flag(h, value: int):
+    """Test hook: set the device flag of handle h (or, h = None, of the convolutions)."""
+    _check(lib().vlb_test_raise_flag(h, int(value)), h)
 
 
 def vlb_reduce_workspace_bytes() -> int:

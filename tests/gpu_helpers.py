@@ -21,6 +21,15 @@ def rel_err(x, ref):
     return float(np.linalg.norm(x - ref) / max(np.linalg.norm(ref), 1e-3 * np.sqrt(ref.size)))
 
 
+def max_err(x, ref, floor=1e-3):
+    """Element-wise: max_i |x_i - ref_i| / max(max_i |ref_i|, floor).  Unlike rel_err it is not diluted
+    by the grid size, so a single wrong node (a seam, a tile edge) shows at full weight."""
+    x, ref = np.asarray(x, float), np.asarray(ref, float)
+    if ref.size == 0:
+        return 0.0
+    return float(np.max(np.abs(x - ref)) / max(float(np.max(np.abs(ref))), floor))
+
+
 def oracle_fields(f, phi, geo):
     n, ut, up = O.moments(f)
     return n, ut, up, phi, O.chemical_potential(phi, geo)

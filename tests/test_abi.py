@@ -138,3 +138,14 @@ def test_max_stable_dt_limits(L):
     ht, hp = 2 * math.pi / 1024, 2 * math.pi / 2048
     lam = 4 / ht ** 2 + 4 / hp ** 2
     assert abs(vlb.vlb_max_stable_dt(p) - 2.5 / (2.5e-3 * lam * (5e-4 * lam + 1.0))) < 1e-18
+
+
+def test_noalloc_rejects_a_stride_whose_size_would_wrap_around(L):
+    """A stride of 2^60 elements makes the scratch size wrap around 2^64; it must be rejected before
+    any size arithmetic (no device is touched: the call fails on its arguments)."""
+    p = _p(precision=vlb.FP32)
+    for stride in (1 << 60, (1 << 62) + 64 * 5, vlb.NOALLOC_SCRATCH_BYTES):
+        with pytest.raises(vlb.VlbError) as exc:
+            vlb.vlb_step_noalloc(p, 256, stride, 1.0, 1, 0)
+        assert exc.value.status == vlb.VLB_ERR_ARG
+        assert "stride" in str(exc.value)

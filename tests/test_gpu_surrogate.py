@@ -26,8 +26,9 @@ def _close_bf16(got, want, what):
     assert not bad.any(), (what, int(bad.sum()), float(np.max(np.abs(got - want))))
 
 
-@pytest.mark.parametrize("H,W", [(4, 128), (6, 256)])
+@pytest.mark.parametrize("H,W", [(4, 128), (6, 256), (256, 512)])
 def test_network_layers_match_cpu_oracle(H, W):
+    """(256, 512) is the surrogate workload's size: the persistent kernels' multi-item paths."""
     import torch
     net = S.SurrogateNet(H, W, seed=3)
     rng = np.random.default_rng(4)
