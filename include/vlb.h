@@ -270,6 +270,68 @@ vlb_status vlb_adam_step(int64_t n, float* p, const float* g, float* m, float* v
                          float b2, float eps, void* p_bf16, void* cuda_stream);
 vlb_status vlb_to_bf16(int64_t n, const float* x, void* y, void* cuda_stream);
 
+/* ---- Surrogate-accelerated stepping (not in the paper) ----
+ * A learned network stands in for windows of solver steps, with the solver as judge and fallback.
+ * The network is the 8-layer periodic 3 x 3 CNN of the kernels above: 16 -> 64, six 64 -> 64 and
+ * 64 -> 16 channels, ReLU between layers; input = vlb_surrogate_features of the solver's snapshot
+ * scaled by vlb_surrogate_norm (with s_n, s_u, g below); output = the window's change, applied by
+ * vlb_surrogate_apply.  It is trained elsewhere (the kernels above; paper_1904_10070_gb300/surrogate.py). */
+typedef struct {
+  const void* weights_bf16;  /* the layers' weights, bf16 [C_out][3][3][C_in], concatenated in layer
+                                order (239616 values); host or device memory, copied at create */
+  const float* biases;       /* the layers' FP32 biases, concatenated (464 values); host or device */
+  float s_n, s_u;            /* fixed input scales of n - mean(n) and of u (> 0) */
+  float g[4];                /* output ratios: change of channel c = g[c] * (input scale of c) * output c */
+  int32_t window;            /* solver steps that one prediction stands for (> 0) */
+  int32_t reserved;          /* must be 0 */
+} vlb_surrogate_net;
+
+/* Window kinds reported by vlb_surrogate_advance. */
+enum { VLB_WINDOW_SURROGATE = 0, VLB_WINDOW_CHECKED = 1, VLB_WINDOW_FALLBACK = 2, VLB_WINDOW_SOLVER = 3 };
+/* Options of vlb_surrogate_advance (bit flags). */
+enum { VLB_SUR_JUDGE_LINF = 1, VLB_SUR_NO_GRAPH = 2 };
+
+/* Workspace bytes of a surrogate for the solver grid `geom` (FP32, N_theta even, N_phi a multiple of
+ * 128); 0 if invalid.  About 60 MB at 256 x 512. */
+size_t vlb_surrogate_workspace_bytes(const vlb_params* geom);
+
+/* Create a surrogate handle for solvers with the grid and radii of geom, over a caller-owned device
+ * workspace (256-byte aligned).  The network is copied into the workspace (synchronous on cuda_stream).
+ * Release with vlb_destroy. */
+vlb_status vlb_surrogate_create(const vlb_params* geom, const vlb_surrogate_net* net, void* d_workspace,
+                                size_t bytes, void* cuda_stream, vlb_handle** out);
+
+/* Advance the FP32 solver (a solver handle or an ensemble member view with the network's grid) by
+ * nwindows windows of net->window steps, on the solver's stream.  Window k (counted from the first
+ * call on this solver) is
+ *   - judged when check_every > 0 and k % check_every == 0 (k from 1): the network predicts the
+ *     window and the solver runs it from the same state; their phi fields are compared by the
+ *     relative L2 error ||phi_net - phi_solver||_2 / ||phi_solver||_2, or with VLB_SUR_JUDGE_LINF by
+ *     the relative L-infinity error max|phi_net - phi_solver| / max|phi_solver|.  Within phi_tol the
+ *     solver's result is kept (VLB_WINDOW_CHECKED).  Otherwise (or if a value is not finite) the state
+ *     returns to the last judged one, the solver redoes the windows since then and this one, and runs
+ *     the next check_every windows alone (VLB_WINDOW_FALLBACK, then VLB_WINDOW_SOLVER);
+ *   - otherwise predicted (VLB_WINDOW_SURROGATE): snapshot, network, and a restart of the solver from
+ *     the prediction that keeps the non-equilibrium part of f (vlb_set_snapshot, keep_nonequilibrium)
+ *     with the totals int n sqrt(g) and int phi sqrt(g) held at their values when the surrogate was
+ *     bound to this solver.  Nothing is read back to the host; on a stream other than the default
+ *     streams the second and later predicted windows replay one captured CUDA graph (VLB_SUR_NO_GRAPH:
+ *     always eager).
+ * The first call with a given solver binds the surrogate to it (reads its totals, synchronous); a call
+ * with another solver starts a new binding.  The solver's step count advances by the window per
+ * window (a rollback restores it).  kinds (nwindows ints) and errors (2 nwindows doubles: relative L2
+ * and L-infinity error of judged windows, NaN otherwise) may be NULL; *fell_back (may be NULL)
+ * receives the number of fallbacks in this call.  Judged windows synchronise the stream; a raised
+ * tensor-core flag (see vlb_conv_status) returns VLB_ERR_TIMEOUT there.  Errors of the solver calls
+ * inside are returned with their message on the surrogate handle. */
+vlb_status vlb_surrogate_advance(vlb_handle* solver, vlb_handle* sur, int32_t nwindows, int32_t check_every,
+                                 double phi_tol, int32_t options, int32_t* kinds, double* errors,
+                                 int32_t* fell_back);
+
+/* Counters of the current binding: out[0] windows, out[1] predicted windows, out[2] fallbacks,
+ * out[3] 1 if a predicted window has been captured as a CUDA graph. */
+vlb_status vlb_surrogate_stats(const vlb_handle* sur, int64_t out[4]);
+
 /* Fixed size, in bytes, of the device scratch that vlb_step_noalloc uses. */
 #define VLB_NOALLOC_SCRATCH_BYTES (24u * 1024u * 1024u)
 

@@ -16,47 +16,12 @@
 #include <new>
 #include <vector>
 
-#include "vlb_internal.cuh"
+#include "vlb_handle.cuh"
 
 // Raises the handle's device flag when a diagnostic vector shows an unstable state.
 cudaError_t vlb_internal_flag(const double* diag, int* flag, cudaStream_t s);
 
-struct vlb_handle {
-  vlb_params p;
-  cudaStream_t stream;
-  int device;
-  int64_t N;       // n_theta * n_phi
-  int64_t stride;  // elements between state arrays
-  size_t esize;    // 4 or 8
-  unsigned char* ws;
-  size_t ws_bytes;
-  void* U[3];          // U^n, U^(1), U^(2)
-  void* coefT;         // [NCOEF][n_theta] in state precision
-  double* coefD;       // [NCOEF][n_theta] FP64
-  double* staging;     // 17 N doubles
-  double* partials;    // totals_blocks() * 8
-  double* totals;      // 8 doubles (read-out)
-  double* diag;        // 8 doubles (last in-step diagnostic)
-  int* flag;           // device flag: diagnostics found an unstable state (1) or a bulk copy gave up (2)
-  vlb::StageMaps* maps = nullptr;  // FP32 UW3: tensor maps of the three stage inputs (NULL: per-thread copies)
-  vlb::EnsembleMaps* ens_maps = nullptr;  // ensemble: members' tensor maps, passed to each launch
-  double n0;           // reference density of the stored deviations g = f - n0 w_i w_j
-  int64_t steps_done;
-  char err[512];
-  // ensembles
-  int kind = 0;                              // 0 solver, 1 ensemble, 2 member view of an ensemble
-  vlb_handle* parent = nullptr;              // view: its ensemble
-  int index = 0;                             // view: member index
-  int count = 0;                             // ensemble: members
-  vlb_handle** views = nullptr;              // ensemble: one view per member
-  vlb::EnsembleMember* d_members = nullptr;  // ensemble: device descriptors
-  int2* d_items[2] = {nullptr, nullptr};     // ensemble: work lists for tile rows 16 and 8
-  int nitems[2] = {0, 0};
-  int tile_rows = 0;                         // ensemble: autotuner's choice, 0 = not tuned yet
-  float tune_ms[2] = {0.0f, 0.0f};
-  cudaStream_t capture_stream = nullptr;
-  cudaGraphExec_t graph_1 = nullptr, graph_32 = nullptr;  // one step, 32 steps
-};
+// struct vlb_handle is defined in vlb_handle.cuh.
 
 namespace {
 
@@ -307,6 +272,7 @@ vlb_status totals_impl(vlb_handle* h) {
 
 vlb_status check_handle(vlb_handle* h, bool ensemble_ok = false) {
   if (!h) return fail(nullptr, VLB_ERR_ARG, "handle is NULL");
+  if (h->kind == 3) return fail(h, VLB_ERR_ARG, "surrogate handle: pass it to vlb_surrogate_advance");
   if (h->kind == 1 && !ensemble_ok)
     return fail(h, VLB_ERR_ARG, "ensemble handle: use vlb_ensemble_step, or a member view from vlb_ensemble_member");
   int dev = -1;
@@ -339,6 +305,8 @@ vlb_status sync_and_check(vlb_handle* h, const char* what, bool unstable_too) {
 }
 
 }  // namespace
+
+vlb_status vlb_internal_fail(vlb_handle* h, vlb_status st, const char* msg) { return fail(h, st, "%s", msg); }
 
 // Flags an unstable state: non-finite values or |u| > 2 in the diagnostic vector.
 __global__ void vlb_flag_kernel(const double* diag, int* flag) {
@@ -565,6 +533,7 @@ vlb_status vlb_create(const vlb_params* p, void* d_workspace, size_t bytes, void
 
 vlb_status vlb_destroy(vlb_handle* h) {
   if (!h || h->kind == 2) return VLB_OK;  // member views are owned by their ensemble
+  if (h->kind == 3 && h->sur_graph) cudaGraphExecDestroy(h->sur_graph);
   if (h->kind == 1) {
     if (h->graph_1) cudaGraphExecDestroy(h->graph_1);
     if (h->graph_32) cudaGraphExecDestroy(h->graph_32);

@@ -1,0 +1,67 @@
+// The handle behind the C ABI's opaque vlb_handle (internal to libvlb).  One struct serves the
+// four kinds of handle: a solver, an ensemble, a member view of an ensemble, and a surrogate.
+#pragma once
+
+#include "vlb_internal.cuh"
+
+struct vlb_handle {
+  vlb_params p;
+  cudaStream_t stream;
+  int device;
+  int64_t N;       // n_theta * n_phi
+  int64_t stride;  // elements between state arrays
+  size_t esize;    // 4 or 8
+  unsigned char* ws;
+  size_t ws_bytes;
+  void* U[3];          // U^n, U^(1), U^(2)
+  void* coefT;         // [NCOEF][n_theta] in state precision
+  double* coefD;       // [NCOEF][n_theta] FP64
+  double* staging;     // 17 N doubles
+  double* partials;    // totals_blocks() * 8
+  double* totals;      // 8 doubles (read-out)
+  double* diag;        // 8 doubles (last in-step diagnostic)
+  int* flag;           // device flag: diagnostics found an unstable state (1) or a bulk copy gave up (2)
+  vlb::StageMaps* maps = nullptr;  // FP32 UW3: tensor maps of the three stage inputs (NULL: per-thread copies)
+  vlb::EnsembleMaps* ens_maps = nullptr;  // ensemble: members' tensor maps, passed to each launch
+  double n0;           // reference density of the stored deviations g = f - n0 w_i w_j
+  int64_t steps_done;
+  char err[512];
+  // ensembles
+  int kind = 0;                              // 0 solver, 1 ensemble, 2 member view, 3 surrogate
+  vlb_handle* parent = nullptr;              // view: its ensemble
+  int index = 0;                             // view: member index
+  int count = 0;                             // ensemble: members
+  vlb_handle** views = nullptr;              // ensemble: one view per member
+  vlb::EnsembleMember* d_members = nullptr;  // ensemble: device descriptors
+  int2* d_items[2] = {nullptr, nullptr};     // ensemble: work lists for tile rows 16 and 8
+  int nitems[2] = {0, 0};
+  int tile_rows = 0;                         // ensemble: autotuner's choice, 0 = not tuned yet
+  float tune_ms[2] = {0.0f, 0.0f};
+  cudaStream_t capture_stream = nullptr;
+  cudaGraphExec_t graph_1 = nullptr, graph_32 = nullptr;  // one step, 32 steps
+  // surrogate (kind 3): the network, its buffers in the workspace and the state of the advance loop
+  int sur_H = 0, sur_W = 0, sur_window = 0;
+  double sur_r_over_R = 0.0;
+  float sur_s_n = 0.0f, sur_s_u = 0.0f, sur_g[4] = {1.0f, 1.0f, 1.0f, 1.0f};
+  void* sur_w = nullptr;       // the 8 layers' bf16 weights, concatenated
+  float* sur_b = nullptr;      // their FP32 biases, concatenated
+  void* sur_act[3] = {nullptr, nullptr, nullptr};  // input features (16 ch), two 64-channel buffers
+  float* sur_out = nullptr;    // last layer, FP32 16 channels
+  float* sur_snap = nullptr;   // snapshot of the solver, prediction, solver's check: FP32 [N][4]
+  float* sur_pred = nullptr;
+  float* sur_check = nullptr;
+  float* sur_norm = nullptr;   // 8 floats: input statistics and output scales
+  double* sur_cmp = nullptr;   // 4 doubles: comparison of prediction and check
+  double* sur_red = nullptr;   // reduction scratch
+  double* sur_sums = nullptr;  // 8 doubles
+  void* sur_good = nullptr;    // the last judged state of the bound solver
+  vlb_handle* sur_bound = nullptr;  // the solver the advance loop follows
+  double sur_conserve[2] = {0.0, 0.0};
+  int64_t sur_count = 0, sur_predicted = 0, sur_fallbacks = 0, sur_good_steps = 0;
+  int sur_solver_only = 0, sur_since_good = 0;
+  cudaGraphExec_t sur_graph = nullptr;  // one predicted window, replayed on the bound solver's stream
+  cudaStream_t sur_graph_stream = nullptr;
+};
+
+// Records msg as the last error of h (or of the calling thread when h is NULL) and returns st.
+vlb_status vlb_internal_fail(vlb_handle* h, vlb_status st, const char* msg);

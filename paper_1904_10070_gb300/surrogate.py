@@ -298,128 +298,54 @@ class Trainer:
 
 
 # ------------------------------------------------------------------------------------------------
-# Surrogate-accelerated stepping with the solver as fallback and judge
+# Surrogate-accelerated stepping with the solver as fallback and judge (in the library)
 # ------------------------------------------------------------------------------------------------
 
-class Advancer:
-    """Advances an FP32 solver by windows of `window` steps, most of them with the network.
+def export(trainer: Trainer):
+    """The trained network as vlb_surrogate_create takes it: (bf16 weights of all layers concatenated,
+    FP32 biases concatenated, s_n, s_u, g)."""
+    import torch
+    net = trainer.net
+    w = torch.cat([t.reshape(-1) for t in net.wb]).contiguous()
+    b = torch.cat([t.reshape(-1) for t in net.b32]).contiguous()
+    return w, b, trainer.s_n, trainer.s_u, list(trainer.g)
 
-    Every `check_every`-th window is a check: the network predicts the window, the solver runs it from
-    the same state, and the two phi fields are compared (vlb_snapshot_compare) by their relative L2
-    error ||phi_net - phi_solver||_2 / ||phi_solver||_2 (norm="l2") or relative L-infinity error
-    (norm="linf").  The solver's result is kept.  A check whose error exceeds `phi_tol` (or a
-    non-finite state) is a fallback: the state returns to the last checked one, the solver redoes the
-    windows since then and runs the next `check_every` windows alone.  A taken prediction (n', u',
-    phi') replaces the state by f + f^eq(n', u') - f^eq(n, u), keeping the non-equilibrium part of f
-    (it relaxes over tau / dt steps, many windows when tau >> dt), with the conserved totals
-    int n sqrt(g) and int phi sqrt(g) restored to their values at the start (vlb_set_snapshot).  Between checks nothing is read back to the host,
-    and a predicted window (snapshot, statistics, features, eight convolutions, restart) replays as
-    one CUDA graph when the solver runs on its own (non-default) stream.  Advancers that share a
-    Trainer share its network's activation buffers: run them one after another, with the streams
-    synchronised in between.
-    """
+
+class Advancer:
+    """Advances an FP32 solver by windows of `window` steps, most of them with the network, through the
+    library's vlb_surrogate_advance: every `check_every`-th window the solver judges the prediction by
+    the relative L2 (norm="l2") or relative L-infinity (norm="linf") error of phi against `phi_tol`,
+    keeping its own result, and rolls back and runs alone after a failed check (include/vlb.h has the
+    full contract).  The network is copied from the trainer when the Advancer is made."""
 
     def __init__(self, trainer: Trainer, solver: vlb.Solver, window: int = 50, check_every: int = 4,
                  phi_tol: float = 1e-2, norm: str = "l2", graph: bool = True):
-        import torch
         if solver.p.precision != vlb.FP32:
             raise ValueError("the surrogate advances FP32 solvers")
         if norm not in ("l2", "linf"):
             raise ValueError("norm must be 'l2' or 'linf'")
-        self.tr, self.s, self.window = trainer, solver, window
-        self.check_every, self.phi_tol, self.norm = check_every, phi_tol, norm
-        self.R = solver.p.R
-        self.stream = solver.stream
-        self.use_graph = graph and self.stream.cuda_stream != 0
-        self.graph = None
-        N = solver.p.n_theta * solver.p.n_phi
-        dev = "cuda"
-        with torch.cuda.stream(self.stream):
-            self.snap = torch.empty((N, 4), dtype=torch.float32, device=dev)
-            self.pred = torch.empty((N, 4), dtype=torch.float32, device=dev)
-            self.check = torch.empty((N, 4), dtype=torch.float32, device=dev)
-            self.norm8 = torch.empty(8, dtype=torch.float32, device=dev)
-            self.cmp = torch.empty(4, dtype=torch.float64, device=dev)
-            self.work = torch.empty(vlb.vlb_reduce_workspace_bytes(), dtype=torch.uint8, device=dev)
-            ptr, stride = vlb.vlb_state_device(solver.h)
-            off = ptr - solver.workspace.data_ptr()
-            self.state = solver.workspace[off:off + 18 * stride * 4]  # the 18 FP32 state arrays
-            self.good = torch.empty_like(self.state)
-        t = solver.totals()
-        self.conserve = (t[0], t[1])
-        self.solver_only = 0
-        self.since_good = 0
-        self.count = 0
-        self.predicted = 0
-        self.kinds = []
-        self.errors = []
-        self.errors_linf = []
+        self.s, self.window = solver, window
+        self.check_every, self.phi_tol, self.norm, self.use_graph = check_every, phi_tol, norm, graph
+        w, b, s_n, s_u, g = export(trainer)
+        self.sur = vlb.Surrogate(solver.p, w, b, s_n, s_u, g, window, stream=solver.stream)
+        self.kinds, self.errors, self.errors_linf = [], [], []
 
-    def _save(self):
-        self.good.copy_(self.state)
-        self.since_good = 0
-
-    def _predict_window(self):
-        vlb.vlb_get_snapshot(self.s.h, self.snap)
-        self.tr.predict(self.snap, self.R, self.norm8, self.pred)
-        vlb.vlb_set_snapshot(self.s.h, self.pred, self.conserve, keep_neq=True)
-
-    def _surrogate_window(self):
-        import torch
-        self.predicted += 1
-        if not self.use_graph or self.predicted == 1:  # the first one runs eagerly (module loading)
-            self._predict_window()
-            return
-        if self.graph is None:
-            self.graph = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(self.graph, stream=self.stream):
-                self._predict_window()
-        self.graph.replay()
-
-    def window_step(self) -> str:
-        import torch
-        with torch.cuda.stream(self.stream):
-            return self._window_step()
-
-    def _window_step(self) -> str:
-        s, w = self.s, self.window
-        if self.count == 0:
-            self._save()
-        self.count += 1
-        if self.solver_only > 0:
-            s.step(w)
-            self.solver_only -= 1
-            self.since_good += 1
-            if self.solver_only == 0:
-                self._save()
-            kind = "solver"
-        elif self.check_every > 0 and self.count % self.check_every == 0:
-            vlb.vlb_get_snapshot(s.h, self.snap)
-            self.tr.predict(self.snap, self.R, self.norm8, self.pred)
-            s.step(w)
-            vlb.vlb_get_snapshot(s.h, self.check)
-            vlb.vlb_snapshot_compare(self.pred.shape[0], self.pred, self.check, self.work, self.cmp, self.stream.cuda_stream)
-            dmax, bmax, d2, b2 = (float(x) for x in self.cmp.cpu())
-            e_inf = dmax / bmax if bmax > 0 else math.inf
-            e_2 = math.sqrt(d2 / b2) if b2 > 0 else math.inf
-            self.errors.append(e_2)
-            self.errors_linf.append(e_inf)
-            err = e_2 if self.norm == "l2" else e_inf
-            if err <= self.phi_tol:
-                self._save()
-                kind = "checked"
-            else:
-                self.state.copy_(self.good)
-                s.step(w * (self.since_good + 1))
-                self.solver_only = self.check_every
-                self._save()
-                kind = "fallback"
-        else:
-            self._surrogate_window()
-            self.since_good += 1
-            kind = "surrogate"
-        self.kinds.append(kind)
-        return kind
+    @property
+    def graph(self):
+        return True if self.sur.stats()["graph"] else None
 
     def advance(self, nwin: int):
-        return [self.window_step() for _ in range(nwin)]
+        kinds, errs, _ = self.sur.advance(self.s.h, nwin, self.check_every, self.phi_tol,
+                                          judge_linf=self.norm == "linf", graph=self.use_graph)
+        for k, (e2, einf) in zip(kinds, errs):
+            if k in ("checked", "fallback"):
+                self.errors.append(float(e2))
+                self.errors_linf.append(float(einf))
+        self.kinds += kinds
+        return kinds
+
+    def window_step(self) -> str:
+        return self.advance(1)[0]
+
+    def close(self):
+        self.sur.close()

@@ -29,9 +29,20 @@ EXPORTS = ["vlb_workspace_bytes", "vlb_max_stable_dt", "vlb_create", "vlb_destro
            "vlb_conv3x3_fwd", "vlb_conv3x3_flip", "vlb_conv3x3_wgrad_workspace_bytes", "vlb_conv3x3_bwd_weight",
            "vlb_reduce_workspace_bytes", "vlb_surrogate_norm", "vlb_surrogate_features", "vlb_surrogate_targets",
            "vlb_surrogate_apply", "vlb_snapshot_compare", "vlb_channel_sums", "vlb_mse_loss", "vlb_adam_step", "vlb_to_bf16",
-           "vlb_conv_status", "vlb_test_raise_flag"]
+           "vlb_conv_status", "vlb_test_raise_flag", "vlb_surrogate_workspace_bytes", "vlb_surrogate_create",
+           "vlb_surrogate_advance", "vlb_surrogate_stats"]
 
 NOALLOC_SCRATCH_BYTES = 24 * 1024 * 1024
+
+
+WINDOW_KINDS = {0: "surrogate", 1: "checked", 2: "fallback", 3: "solver"}
+SUR_JUDGE_LINF, SUR_NO_GRAPH = 1, 2
+
+
+class vlb_surrogate_net(ctypes.Structure):
+    _fields_ = [("weights_bf16", ctypes.c_void_p), ("biases", ctypes.c_void_p), ("s_n", ctypes.c_float),
+                ("s_u", ctypes.c_float), ("g", ctypes.c_float * 4), ("window", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class vlb_params(ctypes.Structure):
@@ -97,6 +108,13 @@ def lib() -> ctypes.CDLL:
     L.vlb_get_snapshot.argtypes, L.vlb_get_snapshot.restype = [P, P], I32
     L.vlb_set_snapshot.argtypes, L.vlb_set_snapshot.restype = [P, P, DP, I32], I32
     L.vlb_conv_status.argtypes, L.vlb_conv_status.restype = [P, I32], I32
+    L.vlb_surrogate_workspace_bytes.argtypes, L.vlb_surrogate_workspace_bytes.restype = [PP], S
+    L.vlb_surrogate_create.argtypes = [PP, ctypes.POINTER(vlb_surrogate_net), P, S, P, ctypes.POINTER(P)]
+    L.vlb_surrogate_create.restype = I32
+    L.vlb_surrogate_advance.argtypes = [P, P, I32, I32, ctypes.c_double, I32, ctypes.POINTER(I32), D,
+                                        ctypes.POINTER(I32)]
+    L.vlb_surrogate_advance.restype = I32
+    L.vlb_surrogate_stats.argtypes, L.vlb_surrogate_stats.restype = [P, ctypes.POINTER(I64)], I32
     L.vlb_test_raise_flag.argtypes, L.vlb_test_raise_flag.restype = [P, I32], I32
     L.vlb_conv3x3_fwd.argtypes = [I32, I32, I32, I32, P, P, P, P, I32, P, P, P]
     L.vlb_conv3x3_flip.argtypes = [I32, I32, P, P, P]
@@ -410,6 +428,55 @@ class Solver:
 
     def interface_length(self):
         return vlb_interface_length(self.h)
+
+    def close(self):
+        if self.h is not None:
+            vlb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Surrogate:
+    """A surrogate handle (vlb_surrogate_create) over a torch-allocated workspace: the network's
+    weights (a bf16 device tensor of all layers, concatenated) and biases (FP32), its input scales
+    and output ratios, for solvers with the grid of `geom`."""
+
+    def __init__(self, geom: vlb_params, weights_bf16, biases, s_n: float, s_u: float, g, window: int, stream=None):
+        import torch
+        self.geom = geom
+        self.nbytes = lib().vlb_surrogate_workspace_bytes(ctypes.byref(geom))
+        if self.nbytes == 0:
+            _check(VLB_ERR_ARG)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.workspace = torch.empty(self.nbytes, dtype=torch.uint8, device="cuda")
+        net = vlb_surrogate_net(weights_bf16=weights_bf16.data_ptr(), biases=biases.data_ptr(), s_n=float(s_n),
+                                s_u=float(s_u), g=(ctypes.c_float * 4)(*[float(x) for x in g]), window=int(window),
+                                reserved=0)
+        self.h = ctypes.c_void_p()
+        _check(lib().vlb_surrogate_create(ctypes.byref(geom), ctypes.byref(net),
+                                          ctypes.c_void_p(self.workspace.data_ptr()), self.nbytes,
+                                          ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self.h)))
+
+    def advance(self, solver_h, nwin: int, check_every: int, phi_tol: float, judge_linf=False, graph=True):
+        """Returns (kinds, errors, fallbacks): kinds as strings, errors an (nwin, 2) array of
+        (relative L2, relative L-infinity) phi errors of judged windows (NaN elsewhere)."""
+        kinds = (ctypes.c_int32 * max(nwin, 1))()
+        errs = np.empty((max(nwin, 1), 2))
+        fb = ctypes.c_int32()
+        opts = (SUR_JUDGE_LINF if judge_linf else 0) | (0 if graph else SUR_NO_GRAPH)
+        _check(lib().vlb_surrogate_advance(solver_h, self.h, nwin, check_every, float(phi_tol), opts, kinds,
+                                           _dptr(errs), ctypes.byref(fb)), self.h)
+        return [WINDOW_KINDS[kinds[i]] for i in range(nwin)], errs[:nwin], fb.value
+
+    def stats(self):
+        out = (ctypes.c_int64 * 4)()
+        _check(lib().vlb_surrogate_stats(self.h, out), self.h)
+        return {"windows": out[0], "predicted": out[1], "fallbacks": out[2], "graph": bool(out[3])}
 
     def close(self):
         if self.h is not None:
