@@ -260,8 +260,10 @@ def run_reference(args):
 
 
 def ensemble_measurement(steps: int = 60, seq_steps: int = 10):
-    """The 48-tori batched ensemble: graph-replayed batched launches vs the same members stepped one
-    after another with per-member launches (both timed with CUDA events on the ensemble's stream)."""
+    """The 48-tori ensemble: the autotuner's choice, then each execution mode at its best tile height --
+    one batched launch per stage (graph-replayed) and one persistent cooperative launch per block of
+    steps (grid barrier between stages) -- and the same members stepped one after another with
+    per-member launches.  All timed with CUDA events on the ensemble's stream."""
     import torch
     from paper_1904_10070_gb300 import inputs, vlb
     work = inputs.ensemble_workload(48)
@@ -273,30 +275,39 @@ def ensemble_measurement(steps: int = 60, seq_steps: int = 10):
     ens = vlb.Ensemble(params)
     for v, w in zip(ens.views, work):
         vlb.vlb_set_fields(v, w["rho"], w["ut"], w["up"], w["phi"])
-    ens.step(3)  # autotune + graph recording
     st = ens.stream
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(st)
-    ens.step(steps)
-    e1.record(st)
-    e1.synchronize()
-    ms = e0.elapsed_time(e1) / steps
-    e0.record(st)
-    for v in ens.views:
-        vlb.vlb_step(v, seq_steps)
-    e1.record(st)
-    e1.synchronize()
-    ms_seq = e0.elapsed_time(e1) / seq_steps
+
+    def timed(n, fn):
+        torch.cuda.synchronize()
+        e0.record(st)
+        fn(n)
+        e1.record(st)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    ens.step(3)  # autotune + graph recording
+    chosen = ens.config()
+    ms = timed(steps, ens.step)
+    per_mode = {}
+    for mode, name, rows in ((vlb.ENS_BATCHED, "batched", 16 if chosen["ms"][0] <= chosen["ms"][1] else 8),
+                             (vlb.ENS_PERSISTENT, "persistent", 16 if chosen["ms"][2] <= chosen["ms"][3] else 8)):
+        ens.configure(mode=mode, tile_rows=rows)
+        ens.step(3)
+        per_mode[name] = {"tile_rows": rows, "ms_per_step": timed(steps, ens.step)}
+    ms_seq = timed(seq_steps, lambda n: [vlb.vlb_step(v, n) for v in ens.views])
     nodes = sum(p.n_theta * p.n_phi for p in params)
-    rows = ens.tile_rows()
     ok = all(np.all(np.isfinite(vlb.vlb_get_totals(v))) for v in ens.views)
     ens.close()
     return {"members": 48, "nodes": nodes, "value": 16.0 * nodes / (ms * 1e-3), "unit": UNIT,
-            "ms_per_step": ms, "sequential_ms_per_step": ms_seq, "speedup_vs_sequential": ms_seq / ms,
-            "tile_rows": rows[0], "autotune_ms_16_8": [rows[1], rows[2]], "finite": ok,
-            "what": "48 tori, R/r in [1.3, 5], grids 64x128..512x1024, FP32 UW3, per-torus dt; one batched "
-                    "launch per stage replayed from a CUDA graph vs per-member launches"}
+            "ms_per_step": ms, "chosen": {"mode": chosen["mode"], "tile_rows": chosen["tile_rows"]},
+            "autotune_ms_stage0": {"batched16": chosen["ms"][0], "batched8": chosen["ms"][1],
+                                   "persistent16": chosen["ms"][2], "persistent8": chosen["ms"][3]},
+            "modes": per_mode, "sequential_ms_per_step": ms_seq, "speedup_vs_sequential": ms_seq / ms,
+            "finite": ok,
+            "what": "48 tori, R/r in [1.3, 5], grids 64x128..512x1024, FP32 UW3, per-torus dt; the autotuner's "
+                    "choice among batched launches per stage and one persistent cooperative launch (grid barrier "
+                    "between stages), 16- or 8-row tiles, vs per-member launches"}
 
 
 def surrogate_measurement(ntraj: int = 2000, pairs: int = 4, spacing: int = 400, start: int = 100, epochs: int = 3,

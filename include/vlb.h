@@ -161,12 +161,31 @@ vlb_status vlb_steps_done(const vlb_handle* h, int64_t* out);
  * h is NULL).  Never NULL; empty when there was none. */
 const char* vlb_last_error(const vlb_handle* h);
 
-/* ---- Ensembles: many tori in one batched launch per Runge-Kutta stage ----
+/* ---- Ensembles: many tori stepped together ----
  * Members are independent problems (own geometry, grid, time step, seed) in FP32 with UW3
- * advection and one common ch_mode.  Each stage of all members is one launch over a work list of
- * (member, tile) items; the per-step launch sequence is recorded into CUDA graphs (1 and 32
- * steps) on the first vlb_ensemble_step and replayed on the caller's stream afterwards.  The tile
- * height (16 or 8 theta rows) is chosen on that first call by timing both on the ensemble. */
+ * advection and one common ch_mode.  The tiles of all members form one work list of (member, tile)
+ * items, run in one of two ways:
+ *   - batched: each Runge-Kutta stage of all members is one launch over the work list;
+ *   - persistent: one cooperative launch runs whole steps; its CTAs (all resident at once) take
+ *     the items of a stage round-robin and meet at a grid barrier before the next stage.  A CTA
+ *     waits at the barrier for a bounded number of SM clock cycles; on expiry it raises the
+ *     ensemble's device flag and every CTA returns, so a lost CTA ends the launch with
+ *     VLB_ERR_TIMEOUT on the next synchronous call of a member view, never with a hang.
+ * The mode and the tile height (16 or 8 theta rows) are chosen on the first vlb_ensemble_step by
+ * timing the four candidates on the ensemble (or taken from vlb_ensemble_configure); the choice is
+ * cached per process and, if the environment variable VLB_AUTOTUNE_CACHE names a file, in that file
+ * (one JSON object per line, keyed by the members' grids, ch_mode and the device's SM count).  The
+ * per-step launch sequence is then recorded into CUDA graphs (1 and 32 steps) and replayed on the
+ * caller's stream; a launch that cannot be captured runs eagerly instead. */
+enum { VLB_ENS_AUTO = 0, VLB_ENS_BATCHED = 1, VLB_ENS_PERSISTENT = 2 };
+typedef struct {
+  int32_t mode;            /* VLB_ENS_AUTO (timed and chosen), VLB_ENS_BATCHED or VLB_ENS_PERSISTENT */
+  int32_t tile_rows;       /* 0 (chosen with the mode), 16 or 8 */
+  int32_t ctas_per_sm;     /* persistent launches: 0 = as many as fit, else 1 .. that limit */
+  int32_t test_skip_cta;   /* -1; a CTA index of the persistent launch that skips its barrier arrivals
+                              (a test of the timeout path: the launch then ends with the flag raised) */
+  int64_t barrier_budget;  /* SM clock cycles a CTA waits at a grid barrier; 0 = 2^31 (about a second) */
+} vlb_ensemble_config;
 
 /* Workspace bytes for an ensemble of `count` members p[0..count-1]; 0 if invalid. */
 size_t vlb_ensemble_workspace_bytes(const vlb_params* p, int32_t count);
@@ -186,9 +205,18 @@ vlb_status vlb_ensemble_step(vlb_handle* h, int64_t nsteps);
  * is a no-op, vlb_destroy on the ensemble releases them. */
 vlb_status vlb_ensemble_member(vlb_handle* h, int32_t idx, vlb_handle** view);
 
-/* The autotuner's tile height (16 or 8; 0 before the first vlb_ensemble_step) and the measured
- * time of one first-stage launch for each candidate (ms; either pointer may be NULL). */
+/* The chosen tile height (16 or 8; 0 before the first vlb_ensemble_step) and the autotuner's time of
+ * one batched first-stage pass for 16- and 8-row tiles (ms; either pointer may be NULL). */
 vlb_status vlb_ensemble_tile_rows(const vlb_handle* h, int32_t* rows, float* ms16, float* ms8);
+
+/* Request a mode, tile height, persistent CTAs per SM, barrier budget or the skip test hook (fields
+ * left 0 are chosen by timing on the next vlb_ensemble_step).  Synchronises the stream; the next
+ * step re-chooses and re-records its graphs. */
+vlb_status vlb_ensemble_configure(vlb_handle* h, const vlb_ensemble_config* c);
+/* The execution in use (mode 0 before the first step) and the autotuner's times of one first-stage
+ * pass per candidate, ms[4] = {batched 16 rows, batched 8, persistent 16, persistent 8} (0 = not
+ * timed; ms may be NULL). */
+vlb_status vlb_ensemble_get_config(const vlb_handle* h, vlb_ensemble_config* c, float ms[4]);
 
 /* ---- Snapshots: device FP32 [N][4] = (phi, n, u_theta, u_phi), node-major ----
  * vlb_get_snapshot: moments of the state (Sec. 2.3) and phi; asynchronous on the handle's stream.

@@ -13,7 +13,10 @@
 
 #include <algorithm>
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "vlb_handle.cuh"
@@ -697,7 +700,7 @@ namespace {
 constexpr int kTileRows[2] = {16, 8};
 
 struct EnsLayout {
-  size_t off_staging, off_partials, off_totals, off_diag, off_flag, off_members, off_items[2];
+  size_t off_staging, off_partials, off_totals, off_diag, off_flag, off_bar, off_members, off_items[2];
   std::vector<size_t> off_member;  // start of member m's region: coefT, coefD, U0, U1, U2
   std::vector<Layout> member;
   int nitems[2];
@@ -738,6 +741,8 @@ EnsLayout ens_layout(const vlb_params* p, int count) {
   off = align_up(off + 64, 256);
   E.off_flag = off;
   off = align_up(off + 256, 256);
+  E.off_bar = off;
+  off = align_up(off + 256, 256);
   E.off_members = off;
   off = align_up(off + sizeof(vlb::EnsembleMember) * count, 256);
   for (int k = 0; k < 2; ++k) {
@@ -754,57 +759,209 @@ EnsLayout ens_layout(const vlb_params* p, int count) {
   return E;
 }
 
-vlb_status ens_launch_step(vlb_handle* h, int rows_idx, cudaStream_t st) {
-  for (int stage = 0; stage < 3; ++stage)
-    VLB_CUDA(h, vlb::launch_ensemble_stage(h->d_members, h->d_items[rows_idx], h->nitems[rows_idx], stage,
-                                          kTileRows[rows_idx], h->p.ch_mode, h->flag, st, h->ens_maps));
+constexpr long long kBarrierBudget = 1ll << 31;  // SM clock cycles, about a second at 2 GHz
+
+// nsteps steps of every member in the chosen mode (rows_idx: 0 = 16-row tiles, 1 = 8-row tiles).
+vlb_status ens_launch_steps(vlb_handle* h, int mode, int rows_idx, int nsteps, cudaStream_t st) {
+  if (mode == 2) {
+    VLB_CUDA(h, vlb::launch_ensemble_persistent(h->d_members, h->d_items[rows_idx], h->nitems[rows_idx], nsteps, 0,
+                                                kTileRows[rows_idx], h->p.ch_mode, h->ens_bar, h->flag,
+                                                h->ens_budget > 0 ? h->ens_budget : kBarrierBudget, h->ens_skip,
+                                                h->ens_ctas, st, h->ens_maps, &h->ens_grid));
+    return VLB_OK;
+  }
+  for (int n = 0; n < nsteps; ++n)
+    for (int stage = 0; stage < 3; ++stage)
+      VLB_CUDA(h, vlb::launch_ensemble_stage(h->d_members, h->d_items[rows_idx], h->nitems[rows_idx], stage,
+                                            kTileRows[rows_idx], h->p.ch_mode, h->flag, st, h->ens_maps));
   return VLB_OK;
 }
 
-// Autotuner: times the first Runge-Kutta stage (which writes only the scratch U^(1)) with each tile
-// height and keeps the faster one.
-vlb_status ens_autotune(vlb_handle* h) {
+// One timing of a candidate: three passes of the first Runge-Kutta stage (which writes only the
+// scratch U^(1), so the state does not advance), after a warm-up pass.  Batched: three launches;
+// persistent: one launch with grid barriers between the passes.
+vlb_status ens_time(vlb_handle* h, int mode, int rows_idx, float* ms) {
   cudaEvent_t e0, e1;
   VLB_CUDA(h, cudaEventCreate(&e0));
   VLB_CUDA(h, cudaEventCreate(&e1));
-  float best = 1e30f;
-  for (int k = 0; k < 2; ++k) {
-    VLB_CUDA(h, vlb::launch_ensemble_stage(h->d_members, h->d_items[k], h->nitems[k], 0, kTileRows[k],
-                                          h->p.ch_mode, h->flag, h->stream, h->ens_maps));  // warm-up
-    VLB_CUDA(h, cudaEventRecord(e0, h->stream));
-    for (int r = 0; r < 3; ++r)
-      VLB_CUDA(h, vlb::launch_ensemble_stage(h->d_members, h->d_items[k], h->nitems[k], 0, kTileRows[k],
-                                            h->p.ch_mode, h->flag, h->stream, h->ens_maps));
-    VLB_CUDA(h, cudaEventRecord(e1, h->stream));
-    VLB_CUDA(h, cudaEventSynchronize(e1));
-    float ms = 0.0f;
-    VLB_CUDA(h, cudaEventElapsedTime(&ms, e0, e1));
-    h->tune_ms[k] = ms / 3.0f;
-    if (ms < best) {
-      best = ms;
-      h->tile_rows = kTileRows[k];
+  auto pass = [&](int reps) -> cudaError_t {
+    if (mode == 2)
+      return vlb::launch_ensemble_persistent(h->d_members, h->d_items[rows_idx], h->nitems[rows_idx], reps, 1,
+                                             kTileRows[rows_idx], h->p.ch_mode, h->ens_bar, h->flag, kBarrierBudget,
+                                             -1, h->ens_ctas, h->stream, h->ens_maps, nullptr);
+    for (int r = 0; r < reps; ++r) {
+      cudaError_t e = vlb::launch_ensemble_stage(h->d_members, h->d_items[rows_idx], h->nitems[rows_idx], 0,
+                                                 kTileRows[rows_idx], h->p.ch_mode, h->flag, h->stream, h->ens_maps);
+      if (e != cudaSuccess) return e;
     }
-  }
+    return cudaSuccess;
+  };
+  VLB_CUDA(h, pass(1));
+  VLB_CUDA(h, cudaEventRecord(e0, h->stream));
+  VLB_CUDA(h, pass(3));
+  VLB_CUDA(h, cudaEventRecord(e1, h->stream));
+  VLB_CUDA(h, cudaEventSynchronize(e1));
+  float t = 0.0f;
+  VLB_CUDA(h, cudaEventElapsedTime(&t, e0, e1));
+  *ms = t / 3.0f;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return VLB_OK;
 }
 
-vlb_status ens_capture(vlb_handle* h, int rows_idx, int steps, cudaGraphExec_t* out) {
+// ---- autotune cache: one JSON object per line, keyed by the members' grids, ch_mode and SM count.
+// The file is VLB_AUTOTUNE_CACHE if that is set; every process also keeps its own entries.
+struct EnsChoice {
+  int mode, rows, ctas;
+  float ms[4];
+};
+std::mutex g_tune_mu;
+std::map<std::string, EnsChoice> g_tune;
+
+std::string ens_key(const vlb_handle* h, int sms) {
+  uint64_t x = 1469598103934665603ull;  // FNV-1a over the members' grids
+  auto mix = [&](uint64_t v) {
+    for (int b = 0; b < 8; ++b) {
+      x ^= (v >> (8 * b)) & 0xFF;
+      x *= 1099511628211ull;
+    }
+  };
+  mix((uint64_t)h->count);
+  mix((uint64_t)h->p.ch_mode);
+  for (int m = 0; m < h->count; ++m) {
+    mix((uint64_t)h->views[m]->p.n_theta);
+    mix((uint64_t)h->views[m]->p.n_phi);
+  }
+  char buf[64];
+  snprintf(buf, sizeof buf, "%016llx-%d", (unsigned long long)x, sms);
+  return buf;
+}
+
+bool cache_lookup(const std::string& key, EnsChoice* out) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tune.find(key);
+  if (it != g_tune.end()) {
+    *out = it->second;
+    return true;
+  }
+  const char* path = getenv("VLB_AUTOTUNE_CACHE");
+  if (!path || !*path) return false;
+  FILE* fh = fopen(path, "r");
+  if (!fh) return false;
+  char line[512];
+  bool found = false;
+  while (fgets(line, sizeof line, fh)) {
+    char k[64];
+    EnsChoice c;
+    int sms = 0, members = 0;
+    if (sscanf(line,
+               "{\"key\": \"%63[^\"]\", \"kind\": \"ensemble\", \"sms\": %d, \"members\": %d, \"mode\": %d, "
+               "\"tile_rows\": %d, \"ctas_per_sm\": %d, \"ms\": [%f, %f, %f, %f]}",
+               k, &sms, &members, &c.mode, &c.rows, &c.ctas, &c.ms[0], &c.ms[1], &c.ms[2], &c.ms[3]) == 10 &&
+        key == k && (c.mode == 1 || c.mode == 2) && (c.rows == 16 || c.rows == 8)) {
+      *out = c;  // the last entry for a key wins
+      found = true;
+    }
+  }
+  fclose(fh);
+  if (found) g_tune[key] = *out;
+  return found;
+}
+
+void cache_store(const std::string& key, const EnsChoice& c, int sms, int members) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune[key] = c;
+  const char* path = getenv("VLB_AUTOTUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* fh = fopen(path, "a");
+  if (!fh) return;  // an unwritable cache only costs a re-tune
+  fprintf(fh,
+          "{\"key\": \"%s\", \"kind\": \"ensemble\", \"sms\": %d, \"members\": %d, \"mode\": %d, \"tile_rows\": %d, "
+          "\"ctas_per_sm\": %d, \"ms\": [%.6f, %.6f, %.6f, %.6f]}\n",
+          key.c_str(), sms, members, c.mode, c.rows, c.ctas, c.ms[0], c.ms[1], c.ms[2], c.ms[3]);
+  fclose(fh);
+}
+
+// Chooses the execution of the ensemble: the requested mode and tile height, or the fastest of
+// batched and persistent launches with 16- and 8-row tiles (cached).
+vlb_status ens_choose(vlb_handle* h) {
+  int dev = 0, sms = 0;
+  VLB_CUDA(h, cudaGetDevice(&dev));
+  VLB_CUDA(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  h->ens_ctas = h->ens_req_ctas;
+  if (h->ens_req_mode != 0 && h->ens_req_rows != 0) {
+    h->ens_mode = h->ens_req_mode;
+    h->tile_rows = h->ens_req_rows;
+    return VLB_OK;
+  }
+  const std::string key = ens_key(h, sms);
+  EnsChoice c;
+  const bool any = h->ens_req_mode == 0 && h->ens_req_rows == 0 && h->ens_req_ctas == 0;
+  if (any && cache_lookup(key, &c)) {
+    h->ens_mode = c.mode;
+    h->tile_rows = c.rows;
+    h->ens_ctas = c.ctas;
+    for (int k = 0; k < 4; ++k) h->ens_ms[k] = c.ms[k];
+    h->tune_ms[0] = c.ms[0];
+    h->tune_ms[1] = c.ms[1];
+    h->ens_from_cache = 1;
+    return VLB_OK;
+  }
+  float best = 1e30f;
+  for (int mode = 1; mode <= 2; ++mode)
+    for (int k = 0; k < 2; ++k) {
+      float& ms = h->ens_ms[2 * (mode - 1) + k];
+      ms = 0.0f;
+      if ((h->ens_req_mode && h->ens_req_mode != mode) || (h->ens_req_rows && h->ens_req_rows != kTileRows[k]))
+        continue;
+      vlb_status st = ens_time(h, mode, k, &ms);
+      if (st) return st;
+      if (ms < best) {
+        best = ms;
+        h->ens_mode = mode;
+        h->tile_rows = kTileRows[k];
+      }
+    }
+  h->tune_ms[0] = h->ens_ms[0];
+  h->tune_ms[1] = h->ens_ms[1];
+  if (any) {
+    c.mode = h->ens_mode;
+    c.rows = h->tile_rows;
+    c.ctas = h->ens_ctas;
+    for (int k = 0; k < 4; ++k) c.ms[k] = h->ens_ms[k];
+    cache_store(key, c, sms, h->count);
+  }
+  return VLB_OK;
+}
+
+vlb_status ens_capture(vlb_handle* h, int steps, cudaGraphExec_t* out) {
+  const int k = h->tile_rows == kTileRows[0] ? 0 : 1;
   cudaGraph_t g = nullptr;
   VLB_CUDA(h, cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
-  vlb_status st = VLB_OK;
-  for (int n = 0; n < steps && st == VLB_OK; ++n) st = ens_launch_step(h, rows_idx, h->capture_stream);
+  vlb_status st = ens_launch_steps(h, h->ens_mode, k, steps, h->capture_stream);
   cudaError_t e = cudaStreamEndCapture(h->capture_stream, &g);
-  if (st != VLB_OK) {
+  if (st != VLB_OK || e != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
-    return st;
+    cudaGetLastError();  // a launch that cannot be captured is replayed eagerly instead
+    h->ens_graphs = false;
+    *out = nullptr;
+    return VLB_OK;
   }
-  if (e != cudaSuccess) return fail(h, VLB_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
   e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
-  if (e != cudaSuccess) return fail(h, VLB_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    h->ens_graphs = false;
+    *out = nullptr;
+  }
   return VLB_OK;
+}
+
+void ens_drop_graphs(vlb_handle* h) {
+  if (h->graph_1) cudaGraphExecDestroy(h->graph_1);
+  if (h->graph_32) cudaGraphExecDestroy(h->graph_32);
+  h->graph_1 = h->graph_32 = nullptr;
+  h->ens_graphs = true;
 }
 
 }  // namespace
@@ -844,6 +1001,7 @@ vlb_status vlb_ensemble_create(const vlb_params* p, int32_t count, void* d_works
   h->totals = (double*)(ws + E.off_totals);
   h->diag = (double*)(ws + E.off_diag);
   h->flag = (int*)(ws + E.off_flag);
+  h->ens_bar = (unsigned*)(ws + E.off_bar);
   h->d_members = (vlb::EnsembleMember*)(ws + E.off_members);
   for (int k = 0; k < 2; ++k) {
     h->d_items[k] = (int2*)(ws + E.off_items[k]);
@@ -945,6 +1103,7 @@ vlb_status vlb_ensemble_create(const vlb_params* p, int32_t count, void* d_works
     e = cudaMemcpyAsync(h->d_items[k], items[k].data(), sizeof(int2) * items[k].size(), cudaMemcpyHostToDevice,
                         h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->ens_bar, 0, 256, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
@@ -962,21 +1121,67 @@ vlb_status vlb_ensemble_step(vlb_handle* h, int64_t nsteps) {
   if (nsteps < 0) return fail(h, VLB_ERR_ARG, "nsteps must be >= 0");
   if (nsteps == 0) return VLB_OK;
   int64_t left = nsteps;
-  if (!h->graph_1) {
-    // first call: choose the tile height, take one step eagerly (every kernel variant is then set
-    // up outside any capture), and record the 1-step and 32-step graphs
-    if ((st = ens_autotune(h))) return st;
+  if (!h->ens_mode) {
+    // first call (or after vlb_ensemble_configure): choose the execution, take one step eagerly (every
+    // kernel variant is then set up outside any capture), and record the 1-step and 32-step graphs
+    if ((st = ens_choose(h))) return st;
     const int k = h->tile_rows == kTileRows[0] ? 0 : 1;
-    if ((st = ens_launch_step(h, k, h->stream))) return st;
+    if ((st = ens_launch_steps(h, h->ens_mode, k, 1, h->stream))) return st;
     VLB_CUDA(h, cudaStreamSynchronize(h->stream));
     --left;
-    if ((st = ens_capture(h, k, 1, &h->graph_1))) return st;
-    if ((st = ens_capture(h, k, 32, &h->graph_32))) return st;
+    ens_drop_graphs(h);
+    if ((st = ens_capture(h, 1, &h->graph_1))) return st;
+    if (h->ens_graphs && (st = ens_capture(h, 32, &h->graph_32))) return st;
   }
-  for (; left >= 32; left -= 32) VLB_CUDA(h, cudaGraphLaunch(h->graph_32, h->stream));
-  for (; left > 0; --left) VLB_CUDA(h, cudaGraphLaunch(h->graph_1, h->stream));
+  const int k = h->tile_rows == kTileRows[0] ? 0 : 1;
+  if (h->ens_graphs && h->graph_1 && h->graph_32) {
+    for (; left >= 32; left -= 32) VLB_CUDA(h, cudaGraphLaunch(h->graph_32, h->stream));
+    for (; left > 0; --left) VLB_CUDA(h, cudaGraphLaunch(h->graph_1, h->stream));
+  } else {
+    while (left > 0) {
+      const int chunk = (int)std::min<int64_t>(left, 256);
+      if ((st = ens_launch_steps(h, h->ens_mode, k, chunk, h->stream))) return st;
+      left -= chunk;
+    }
+  }
   h->steps_done += nsteps;
   for (int m = 0; m < h->count; ++m) h->views[m]->steps_done += nsteps;
+  return VLB_OK;
+}
+
+vlb_status vlb_ensemble_configure(vlb_handle* h, const vlb_ensemble_config* c) {
+  if (!h || !c) return fail(h, VLB_ERR_ARG, "vlb_ensemble_configure: NULL argument");
+  if (h->kind != 1) return fail(h, VLB_ERR_ARG, "not an ensemble handle");
+  if (c->mode < VLB_ENS_AUTO || c->mode > VLB_ENS_PERSISTENT)
+    return fail(h, VLB_ERR_ARG, "vlb_ensemble_configure: mode must be VLB_ENS_AUTO, _BATCHED or _PERSISTENT");
+  if (c->tile_rows != 0 && c->tile_rows != 16 && c->tile_rows != 8)
+    return fail(h, VLB_ERR_ARG, "vlb_ensemble_configure: tile_rows must be 0, 16 or 8");
+  if (c->ctas_per_sm < 0 || c->ctas_per_sm > 32 || c->test_skip_cta < -1 || c->barrier_budget < 0)
+    return fail(h, VLB_ERR_ARG, "vlb_ensemble_configure: bad ctas_per_sm, test_skip_cta or barrier_budget");
+  vlb_status st = check_handle(h, true);
+  if (st) return st;
+  VLB_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->ens_req_mode = c->mode;
+  h->ens_req_rows = c->tile_rows;
+  h->ens_req_ctas = c->ctas_per_sm;
+  h->ens_skip = c->test_skip_cta;
+  h->ens_budget = c->barrier_budget;
+  h->ens_mode = 0;  // re-chosen (and the graphs re-recorded) by the next vlb_ensemble_step
+  h->ens_from_cache = 0;
+  ens_drop_graphs(h);
+  return VLB_OK;
+}
+
+vlb_status vlb_ensemble_get_config(const vlb_handle* h, vlb_ensemble_config* c, float ms[4]) {
+  if (!h || !c) return fail(const_cast<vlb_handle*>(h), VLB_ERR_ARG, "vlb_ensemble_get_config: NULL argument");
+  if (h->kind != 1) return fail(const_cast<vlb_handle*>(h), VLB_ERR_ARG, "not an ensemble handle");
+  c->mode = h->ens_mode;
+  c->tile_rows = h->tile_rows;
+  c->ctas_per_sm = h->ens_ctas;
+  c->test_skip_cta = h->ens_skip;
+  c->barrier_budget = h->ens_budget > 0 ? h->ens_budget : kBarrierBudget;
+  if (ms)
+    for (int k = 0; k < 4; ++k) ms[k] = h->ens_ms[k];
   return VLB_OK;
 }
 

@@ -39,6 +39,16 @@ struct vlb_handle {
   float tune_ms[2] = {0.0f, 0.0f};
   cudaStream_t capture_stream = nullptr;
   cudaGraphExec_t graph_1 = nullptr, graph_32 = nullptr;  // one step, 32 steps
+  // ensemble execution: mode 1 = one batched launch per stage, 2 = one persistent cooperative launch
+  // per block of steps (grid barrier between stages); 0 = not chosen yet
+  int ens_mode = 0, ens_ctas = 0, ens_grid = 0;
+  int ens_req_mode = 0, ens_req_rows = 0, ens_req_ctas = 0;  // requested by vlb_ensemble_configure (0 = tune)
+  int ens_skip = -1;                 // test hook: a persistent CTA that skips its barrier arrivals
+  long long ens_budget = 0;          // grid-barrier budget in SM cycles (0 = default)
+  unsigned* ens_bar = nullptr;       // grid barrier: arrival counter, generation
+  float ens_ms[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // autotuner: batched 16 / 8, persistent 16 / 8
+  int ens_from_cache = 0;
+  bool ens_graphs = true;            // false if the launch could not be captured (replayed eagerly)
   // surrogate (kind 3): the network, its buffers in the workspace and the state of the advance loop
   int sur_H = 0, sur_W = 0, sur_window = 0;
   double sur_r_over_R = 0.0;

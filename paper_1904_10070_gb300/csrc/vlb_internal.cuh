@@ -108,6 +108,15 @@ struct EnsembleMaps {
 // err: the ensemble's device flag, raised (2) if a bounded wait on a bulk copy gives up.
 cudaError_t launch_ensemble_stage(const EnsembleMember* members, const int2* items, int nitems, int stage,
                                   int tile_rows, int ch_mode, int* err, cudaStream_t s, const EnsembleMaps* maps);
+// Persistent ensemble: one cooperative launch over the same work list runs nsteps steps (with only0,
+// nsteps passes of the first stage alone), with a grid barrier between stages that gives up after
+// `budget` SM cycles and raises err (2).  bar: two unsigned words in device memory (arrival counter,
+// generation).  skip_cta >= 0 makes that CTA skip its arrivals (a test of the timeout path).
+// ctas_per_sm 0 = the occupancy limit; *grid_out = the grid used.
+cudaError_t launch_ensemble_persistent(const EnsembleMember* members, const int2* items, int nitems, int nsteps,
+                                       int only0, int tile_rows, int ch_mode, unsigned* bar, int* err, long long budget,
+                                       int skip_cta, int ctas_per_sm, cudaStream_t s, const EnsembleMaps* maps,
+                                       int* grid_out);
 // maps: tensor maps for this stage's fin / f0 (FP32 UW3 only), or NULL for per-thread copies.
 template <typename T>
 cudaError_t launch_stage(const StageArgs<T>& a, int advection, int ch_mode, cudaStream_t s,

@@ -791,9 +791,12 @@ __device__ __forceinline__ void tile_body(const StageArgs<T>& a, const VConst<T>
 // Steps 1-3 for an interior tile (box inside the grid, no wrap-around) of the FP32 UW3 pair path,
 // with the box and the U^n tile staged by two tensor-map copies issued by one thread and
 // completing on two mbarriers.  The layout in shared memory is the one issue_box / issue_u0 produce.
+// A persistent CTA (which stages many tiles) initialises the two mbarriers once and passes init =
+// false with the parity of each barrier's current phase.
 template <typename L, int CH, bool F0>
 __device__ __forceinline__ void tile_body_tma(const StageArgs<float>& a, const VConst<float>& vc, float* sm, int tid,
-                                              int q0, int s0, const CUtensorMap* tmb, const CUtensorMap* tmu) {
+                                              int q0, int s0, const CUtensorMap* tmb, const CUtensorMap* tmu,
+                                              bool init = true, unsigned ph_box = 0, unsigned ph_u0 = 0) {
   constexpr unsigned BOX_BYTES = sizeof(float) * L::NST * L::BQ * L::BS;
   constexpr unsigned U0_BYTES = sizeof(float) * L::NST * L::TQ * TS;
   static_assert((L::BOX_OFF * sizeof(float)) % 128 == 0 && (L::U0_OFF * sizeof(float)) % 128 == 0,
@@ -802,12 +805,14 @@ __device__ __forceinline__ void tile_body_tma(const StageArgs<float>& a, const V
   float* box = sm + L::BOX_OFF;
   float* co = sm + L::CO_OFF;
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L::MB_OFF);
-  if (tid == 0) {
-    mbar_init(bar, 1);
-    mbar_init(bar + 1, 1);
-    fence_mbar_init();
+  if (init) {
+    if (tid == 0) {
+      mbar_init(bar, 1);
+      mbar_init(bar + 1, 1);
+      fence_mbar_init();
+    }
+    __syncthreads();
   }
-  __syncthreads();
   pdl_wait();
   issue_co<L>(a, co, q0, tid);
   cp_async_commit();
@@ -829,21 +834,21 @@ __device__ __forceinline__ void tile_body_tma(const StageArgs<float>& a, const V
     }
   }
   cp_async_wait<0>();
-  bool ok = mbar_wait(bar, 0);
+  bool ok = mbar_wait(bar, ph_box);
   if (__syncthreads_or(!ok)) {  // a copy did not land: flag it, let the copies settle, skip the tile
     if (tid == 0) {
       if (a.err) atomicExch(a.err, 2);
-      mbar_wait(bar, 0);
-      if (F0) mbar_wait(bar + 1, 0);
+      mbar_wait(bar, ph_box);
+      if (F0) mbar_wait(bar + 1, ph_u0);
     }
     return;
   }
   phase2_pair<L>(a, vc, box, co, sm, tid);
-  ok = F0 ? mbar_wait(bar + 1, 0) : true;
+  ok = F0 ? mbar_wait(bar + 1, ph_u0) : true;
   if (__syncthreads_or(!ok)) {
     if (tid == 0) {
       if (a.err) atomicExch(a.err, 2);
-      mbar_wait(bar + 1, 0);
+      mbar_wait(bar + 1, ph_u0);
     }
     return;
   }
@@ -930,6 +935,148 @@ __global__ void __launch_bounds__(TQR * (TS / 2)) ensemble_stage_kernel(const En
     }
   }
   tile_body<L, float, VLB_UW3, CH, F0, 2>(a, vc, sm, threadIdx.x, q0, s0);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Persistent ensemble: one cooperative launch runs whole steps.  Its CTAs (all resident at once)
+// take the work items of a stage round-robin and meet at a grid barrier before the next stage.
+// The barrier is a counter and a generation word in global memory; a CTA waits for the generation
+// to change for at most `budget` SM clock cycles.  On expiry it raises the ensemble's flag (2), and
+// every CTA that sees the flag raised while waiting returns, so a CTA that never arrives (a lost
+// CTA, or the test hook skip_cta) ends the launch with an error status instead of a hang.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_volatile_i32(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
+// ordering between this thread's generic-proxy accesses and later bulk (async-proxy) copies
+__device__ __forceinline__ void fence_proxy_async_all() { asm volatile("fence.proxy.async;\n" ::: "memory"); }
+
+// bar[0]: arrivals, bar[1]: generation.  Returns false if the barrier gave up (flag raised).
+__device__ bool grid_barrier(unsigned* bar, int* err, long long budget, bool skip, int* s_ok) {
+  fence_proxy_async_all();  // this thread's stores of the stage, before the next stage's bulk copies
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned g = ld_acquire_u32(bar + 1);  // the generation cannot change before this CTA arrives
+    __threadfence();                              // the CTA's stores (ordered by the CTA barrier) first
+    if (!skip && atomicAdd(bar, 1u) + 1u == gridDim.x) {
+      atomicExch(bar, 0u);
+      st_release_u32(bar + 1, g + 1u);
+    }
+    const long long t0 = clock64();
+    while (ld_acquire_u32(bar + 1) == g) {
+      if (ld_volatile_i32(err) == 2) {  // another CTA gave up
+        ok = 0;
+        break;
+      }
+      if (clock64() - t0 > budget) {
+        atomicCAS(err, 0, 2);
+        atomicCAS(err, 1, 2);
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+    fence_proxy_async_all();  // the other CTAs' stores, before this CTA's bulk copies read them
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+__device__ __forceinline__ StageArgs<float> member_args(const EnsembleMember& d, int stage, int* err) {
+  StageArgs<float> a;
+  a.fin = d.U[stage == 0 ? 0 : stage];  // stage 0 reads U^n, 1 reads U^(1), 2 reads U^(2)
+  a.f0 = stage == 0 ? nullptr : d.U[0];
+  a.fout = d.U[stage == 2 ? 0 : stage + 1];
+  a.coef = d.coef;
+  a.nt = d.nt;
+  a.ns = d.ns;
+  a.stride = d.stride;
+  a.b = stage == 0 ? 1.0f : (stage == 1 ? 0.25f : 2.0f / 3.0f);
+  a.dt = d.dt;
+  a.inv_tau = d.inv_tau;
+  a.M = d.M;
+  a.A = d.A;
+  a.kappa = d.kappa;
+  a.gt = d.gt;
+  a.n0 = d.n0;
+  a.err = err;
+  a.ahead = 0;
+  return a;
+}
+
+// nsteps whole steps, or with only0 nsteps passes of the first stage alone (which writes only the
+// scratch U^(1), so the autotuner can time it without advancing the state).
+template <int TQR, int CH>
+__global__ void __launch_bounds__(TQR * (TS / 2), TQR == 16 ? 2 : 3) ensemble_persistent_kernel(
+    const EnsembleMember* members, const int2* items, int nitems, int nsteps, int only0, unsigned* bar, int* err,
+    long long budget, int skip_cta, VConst<float> vc, const __grid_constant__ EnsembleMaps maps) {
+  using L = EnsLay<TQR>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ int s_ok;
+  float* sm = reinterpret_cast<float*>(smem_raw);
+  const int tid = threadIdx.x;
+  if (TQR == 16 && tid == 0) {
+    uint64_t* mb = reinterpret_cast<uint64_t*>(sm + L::MB_OFF);
+    mbar_init(mb, 1);
+    mbar_init(mb + 1, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  unsigned ph_box = 0, ph_u0 = 0;
+  const bool skip = (int)blockIdx.x == skip_cta;
+  bool first = true;
+  for (int n = 0; n < nsteps; ++n) {
+    for (int stage = 0; stage <= (only0 ? 0 : 2); ++stage) {
+      if (!first && !grid_barrier(bar, err, budget, skip, &s_ok)) return;
+      first = false;
+      for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+        fence_proxy_async_all();  // the previous tile's shared-memory reads, before new copies land
+        __syncthreads();
+        const int2 it = items[w];
+        const EnsembleMember& d = members[it.x];
+        const StageArgs<float> a = member_args(d, stage, err);
+        const int tiles_s = (d.ns + TS - 1) / TS;
+        const int q0 = (it.y / tiles_s) * TQR, s0 = (it.y % tiles_s) * TS;
+        bool tma = false;
+        if constexpr (TQR == 16) {
+          if (tid == 0 && w + (int)gridDim.x < nitems) {  // this CTA's next tile, into L2
+            const int2 nx = items[w + gridDim.x];
+            const EnsembleMember& e = members[nx.x];
+            const int ts = (e.ns + TS - 1) / TS, qn = (nx.y / ts) * TQR, sn = (nx.y % ts) * TS;
+            if (e.maps >= 0 && qn >= L::H && qn + TQR + L::H <= e.nt && sn >= L::HS && sn + TS + L::HS <= e.ns) {
+              tma_prefetch_3d(&maps.m[e.maps + stage], sn - L::HS, qn - L::H, 0);
+              if (stage > 0) tma_prefetch_3d(&maps.m[e.maps + 3], sn, qn, 0);
+            }
+          }
+          tma = d.maps >= 0 && q0 >= L::H && q0 + TQR + L::H <= d.nt && s0 >= L::HS && s0 + TS + L::HS <= d.ns;
+          if (tma) {
+            if (stage == 0)
+              tile_body_tma<L, CH, false>(a, vc, sm, tid, q0, s0, &maps.m[d.maps], &maps.m[d.maps + 3], false, ph_box,
+                                          ph_u0);
+            else
+              tile_body_tma<L, CH, true>(a, vc, sm, tid, q0, s0, &maps.m[d.maps + stage], &maps.m[d.maps + 3], false,
+                                         ph_box, ph_u0);
+            ph_box ^= 1u;
+            if (stage > 0) ph_u0 ^= 1u;
+          }
+        }
+        if (!tma) {
+          if (stage == 0)
+            tile_body<L, float, VLB_UW3, CH, false, 2>(a, vc, sm, tid, q0, s0);
+          else
+            tile_body<L, float, VLB_UW3, CH, true, 2>(a, vc, sm, tid, q0, s0);
+        }
+      }
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1214,6 +1361,47 @@ cudaError_t launch_ens(const EnsembleMember* members, const int2* items, int nit
   return cudaGetLastError();
 }
 
+template <int TQR, int CH>
+cudaError_t launch_pers(const EnsembleMember* members, const int2* items, int nitems, int nsteps, int only0,
+                        unsigned* bar, int* err, long long budget, int skip_cta, int ctas_per_sm, cudaStream_t st,
+                        const EnsembleMaps& maps, int* grid_out) {
+  using L = EnsLay<TQR>;
+  static int mask = 0;
+  cudaError_t e = ensure_smem(ensemble_persistent_kernel<TQR, CH>, L::BYTES, mask);
+  if (e != cudaSuccess) return e;
+  static const VConst<float> vc = make_vconst<float>();
+  static int occ[32] = {0}, sms[32] = {0};
+  int dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if (dev >= 32) return cudaErrorInvalidDevice;
+  if (occ[dev] == 0) {
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[dev], ensemble_persistent_kernel<TQR, CH>, L::NTH,
+                                                           L::BYTES)) != cudaSuccess)
+      return e;
+    if ((e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if (occ[dev] < 1) return cudaErrorInvalidConfiguration;
+  }
+  const int per_sm = ctas_per_sm > 0 && ctas_per_sm < occ[dev] ? ctas_per_sm : occ[dev];
+  int grid = per_sm * sms[dev];
+  if (grid > nitems) grid = nitems;
+  if (grid_out) *grid_out = grid;
+  if (grid < 1 || nsteps < 1) return cudaSuccess;
+  // the barrier's counter starts at zero (a launch that gave up may have left arrivals behind)
+  if ((e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st)) != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(L::NTH);
+  cfg.dynamicSmemBytes = L::BYTES;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;  // all CTAs resident at once: the grid barrier is safe
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, ensemble_persistent_kernel<TQR, CH>, members, items, nitems, nsteps, only0, bar, err,
+                            budget, skip_cta, vc, maps);
+}
+
 template <int TQR>
 cudaError_t launch_ens_rows(const EnsembleMember* members, const int2* items, int nitems, int stage, int ch_mode,
                             int* err, cudaStream_t st, const EnsembleMaps& maps) {
@@ -1311,6 +1499,24 @@ cudaError_t launch_ensemble_stage(const EnsembleMember* members, const int2* ite
   const EnsembleMaps& m = maps ? *maps : none;
   if (tile_rows == 8) return launch_ens_rows<8>(members, items, nitems, stage, ch_mode, err, s, m);
   return launch_ens_rows<16>(members, items, nitems, stage, ch_mode, err, s, m);
+}
+
+cudaError_t launch_ensemble_persistent(const EnsembleMember* members, const int2* items, int nitems, int nsteps,
+                                       int only0, int tile_rows, int ch_mode, unsigned* bar, int* err, long long budget,
+                                       int skip_cta, int ctas_per_sm, cudaStream_t s, const EnsembleMaps* maps,
+                                       int* grid_out) {
+  if (nitems <= 0) return cudaSuccess;
+  static const EnsembleMaps none = {};
+  const EnsembleMaps& m = maps ? *maps : none;
+  if (tile_rows == 8)
+    return ch_mode == VLB_HYDRO ? launch_pers<8, VLB_HYDRO>(members, items, nitems, nsteps, only0, bar, err, budget,
+                                                             skip_cta, ctas_per_sm, s, m, grid_out)
+                                : launch_pers<8, VLB_DIFFUSIVE>(members, items, nitems, nsteps, only0, bar, err, budget,
+                                                                 skip_cta, ctas_per_sm, s, m, grid_out);
+  return ch_mode == VLB_HYDRO ? launch_pers<16, VLB_HYDRO>(members, items, nitems, nsteps, only0, bar, err, budget,
+                                                            skip_cta, ctas_per_sm, s, m, grid_out)
+                              : launch_pers<16, VLB_DIFFUSIVE>(members, items, nitems, nsteps, only0, bar, err, budget,
+                                                                skip_cta, ctas_per_sm, s, m, grid_out);
 }
 
 template <typename T>

@@ -30,7 +30,7 @@ EXPORTS = ["vlb_workspace_bytes", "vlb_max_stable_dt", "vlb_create", "vlb_destro
            "vlb_reduce_workspace_bytes", "vlb_surrogate_norm", "vlb_surrogate_features", "vlb_surrogate_targets",
            "vlb_surrogate_apply", "vlb_snapshot_compare", "vlb_channel_sums", "vlb_mse_loss", "vlb_adam_step", "vlb_to_bf16",
            "vlb_conv_status", "vlb_test_raise_flag", "vlb_surrogate_workspace_bytes", "vlb_surrogate_create",
-           "vlb_surrogate_advance", "vlb_surrogate_stats"]
+           "vlb_surrogate_advance", "vlb_surrogate_stats", "vlb_ensemble_configure", "vlb_ensemble_get_config"]
 
 NOALLOC_SCRATCH_BYTES = 24 * 1024 * 1024
 
@@ -43,6 +43,14 @@ class vlb_surrogate_net(ctypes.Structure):
     _fields_ = [("weights_bf16", ctypes.c_void_p), ("biases", ctypes.c_void_p), ("s_n", ctypes.c_float),
                 ("s_u", ctypes.c_float), ("g", ctypes.c_float * 4), ("window", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
+
+
+ENS_AUTO, ENS_BATCHED, ENS_PERSISTENT = 0, 1, 2
+
+
+class vlb_ensemble_config(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("tile_rows", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("test_skip_cta", ctypes.c_int32), ("barrier_budget", ctypes.c_int64)]
 
 
 class vlb_params(ctypes.Structure):
@@ -115,6 +123,10 @@ def lib() -> ctypes.CDLL:
                                         ctypes.POINTER(I32)]
     L.vlb_surrogate_advance.restype = I32
     L.vlb_surrogate_stats.argtypes, L.vlb_surrogate_stats.restype = [P, ctypes.POINTER(I64)], I32
+    L.vlb_ensemble_configure.argtypes = [P, ctypes.POINTER(vlb_ensemble_config)]
+    L.vlb_ensemble_configure.restype = I32
+    L.vlb_ensemble_get_config.argtypes = [P, ctypes.POINTER(vlb_ensemble_config), ctypes.POINTER(ctypes.c_float)]
+    L.vlb_ensemble_get_config.restype = I32
     L.vlb_test_raise_flag.argtypes, L.vlb_test_raise_flag.restype = [P, I32], I32
     L.vlb_conv3x3_fwd.argtypes = [I32, I32, I32, I32, P, P, P, P, I32, P, P, P]
     L.vlb_conv3x3_flip.argtypes = [I32, I32, P, P, P]
@@ -370,6 +382,19 @@ class Ensemble:
 
     def step(self, n: int):
         _check(lib().vlb_ensemble_step(self.h, n), self.h)
+
+    def configure(self, mode=ENS_AUTO, tile_rows=0, ctas_per_sm=0, test_skip_cta=-1, barrier_budget=0):
+        c = vlb_ensemble_config(mode=mode, tile_rows=tile_rows, ctas_per_sm=ctas_per_sm, test_skip_cta=test_skip_cta,
+                                barrier_budget=barrier_budget)
+        _check(lib().vlb_ensemble_configure(self.h, ctypes.byref(c)), self.h)
+
+    def config(self):
+        """(mode, tile_rows, ctas_per_sm, ms of the four candidates: batched 16/8, persistent 16/8)."""
+        c = vlb_ensemble_config()
+        ms = (ctypes.c_float * 4)()
+        _check(lib().vlb_ensemble_get_config(self.h, ctypes.byref(c), ms), self.h)
+        return {"mode": {0: None, 1: "batched", 2: "persistent"}[c.mode], "tile_rows": c.tile_rows,
+                "ctas_per_sm": c.ctas_per_sm, "barrier_budget": c.barrier_budget, "ms": list(ms)}
 
     def tile_rows(self):
         rows = ctypes.c_int32()

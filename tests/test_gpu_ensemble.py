@@ -31,9 +31,13 @@ def _members(specs, seed0=300):
 SPECS = [(40, 64, 2.0), (64, 128, 3.1), (20, 44, 1.6), (33, 70, 2.5), (72, 96, 4.2)]
 
 
-def test_ensemble_matches_members_stepped_alone_and_the_oracle():
+@pytest.mark.parametrize("mode,rows", [(vlb.ENS_AUTO, 0), (vlb.ENS_BATCHED, 8), (vlb.ENS_PERSISTENT, 16),
+                                       (vlb.ENS_PERSISTENT, 8)])
+def test_ensemble_matches_members_stepped_alone_and_the_oracle(mode, rows):
     mem = _members(SPECS)
     ens = vlb.Ensemble([vlb.make_params(**p, precision=vlb.FP32) for p, _ in mem])
+    if mode != vlb.ENS_AUTO:
+        ens.configure(mode=mode, tile_rows=rows)
     solo = []
     for v, (p, f) in zip(ens.views, mem):
         vlb.vlb_set_fields(v, f["rho"], f["ut"], f["up"], f["phi"])
@@ -43,8 +47,13 @@ def test_ensemble_matches_members_stepped_alone_and_the_oracle():
     steps = 12
     ens.step(5)
     ens.step(steps - 5)  # second call replays the recorded graphs
-    rows, ms16, ms8 = ens.tile_rows()
-    assert rows in (8, 16) and ms16 > 0 and ms8 > 0
+    cfg = ens.config()
+    assert cfg["tile_rows"] in (8, 16)
+    if mode == vlb.ENS_AUTO:
+        assert all(ms > 0 for ms in cfg["ms"]), cfg  # all four candidates were timed
+    else:
+        assert cfg["mode"] == {vlb.ENS_BATCHED: "batched", vlb.ENS_PERSISTENT: "persistent"}[mode]
+        assert cfg["tile_rows"] == rows
     for i, (v, (p, f)) in enumerate(zip(ens.views, mem)):
         solo[i].step(steps)
         g = vlb.vlb_get_fields(v, p["n_theta"], p["n_phi"])
@@ -96,3 +105,69 @@ def test_forty_eight_tori_conserve_and_beat_sequential_launches():
         assert abs(t1[1] - tt[1]) <= 1e-6 * np.abs(tt[0])
     assert t_ens < t_seq
     ens.close()
+
+
+def test_persistent_and_batched_launches_agree_bit_for_bit():
+    """The persistent launch runs the same tile arithmetic as the batched launches, only scheduled
+    differently, so the states agree bit for bit (both tile heights, 40 steps over several graph
+    replays and an eager remainder)."""
+    mem = _members(SPECS, seed0=500)
+    states = []
+    for mode, rows in ((vlb.ENS_BATCHED, 16), (vlb.ENS_PERSISTENT, 16), (vlb.ENS_PERSISTENT, 8)):
+        ens = vlb.Ensemble([vlb.make_params(**p, precision=vlb.FP32) for p, _ in mem])
+        ens.configure(mode=mode, tile_rows=rows)
+        for v, (p, f) in zip(ens.views, mem):
+            vlb.vlb_set_fields(v, f["rho"], f["ut"], f["up"], f["phi"])
+        ens.step(7)
+        ens.step(33)
+        states.append([vlb.vlb_get_state(v, p["n_theta"], p["n_phi"]) for v, (p, _) in zip(ens.views, mem)])
+        ens.close()
+    for other in states[1:]:
+        for (fa, pa), (fb, pb) in zip(states[0], other):
+            np.testing.assert_array_equal(fa, fb)
+            np.testing.assert_array_equal(pa, pb)
+
+
+def test_persistent_barrier_times_out_instead_of_hanging():
+    """A CTA that never arrives at the grid barrier (the test hook) makes the others give up after the
+    barrier budget (here about a millisecond of SM cycles): the launch ends, the ensemble's flag is
+    raised, the members report VLB_ERR_TIMEOUT, and a reset state steps normally again."""
+    mem = _members(SPECS[:3], seed0=600)
+    ens = vlb.Ensemble([vlb.make_params(**p, precision=vlb.FP32) for p, _ in mem])
+    ens.configure(mode=vlb.ENS_PERSISTENT, tile_rows=16, test_skip_cta=0, barrier_budget=2_000_000)
+    for v, (p, f) in zip(ens.views, mem):
+        vlb.vlb_set_fields(v, f["rho"], f["ut"], f["up"], f["phi"])
+    ens.step(3)
+    for v in ens.views:
+        with pytest.raises(vlb.VlbError) as exc:
+            vlb.vlb_get_totals(v)
+        assert exc.value.status == vlb.VLB_ERR_TIMEOUT
+    ens.configure(mode=vlb.ENS_PERSISTENT, tile_rows=16)
+    for v, (p, f) in zip(ens.views, mem):
+        vlb.vlb_set_fields(v, f["rho"], f["ut"], f["up"], f["phi"])
+    ens.step(3)
+    for v in ens.views:
+        assert np.all(np.isfinite(vlb.vlb_get_totals(v)))
+    ens.close()
+
+
+def test_autotune_choice_is_cached(tmp_path, monkeypatch):
+    """The first ensemble times the four candidates and writes its choice to VLB_AUTOTUNE_CACHE; a second
+    ensemble with the same grids takes the cached choice (the same timings, to the bit) without timing."""
+    cache = tmp_path / "tune.jsonl"
+    monkeypatch.setenv("VLB_AUTOTUNE_CACHE", str(cache))
+    specs = [(24, 64, 2.2), (48, 128, 3.3), (36, 96, 1.9)]
+    mem = _members(specs, seed0=700)
+    cfgs = []
+    for _ in range(2):
+        ens = vlb.Ensemble([vlb.make_params(**p, precision=vlb.FP32) for p, _ in mem])
+        for v, (p, f) in zip(ens.views, mem):
+            vlb.vlb_set_fields(v, f["rho"], f["ut"], f["up"], f["phi"])
+        ens.step(2)
+        cfgs.append(ens.config())
+        ens.close()
+    assert cfgs[0] == cfgs[1]
+    lines = cache.read_text().strip().splitlines()
+    assert len(lines) == 1 and '"kind": "ensemble"' in lines[0]
+    mode = {"batched": 1, "persistent": 2}[cfgs[0]["mode"]]
+    assert f'"mode": {mode}, "tile_rows": {cfgs[0]["tile_rows"]}' in lines[0]
