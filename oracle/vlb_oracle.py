@@ -126,6 +126,7 @@ class Params:
     geometry: int = TORUS
     advection: int = UW3
     ch_mode: int = HYDRO  # DIFFUSIVE: no advection in CH and no force on the fluid (Sec. 4.1.1)
+    ch_stab: int = 0      # 1: stabilised semi-implicit Cahn-Hilliard stages (not in the paper; see stabiliser)
 
 
 class Geometry:
@@ -311,16 +312,51 @@ def rhs(f, phi, geo: Geometry):
     return Lf, Lphi
 
 
+# --------------------------------------------------------------------------------------
+# Stabilised semi-implicit Cahn-Hilliard (not in the paper: it lifts the explicit dt ~ h^4 limit)
+# --------------------------------------------------------------------------------------
+
+def biharmonic_symbol(geo: Geometry) -> np.ndarray:
+    """lambda(k) = (symbol of the constant-coefficient periodic five-point Laplacian)^2 for every
+    discrete Fourier mode k = (k_theta, k_phi) of the grid, with the finest spacings of the domain:
+    h_theta = r dtheta and h_phi = (R - r) dvarphi on the torus (the inner equator), R dvarphi flat.
+    The symbol of the Laplacian is -(4/h_theta^2) sin^2(pi m/N_theta) - (4/h_phi^2) sin^2(pi n/N_phi)."""
+    p = geo.p
+    h_t = p.r * geo.dth
+    h_p = ((p.R - p.r) if p.geometry == TORUS else p.R) * geo.dph
+    m = np.arange(p.n_theta)[:, None]
+    n = np.arange(p.n_phi)[None, :]
+    lap = 4.0 / h_t ** 2 * np.sin(np.pi * m / p.n_theta) ** 2 + 4.0 / h_p ** 2 * np.sin(np.pi * n / p.n_phi) ** 2
+    return lap * lap
+
+
+def stabiliser(x, geo: Geometry):
+    """P x = J^{-1} F^{-1}[ F[J x] / (1 + dt sigma lambda(k)) ] with sigma = M kappa (F: the 2-D
+    discrete Fourier transform).  P is the inverse of I + dt sigma J^{-1} D^2 J, D the constant-
+    coefficient Laplacian above: every mode of J x is damped, the mean of J x (k = 0) is kept, so
+    P conserves sum J x, i.e. the integral of x sqrt(g)."""
+    p = geo.p
+    lam = biharmonic_symbol(geo)
+    z = np.fft.fft2(geo.J * x)
+    return np.real(np.fft.ifft2(z / (1.0 + p.dt * p.M * p.kappa * lam))) / geo.J
+
+
 def step(f, phi, geo: Geometry):
-    """One SSP-RK3 step (Shu-Osher form) of the coupled (f, phi) system."""
+    """One SSP-RK3 step (Shu-Osher form) of the coupled (f, phi) system.
+
+    With ch_stab the phi equation is advanced as phi' = P L_phi(f, phi) with the fixed preconditioner
+    P of `stabiliser` (the same for the three stages): the stiff kappa Delta^2 modes, whose explicit
+    limit is dt ~ h^4 / (M kappa), are damped to dt-eigenvalues within [-1, 0], while P -> I as
+    dt -> 0 (a first-order perturbation of the time derivative)."""
     dt = geo.p.dt
+    P = (lambda x: stabiliser(x, geo)) if geo.p.ch_stab else (lambda x: x)
     Lf, Lp = rhs(f, phi, geo)
-    f1, p1 = f + dt * Lf, phi + dt * Lp
+    f1, p1 = f + dt * Lf, phi + P(dt * Lp)
     Lf, Lp = rhs(f1, p1, geo)
-    f2, p2 = 0.75 * f + 0.25 * (f1 + dt * Lf), 0.75 * phi + 0.25 * (p1 + dt * Lp)
+    f2, p2 = 0.75 * f + 0.25 * (f1 + dt * Lf), 0.75 * phi + 0.25 * (p1 + P(dt * Lp))
     Lf, Lp = rhs(f2, p2, geo)
     return (f / 3.0 + 2.0 / 3.0 * (f2 + dt * Lf),
-            phi / 3.0 + 2.0 / 3.0 * (p2 + dt * Lp))
+            phi / 3.0 + 2.0 / 3.0 * (p2 + P(dt * Lp)))
 
 
 def step_window(f, phi, p: Params, q: int, s: int, half: int = 12):
@@ -331,6 +367,8 @@ def step_window(f, phi, p: Params, q: int, s: int, half: int = 12):
     Runge-Kutta stage (the widest stencil, WENO5 advection), so with half >= 9 the centre is
     exactly the full-grid result.  Returns (f[:, :, centre], phi[centre]).
     """
+    if p.ch_stab:
+        raise ValueError("step_window: the stabilised step is global (Fourier) and has no node window")
     rows = np.arange(q - half, q + half + 1) % p.n_theta
     cols = np.arange(s - half, s + half + 1) % p.n_phi
     geo = Geometry(p, rows=rows)
