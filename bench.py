@@ -17,6 +17,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import subprocess
 import sys
@@ -311,12 +312,13 @@ def ensemble_measurement(steps: int = 60, seq_steps: int = 10):
 
 
 def surrogate_measurement(ntraj: int = 2000, pairs: int = 4, spacing: int = 400, start: int = 100, epochs: int = 3,
-                          seeds=(20001, 20002, 20003, 20004), warm: int = 400, nwin: int = 64, check: int = 4):
+                          seeds=(20001, 20002, 20003, 20004), warm: int = 400, nwin: int = 1000, check: int = 4):
     """The learned surrogate on 256 x 512 tori (R / r in [1.5, 4], seeded quenched noise): trained here on
-    `ntraj` solver trajectories by the library's kernels, then advancing held-out tori with the solver
-    as judge every `check` windows (relative L2 error in phi <= 1e-2, else fallback).  Solver and
-    surrogate runs are timed with CUDA events on their own streams in segments of `check` windows;
-    the domain length L_d = A / L_I is read between segments, outside the timed regions."""
+    `ntraj` solver trajectories by the library's kernels, then advancing each held-out torus by `nwin`
+    windows of 50 steps through vlb_surrogate_advance, judged by the solver every `check` windows --
+    once with the relative L2 error of phi <= 1e-2 as the judge, once with the relative L-infinity error
+    <= 1e-2 -- beside the plain solver from the same state.  Every window is timed with CUDA events on its
+    stream; the domain length L_d = A / L_I of both runs is read after every window, outside the timing."""
     import torch
     from paper_1904_10070_gb300 import surrogate as S
     from paper_1904_10070_gb300 import vlb
@@ -331,52 +333,105 @@ def surrogate_measurement(ntraj: int = 2000, pairs: int = 4, spacing: int = 400,
     _, train_s = tr.fit(ds, epochs=epochs, lr=1e-3)
     del ds
     torch.cuda.empty_cache()
-    t_ref = t_sur = 0.0
-    ld_dev, errs, errs_inf, fallbacks, kinds_all = [], [], [], 0, []
-    for seed in seeds:
-        R = S.radius_for(seed)
-        p = S.member_params(R, H, W)
-        phi = S.initial_phi(seed, H, W)
-        z = np.zeros_like(phi)
 
-        def solver():
-            s = vlb.Solver(vlb.make_params(**p, precision=vlb.FP32), stream=torch.cuda.Stream())
-            s.set_fields(np.ones_like(phi), z, z, phi)
-            s.step(warm)
-            return s
+    def run(norm):
+        t_ref = t_sur = 0.0
+        ld_dev, ld_curves, errs, errs_inf, kinds_all = [], [], [], [], []
+        for seed in seeds:
+            R = S.radius_for(seed)
+            p = S.member_params(R, H, W)
+            phi = S.initial_phi(seed, H, W)
+            z = np.zeros_like(phi)
 
-        ref, sur = solver(), solver()
-        adv = S.Advancer(tr, sur, window=50, check_every=check, phi_tol=1e-2)
-        for _ in range(nwin // check):
-            for s_, run in ((ref, lambda: ref.step(50 * check)), (sur, lambda: adv.advance(check))):
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                torch.cuda.synchronize()
-                e0.record(s_.stream)
-                run()
-                e1.record(s_.stream)
-                e1.synchronize()
-                if s_ is ref:
-                    t_ref += e0.elapsed_time(e1)
-                else:
-                    t_sur += e0.elapsed_time(e1)
-            ld_dev.append(abs(ref.interface_length() / sur.interface_length() - 1.0))
-        errs += adv.errors
-        errs_inf += adv.errors_linf
-        fallbacks += adv.kinds.count("fallback")
-        kinds_all += adv.kinds
-        ref.close()
-        sur.close()
-    n = len(seeds) * nwin
-    return {"workload": "surrogate_torus_256x512 (R/r in [1.5, 4], quenched seeded noise, FP32 solver)",
-            "train_trajectories": ntraj, "train_pairs": n_pairs, "train_iters": n_pairs * epochs,
-            "gen_s": gen_s, "train_s": train_s, "window_steps": 50, "check_every": check,
-            "held_out_tori": len(seeds), "windows": n,
-            "predicted_windows": kinds_all.count("surrogate"), "fallbacks": fallbacks,
-            "solver_ms_per_window": t_ref / n, "surrogate_ms_per_window": t_sur / n,
-            "speedup": t_ref / t_sur,
-            "phi_l2_err_max": max(errs), "phi_linf_err_max": max(errs_inf),
-            "Ld_max_rel_dev": max(ld_dev),
-            "judge": "relative L2 error of phi <= 1e-2 on every 4th window (solver result kept)"}
+            def solver():
+                s = vlb.Solver(vlb.make_params(**p, precision=vlb.FP32), stream=torch.cuda.Stream())
+                s.set_fields(np.ones_like(phi), z, z, phi)
+                s.step(warm)
+                return s
+
+            ref, sur = solver(), solver()
+            adv = S.Advancer(tr, sur, window=50, check_every=check, phi_tol=1e-2, norm=norm)
+            area = 4.0 * math.pi ** 2 * p["r"] * p["R"]
+            curve = []
+            for k in range(nwin):
+                for s_, fn in ((ref, lambda: ref.step(50)), (sur, lambda: adv.advance(1))):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize()
+                    e0.record(s_.stream)
+                    fn()
+                    e1.record(s_.stream)
+                    e1.synchronize()
+                    if s_ is ref:
+                        t_ref += e0.elapsed_time(e1)
+                    else:
+                        t_sur += e0.elapsed_time(e1)
+                l_ref, l_sur = area / ref.interface_length(), area / sur.interface_length()
+                ld_dev.append(abs(l_sur / l_ref - 1.0))
+                if k % 50 == 49:
+                    curve.append([50 * (k + 1), round(l_ref, 5), round(l_sur, 5)])
+            ld_curves.append({"R": round(R, 4), "t_steps_Ld_solver_Ld_surrogate": curve})
+            errs += adv.errors
+            errs_inf += adv.errors_linf
+            kinds_all += adv.kinds
+            adv.close()
+            ref.close()
+            sur.close()
+        n = len(seeds) * nwin
+        judged = kinds_all.count("checked") + kinds_all.count("fallback")
+        return {"judge": f"relative {'L2' if norm == 'l2' else 'L-infinity'} error of phi <= 1e-2 on every "
+                         f"{check}th window (solver result kept)",
+                "windows": n, "predicted_windows": kinds_all.count("surrogate"),
+                "fallbacks": kinds_all.count("fallback"), "fallback_rate_of_judged": kinds_all.count("fallback") / max(judged, 1),
+                "solver_ms_per_window": t_ref / n, "surrogate_ms_per_window": t_sur / n, "speedup": t_ref / t_sur,
+                "phi_l2_err_max": max(errs) if errs else None, "phi_l2_err_median": float(np.median(errs)) if errs else None,
+                "phi_linf_err_max": max(errs_inf) if errs_inf else None,
+                "Ld_max_rel_dev": max(ld_dev), "Ld_rel_dev_final_mean": float(np.mean(ld_dev[nwin - 1::nwin])),
+                "Ld_curves_every_50_windows": ld_curves}
+
+    out = {"workload": "surrogate_torus_256x512 (R/r in [1.5, 4], quenched seeded noise, FP32 solver)",
+           "train_trajectories": ntraj, "train_pairs": n_pairs, "train_iters": n_pairs * epochs,
+           "gen_s": gen_s, "train_s": train_s, "window_steps": 50, "check_every": check,
+           "held_out_tori": len(seeds), "windows_per_torus": nwin, "warm_start_steps": warm}
+    out["l2_judge"] = run("l2")
+    out["linf_judge"] = run("linf")
+    # headline figures: the L2 judge
+    for k in ("speedup", "fallbacks", "Ld_max_rel_dev", "phi_l2_err_max", "phi_linf_err_max", "solver_ms_per_window",
+              "surrogate_ms_per_window"):
+        out[k] = out["l2_judge"][k]
+    return out
+
+
+def stabilised_measurement(steps: int = 200):
+    """The coarsening workload with the stabilised semi-implicit Cahn-Hilliard stages (ch_stab = 1):
+    ms per step at its own stable step, and simulated time per wall second against the explicit step
+    at the explicit limit (CUDA events on the solver's stream, FP32, same initial state)."""
+    import torch
+    from paper_1904_10070_gb300 import inputs, vlb
+    w = inputs.workload(WORKLOAD)
+    out = {}
+    for stab in (0, 1):
+        p = dict(w["params"])
+        dt_max = vlb.vlb_max_stable_dt(vlb.make_params(**{k: p[k] for k in PKEYS}, ch_stab=stab))
+        p["dt"] = min(p["dt"], dt_max) if stab == 0 else 0.8 * dt_max
+        s = vlb.Solver(vlb.make_params(**{k: p[k] for k in PKEYS}, precision=vlb.FP32, ch_stab=stab))
+        s.set_fields(w["rho"], w["ut"], w["up"], w["phi"])
+        s.step(5)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s.stream)
+        s.step(steps)
+        e1.record(s.stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        finite = bool(np.all(np.isfinite(s.totals())))
+        s.close()
+        out["stabilised" if stab else "explicit"] = {"dt": p["dt"], "ms_per_step": ms,
+                                                      "simulated_time_per_s": p["dt"] / (ms * 1e-3), "finite": finite}
+    out["speedup_simulated_time"] = (out["stabilised"]["simulated_time_per_s"] /
+                                     out["explicit"]["simulated_time_per_s"])
+    out["what"] = ("1024x2048 coarsening workload: explicit step at the workload dt (its Cahn-Hilliard limit) vs "
+                   "the stabilised semi-implicit Cahn-Hilliard stages at 0.8 of their own stable dt")
+    return out
 
 
 def main():
@@ -500,6 +555,8 @@ def main():
     }
     if world == 1 and not args.no_ensemble:
         line["ensemble"] = ensemble_measurement()
+    if world == 1:
+        line["stabilised_ch"] = stabilised_measurement()
     if world == 1 and not args.no_surrogate:
         line["surrogate"] = surrogate_measurement()
     if world == 1 and not args.no_cpu_baseline:

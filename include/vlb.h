@@ -56,7 +56,12 @@ enum { VLB_HYDRO = 0, VLB_DIFFUSIVE = 1 };
 
 /* Problem definition.  Sec. 2 (Eqs. Landau, mu, CH, boltz_tor, nu) and App. A (Eq. torus).
  * tau may be +infinity (no collisions).  Flat geometry: J = 1, Gamma = 0, dx = 2 pi R / N_phi,
- * dy = 2 pi r / N_theta.  Nodes sit at theta_q = q 2pi/N_theta, varphi_s = s 2pi/N_phi. */
+ * dy = 2 pi r / N_theta.  Nodes sit at theta_q = q 2pi/N_theta, varphi_s = s 2pi/N_phi.
+ * ch_stab = 1 advances phi in every Runge-Kutta stage by P(dt L_phi) instead of dt L_phi, with the
+ * fixed preconditioner P = J^{-1} (I + dt M kappa D^2)^{-1} J, D the constant-coefficient periodic
+ * five-point Laplacian at the finest spacings (r dtheta and (R - r) dvarphi; R dvarphi flat), applied
+ * by FFTs on the device.  P damps the stiff kappa Delta^2 modes, conserves the integral of phi sqrt(g)
+ * and tends to the identity as dt -> 0 (a first-order change of the time derivative). */
 typedef struct {
   int32_t geometry;    /* VLB_TORUS or VLB_FLAT                                            */
   int32_t n_theta;     /* N_theta >= 4 (>= 6 for WENO5)                                    */
@@ -65,7 +70,9 @@ typedef struct {
   int32_t advection;   /* VLB_UW3 or VLB_WENO5                                             */
   int32_t ch_mode;     /* VLB_HYDRO, or VLB_DIFFUSIVE: no CH advection and no force (Sec. 4.1.1) */
   int32_t diag_every;  /* steps between finiteness checks inside vlb_step; 0 = never       */
-  int32_t reserved;    /* must be 0                                                        */
+  int32_t ch_stab;     /* 0: explicit Cahn-Hilliard (the paper's scheme); 1: stabilised semi-
+                          implicit stages (not in the paper; N_theta, N_phi powers of two in
+                          4 .. 4096, solver handles only), see vlb_max_stable_dt             */
   double R, r;         /* torus radii, R > r > 0 (flat: domain 2 pi R x 2 pi r)            */
   double dt;           /* time step > 0                                                     */
   double tau;          /* BGK relaxation time > 0 (nu = tau, Eq. nu)                        */
@@ -81,6 +88,8 @@ size_t vlb_workspace_bytes(const vlb_params* p);
  *          (b) BGK        dt <= 2.5 tau  (SSP-RK3 reaches -2.51 on the real axis);
  *          (c) Cahn-Hilliard  dt <= 2.5 / (M lambda (kappa lambda + 2 A)),
  *              lambda = 4/h_theta^2 + 4/h_phi,min^2, h_phi,min = (R - r) dvarphi on the torus;
+ *              with ch_stab the stiff part is damped and (c) becomes dt <= 6.25 kappa / (A^2 M)
+ *              (the largest preconditioned rate of the spinodal term, A sqrt(dt M / kappa), at 2.5);
  *          (d) relaxation and advection together: the largest dt at which one SSP-RK3 step of
  *              dg/dt = -(v_i/h_theta) D(k_theta) g - (v_j/h_phi,min) D(k_phi) g - g/tau has
  *              |1 + z + z^2/2 + z^3/6| <= 1 on a 64 x 64 grid of Fourier modes and all velocity

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvlb.so")
 SOURCES = ["vlb_stage.cu", "vlb_aux.cu", "vlb_capi.cu", "vlb_noalloc.cu", "vlb_conv.cu", "vlb_conv_tc.cu", "vlb_surrogate.cu",
-           "vlb_surrogate_api.cu"]
+           "vlb_surrogate_api.cu", "vlb_chsolve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -62,7 +62,9 @@ bool params_ok(const vlb_params* p, char* why, size_t n) {
   if (p->n_theta > 65535 * 16) return snprintf(why, n, "n_theta must be <= %d", 65535 * 16), false;
   if ((int64_t)p->n_theta * p->n_phi > (int64_t)1 << 31) return snprintf(why, n, "grid larger than 2^31 nodes"), false;
   if (p->diag_every < 0) return snprintf(why, n, "diag_every must be >= 0"), false;
-  if (p->reserved != 0) return snprintf(why, n, "reserved must be 0"), false;
+  if (p->ch_stab != 0 && p->ch_stab != 1) return snprintf(why, n, "ch_stab must be 0 or 1"), false;
+  if (p->ch_stab && !vlb::ch_stab_shape_ok(p->n_theta, p->n_phi))
+    return snprintf(why, n, "ch_stab needs n_theta and n_phi powers of two in 4 .. 4096"), false;
   if (!(p->r > 0.0) || !(p->R > 0.0) || !isfinite(p->r) || !isfinite(p->R))
     return snprintf(why, n, "radii must be finite and positive"), false;
   if (p->geometry == VLB_TORUS && !(p->R > p->r)) return snprintf(why, n, "torus needs R > r"), false;
@@ -77,7 +79,8 @@ bool params_ok(const vlb_params* p, char* why, size_t n) {
 struct Layout {
   int64_t N, stride;
   size_t esize;
-  size_t off_coefT, off_coefD, off_U[3], off_staging, off_partials, off_totals, off_diag, off_flag, total;
+  size_t off_coefT, off_coefD, off_U[3], off_staging, off_partials, off_totals, off_diag, off_flag, off_dphi, off_fft,
+      total;
 };
 
 Layout layout(const vlb_params* p) {
@@ -104,6 +107,13 @@ Layout layout(const vlb_params* p) {
   off = align_up(off + 8 * 8, 256);
   L.off_flag = off;
   off = align_up(off + 256, 256);
+  L.off_dphi = L.off_fft = 0;
+  if (p->ch_stab) {  // dt L_phi of a stage and the complex spectrum of the stabilised solve
+    L.off_dphi = off;
+    off = align_up(off + (size_t)L.N * L.esize, 256);
+    L.off_fft = off;
+    off = align_up(off + vlb::ch_stab_buffer_bytes(p->n_theta, p->n_phi, L.esize), 256);
+  }
   L.total = off;
   return L;
 }
@@ -227,7 +237,7 @@ vlb_status run_steps(vlb_handle* h, int64_t nsteps) {
   T* U0 = (T*)h->U[0];
   T* U1 = (T*)h->U[1];
   T* U2 = (T*)h->U[2];
-  if (p.n_phi == 1 && p.n_theta <= vlb::kAxiMaxRows) {
+  if (p.n_phi == 1 && p.n_theta <= vlb::kAxiMaxRows && !p.ch_stab) {
     // axisymmetric grid: up to 256 steps per single-CTA launch, cut at the diagnostic steps
     int64_t n = 0;
     while (n < nsteps) {
@@ -244,16 +254,31 @@ vlb_status run_steps(vlb_handle* h, int64_t nsteps) {
     }
     return VLB_OK;
   }
+  // stabilised Cahn-Hilliard: the stage kernel writes dt L_phi, the Fourier solve forms phi
+  T* dphi = p.ch_stab ? (T*)h->dphi : nullptr;
+  a.dphi = dphi;
+  const double h_t = p.r * (2.0 * M_PI / p.n_theta);
+  const double h_p = (p.geometry == VLB_TORUS ? p.R - p.r : p.R) * (2.0 * M_PI / p.n_phi);
+  const double* Jrow = h->coefD + (size_t)vlb::C_J * p.n_theta;
+  auto solve = [&](const T* fin, const T* f0, T* fout, T b) -> cudaError_t {
+    if (!dphi) return cudaSuccess;
+    return vlb::launch_ch_stab<T>(p.n_theta, p.n_phi, p.dt * p.M * p.kappa, h_t, h_p, Jrow, dphi, h->fft,
+                                  fin + vlb::NPOP * h->stride, f0 ? f0 + vlb::NPOP * h->stride : nullptr,
+                                  fout + vlb::NPOP * h->stride, h->stride, b, h->stream);
+  };
   for (int64_t n = 0; n < nsteps; ++n) {
     // SSP-RK3 (Shu & Osher 1988): U1 = U + dt L(U); U2 = 3/4 U + 1/4 (U1 + dt L(U1));
     // U <- 1/3 U + 2/3 (U2 + dt L(U2))
     const vlb::StageMaps* m = h->maps;
     a.fin = U0; a.f0 = nullptr; a.fout = U1; a.b = (T)1;
     VLB_CUDA(h, vlb::launch_stage<T>(a, p.advection, p.ch_mode, h->stream, m ? m + 0 : nullptr));
+    VLB_CUDA(h, solve(U0, nullptr, U1, (T)1));
     a.fin = U1; a.f0 = U0; a.fout = U2; a.b = (T)0.25;
     VLB_CUDA(h, vlb::launch_stage<T>(a, p.advection, p.ch_mode, h->stream, m ? m + 1 : nullptr));
+    VLB_CUDA(h, solve(U1, U0, U2, (T)0.25));
     a.fin = U2; a.f0 = U0; a.fout = U0; a.b = (T)(2.0 / 3.0);
     VLB_CUDA(h, vlb::launch_stage<T>(a, p.advection, p.ch_mode, h->stream, m ? m + 2 : nullptr));
+    VLB_CUDA(h, solve(U2, U0, U0, (T)(2.0 / 3.0)));
     h->steps_done++;
     if (p.diag_every > 0 && (h->steps_done % p.diag_every == 0 || n + 1 == nsteps)) {
       VLB_CUDA(h, vlb::launch_totals<T>(U0, h->stride, h->coefD, p.n_theta, p.n_phi, p.R, p.r, p.A, p.kappa,
@@ -451,8 +476,13 @@ vlb_status vlb_max_stable_dt(const vlb_params* p, double* dt_out) {
   if (isfinite(p->tau)) dt = fmin(dt, 2.5 * p->tau);
   dt = fmin(dt, combined_rk3_dt(ht, hp, p->tau, p->advection, p->n_phi > 1, vmax));
   const double lam = 4.0 / (ht * ht) + (p->n_phi > 1 ? 4.0 / (hp * hp) : 0.0);
-  const double ch = p->M * lam * (p->kappa * lam + 2.0 * p->A);
-  if (ch > 0.0) dt = fmin(dt, 2.5 / ch);
+  if (p->ch_stab) {
+    // preconditioned spinodal rate dt 2 M A lam / (1 + dt M kappa lam^2) peaks at A sqrt(dt M / kappa)
+    if (p->A > 0.0 && p->M > 0.0) dt = fmin(dt, 6.25 * p->kappa / (p->A * p->A * p->M));
+  } else {
+    const double ch = p->M * lam * (p->kappa * lam + 2.0 * p->A);
+    if (ch > 0.0) dt = fmin(dt, 2.5 / ch);
+  }
   *dt_out = dt;
   return VLB_OK;
 }
@@ -484,6 +514,8 @@ vlb_status vlb_create(const vlb_params* p, void* d_workspace, size_t bytes, void
   h->totals = (double*)(h->ws + L.off_totals);
   h->diag = (double*)(h->ws + L.off_diag);
   h->flag = (int*)(h->ws + L.off_flag);
+  h->dphi = p->ch_stab ? h->ws + L.off_dphi : nullptr;
+  h->fft = p->ch_stab ? h->ws + L.off_fft : nullptr;
   h->steps_done = 0;
   h->n0 = 1.0;
   h->err[0] = 0;
@@ -716,6 +748,7 @@ bool ensemble_params_ok(const vlb_params* p, int count, char* why, size_t n) {
     if (p[m].precision != VLB_FP32 || p[m].advection != VLB_UW3)
       return snprintf(why, n, "member %d: ensembles run FP32 UW3", m), false;
     if (p[m].ch_mode != p[0].ch_mode) return snprintf(why, n, "member %d: all members share ch_mode", m), false;
+    if (p[m].ch_stab) return snprintf(why, n, "member %d: ensembles run the explicit Cahn-Hilliard step", m), false;
   }
   return true;
 }

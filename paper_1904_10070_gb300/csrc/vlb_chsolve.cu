@@ -1,0 +1,234 @@
+// Stabilised semi-implicit Cahn-Hilliard stage (not part of the paper's method, which advances Eq. CH
+// explicitly; the explicit step is limited to dt ~ h^4 / (M kappa)).
+//
+// With the stabilisation the phi part of every SSP-RK3 stage reads
+//   phi_out = phi^n + b (phi_in - phi^n + P(dt L_phi(phi_in))),   (first stage: phi^n = phi_in, b = 1)
+// with the fixed preconditioner P = J^{-1} (I + dt M kappa D^2)^{-1} J, D the constant-coefficient
+// periodic five-point Laplacian at the finest spacings of the grid (h_theta = r dtheta, h_phi =
+// (R - r) dvarphi on the torus, R dvarphi flat).  P is diagonal in the discrete Fourier basis of J x:
+// a mode (m, n) is divided by 1 + dt M kappa lambda(m, n) with lambda = ((4/h_theta^2) sin^2(pi m/N_theta)
+// + (4/h_phi^2) sin^2(pi n/N_phi))^2; the mean (m = n = 0) is kept, so P conserves sum J x (the
+// integral of x sqrt(g)).  The stage kernel writes dt L_phi into a scratch array; three kernels then
+//   1. transform every theta row of J dt L_phi (complex FFT of real data, one CTA per row),
+//   2. transform strips of columns, divide by 1 + dt M kappa lambda and transform them back,
+//   3. transform every row back, take the real part / (N_theta N_phi J), and form phi_out (in FP32 as
+//      the float pair hi + lo with an error-free sum, as the stage kernel does).
+// The FFTs are in-place radix-2 (decimation in time, bit-reversed load) in shared memory, in the
+// state's precision, with twiddles from sincospi; N_theta and N_phi are powers of two <= 4096.
+#include <math.h>
+
+#include "vlb_internal.cuh"
+
+namespace vlb {
+
+namespace {
+
+template <typename T>
+struct C2 {
+  T x, y;
+};
+
+__device__ __forceinline__ void sincospi_t(double a, double* s, double* c) { sincospi(a, s, c); }
+__device__ __forceinline__ void sincospi_t(float a, float* s, float* c) { sincospif(a, s, c); }
+
+__device__ __forceinline__ int bitrev(int i, int logn) { return (int)(__brev((unsigned)i) >> (32 - logn)); }
+
+// tw[k] = exp(-2 pi i k / n), k < n / 2
+template <typename T>
+__device__ void twiddles(C2<T>* tw, int n) {
+  for (int k = threadIdx.x; k < n / 2; k += blockDim.x) {
+    T s, c;
+    sincospi_t((T)(-2.0 * k / n), &s, &c);
+    tw[k].x = c;
+    tw[k].y = s;
+  }
+}
+
+// In-place radix-2 FFT along the first index of a[i * w + c] (w interleaved sequences of length n,
+// loaded in bit-reversed order of i).  inverse: conjugate twiddles (unnormalised).
+template <typename T>
+__device__ void fft_strided(C2<T>* a, int n, int logn, int w, const C2<T>* tw, bool inverse) {
+  const int nb = (n >> 1) * w;
+  for (int l = 1; l <= logn; ++l) {
+    const int half = 1 << (l - 1), step = n >> l;
+    for (int idx = threadIdx.x; idx < nb; idx += blockDim.x) {
+      const int i = idx / w, c = idx - i * w;
+      const int grp = i / half, j = i - grp * half;
+      const int i0 = grp * 2 * half + j, i1 = i0 + half;
+      C2<T> t = tw[j * step];
+      if (inverse) t.y = -t.y;
+      const C2<T> u = a[i0 * w + c], v = a[i1 * w + c];
+      const C2<T> vt = {v.x * t.x - v.y * t.y, v.x * t.y + v.y * t.x};
+      a[i0 * w + c] = {u.x + vt.x, u.y + vt.y};
+      a[i1 * w + c] = {u.x - vt.x, u.y - vt.y};
+    }
+    __syncthreads();
+  }
+}
+
+// 1. Row q: F_phi[J_q dt L_phi(q, .)] -> buf row q.
+template <typename T>
+__global__ void __launch_bounds__(256) row_fwd_kernel(int ns, int logns, const T* dphi, const double* J,
+                                                      C2<T>* buf) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  C2<T>* a = reinterpret_cast<C2<T>*>(raw);
+  C2<T>* tw = a + ns;
+  const int q = blockIdx.x;
+  twiddles(tw, ns);
+  const T jq = (T)J[q];
+  for (int s = threadIdx.x; s < ns; s += blockDim.x) a[bitrev(s, logns)] = {jq * dphi[(int64_t)q * ns + s], T(0)};
+  __syncthreads();
+  fft_strided(a, ns, logns, 1, tw, false);
+  for (int s = threadIdx.x; s < ns; s += blockDim.x) buf[(int64_t)q * ns + s] = a[s];
+}
+
+// 2. Columns n0 .. n0 + cw - 1: F_theta, division by 1 + s lambda(m, n), inverse F_theta.
+template <typename T>
+__global__ void __launch_bounds__(256) col_solve_kernel(int nt, int lognt, int ns, int cw, double sfac, double ct,
+                                                        double cp, C2<T>* buf) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  C2<T>* a = reinterpret_cast<C2<T>*>(raw);
+  C2<T>* tw = a + (size_t)nt * cw;
+  const int n0 = blockIdx.x * cw;
+  twiddles(tw, nt);
+  for (int idx = threadIdx.x; idx < nt * cw; idx += blockDim.x) {
+    const int q = idx / cw, c = idx - q * cw;
+    a[bitrev(q, lognt) * cw + c] = buf[(int64_t)q * ns + n0 + c];
+  }
+  __syncthreads();
+  fft_strided(a, nt, lognt, cw, tw, false);
+  for (int idx = threadIdx.x; idx < nt * cw; idx += blockDim.x) {
+    const int m = idx / cw, c = idx - m * cw;
+    const double sm = sinpi((double)m / nt), sn = sinpi((double)(n0 + c) / ns);
+    const double lap = ct * sm * sm + cp * sn * sn;
+    const T g = (T)(1.0 / (1.0 + sfac * lap * lap));
+    a[idx].x *= g;
+    a[idx].y *= g;
+  }
+  __syncthreads();
+  // back to bit-reversed order for the inverse transform: in-place swaps of the pairs (m, rev(m))
+  for (int idx = threadIdx.x; idx < nt * cw; idx += blockDim.x) {
+    const int m = idx / cw, c = idx - m * cw, r = bitrev(m, lognt);
+    if (m < r) {
+      const C2<T> t = a[idx];
+      a[idx] = a[r * cw + c];
+      a[r * cw + c] = t;
+    }
+  }
+  __syncthreads();
+  fft_strided(a, nt, lognt, cw, tw, true);
+  for (int idx = threadIdx.x; idx < nt * cw; idx += blockDim.x) {
+    const int q = idx / cw, c = idx - q * cw;
+    buf[(int64_t)q * ns + n0 + c] = a[idx];
+  }
+}
+
+// (hi, lo) <- (base, base_lo) + inc with an error-free sum, renormalised (FP32 float pair)
+__device__ __forceinline__ void pair_add(float base, float base_lo, float inc, float& hi, float& lo) {
+  const float s1 = base + inc;
+  const float bb = s1 - base;
+  const float err = (base - (s1 - bb)) + (inc - bb);
+  const float lo2 = base_lo + err;
+  hi = s1 + lo2;
+  lo = lo2 - (hi - s1);
+}
+
+// 3. Row q: inverse F_phi, y = Re / (N J_q), phi_out = phi^n + b (phi_in - phi^n + y).
+template <typename T>
+__global__ void __launch_bounds__(256) row_inv_kernel(int ns, int logns, double inv_n, const double* J,
+                                                      const C2<T>* buf, const T* phin, const T* phi0, T* phiout,
+                                                      int64_t lo_off, T b) {
+  constexpr bool DF = sizeof(T) == 4;  // phi as a float pair
+  extern __shared__ __align__(16) unsigned char raw[];
+  C2<T>* a = reinterpret_cast<C2<T>*>(raw);
+  C2<T>* tw = a + ns;
+  const int q = blockIdx.x;
+  twiddles(tw, ns);
+  for (int s = threadIdx.x; s < ns; s += blockDim.x) a[bitrev(s, logns)] = buf[(int64_t)q * ns + s];
+  __syncthreads();
+  fft_strided(a, ns, logns, 1, tw, true);
+  const T scale = (T)(inv_n / J[q]);
+  for (int s = threadIdx.x; s < ns; s += blockDim.x) {
+    const int64_t g = (int64_t)q * ns + s;
+    const T y = a[s].x * scale;
+    const T ph = phin[g], lo = DF ? phin[g + lo_off] : T(0);
+    T base = ph, base_lo = lo, inc = y;
+    if (phi0) {
+      base = phi0[g];
+      base_lo = DF ? phi0[g + lo_off] : T(0);
+      inc = b * (((ph - base) + (lo - base_lo)) + y);
+    }
+    if constexpr (DF) {
+      float hi_o, lo_o;
+      pair_add(base, base_lo, inc, hi_o, lo_o);
+      phiout[g] = hi_o;
+      phiout[g + lo_off] = lo_o;
+    } else {
+      phiout[g] = base + inc;
+    }
+  }
+}
+
+int ilog2(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+
+template <typename K>
+cudaError_t smem_attr(K kernel, size_t bytes, int& mask) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 32 && (mask & (1 << dev))) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess && dev < 32) mask |= 1 << dev;
+  return e;
+}
+
+constexpr size_t kColBudget = 96 * 1024;  // shared bytes of a column strip (without twiddles)
+
+}  // namespace
+
+bool ch_stab_shape_ok(int nt, int ns) {
+  auto pow2 = [](int n) { return n >= 4 && n <= 4096 && (n & (n - 1)) == 0; };
+  return pow2(nt) && pow2(ns);
+}
+
+size_t ch_stab_buffer_bytes(int nt, int ns, size_t esize) { return (size_t)nt * ns * 2 * esize; }
+
+template <typename T>
+cudaError_t launch_ch_stab(int nt, int ns, double dt_m_kappa, double h_t, double h_p, const double* J, const T* dphi,
+                           void* buf, const T* phin, const T* phi0, T* phiout, int64_t lo_off, T b, cudaStream_t st) {
+  if (!ch_stab_shape_ok(nt, ns)) return cudaErrorInvalidValue;
+  const int lognt = ilog2(nt), logns = ilog2(ns);
+  C2<T>* cb = reinterpret_cast<C2<T>*>(buf);
+  const size_t row_bytes = sizeof(C2<T>) * (size_t)ns * 3 / 2;
+  int cw = 1;
+  while (cw < 32 && cw * 2 <= ns && (size_t)nt * cw * 2 * sizeof(C2<T>) <= kColBudget) cw *= 2;
+  const size_t col_bytes = sizeof(C2<T>) * ((size_t)nt * cw + nt / 2);
+  // the attribute is set once per device to the largest size any grid needs (setting it to a
+  // smaller size would cap later launches on larger grids)
+  constexpr size_t row_max = sizeof(C2<T>) * 4096 * 3 / 2;
+  constexpr size_t col_max = kColBudget + sizeof(C2<T>) * 2048;
+  static int m1 = 0, m2 = 0, m3 = 0;
+  cudaError_t e;
+  if ((e = smem_attr(row_fwd_kernel<T>, row_max, m1)) != cudaSuccess) return e;
+  if ((e = smem_attr(col_solve_kernel<T>, col_max, m2)) != cudaSuccess) return e;
+  if ((e = smem_attr(row_inv_kernel<T>, row_max, m3)) != cudaSuccess) return e;
+  row_fwd_kernel<T><<<nt, 256, row_bytes, st>>>(ns, logns, dphi, J, cb);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  col_solve_kernel<T><<<ns / cw, 256, col_bytes, st>>>(nt, lognt, ns, cw, dt_m_kappa, 4.0 / (h_t * h_t),
+                                                      4.0 / (h_p * h_p), cb);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  row_inv_kernel<T><<<nt, 256, row_bytes, st>>>(ns, logns, 1.0 / ((double)nt * ns), J, cb, phin, phi0, phiout, lo_off,
+                                               b);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_ch_stab<float>(int, int, double, double, double, const double*, const float*, void*,
+                                           const float*, const float*, float*, int64_t, float, cudaStream_t);
+template cudaError_t launch_ch_stab<double>(int, int, double, double, double, const double*, const double*, void*,
+                                            const double*, const double*, double*, int64_t, double, cudaStream_t);
+
+}  // namespace vlb

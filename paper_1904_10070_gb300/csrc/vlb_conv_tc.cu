@@ -1,24 +1,24 @@
 // 3x3 periodic convolution forward on the 5th-generation tensor cores (tcgen05.mma, BF16 x BF16 ->
-// FP32 accumulators in tensor memory), for the learned surrogate.  Same contract as the forward of
-// vlb_conv.cu: Y[p][co] = act(sum_{t,ci} X[p + d_t][ci] W[co][t][ci] + b[co]) on NHWC bf16 tensors,
-// periodic in both directions, with the optional bias, ReLU, mask (outputs where mask <= 0 are
-// zeroed) and bf16 / f32 outputs.  The backward-data convolution is this kernel on flipped weights.
+// FP32 accumulators in tensor memory), for the learned surrogate.  Y[p][co] = act(sum_{t,ci}
+// X[p + d_t][ci] W[co][t][ci] + b[co]) on NHWC bf16 tensors, periodic in both directions, with the
+// optional bias, ReLU, mask (outputs where mask <= 0 are zeroed) and bf16 / f32 outputs.  The
+// backward-data convolution is this kernel on flipped weights.
 //
-// Implicit GEMM.  A work item is two output rows of 128 pixels; per row, D[m][n] (m = pixel, n =
-// output channel, M = 128, N = C_out) accumulates over K = 9 taps x C_in:
+// Implicit GEMM.  A work item is one output row segment of 128 pixels: D[m][n] (m = pixel, n =
+// output channel, M = 128, N = C_out) accumulates over K = 9 taps x C_in,
 //   A_t[m][k] = X[pixel m shifted by tap t][k],  B_t[n][k] = W[n][t][k],  D = sum_t A_t B_t^T.
-// Shared-memory operands use the no-swizzle K-major layout of 8 x 16-byte core matrices: element
-// (m, k) of a matrix sits at (k / 8) * LBO + m * 16 + (k % 8) * 2 bytes (the row-group stride SBO is
-// 128 bytes, so rows are simply 16 bytes apart).  The input patch (4 rows x 130 pixels) is stored as
-// [16-byte channel chunk][patch row][patch column]; the A matrix of tap (dy, dx) for output row r is
-// then the same layout starting (r + dy) * 130 + dx pixels in: a shifted window needs no copy.
-// Weights are stored [tap][chunk][c_out] once per CTA (the CTA is persistent over work items).
+// The input patch (3 rows x 130 pixels) is staged once per item; the A matrix of tap (dy, dx) is the
+// same buffer with its descriptor start shifted by whole pixel rows, so a shifted window needs no
+// copy.  The weights are staged once per CTA (the CTA is persistent over work items).
 //
-// One 128-thread CTA per SM, persistent and pipelined two deep (see the kernel): thread 0 issues the
-// 2 x 9 x C_in / 16 MMAs of an item (M = 128, N = C_out, K = 16 each) and commits them to an
-// mbarrier; the four warps read the accumulators from tensor memory (warp w owns lanes 32w .. 32w + 31,
-// i.e. those pixels) and run the epilogue of the previous item while the next MMAs execute.
+// One 192-thread CTA per SM with six warps in fixed roles: warps 0-3 run the epilogue (warp w reads
+// tensor-memory lanes 32w .. 32w + 31, i.e. those pixels: bias, ReLU, mask, bf16/f32 stores), warp 4
+// allocates tensor memory and one of its threads issues the MMAs, warp 5 issues the copies (the
+// weights once, then one patch per item, three deep, and the periodic fix-ups of edge items).  Two
+// accumulators let the epilogue of one item overlap the MMAs of the next.  Hand-offs are mbarriers
+// and every wait is bounded.
 #include <cuda_bf16.h>
+#include <string.h>
 
 #include "vlb_internal.cuh"
 
@@ -28,33 +28,37 @@ namespace {
 
 using bf16 = __nv_bfloat16;
 
-constexpr int TPX = 128;                 // pixels per accumulator tile (the MMA's M)
-constexpr int TROWS = 2;                 // output rows per work item
-constexpr int TPR = TROWS + 2, TPW = TPX + 2;  // patch rows, patch columns
+constexpr int TPX = 128;                 // pixels per work item (the MMA's M)
+constexpr int TPR = 3, TPW = TPX + 2;    // patch rows, patch columns
 // Warp roles: 0-3 epilogue (warp w reads tensor-memory lanes 32w .. 32w + 31), 4 MMA issue and
-// tensor-memory allocation, 5 loads (tensor-map copy of the patch and the periodic fix-ups).
-constexpr int TTHR = 192;
-constexpr int MMA_WARP = 4, LOAD_WARP = 5;
+// tensor-memory allocation, 5 issues the tensor-map copies (waiting only for a free buffer), 6
+// completes them (waits for a copy to land, applies the periodic fix-ups of edge items and hands the
+// buffer to the MMA warp), so that the latency of the fix-ups never delays the next copy.
+constexpr int TTHR = 224;
+constexpr int MMA_WARP = 4, LOAD_WARP = 5, FIX_WARP = 6;
 
 template <int CIN, int COUT>
 struct TcLay {
   // C_in = 64: 128-byte pixel rows in the 128-byte-swizzled K-major layout (fast row copies);
-  // C_in = 16: the no-swizzle chunk-major layout described above
+  // C_in = 16: the no-swizzle chunk-major layout [16-byte chunk][patch row][patch column]
   static constexpr bool SW = CIN == 64;
-  static constexpr int CH = CIN / 8;                        // 16-byte channel chunks per pixel
+  static constexpr int CH = CIN / 8;                         // 16-byte channel chunks per pixel
+  static constexpr int NBUF = 3;                             // patch buffers
   static constexpr int WTS = 9 * CH * COUT * 16;             // weight bytes
-  static constexpr int PATCH = CH * TPR * TPW * 16;          // patch bytes
-  static constexpr int W_OFF = 0, P_OFF = WTS, BAR_OFF = WTS + 2 * PATCH;  // two patch buffers
-  static constexpr int NBAR = 10;                            // tma, pfull, pempty, afull, aempty (x 2)
+  static constexpr int PATCH_RAW = CH * TPR * TPW * 16;      // patch bytes
+  static constexpr int PATCH = SW ? (PATCH_RAW + 1023) / 1024 * 1024 : (PATCH_RAW + 127) / 128 * 128;
+  static constexpr int W_OFF = 0, P_OFF = WTS, BAR_OFF = WTS + NBUF * PATCH;
+  static constexpr int NBAR = 3 * NBUF + 5;                  // tma, pfull, pempty (x NBUF), afull, aempty (x 2), w
   static constexpr int TSLOT_OFF = BAR_OFF + 8 * NBAR;       // tensor-memory address
   static constexpr int BIAS_OFF = TSLOT_OFF + 16;
   static constexpr int BYTES = BIAS_OFF + 4 * COUT;
-  static constexpr int ACC = TROWS * COUT;                   // accumulator columns of one work item
+  static constexpr int ACC = COUT;                           // accumulator columns of one work item
   static constexpr int COLS = 2 * ACC <= 32 ? 32 : (2 * ACC <= 64 ? 64 : (2 * ACC <= 128 ? 128 : 256));
   static constexpr uint32_t LBO_A = TPR * TPW * 16;          // next channel chunk of the patch
   static constexpr uint32_t LBO_B = COUT * 16;               // next channel chunk of a tap's weights
   static_assert(SW ? (WTS % 1024 == 0 && PATCH % 1024 == 0) : (WTS % 128 == 0 && PATCH % 128 == 0),
                 "operand buffers stay aligned to the swizzle atom (1024 bytes) or the core matrix (128 bytes)");
+  static_assert(BYTES <= 232448, "fits the opt-in shared memory of one CTA");
   static_assert(COUT % 16 == 0 && COUT <= 256 && CIN % 16 == 0, "MMA shape M = 128, N = C_out, K = 16");
 };
 
@@ -169,12 +173,12 @@ __device__ __forceinline__ int patch_off(int c, int pr, int pc) {
 // positions): out-of-range patch rows get whole wrapped rows, out-of-range columns the wrapped pixel.
 // Run by the 32 lanes of the load warp; returns whether anything was copied.
 template <int CIN>
-__device__ __forceinline__ bool fix_patch(unsigned char* dst, const bf16* x, int H, int W, int row0, int x0, int lane) {
+__device__ __forceinline__ bool fix_patch(unsigned char* dst, const bf16* x, int H, int W, int row, int x0, int lane) {
   constexpr int CH = CIN / 8;
-  const bool top = row0 == 0, bottom = row0 + TROWS == H, left = x0 == 0, right = x0 + TPX == W;
+  const bool top = row == 0, bottom = row + 1 == H, left = x0 == 0, right = x0 + TPX == W;
   if (!(top || bottom || left || right)) return false;
   for (int pr = 0; pr < TPR; ++pr) {
-    const int yy = row0 + pr - 1;
+    const int yy = row + pr - 1;
     const int gy = yy < 0 ? yy + H : (yy >= H ? yy - H : yy);
     if (gy != yy) {  // a whole wrapped row
       for (int i = lane; i < TPW * CH; i += 32) {
@@ -197,76 +201,76 @@ __device__ __forceinline__ bool fix_patch(unsigned char* dst, const bf16* x, int
   return true;
 }
 
-// Epilogue of work item `item` from the accumulators at column `col0`: thread (warp, lane) owns
-// pixel x0 + 32 warp + lane of each row; all C_out columns of a row are read before one wait.
+// Epilogue of work item `item` (row item % H, segment item / H: consecutive items of a CTA fall in
+// different segments) from the accumulator at column `col0`: thread (warp, lane) owns pixel
+// x0 + 32 warp + lane of the item's row; all C_out columns are read before one wait.
 template <int COUT>
-__device__ __forceinline__ void epilogue(uint32_t tmem, uint32_t col0, int W, int item, int warp, int lane,
+__device__ __forceinline__ void epilogue(uint32_t tmem, uint32_t col0, int H, int W, int item, int warp, int lane,
                                          const float* sbias, const bf16* mask, int relu, bf16* y, float* yf) {
-  const int segs = W / TPX, row0 = (item / segs) * TROWS, x0 = (item % segs) * TPX;
-#pragma unroll 1
-  for (int r = 0; r < TROWS; ++r) {
-    const size_t p = (size_t)(row0 + r) * W + x0 + 32 * warp + lane;
-    uint32_t raw[COUT];
+  const int row = item % H, x0 = (item / H) * TPX;
+  const size_t p = (size_t)row * W + x0 + 32 * warp + lane;
+  uint32_t raw[COUT];
 #pragma unroll
-    for (int j = 0; j < COUT / 16; ++j)
-      tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + col0 + (uint32_t)(r * COUT + 16 * j), raw + 16 * j);
-    tmem_wait_ld();
+  for (int j = 0; j < COUT / 16; ++j)
+    tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + col0 + (uint32_t)(16 * j), raw + 16 * j);
+  tmem_wait_ld();
 #pragma unroll
-    for (int j = 0; j < COUT / 16; ++j) {
-      float v[16];
-      const int co = 16 * j;
+  for (int j = 0; j < COUT / 16; ++j) {
+    float v[16];
+    const int co = 16 * j;
 #pragma unroll
-      for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(raw[co + i]) + sbias[co + i];
-      if (relu) {
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(raw[co + i]) + sbias[co + i];
+    if (relu) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.0f);
+      for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.0f);
+    }
+    if (mask) {
+      const uint4* mp = reinterpret_cast<const uint4*>(mask + p * COUT + co);
+      const uint4 m0 = mp[0], m1 = mp[1];
+      const __nv_bfloat162* mh = reinterpret_cast<const __nv_bfloat162*>(&m0);
+      const __nv_bfloat162* mh1 = reinterpret_cast<const __nv_bfloat162*>(&m1);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (!(__low2float(mh[i]) > 0.0f)) v[2 * i] = 0.0f;
+        if (!(__high2float(mh[i]) > 0.0f)) v[2 * i + 1] = 0.0f;
+        if (!(__low2float(mh1[i]) > 0.0f)) v[8 + 2 * i] = 0.0f;
+        if (!(__high2float(mh1[i]) > 0.0f)) v[8 + 2 * i + 1] = 0.0f;
       }
-      if (mask) {
-        const uint4* mp = reinterpret_cast<const uint4*>(mask + p * COUT + co);
-        const uint4 m0 = mp[0], m1 = mp[1];
-        const __nv_bfloat162* mh = reinterpret_cast<const __nv_bfloat162*>(&m0);
-        const __nv_bfloat162* mh1 = reinterpret_cast<const __nv_bfloat162*>(&m1);
+    }
+    if (y) {
+      uint4 o[2];
+      __nv_bfloat162* oh = reinterpret_cast<__nv_bfloat162*>(o);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          if (!(__low2float(mh[i]) > 0.0f)) v[2 * i] = 0.0f;
-          if (!(__high2float(mh[i]) > 0.0f)) v[2 * i + 1] = 0.0f;
-          if (!(__low2float(mh1[i]) > 0.0f)) v[8 + 2 * i] = 0.0f;
-          if (!(__high2float(mh1[i]) > 0.0f)) v[8 + 2 * i + 1] = 0.0f;
-        }
-      }
-      if (y) {
-        uint4 o[2];
-        __nv_bfloat162* oh = reinterpret_cast<__nv_bfloat162*>(o);
+      for (int i = 0; i < 8; ++i) oh[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+      uint4* yp = reinterpret_cast<uint4*>(y + p * COUT + co);
+      yp[0] = o[0];
+      yp[1] = o[1];
+    }
+    if (yf) {
+      float4* fp = reinterpret_cast<float4*>(yf + p * COUT + co);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) oh[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-        uint4* yp = reinterpret_cast<uint4*>(y + p * COUT + co);
-        yp[0] = o[0];
-        yp[1] = o[1];
-      }
-      if (yf) {
-        float4* fp = reinterpret_cast<float4*>(yf + p * COUT + co);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) fp[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-      }
+      for (int i = 0; i < 4; ++i) fp[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
     }
   }
 }
 
-// Persistent over work items item_k = blockIdx.x + k gridDim.x with warp-specialised roles and a
-// two-deep pipeline: patch buffer and accumulator k % 2 serve item k.  The load warp copies patch
-// k while the MMA warp works on item k - 1 and the epilogue warps drain item k - 2.  Hand-offs are
-// mbarriers: tma[b] (copy landed), pfull[b] (patch ready, fix-ups included), pempty[b] (its MMAs
-// are done), afull[b] (accumulator ready), aempty[b] (accumulator read, 4 arrivals).
+// Persistent over work items item_k = blockIdx.x + k gridDim.x with warp-specialised roles: patch
+// buffer k % 3 and accumulator k % 2 serve item k.  The load warp copies patch k while the MMA warp
+// works on earlier items and the epilogue warps drain the accumulator of item k - 2.  Hand-offs are
+// mbarriers: tma[b] (copy landed), pfull[b] (patch ready, fix-ups included), pempty[b] (its MMAs are
+// done), afull[a] (accumulator ready), aempty[a] (accumulator read, 4 arrivals), w (weights landed).
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(TTHR, 1)
     conv_fwd_tc_kernel(int H, int W, const bf16* __restrict__ x, const bf16* __restrict__ w,
                        const float* __restrict__ bias, const bf16* __restrict__ mask, int relu, bf16* y, float* yf,
-                       int* err, const __grid_constant__ CUtensorMap xmap) {
+                       int* err, const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap wmap) {
   using L = TcLay<CIN, COUT>;
+  constexpr int NB = L::NBUF;
   extern __shared__ __align__(1024) unsigned char sm[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L::BAR_OFF);
-  uint64_t *tma = bars, *pfull = bars + 2, *pempty = bars + 4, *afull = bars + 6, *aempty = bars + 8;
+  uint64_t *tma = bars, *pfull = bars + NB, *pempty = bars + 2 * NB, *afull = bars + 3 * NB,
+           *aempty = bars + 3 * NB + 2, *wbar = bars + 3 * NB + 4;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::TSLOT_OFF);
   float* sbias = reinterpret_cast<float*>(sm + L::BIAS_OFF);
   if (warp == MMA_WARP) {
@@ -276,99 +280,139 @@ __global__ void __launch_bounds__(TTHR, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
   if (tid == 0) {
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NB; ++b) {
       mbar_init(tma + b, 1);
       mbar_init(pfull + b, 1);
       mbar_init(pempty + b, 1);
-      mbar_init(afull + b, 1);
-      mbar_init(aempty + b, 4);
     }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(afull + a, 1);
+      mbar_init(aempty + a, 4);
+    }
+    mbar_init(wbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   for (int i = tid; i < COUT; i += TTHR) sbias[i] = bias ? bias[i] : 0.0f;
-  // weights once: chunk c of W[co][t][:] -> tap t's B matrix (row co): swizzled 128-byte rows for
-  // C_in = 64 ([t][co][128 B], 1024-byte atoms), chunk-major [t][c][co] for C_in = 16
-  for (int i = tid; i < COUT * 9 * L::CH; i += TTHR) {
-    const int c = i % L::CH, t = (i / L::CH) % 9, co = i / (9 * L::CH);
-    const int off = L::SW ? (t * COUT + co) * 128 + ((c ^ (co & 7)) << 4) : ((t * L::CH + c) * COUT + co) * 16;
-    cp16(sm + L::W_OFF + off, w + ((size_t)co * 9 + t) * CIN + c * 8);
+  if constexpr (!L::SW) {
+    // 16-channel weights (18 KB), chunk-major [t][c][co]: per-thread copies before the roles split
+    for (int i = tid; i < COUT * 9 * L::CH; i += TTHR) {
+      const int c = i % L::CH, t = (i / L::CH) % 9, co = i / (9 * L::CH);
+      cp16(sm + L::W_OFF + ((t * L::CH + c) * COUT + co) * 16, w + ((size_t)co * 9 + t) * CIN + c * 8);
+    }
+    asm volatile("cp.async.commit_group;\n" ::);
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    fence_async_smem();
   }
-  asm volatile("cp.async.commit_group;\n" ::);
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-  fence_async_smem();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  const int segs = W / TPX, nitems = (H / TROWS) * segs;
+  const int segs = W / TPX, nitems = H * segs;
   const int nmine = blockIdx.x < nitems ? (nitems - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   bool ok = true;
   if (warp == LOAD_WARP) {
+    if constexpr (L::SW) {
+      // 64-channel weights (72 KB): nine tensor-map copies, one per tap, of the box (64 c_in, 1 tap,
+      // C_out), each landing as C_out rows of 128 bytes with the 128-byte swizzle at [tap][c_out]; they
+      // overlap the first patch copies
+      if (lane == 0) {
+        mbar_expect_tx(wbar, L::WTS);
+        for (int t = 0; t < 9; ++t)
+          asm volatile(
+              "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, "
+              "%5}], [%2];\n" ::"r"(su32(sm + L::W_OFF + t * COUT * 128)),
+              "l"(reinterpret_cast<uint64_t>(&wmap)), "r"(su32(wbar)), "r"(0), "r"(t), "r"(0)
+              : "memory");
+      }
+    }
     for (int k = 0; k < nmine && ok; ++k) {
-      const int b = k & 1, item = blockIdx.x + k * gridDim.x;
-      const int row0 = (item / segs) * TROWS, x0 = (item % segs) * TPX;
-      unsigned char* dst = sm + L::P_OFF + b * L::PATCH;
-      if (k >= 2) ok = mbar_wait(pempty + b, ((k - 2) >> 1) & 1);  // the MMAs of item k - 2 read it
+      const int b = k % NB, use = k / NB, item = blockIdx.x + k * gridDim.x;
+      const int row = item % H, x0 = (item / H) * TPX;
+      if (k >= NB) ok = mbar_wait(pempty + b, (use - 1) & 1);  // the MMAs of item k - NB read it
       if (!ok) break;
       if (lane == 0) {
-        mbar_expect_tx(tma + b, L::PATCH);
+        unsigned char* dst = sm + L::P_OFF + b * L::PATCH;
+        mbar_expect_tx(tma + b, L::PATCH_RAW);
         if constexpr (L::SW)
-          tma_load_3d(dst, &xmap, tma + b, x0 - 1, row0 - 1);
+          tma_load_3d(dst, &xmap, tma + b, x0 - 1, row - 1);
         else
-          tma_load_4d(dst, &xmap, tma + b, x0 - 1, row0 - 1);
+          tma_load_4d(dst, &xmap, tma + b, x0 - 1, row - 1);
       }
-      ok = mbar_wait(tma + b, (k >> 1) & 1);
+      __syncwarp();
+    }
+    if (L::SW && nmine == 0 && lane == 0) mbar_wait(wbar, 0);  // the weight copy lands before the CTA exits
+  } else if (warp == FIX_WARP) {
+    for (int k = 0; k < nmine && ok; ++k) {
+      const int b = k % NB, item = blockIdx.x + k * gridDim.x;
+      const int row = item % H, x0 = (item / H) * TPX;
+      unsigned char* dst = sm + L::P_OFF + b * L::PATCH;
+      const bool left = x0 == 0, right = x0 + TPX == W;
+      const bool slow = row == 0 || row + 1 == H || (left && right);  // wrapped rows, or both sides wrap
+      // column wrap of an edge segment: the TPR x CH 16-byte chunks of the wrapped pixel, loaded into
+      // registers before the copy lands (their latency overlaps the copy), stored after it
+      uint4 v = make_uint4(0, 0, 0, 0);
+      const bool col_fix = (left || right) && !slow && lane < TPR * L::CH;
+      const int pr = lane / L::CH, c = lane % L::CH, pc = left ? 0 : TPW - 1;
+      if (col_fix) {
+        const int gx = left ? W - 1 : 0, gy = row + pr - 1;
+        v = *reinterpret_cast<const uint4*>(x + ((size_t)gy * W + gx) * CIN + c * 8);
+      }
+      ok = mbar_wait(tma + b, (k / NB) & 1);
       if (!ok) break;
-      if (fix_patch<CIN>(dst, x, H, W, row0, x0, lane)) fence_async_smem();
+      if (slow) {  // the first or last row of the grid, or a one-segment-wide grid (rare)
+        if (fix_patch<CIN>(dst, x, H, W, row, x0, lane)) fence_async_smem();
+      } else if (left || right) {
+        if (col_fix) *reinterpret_cast<uint4*>(dst + patch_off<CIN>(c, pr, pc)) = v;
+        fence_async_smem();
+      }
       __syncwarp();
       if (lane == 0) mbar_arrive(pfull + b);
     }
   } else if (warp == MMA_WARP) {
     if (lane == 0) {
       constexpr uint32_t ID = idesc<COUT>();
+      if (L::SW && nmine > 0) ok = mbar_wait(wbar, 0);
       const uint64_t bd0 = sdesc(su32(sm + L::W_OFF), L::LBO_B, 128);
       for (int k = 0; k < nmine && ok; ++k) {
-        const int b = k & 1;
-        ok = mbar_wait(pfull + b, (k >> 1) & 1);
-        if (ok && k >= 2) ok = mbar_wait(aempty + b, ((k - 2) >> 1) & 1);  // epilogue of item k - 2
+        const int b = k % NB, a = k & 1;
+        ok = mbar_wait(pfull + b, (k / NB) & 1);
+        if (ok && k >= 2) ok = mbar_wait(aempty + a, ((k - 2) >> 1) & 1);  // epilogue of item k - 2
         if (!ok) break;
         tc_fence_after();
         // descriptors differ only in the start address (low 14 bits, 16-byte units): constant offsets
         const uint32_t pb = su32(sm + L::P_OFF + b * L::PATCH), wb = su32(sm + L::W_OFF);
         const uint64_t ad0 = sdesc(pb, L::LBO_A, 128);
-        const uint32_t acc0 = tmem + (uint32_t)(b * L::ACC);
+        const uint32_t acc = tmem + (uint32_t)(a * L::ACC);
 #pragma unroll
-        for (int r = 0; r < TROWS; ++r)
+        for (int t = 0; t < 9; ++t)
 #pragma unroll
-          for (int t = 0; t < 9; ++t)
-#pragma unroll
-            for (int s2 = 0; s2 < CIN / 16; ++s2) {
-              uint64_t ad, bdd;
-              if constexpr (L::SW) {  // rows (r + dy) * TPW + dx + m; K step s2 is 32 bytes into the row
-                ad = sdesc_sw128(pb + (uint32_t)(((r + t / 3) * TPW + t % 3) * 128 + 32 * s2));
-                bdd = sdesc_sw128(wb + (uint32_t)(t * COUT * 128 + 32 * s2));
-              } else {
-                ad = ad0 + (uint32_t)(((2 * s2) * TPR + r + t / 3) * TPW + t % 3);
-                bdd = bd0 + (uint32_t)((t * L::CH + 2 * s2) * COUT);
-              }
-              umma(acc0 + r * COUT, ad, bdd, ID, (t | s2) != 0);
+          for (int s2 = 0; s2 < CIN / 16; ++s2) {
+            uint64_t ad, bdd;
+            if constexpr (L::SW) {  // rows (t / 3) * TPW + t % 3 + m; K step s2 is 32 bytes into the row
+              ad = sdesc_sw128(pb + (uint32_t)(((t / 3) * TPW + t % 3) * 128 + 32 * s2));
+              bdd = sdesc_sw128(wb + (uint32_t)(t * COUT * 128 + 32 * s2));
+            } else {
+              ad = ad0 + (uint32_t)(((2 * s2) * TPR + t / 3) * TPW + t % 3);
+              bdd = bd0 + (uint32_t)((t * L::CH + 2 * s2) * COUT);
             }
+            umma(acc, ad, bdd, ID, (t | s2) != 0);
+          }
         umma_commit(pempty + b);
-        umma_commit(afull + b);
+        umma_commit(afull + a);
       }
     }
     __syncwarp();
   } else {  // epilogue warps 0-3
     for (int k = 0; k < nmine && ok; ++k) {
-      const int b = k & 1;
-      ok = mbar_wait(afull + b, (k >> 1) & 1);
+      const int a = k & 1;
+      ok = mbar_wait(afull + a, (k >> 1) & 1);
       if (!ok) break;
       tc_fence_after();
-      epilogue<COUT>(tmem, (uint32_t)(b * L::ACC), W, blockIdx.x + k * gridDim.x, warp, lane, sbias, mask, relu, y,
-                     yf);
+      epilogue<COUT>(tmem, (uint32_t)(a * L::ACC), H, W, blockIdx.x + k * gridDim.x, warp, lane, sbias, mask, relu,
+                     y, yf);
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(aempty + b);
+      if (lane == 0) mbar_arrive(aempty + a);
     }
   }
   if (!ok && lane == 0 && err) atomicExch(err, 1);  // a wait gave up: flagged, the CTA winds down
@@ -445,30 +489,34 @@ __global__ void __launch_bounds__(TTHR)
   if (warp == LOAD_WARP) {
     for (int k = 0; k < nmine && ok; ++k) {
       const int b = k % NS, use = k / NS, sg = seg0 + k, row = sg / segs_row, x0 = (sg % segs_row) * TPX;
-      unsigned char* dyb = sm + b * L::STAGE;
-      unsigned char* xb = dyb + L::DY;
       if (k >= NS) ok = mbar_wait(empty + b, (use - 1) & 1);  // the MMAs of step k - NS read it
       if (!ok) break;
       const int yy = row + dyr - 1, gy = yy < 0 ? yy + H : (yy >= H ? yy - H : yy);
       if (lane == 0) {
+        unsigned char* dyb = sm + b * L::STAGE;
         mbar_expect_tx(tma + b, L::DY + TPW * 128);
         tma_load_3d(dyb, &dymap, tma + b, x0, row);
-        tma_load_3d(xb, &xmap, tma + b, x0 - 1, gy);  // the row index is wrapped here already
+        tma_load_3d(dyb + L::DY, &xmap, tma + b, x0 - 1, gy);  // the row index is wrapped here already
       }
+      __syncwarp();
+    }
+  } else if (warp == FIX_WARP) {
+    for (int k = 0; k < nmine && ok; ++k) {
+      const int b = k % NS, use = k / NS, sg = seg0 + k, row = sg / segs_row, x0 = (sg % segs_row) * TPX;
+      unsigned char* xb = sm + b * L::STAGE + L::DY;
+      const int yy = row + dyr - 1, gy = yy < 0 ? yy + H : (yy >= H ? yy - H : yy);
+      // the edge pixels of a wrapped segment (pixel j, chunk c at c ^ (j % 8)), loaded into registers
+      // before the copy lands so that their latency overlaps it: lanes 0-7 the left wrap (pixel
+      // j = 0 <- column W - 1), lanes 8-15 the right wrap (j = TPW - 1 <- column 0)
+      const bool left = x0 == 0, right = x0 + TPX == W;
+      const int c = lane % 8, side = lane / 8, j = side == 0 ? 0 : TPW - 1;
+      const bool mine = lane < 16 && ((side == 0 && left) || (side == 1 && right));
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (mine) v = *reinterpret_cast<const uint4*>(x + ((size_t)gy * W + (side == 0 ? W - 1 : 0)) * 64 + c * 8);
       ok = mbar_wait(tma + b, use & 1);
       if (!ok) break;
-      // the two edge pixels of a wrapped segment (pixel j, chunk c at c ^ (j % 8))
-      const bool left = x0 == 0, right = x0 + TPX == W;
       if (left || right) {
-        if (lane < 16) {
-          const int c = lane % 8, side = lane / 8;
-          if ((side == 0 && left) || (side == 1 && right)) {
-            const int j = side == 0 ? 0 : TPW - 1, gx = side == 0 ? W - 1 : 0;
-            cp16(xb + j * 128 + ((c ^ (j & 7)) << 4), x + ((size_t)gy * W + gx) * 64 + c * 8);
-          }
-        }
-        asm volatile("cp.async.commit_group;\n" ::);
-        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        if (mine) *reinterpret_cast<uint4*>(xb + j * 128 + ((c ^ (j & 7)) << 4)) = v;
         fence_async_smem();
       }
       __syncwarp();
@@ -571,21 +619,31 @@ cudaError_t tc_launch(int H, int W, const void* x, const void* w, const float* b
     if ((e = cudaGetSymbolAddress((void**)&err[dev], g_conv_tc_err)) != cudaSuccess) return e;
     ready[dev] = 1;
   }
-  // the input as (8 channels of a chunk, W, H, chunk) so that a 8 x 130 x 4 x CH box lands in the
-  // chunk-major patch layout; out-of-range rows and columns are zero-filled, then fixed up
   EncodeTiled enc = encoder();
   if (!enc) return cudaErrorNotSupported;
-  alignas(64) CUtensorMap xmap;
-  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  alignas(64) CUtensorMap xmap, wmap;
+  memset(&wmap, 0, sizeof wmap);
   CUresult r;
-  if (L::SW) {  // (64 channels = one 128-byte row, W, H), box 64 x 130 x 4, 128-byte swizzle
+  if (L::SW) {
+    // input (64 channels = one 128-byte row, W, H), box 64 x 130 x 3, 128-byte swizzle
+    const cuuint32_t estr[3] = {1, 1, 1};
     const cuuint64_t dims[3] = {(cuuint64_t)CIN, (cuuint64_t)W, (cuuint64_t)H};
     const cuuint64_t strides[2] = {(cuuint64_t)CIN * 2, (cuuint64_t)W * CIN * 2};
     const cuuint32_t box[3] = {(cuuint32_t)CIN, (cuuint32_t)TPW, (cuuint32_t)TPR};
     r = enc(&xmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(x), dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  } else {  // (8 channels of a chunk, W, H, chunk): the box lands chunk-major
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    // weights [c_out][tap][c_in] as (c_in, tap, c_out): the box (64, 1, C_out) of tap t lands as C_out
+    // rows of 128 bytes, 128-byte swizzle (the B operand of tap t)
+    const cuuint64_t wdims[3] = {(cuuint64_t)CIN, 9, (cuuint64_t)COUT};
+    const cuuint64_t wstrides[2] = {(cuuint64_t)CIN * 2, (cuuint64_t)9 * CIN * 2};
+    const cuuint32_t wbox[3] = {(cuuint32_t)CIN, 1, (cuuint32_t)COUT};
+    r = enc(&wmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(w), wdims, wstrides, wbox, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  } else {  // (8 channels of a chunk, W, H, chunk): the box 8 x 130 x 3 x CH lands chunk-major
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
     const cuuint64_t dims[4] = {8, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)L::CH};
     const cuuint64_t strides[3] = {(cuuint64_t)CIN * 2, (cuuint64_t)W * CIN * 2, 16};
     const cuuint32_t box[4] = {8, (cuuint32_t)TPW, (cuuint32_t)TPR, (cuuint32_t)L::CH};
@@ -594,10 +652,11 @@ cudaError_t tc_launch(int H, int W, const void* x, const void* w, const float* b
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   }
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-  const int nitems = (H / TROWS) * (W / TPX);
+  const int nitems = H * (W / TPX);
   const int grid = nitems < grid_max[dev] ? nitems : grid_max[dev];
   conv_fwd_tc_kernel<CIN, COUT><<<grid, TTHR, L::BYTES, st>>>(H, W, (const bf16*)x, (const bf16*)w, b,
-                                                               (const bf16*)mask, relu, (bf16*)y, yf, err[dev], xmap);
+                                                               (const bf16*)mask, relu, (bf16*)y, yf, err[dev], xmap,
+                                                               wmap);
   return cudaGetLastError();
 }
 

@@ -21,6 +21,8 @@ struct vlb_handle {
   double* totals;      // 8 doubles (read-out)
   double* diag;        // 8 doubles (last in-step diagnostic)
   int* flag;           // device flag: diagnostics found an unstable state (1) or a bulk copy gave up (2)
+  void* dphi = nullptr;  // stabilised Cahn-Hilliard: dt L_phi of a stage (state precision, N)
+  void* fft = nullptr;   // stabilised Cahn-Hilliard: complex spectrum (N complex)
   vlb::StageMaps* maps = nullptr;  // FP32 UW3: tensor maps of the three stage inputs (NULL: per-thread copies)
   vlb::EnsembleMaps* ens_maps = nullptr;  // ensemble: members' tensor maps, passed to each launch
   double n0;           // reference density of the stored deviations g = f - n0 w_i w_j

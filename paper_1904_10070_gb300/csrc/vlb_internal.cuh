@@ -71,6 +71,8 @@ struct StageArgs {
   T n0;             // reference density of the stored deviations
   int* err;         // device flag raised if a bounded wait on a bulk copy gives up (may be NULL)
   int ahead;        // tensor-map path: CTAs resident at once; each prefetches the tile this many ahead
+  T* dphi = nullptr;  // stabilised Cahn-Hilliard: receives dt L_phi per node, and phi is not written
+                      // (launch_ch_stab forms it); NULL: the stage writes phi itself
 };
 
 // Tensor maps of the FP32 UW3 stage kernel over the 18 state arrays: the halo box of the stage
@@ -128,6 +130,16 @@ constexpr int kAxiMaxRows = 4096;
 template <typename T>
 cudaError_t launch_axi(const StageArgs<T>& a, int advection, int ch_mode, T* U0, T* U1, T* U2, int steps,
                        cudaStream_t s);
+
+// Stabilised semi-implicit Cahn-Hilliard (vlb_chsolve.cu): phi_out = phi^n + b (phi_in - phi^n +
+// P(dphi)) with P = J^{-1} (I + dt M kappa D^2)^{-1} J (D: the constant-coefficient periodic Laplacian
+// with spacings h_t, h_p); phi0 NULL in the first stage (phi^n = phi_in).  FP32: phi is a float pair,
+// the low word lo_off elements after the high word.  buf: ch_stab_buffer_bytes of scratch.
+bool ch_stab_shape_ok(int nt, int ns);
+size_t ch_stab_buffer_bytes(int nt, int ns, size_t esize);
+template <typename T>
+cudaError_t launch_ch_stab(int nt, int ns, double dt_m_kappa, double h_t, double h_p, const double* J, const T* dphi,
+                           void* buf, const T* phin, const T* phi0, T* phiout, int64_t lo_off, T b, cudaStream_t st);
 
 // Auxiliary kernels (vlb_aux.cu).  Staging arrays are FP64 [n_theta][n_phi].
 template <typename T>

@@ -91,6 +91,7 @@ const char* check_params(const vlb_params* p) {
   if (p->geometry == VLB_TORUS && !(p->R > p->r)) return "torus needs R > r";
   if (!(p->dt > 0.0) || !isfinite(p->dt) || !(p->tau > 0.0)) return "dt must be finite and > 0, tau > 0";
   if (!(p->M >= 0.0) || !(p->A >= 0.0) || !(p->kappa >= 0.0)) return "M, A, kappa must be >= 0";
+  if (p->ch_stab != 0) return "the no-allocation step runs the explicit Cahn-Hilliard step (ch_stab must be 0)";
   return nullptr;
 }
 

@@ -390,7 +390,9 @@ __device__ __forceinline__ void phase3_node(const StageArgs<T>& a, const VConst<
   }
 
   const int64_t gidx = (int64_t)q * a.ns + s;
-  {
+  if (a.dphi) {
+    a.dphi[gidx] = Lphi * a.dt;  // the stabilised Cahn-Hilliard solve forms phi
+  } else {
     const T lo = DF ? sphl[bi] : T(0);
     T base = ph, base_lo = lo, inc = Lphi * a.dt;
     if (F0) {
@@ -650,7 +652,9 @@ __device__ __forceinline__ void phase3_pair(const StageArgs<float>& a, const VCo
   }
 
   const int64_t gidx = (int64_t)q * a.ns + s;  // even
-  {
+  if (a.dphi) {
+    st2(a.dphi + gidx, mul2(Lphi, f2(a.dt)));  // the stabilised Cahn-Hilliard solve forms phi
+  } else {
     const float2 lo = ld2(sphl + bi);
     float2 base = ph, base_lo = lo, inc = mul2(Lphi, f2(a.dt));
     if (F0) {
@@ -696,16 +700,20 @@ __device__ __forceinline__ void phase3_pair(const StageArgs<float>& a, const VCo
     const float2 ai = mul2(f2(vc.v[i]), ut);
     // BGK relaxation and the closed-form reference part share w_i w_j
     const float2 ci = fma2(f2(a.n0 * vc.v[i]), add2(f2(i >= 2 ? Ep : En), Ft), dntau);
+    // theta-advection weights of this velocity row with -v_i folded in (upwind side by sign(v_i))
+    const float mvi = -vc.v[i];
+    const float t0 = mvi * (i >= 2 ? wp0 : wn0), t1 = mvi * (i >= 2 ? wp1 : wn1);
+    const float t2 = mvi * (i >= 2 ? wp2 : wn2), t3 = mvi * (i >= 2 ? wp3 : wn3);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int k = 4 * i + j;
       const float* fk = sf + k * BQ * BS + bi;
       const float2 gk = g[k];
-      float2 Dt;
+      float2 rhs;  // -v_i (theta flux difference) - v_j (varphi flux difference) / (R J dvarphi)
       if (i >= 2)
-        Dt = fma2(f2(wp3), ld2(fk + BS), fma2(f2(wp2), gk, fma2(f2(wp1), ld2(fk - BS), mul2(f2(wp0), ld2(fk - 2 * BS)))));
+        rhs = fma2(f2(t3), ld2(fk + BS), fma2(f2(t2), gk, fma2(f2(t1), ld2(fk - BS), mul2(f2(t0), ld2(fk - 2 * BS)))));
       else
-        Dt = fma2(f2(wn3), ld2(fk + 2 * BS), fma2(f2(wn2), ld2(fk + BS), fma2(f2(wn1), gk, mul2(f2(wn0), ld2(fk - BS)))));
+        rhs = fma2(f2(t3), ld2(fk + 2 * BS), fma2(f2(t2), ld2(fk + BS), fma2(f2(t1), gk, mul2(f2(t0), ld2(fk - BS)))));
       const float2 A = ld2(fk - 2), C = ld2(fk + 2);
       const float2 M1 = make_float2(A.y, gk.x), M2 = make_float2(gk.y, C.x);
       float2 Dp;
@@ -713,15 +721,14 @@ __device__ __forceinline__ void phase3_pair(const StageArgs<float>& a, const VCo
         Dp = fma2(f2(2.0f), M2, fma2(f2(3.0f), gk, fma2(f2(-6.0f), M1, A)));
       else
         Dp = sub2(fma2(f2(6.0f), M2, fma2(f2(-3.0f), gk, mul2(f2(-2.0f), M1))), C);
-      float2 rhs = fma2(f2(-vc.v[j] * cp6), Dp, mul2(f2(-vc.v[i]), Dt));
+      rhs = fma2(f2(-vc.v[j] * cp6), Dp, rhs);
       float2 dvt = mul2(f2(vc.K[i][0]), g[j]);
-      float2 dvp = mul2(f2(vc.K[j][0]), h[0]);
 #pragma unroll
-      for (int mm = 1; mm < 4; ++mm) {
-        dvt = fma2(f2(vc.K[i][mm]), g[4 * mm + j], dvt);
-        dvp = fma2(f2(vc.K[j][mm]), h[mm], dvp);
-      }
-      rhs = add2(fma2(cj[j], dvt, rhs), dvp);
+      for (int mm = 1; mm < 4; ++mm) dvt = fma2(f2(vc.K[i][mm]), g[4 * mm + j], dvt);
+      rhs = fma2(cj[j], dvt, rhs);
+      // the K~ term accumulates straight into the right-hand side
+#pragma unroll
+      for (int mm = 0; mm < 4; ++mm) rhs = fma2(f2(vc.K[j][mm]), h[mm], rhs);
       // BGK towards the third-order Hermite equilibrium (Eq. feq) plus the reference part
       const float2 xi = fma2(f2(vc.v[j]), up, ai);
       const float2 pm1 = fma2(xi, fma2(xi, fma2(xi, f2(sixth), f2(0.5f)), c0), hu);
@@ -939,7 +946,8 @@ __global__ void __launch_bounds__(TQR * (TS / 2)) ensemble_stage_kernel(const En
 
 // ---------------------------------------------------------------------------------------------
 // Persistent ensemble: one cooperative launch runs whole steps.  Its CTAs (all resident at once)
-// take the work items of a stage round-robin and meet at a grid barrier before the next stage.
+// take the work items of a stage from a ticket counter and meet at a grid barrier before the next
+// stage.
 // The barrier is a counter and a generation word in global memory; a CTA waits for the generation
 // to change for at most `budget` SM clock cycles.  On expiry it raises the ensemble's flag (2), and
 // every CTA that sees the flag raised while waiting returns, so a CTA that never arrives (a lost
@@ -957,8 +965,10 @@ __device__ __forceinline__ int ld_volatile_i32(const int* p) { return *reinterpr
 // ordering between this thread's generic-proxy accesses and later bulk (async-proxy) copies
 __device__ __forceinline__ void fence_proxy_async_all() { asm volatile("fence.proxy.async;\n" ::: "memory"); }
 
-// bar[0]: arrivals, bar[1]: generation.  Returns false if the barrier gave up (flag raised).
-__device__ bool grid_barrier(unsigned* bar, int* err, long long budget, bool skip, int* s_ok) {
+// bar[0]: arrivals, bar[1]: generation, bar[2 + k]: the work-item tickets of stages k = 0, 1 (mod 2).
+// The last CTA to arrive resets the ticket counter `reset` for the stage after the barrier before it
+// releases the others.  Returns false if the barrier gave up (flag raised).
+__device__ bool grid_barrier(unsigned* bar, int* err, long long budget, bool skip, int* s_ok, int reset) {
   fence_proxy_async_all();  // this thread's stores of the stage, before the next stage's bulk copies
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -967,6 +977,7 @@ __device__ bool grid_barrier(unsigned* bar, int* err, long long budget, bool ski
     __threadfence();                              // the CTA's stores (ordered by the CTA barrier) first
     if (!skip && atomicAdd(bar, 1u) + 1u == gridDim.x) {
       atomicExch(bar, 0u);
+      atomicExch(bar + 2 + reset, 0u);
       st_release_u32(bar + 1, g + 1u);
     }
     const long long t0 = clock64();
@@ -1032,23 +1043,34 @@ __global__ void __launch_bounds__(TQR * (TS / 2), TQR == 16 ? 2 : 3) ensemble_pe
   __syncthreads();
   unsigned ph_box = 0, ph_u0 = 0;
   const bool skip = (int)blockIdx.x == skip_cta;
-  bool first = true;
+  __shared__ int s_next, s_next2;
+  int gstage = 0;  // stages run so far in this launch: the ticket counter alternates between two words
   for (int n = 0; n < nsteps; ++n) {
-    for (int stage = 0; stage <= (only0 ? 0 : 2); ++stage) {
-      if (!first && !grid_barrier(bar, err, budget, skip, &s_ok)) return;
-      first = false;
-      for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+    for (int stage = 0; stage <= (only0 ? 0 : 2); ++stage, ++gstage) {
+      if (gstage > 0 && !grid_barrier(bar, err, budget, skip, &s_ok, gstage & 1)) return;
+      unsigned* tickets = bar + 2 + (gstage & 1);
+      // work items are handed out by a ticket counter: a CTA holds the tickets of its current and its
+      // next item, so that the next item's box can be prefetched into L2 and the counter's latency
+      // overlaps the current tile
+      if (tid == 0) {
+        s_next = (int)atomicAdd(tickets, 1u);
+        s_next2 = (int)atomicAdd(tickets, 1u);
+      }
+      __syncthreads();
+      int w = s_next, nxw = s_next2;
+      while (w < nitems) {
         fence_proxy_async_all();  // the previous tile's shared-memory reads, before new copies land
-        __syncthreads();
+        __syncthreads();          // ... and every thread has read s_next
         const int2 it = items[w];
         const EnsembleMember& d = members[it.x];
         const StageArgs<float> a = member_args(d, stage, err);
         const int tiles_s = (d.ns + TS - 1) / TS;
         const int q0 = (it.y / tiles_s) * TQR, s0 = (it.y % tiles_s) * TS;
-        bool tma = false;
-        if constexpr (TQR == 16) {
-          if (tid == 0 && w + (int)gridDim.x < nitems) {  // this CTA's next tile, into L2
-            const int2 nx = items[w + gridDim.x];
+        int after = 0;
+        if (tid == 0) {
+          after = (int)atomicAdd(tickets, 1u);  // used only at the end of the tile
+          if (TQR == 16 && nxw < nitems) {      // the next tile of this CTA, into L2
+            const int2 nx = items[nxw];
             const EnsembleMember& e = members[nx.x];
             const int ts = (e.ns + TS - 1) / TS, qn = (nx.y / ts) * TQR, sn = (nx.y % ts) * TS;
             if (e.maps >= 0 && qn >= L::H && qn + TQR + L::H <= e.nt && sn >= L::HS && sn + TS + L::HS <= e.ns) {
@@ -1056,6 +1078,9 @@ __global__ void __launch_bounds__(TQR * (TS / 2), TQR == 16 ? 2 : 3) ensemble_pe
               if (stage > 0) tma_prefetch_3d(&maps.m[e.maps + 3], sn, qn, 0);
             }
           }
+        }
+        bool tma = false;
+        if constexpr (TQR == 16) {
           tma = d.maps >= 0 && q0 >= L::H && q0 + TQR + L::H <= d.nt && s0 >= L::HS && s0 + TS + L::HS <= d.ns;
           if (tma) {
             if (stage == 0)
@@ -1074,6 +1099,10 @@ __global__ void __launch_bounds__(TQR * (TS / 2), TQR == 16 ? 2 : 3) ensemble_pe
           else
             tile_body<L, float, VLB_UW3, CH, true, 2>(a, vc, sm, tid, q0, s0);
         }
+        if (tid == 0) s_next = after;
+        __syncthreads();
+        w = nxw;
+        nxw = s_next;
       }
     }
   }
@@ -1386,8 +1415,10 @@ cudaError_t launch_pers(const EnsembleMember* members, const int2* items, int ni
   if (grid > nitems) grid = nitems;
   if (grid_out) *grid_out = grid;
   if (grid < 1 || nsteps < 1) return cudaSuccess;
-  // the barrier's counter starts at zero (a launch that gave up may have left arrivals behind)
+  // the arrival counter and both ticket counters start at zero (a launch that gave up may have left
+  // arrivals or tickets behind); the generation word keeps counting
   if ((e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(bar + 2, 0, 2 * sizeof(unsigned), st)) != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(L::NTH);

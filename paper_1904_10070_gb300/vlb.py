@@ -56,16 +56,16 @@ class vlb_ensemble_config(ctypes.Structure):
 class vlb_params(ctypes.Structure):
     _fields_ = [("geometry", ctypes.c_int32), ("n_theta", ctypes.c_int32), ("n_phi", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("advection", ctypes.c_int32), ("ch_mode", ctypes.c_int32),
-                ("diag_every", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("diag_every", ctypes.c_int32), ("ch_stab", ctypes.c_int32),
                 ("R", ctypes.c_double), ("r", ctypes.c_double), ("dt", ctypes.c_double),
                 ("tau", ctypes.c_double), ("M", ctypes.c_double), ("A", ctypes.c_double),
                 ("kappa", ctypes.c_double)]
 
 
 def make_params(R, r, n_theta, n_phi, dt, tau, M, A, kappa, geometry=TORUS, precision=FP64, advection=UW3,
-                ch_mode=HYDRO, diag_every=0) -> vlb_params:
+                ch_mode=HYDRO, diag_every=0, ch_stab=0) -> vlb_params:
     return vlb_params(geometry=geometry, n_theta=n_theta, n_phi=n_phi, precision=precision, advection=advection,
-                      ch_mode=ch_mode, diag_every=diag_every, reserved=0, R=R, r=r, dt=dt, tau=tau, M=M, A=A,
+                      ch_mode=ch_mode, diag_every=diag_every, ch_stab=ch_stab, R=R, r=r, dt=dt, tau=tau, M=M, A=A,
                       kappa=kappa)
 
 

@@ -149,3 +149,22 @@ def test_noalloc_rejects_a_stride_whose_size_would_wrap_around(L):
             vlb.vlb_step_noalloc(p, 256, stride, 1.0, 1, 0)
         assert exc.value.status == vlb.VLB_ERR_ARG
         assert "stride" in str(exc.value)
+
+
+def test_stabilised_cahn_hilliard_parameters(L):
+    """ch_stab = 1 needs power-of-two grids (its Fourier solve); it lifts the Cahn-Hilliard limit of
+    vlb_max_stable_dt, and ensembles and the no-allocation step refuse it."""
+    assert vlb.vlb_workspace_bytes(_p(n_theta=48, n_phi=64, ch_stab=1)) == 0
+    assert "powers of two" in L.vlb_last_error(None).decode()
+    assert vlb.vlb_workspace_bytes(_p(ch_stab=2)) == 0
+    base = dict(n_theta=1024, n_phi=2048, R=2.0, M=2.5e-3, A=0.5, kappa=5e-4, tau=0.6)
+    n_exp = vlb.vlb_workspace_bytes(_p(**base))
+    n_stab = vlb.vlb_workspace_bytes(_p(**base, ch_stab=1))
+    assert n_stab >= n_exp + 1024 * 2048 * 8 * 3  # dt L_phi and the complex spectrum
+    dt_exp = vlb.vlb_max_stable_dt(_p(**base))
+    dt_stab = vlb.vlb_max_stable_dt(_p(**base, ch_stab=1))
+    assert dt_stab > 50 * dt_exp  # the explicit Cahn-Hilliard limit (7e-6 here) no longer binds
+    with pytest.raises(vlb.VlbError) as exc:
+        vlb.vlb_step_noalloc(_p(precision=vlb.FP32, ch_stab=1), 256, 2048, 1.0, 1, 0)
+    assert exc.value.status == vlb.VLB_ERR_ARG
+    assert vlb.vlb_ensemble_workspace_bytes([_p(precision=vlb.FP32, ch_stab=1)]) == 0
