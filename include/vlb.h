@@ -155,6 +155,16 @@ vlb_status vlb_get_totals(vlb_handle* h, double out[4]);
  * FP64 on the GPU; the domain length is L_d = 4 pi^2 r R / L_I (Eq. cart_scaling_L0).  Synchronous. */
 vlb_status vlb_interface_length(vlb_handle* h, double* out);
 
+/* Structure-factor length L_S = 2 pi sum S(k) / sum |k| S(k) over k != 0 (a Fourier measure of the
+ * coarsening domain size beside Sec. 4.1's L_d), with S(m, n) = |sum phi e^{-2 pi i (m q / N_theta +
+ * n s / N_phi)}|^2 on the index grid and wavenumbers k = (m'/r, n'/R), m' and n' the signed frequencies
+ * (the physical side lengths 2 pi r along theta and 2 pi R along varphi; on the torus R is the mean
+ * circumference over 2 pi).  The transform and both sums run in FP64 on the GPU (phi in FP32 is
+ * read as hi + lo); the strip sums are added on the host in a fixed order.  *out = +inf for a
+ * uniform phi.  n_theta and n_phi must be powers of two in [4, 4096] (VLB_ERR_ARG otherwise).  Uses
+ * the handle's staging area.  Synchronous. */
+vlb_status vlb_structure_length(vlb_handle* h, double* out);
+
 /* Device pointer of the resident state (for zero-copy readers on the same device): arrays of
  * n_theta*n_phi elements spaced *stride elements apart -- 16 population deviations
  * g_k = f_k - n0 w_i w_j (n0: the area-weighted mean density at the last set call, rounded to

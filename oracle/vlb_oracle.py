@@ -450,3 +450,31 @@ def domain_length(phi, geo: Geometry) -> float:
 def azimuthal_mean(phi):
     """<phi>_q = (1/N_phi) sum_s phi_{s,q}  (Eq. phiavg, discrete form)."""
     return phi.mean(axis=1)
+
+
+def structure_factor(phi):
+    """S(m, n) = |sum_{q,s} phi_{q,s} exp(-2 pi i (m q / N_theta + n s / N_phi))|^2 on the index grid.
+
+    The structure factor of the coarsening runs (Sec. 4.1 measures the domain size; a Fourier
+    measure is the usual alternative to L_d).  A library FFT is the transform."""
+    return np.abs(np.fft.fft2(phi)) ** 2
+
+
+def structure_length(phi, geo: Geometry) -> float:
+    """L_S = 2 pi sum_k S(k) / sum_k |k| S(k) over all k != 0.
+
+    Wavenumbers on the index grid with the physical lengths 2 pi r along theta and 2 pi R along
+    varphi (the flat domain's sides; on the torus R is the mean circumference over 2 pi):
+    k = (m'/r, n'/R) with m', n' the signed integer frequencies (m' = m - N_theta above N_theta/2).
+    A single mode cos(m theta + n varphi) gives L_S = 2 pi / |k| exactly; a uniform phi gives +inf.
+    """
+    p = geo.p
+    nt, ns = phi.shape
+    S = structure_factor(phi)
+    m = np.fft.fftfreq(nt, 1.0 / nt)[:, None]
+    n = np.fft.fftfreq(ns, 1.0 / ns)[None, :]
+    k = np.sqrt((m / p.r) ** 2 + (n / p.R) ** 2)
+    S = S.copy()
+    S[0, 0] = 0.0
+    den = float((k * S).sum())
+    return 2.0 * math.pi * float(S.sum()) / den if den > 0.0 else math.inf  # uniform phi: no domains

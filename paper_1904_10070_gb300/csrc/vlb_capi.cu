@@ -704,6 +704,39 @@ vlb_status vlb_interface_length(vlb_handle* h, double* out) {
   return st;
 }
 
+vlb_status vlb_structure_length(vlb_handle* h, double* out) {
+  vlb_status st = check_handle(h);
+  if (st) return st;
+  if (!out) return fail(h, VLB_ERR_ARG, "out is NULL");
+  const vlb_params& p = h->p;
+  if (!vlb::ch_stab_shape_ok(p.n_theta, p.n_phi))
+    return fail(h, VLB_ERR_ARG, "vlb_structure_length: n_theta and n_phi must be powers of two in [4, 4096]");
+  // scratch: the FP64 staging area (17 N doubles) holds the spectrum (2 N) and the strip sums
+  double* spec = h->staging;
+  double* part = h->staging + 2 * h->N;
+  const int nb = vlb::structure_blocks(p.n_theta, p.n_phi);
+  if (h->esize == 8) {
+    const double* phi = (const double*)h->U[0] + 16 * h->stride;
+    VLB_CUDA(h, vlb::launch_structure_sums<double>(p.n_theta, p.n_phi, p.r, p.R, phi, nullptr, spec, part,
+                                                   h->stream));
+  } else {
+    const float* phi = (const float*)h->U[0] + 16 * h->stride;
+    VLB_CUDA(h, vlb::launch_structure_sums<float>(p.n_theta, p.n_phi, p.r, p.R, phi, phi + h->stride, spec, part,
+                                                  h->stream));
+  }
+  std::vector<double> sums((size_t)2 * nb);
+  VLB_CUDA(h, cudaMemcpyAsync(sums.data(), part, sums.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  st = sync_and_check(h, "vlb_structure_length", false);
+  double s_sum = 0.0, k_sum = 0.0;
+  for (int b = 0; b < nb; ++b) {
+    s_sum += sums[2 * b];
+    k_sum += sums[2 * b + 1];
+  }
+  // a uniform phi has no domains: its length is infinite
+  *out = k_sum > 0.0 ? 2.0 * M_PI * s_sum / k_sum : INFINITY;
+  return st;
+}
+
 vlb_status vlb_state_device(vlb_handle* h, void** f, int64_t* stride) {
   if (!h) return fail(nullptr, VLB_ERR_ARG, "handle is NULL");
   if (h->kind == 1) return fail(h, VLB_ERR_ARG, "ensemble handle: use a member view");

@@ -226,6 +226,111 @@ cudaError_t launch_ch_stab(int nt, int ns, double dt_m_kappa, double h_t, double
   return cudaGetLastError();
 }
 
+namespace {
+
+// ---- Structure factor S(m, n) = |F phi|^2 and its two sums (the L_S diagnostic) --------------------
+// The same radix-2 transforms in FP64 whatever the state's precision (phi in FP32 is the float pair
+// hi + lo, exact in a double): rows first, then strips of columns, whose CTA sums S and |k| S over its
+// strip (k = (m'/r, n'/R), m' and n' the signed frequencies; the mean mode m = n = 0 is left out) and
+// writes the two sums to part[2 b], part[2 b + 1].
+
+template <typename T>
+__global__ void __launch_bounds__(256) sf_row_kernel(int ns, int logns, const T* phi, const T* phi_lo,
+                                                     C2<double>* buf) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  C2<double>* a = reinterpret_cast<C2<double>*>(raw);
+  C2<double>* tw = a + ns;
+  const int q = blockIdx.x;
+  twiddles(tw, ns);
+  for (int s = threadIdx.x; s < ns; s += blockDim.x) {
+    const int64_t g = (int64_t)q * ns + s;
+    const double v = (double)phi[g] + (phi_lo ? (double)phi_lo[g] : 0.0);
+    a[bitrev(s, logns)] = {v, 0.0};
+  }
+  __syncthreads();
+  fft_strided(a, ns, logns, 1, tw, false);
+  for (int s = threadIdx.x; s < ns; s += blockDim.x) buf[(int64_t)q * ns + s] = a[s];
+}
+
+__global__ void __launch_bounds__(256) sf_col_kernel(int nt, int lognt, int ns, int cw, double kt, double kp,
+                                                     const C2<double>* buf, double* part) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  C2<double>* a = reinterpret_cast<C2<double>*>(raw);
+  C2<double>* tw = a + (size_t)nt * cw;
+  __shared__ double red[2][8];
+  const int n0 = blockIdx.x * cw;
+  twiddles(tw, nt);
+  for (int idx = threadIdx.x; idx < nt * cw; idx += blockDim.x) {
+    const int q = idx / cw, c = idx - q * cw;
+    a[bitrev(q, lognt) * cw + c] = buf[(int64_t)q * ns + n0 + c];
+  }
+  __syncthreads();
+  fft_strided(a, nt, lognt, cw, tw, false);
+  double s_sum = 0.0, k_sum = 0.0;
+  for (int idx = threadIdx.x; idx < nt * cw; idx += blockDim.x) {
+    const int m = idx / cw, n = n0 + idx - m * cw;
+    if (m == 0 && n == 0) continue;
+    const int ms = m <= nt / 2 ? m : m - nt, nsg = n <= ns / 2 ? n : n - ns;
+    const double S = a[idx].x * a[idx].x + a[idx].y * a[idx].y;
+    const double k = sqrt((ms * kt) * (ms * kt) + (nsg * kp) * (nsg * kp));
+    s_sum += S;
+    k_sum += k * S;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s_sum += __shfl_xor_sync(0xffffffffu, s_sum, o);
+    k_sum += __shfl_xor_sync(0xffffffffu, k_sum, o);
+  }
+  const int warp = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    red[0][warp] = s_sum;
+    red[1][warp] = k_sum;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a0 = 0.0, a1 = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      a0 += red[0][w];
+      a1 += red[1][w];
+    }
+    part[2 * blockIdx.x] = a0;
+    part[2 * blockIdx.x + 1] = a1;
+  }
+}
+
+}  // namespace
+
+int structure_blocks(int nt, int ns) {
+  int cw = 1;
+  while (cw < 32 && cw * 2 <= ns && (size_t)nt * cw * 2 * sizeof(C2<double>) <= kColBudget) cw *= 2;
+  return ns / cw;
+}
+
+template <typename T>
+cudaError_t launch_structure_sums(int nt, int ns, double r, double R, const T* phi, const T* phi_lo, void* buf,
+                                  double* part, cudaStream_t st) {
+  if (!ch_stab_shape_ok(nt, ns)) return cudaErrorInvalidValue;
+  const int lognt = ilog2(nt), logns = ilog2(ns);
+  const int cw = ns / structure_blocks(nt, ns);
+  C2<double>* cb = reinterpret_cast<C2<double>*>(buf);
+  const size_t row_bytes = sizeof(C2<double>) * (size_t)ns * 3 / 2;
+  const size_t col_bytes = sizeof(C2<double>) * ((size_t)nt * cw + nt / 2);
+  constexpr size_t row_max = sizeof(C2<double>) * 4096 * 3 / 2;
+  constexpr size_t col_max = kColBudget + sizeof(C2<double>) * 2048;
+  static int m1 = 0, m2 = 0;
+  cudaError_t e;
+  if ((e = smem_attr(sf_row_kernel<T>, row_max, m1)) != cudaSuccess) return e;
+  if ((e = smem_attr(sf_col_kernel, col_max, m2)) != cudaSuccess) return e;
+  sf_row_kernel<T><<<nt, 256, row_bytes, st>>>(ns, logns, phi, phi_lo, cb);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  sf_col_kernel<<<ns / cw, 256, col_bytes, st>>>(nt, lognt, ns, cw, 1.0 / r, 1.0 / R, cb, part);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_structure_sums<float>(int, int, double, double, const float*, const float*, void*,
+                                                  double*, cudaStream_t);
+template cudaError_t launch_structure_sums<double>(int, int, double, double, const double*, const double*, void*,
+                                                   double*, cudaStream_t);
+
 template cudaError_t launch_ch_stab<float>(int, int, double, double, double, const double*, const float*, void*,
                                            const float*, const float*, float*, int64_t, float, cudaStream_t);
 template cudaError_t launch_ch_stab<double>(int, int, double, double, double, const double*, const double*, void*,

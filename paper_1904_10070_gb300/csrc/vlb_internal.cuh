@@ -141,6 +141,14 @@ template <typename T>
 cudaError_t launch_ch_stab(int nt, int ns, double dt_m_kappa, double h_t, double h_p, const double* J, const T* dphi,
                            void* buf, const T* phin, const T* phi0, T* phiout, int64_t lo_off, T b, cudaStream_t st);
 
+// Structure-factor sums (vlb_chsolve.cu, same power-of-two shapes): FP64 transform of phi (+ phi_lo
+// when not NULL) into buf (n_theta * n_phi complex doubles), then structure_blocks(nt, ns) CTAs write
+// part[2 b] = sum S and part[2 b + 1] = sum |k| S over their strips (k = (m'/r, n'/R), mean mode left out).
+int structure_blocks(int nt, int ns);
+template <typename T>
+cudaError_t launch_structure_sums(int nt, int ns, double r, double R, const T* phi, const T* phi_lo, void* buf,
+                                  double* part, cudaStream_t st);
+
 // Auxiliary kernels (vlb_aux.cu).  Staging arrays are FP64 [n_theta][n_phi].
 template <typename T>
 cudaError_t launch_init_feq(T* state, int64_t stride, const double* rho, const double* ut,

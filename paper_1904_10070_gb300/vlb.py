@@ -30,7 +30,8 @@ EXPORTS = ["vlb_workspace_bytes", "vlb_max_stable_dt", "vlb_create", "vlb_destro
            "vlb_reduce_workspace_bytes", "vlb_surrogate_norm", "vlb_surrogate_features", "vlb_surrogate_targets",
            "vlb_surrogate_apply", "vlb_snapshot_compare", "vlb_channel_sums", "vlb_mse_loss", "vlb_adam_step", "vlb_to_bf16",
            "vlb_conv_status", "vlb_test_raise_flag", "vlb_surrogate_workspace_bytes", "vlb_surrogate_create",
-           "vlb_surrogate_advance", "vlb_surrogate_stats", "vlb_ensemble_configure", "vlb_ensemble_get_config"]
+           "vlb_surrogate_advance", "vlb_surrogate_stats", "vlb_ensemble_configure", "vlb_ensemble_get_config",
+           "vlb_structure_length"]
 
 NOALLOC_SCRATCH_BYTES = 24 * 1024 * 1024
 
@@ -99,6 +100,7 @@ def lib() -> ctypes.CDLL:
     L.vlb_get_fields.argtypes, L.vlb_get_fields.restype = [P, D, D, D, D, D], I32
     L.vlb_get_totals.argtypes, L.vlb_get_totals.restype = [P, D], I32
     L.vlb_interface_length.argtypes, L.vlb_interface_length.restype = [P, D], I32
+    L.vlb_structure_length.argtypes, L.vlb_structure_length.restype = [P, D], I32
     L.vlb_state_device.argtypes, L.vlb_state_device.restype = [P, ctypes.POINTER(P), ctypes.POINTER(I64)], I32
     L.vlb_steps_done.argtypes, L.vlb_steps_done.restype = [P, ctypes.POINTER(I64)], I32
     L.vlb_last_error.argtypes, L.vlb_last_error.restype = [P], ctypes.c_char_p
@@ -225,6 +227,12 @@ def vlb_get_totals(h) -> np.ndarray:
 def vlb_interface_length(h) -> float:
     out = ctypes.c_double()
     _check(lib().vlb_interface_length(h, ctypes.byref(out)), h)
+    return out.value
+
+
+def vlb_structure_length(h) -> float:
+    out = ctypes.c_double()
+    _check(lib().vlb_structure_length(h, ctypes.byref(out)), h)
     return out.value
 
 
@@ -453,6 +461,9 @@ class Solver:
 
     def interface_length(self):
         return vlb_interface_length(self.h)
+
+    def structure_length(self):
+        return vlb_structure_length(self.h)
 
     def close(self):
         if self.h is not None:
