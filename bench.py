@@ -51,6 +51,9 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--coarsening", type=int, default=0, metavar="STEPS",
+                    help="run only the three 1024x2048 coarsening runs for STEPS steps each and print their L(t)")
+    ap.add_argument("--coarsening-every", type=int, default=1000)
     return ap.parse_args()
 
 
@@ -434,6 +437,63 @@ def stabilised_measurement(steps: int = 200):
     return out
 
 
+def coarsening_runs(steps: int = 50000, every: int = 1000, dt_cap: float = 5e-4):
+    """Spinodal coarsening from noise +-0.01 on the 1024 x 2048 grid (R = 2, r = 1; A = 0.5,
+    kappa = 5e-4, M = 2.5e-3; Sec. 4.1): the hydrodynamic run (tau = 0.6), the diffusive run (no
+    advection in Eq. CH and no force on the fluid, tau = 6) and the flat periodic control
+    (2 pi r x 2 pi R, square cells), FP32 with the stabilised Cahn-Hilliard stages at
+    dt = min(the paper's 5e-4, 0.8 of their stable dt).  Every `every` steps: the domain length
+    L_d = A_total / L_I (Eq. cart_scaling_L0) and the structure-factor length L_S, the phi total
+    (conserved) and max |u|.  The growth exponent is the least-squares slope of log L against log t
+    over the second half of the samples."""
+    import torch
+    from paper_1904_10070_gb300 import inputs, vlb
+    runs = {"hydro_torus": dict(geometry=0, ch_mode=0, tau=0.6),
+            "diffusive_torus": dict(geometry=0, ch_mode=1, tau=6.0),
+            "hydro_flat": dict(geometry=1, ch_mode=0, tau=0.6)}
+    out = {"steps": steps, "every": every}
+    for name, over in runs.items():
+        w = inputs.workload("coarsen_torus_1024x2048")
+        p = dict(w["params"], **over)
+        dt_max = vlb.vlb_max_stable_dt(vlb.make_params(**{k: p[k] for k in PKEYS}, ch_stab=1))
+        p["dt"] = min(dt_cap, 0.8 * dt_max)
+        s = vlb.Solver(vlb.make_params(**{k: p[k] for k in PKEYS}, precision=vlb.FP32, ch_stab=1))
+        s.set_fields(w["rho"], w["ut"], w["up"], w["phi"])
+        area = 4.0 * math.pi ** 2 * p["r"] * p["R"]
+        tot0 = s.totals()
+        rec = {"t": [], "L_d": [], "L_S": [], "max_u": []}
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        step_ms = 0.0
+        for k in range(steps // every):
+            ev0.record(s.stream)
+            s.step(every)
+            ev1.record(s.stream)
+            ev1.synchronize()
+            step_ms += ev0.elapsed_time(ev1)
+            L_I = s.interface_length()
+            rec["t"].append((k + 1) * every * p["dt"])
+            rec["L_d"].append(area / L_I if L_I > 0 else math.inf)
+            rec["L_S"].append(s.structure_length())
+            rec["max_u"].append(float(s.totals()[3]))
+        tot1 = s.totals()
+        s.close()
+
+        def slope(key):
+            t, L = np.array(rec["t"]), np.array(rec[key])
+            h = len(t) // 2
+            ok = np.isfinite(L[h:]) & (L[h:] > 0)
+            if ok.sum() < 2:
+                return None
+            return float(np.polyfit(np.log(t[h:][ok]), np.log(L[h:][ok]), 1)[0])
+
+        out[name] = dict(dt=p["dt"], tau=p["tau"], ch_mode=p["ch_mode"], geometry=p["geometry"],
+                         ms_per_step=step_ms / (steps // every * every), finite=bool(np.all(np.isfinite(tot1))),
+                         phi_total_drift=float(abs(tot1[1] - tot0[1]) / max(abs(tot0[1]), 1e-30)),
+                         phi_total=[float(tot0[1]), float(tot1[1])],
+                         exponent_L_d=slope("L_d"), exponent_L_S=slope("L_S"), **rec)
+    return out
+
+
 def main():
     args = _args()
     world, rank, local = _dist()
@@ -447,6 +507,10 @@ def main():
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA GPU")
     torch.cuda.set_device(local)
+    if args.coarsening > 0:
+        if rank == 0:
+            print(json.dumps({"coarsening": coarsening_runs(args.coarsening, args.coarsening_every)}), flush=True)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist
