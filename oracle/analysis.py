@@ -74,3 +74,29 @@ def equal_area_drop_radius(R, r, xi, theta0, ref_theta0, ref_radius, n_theta=512
         else:
             hi = mid
     return 0.5 * (lo + hi)
+
+
+def stripe_normal_pressure(n, phi, r: float, R: float, A: float, kappa: float, geometry: int = 0) -> np.ndarray:
+    """P^{theta theta} of an azimuthally symmetric profile (n and phi of theta alone, one value per row):
+    n + p_binary(phi) - kappa phi Delta phi + (kappa / 2) (d_theta phi / r)^2, with k_B T = 1.
+
+    The force of Eq. pbin, n F = -grad p_binary + kappa phi grad Delta phi, is minus the divergence of
+    the Korteweg stress (p_binary - kappa phi Delta phi - kappa |grad phi|^2 / 2) delta + kappa grad phi
+    grad phi; for a profile of theta alone its theta-theta component is the expression above.  Where
+    grad phi = 0 (the centre of a band, the bulk) it reduces to n + p_binary - kappa phi Delta phi, and
+    in the bulk to the pressure n + p_binary of Sec. 3.2.  Delta is the Laplace-Beltrami operator of
+    App. A in the scheme's conservative second-order form; d_theta is a central difference."""
+    n = np.asarray(n, dtype=np.float64)
+    phi = np.asarray(phi, dtype=np.float64)
+    nt = phi.size
+    dth = 2.0 * math.pi / nt
+    th = np.arange(nt) * dth
+    a = r / R if geometry == 0 else 0.0
+    J = 1.0 + a * np.cos(th)
+    Jp = 1.0 + a * np.cos(th + 0.5 * dth)
+    Jm = 1.0 + a * np.cos(th - 0.5 * dth)
+    up, dn = np.roll(phi, -1), np.roll(phi, 1)
+    lap = (Jp * (up - phi) - Jm * (phi - dn)) / (r * r * J * dth * dth)
+    dphi = (up - dn) / (2.0 * r * dth)
+    pb = A * (-0.5 * phi ** 2 + 0.75 * phi ** 4)
+    return n + pb - kappa * phi * lap + 0.5 * kappa * dphi ** 2

@@ -89,6 +89,28 @@ def test_laplace_pressure_at_equilibrium(branch, ns):
     assert abs(C.laplace_pressure_eq(R, r, KAPPA, A, w_eq, branch == "subcritical") / expect - 1.0) < 0.01
 
 
+@pytest.mark.parametrize("ns", [1, 4])
+def test_narrow_stripe_laplace_pressure_with_the_gradient_terms(ns):
+    """A narrow sub-critical stripe (w = 0.6 = 12 xi): the interface tails overlap at the band centre,
+    where phi stops short of the bulk value by eps ~ 4 e^(-sqrt2 w / (2 xi)) and Delta phi ~ 2 eps / xi^2.
+    The bulk formula n + p_binary there misses the gradient term -kappa phi Delta phi ~ -2 A eps of the
+    normal pressure (25% of Delta p); the theta-theta component of the pressure tensor of Eq. pbin
+    carries it and meets Eq. stripe_laplace_gen."""
+    area = C.stripe_area(R, r, math.pi, 0.6)
+    tc_eq, w_eq = C.equilibrium(R, r, area)
+    p = _params(0.1, ns=ns)
+    s = _stripe(p, tc_eq, w_eq)
+    s.step(int(30.0 / p["dt"]))
+    tc, w, rho, phi = _measure(s)
+    s.close()
+    expect = C.laplace_pressure(R, r, KAPPA, A, tc, w)
+    dp_bulk = AN.band_pressure_jump(O.pressure(rho, phi, A), tc, w)
+    dp = AN.band_pressure_jump(AN.stripe_normal_pressure(rho, phi, r, R, A, KAPPA), tc, w)
+    print(f"narrow: dp (bulk formula) {dp_bulk:.6g}, dp (normal pressure) {dp:.6g}, Eq. stripe_laplace_gen {expect:.6g}")
+    assert abs(dp / expect - 1.0) < 0.02
+    assert dp_bulk < 0.85 * expect  # the gap the gradient terms close
+
+
 def test_supercritical_stripe_oscillates_at_omega0():
     area = C.stripe_area(R, r, math.pi, 3.4)
     tc_eq, w_eq = C.equilibrium(R, r, area)
