@@ -121,7 +121,9 @@ vlb_status vlb_get_state(vlb_handle* h, double* f16, double* phi);
 
 /* Advance nsteps SSP-RK3 steps (3 fused-stage launches per step), asynchronously on the stream.
  * Axisymmetric grids (N_phi = 1, N_theta <= 4096) run up to 256 whole steps per launch of a
- * single-CTA kernel instead; the result does not depend on how the steps are grouped.
+ * single-CTA kernel instead.  With the wavefront schedule (vlb_set_schedule) up to 4096 whole steps
+ * run per persistent launch, whose bounded dependency waits raise the same flag as the bulk-copy
+ * waits below.  The result does not depend on how the steps are grouped or scheduled (bit for bit).
  * With diag_every > 0 the totals are checked every diag_every steps and at the end, the
  * stream is synchronised, and VLB_ERR_UNSTABLE is returned if a value was non-finite or
  * max |u| exceeded 2.
@@ -175,6 +177,34 @@ vlb_status vlb_state_device(vlb_handle* h, void** f, int64_t* stride);
 
 /* Steps taken since the last set call. */
 vlb_status vlb_steps_done(const vlb_handle* h, int64_t* out);
+
+/* Execution schedule of vlb_step on a solver handle (not part of the method; the results are the
+ * same bit for bit).  VLB_SCHED_STAGES: one launch per Runge-Kutta stage, every stage streaming the
+ * whole state through HBM.  VLB_SCHED_WAVE: whole steps in one persistent cooperative launch whose
+ * CTAs take 16 x 32 tiles of all three stages in a skewed band order (a stage of a band runs once
+ * the previous stage has finished the band and its two neighbours), so that the intermediate
+ * stages are read back from L2 and only the state itself crosses HBM; it needs an FP32 UW3
+ * explicit grid with N_theta a multiple of 16 and >= 176 and N_phi a multiple of 32 (VLB_ERR_ARG
+ * otherwise).  VLB_SCHED_AUTO (the default) takes the per-stage launches: the stage is bound by
+ * instruction issue rather than HBM, and the wavefront's per-tile dependency waits cost more than the
+ * HBM traffic it saves (measured on GB300: 0.469 against 0.236 ms per step at 1024 x 2048).
+ * vlb_get_schedule writes the schedule vlb_step takes (STAGES or WAVE). */
+enum { VLB_SCHED_AUTO = 0, VLB_SCHED_STAGES = 1, VLB_SCHED_WAVE = 2 };
+vlb_status vlb_set_schedule(vlb_handle* h, int32_t schedule);
+vlb_status vlb_get_schedule(const vlb_handle* h, int32_t* active);
+
+/* Host-only self-check of the wavefront ticket order (no GPU needed): VLB_OK if, for n_bands bands,
+ * the given lag and nsteps steps, every band item appears exactly once and after every band item it
+ * depends on; VLB_ERR_ARG otherwise (also when n_bands <= 2 lag + 2 or lag < 3). */
+vlb_status vlb_test_wave_schedule(int32_t n_bands, int32_t lag, int32_t nsteps);
+
+/* Test hook of the wavefront timeout path (not part of the method): CTA skip_cta (-1: none) of every
+ * later wavefront launch on h never reports its finished tiles, and each dependency wait gives up
+ * after `budget` SM cycles (0: the default, about a second).  The waits that depend on the skipped
+ * tiles then run out, raise the handle's flag (2) and end the launch, so vlb_step with diag_every > 0
+ * and the synchronous readers return VLB_ERR_TIMEOUT; the context stays usable.  (-1, 0) restores
+ * normal operation. */
+vlb_status vlb_test_wave_timeout(vlb_handle* h, int32_t skip_cta, int64_t budget);
 
 /* Message of the last failure on h (or of the calling thread's last handle-less failure when
  * h is NULL).  Never NULL; empty when there was none. */

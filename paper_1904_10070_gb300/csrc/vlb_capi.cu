@@ -80,7 +80,7 @@ struct Layout {
   int64_t N, stride;
   size_t esize;
   size_t off_coefT, off_coefD, off_U[3], off_staging, off_partials, off_totals, off_diag, off_flag, off_dphi, off_fft,
-      total;
+      off_wave, total;
 };
 
 Layout layout(const vlb_params* p) {
@@ -113,6 +113,11 @@ Layout layout(const vlb_params* p) {
     off = align_up(off + (size_t)L.N * L.esize, 256);
     L.off_fft = off;
     off = align_up(off + vlb::ch_stab_buffer_bytes(p->n_theta, p->n_phi, L.esize), 256);
+  }
+  L.off_wave = 0;
+  if (L.esize == 4 && p->advection == VLB_UW3 && !p->ch_stab && vlb::wave_apply(p->n_theta, p->n_phi)) {
+    L.off_wave = off;  // band counters and the ticket of the wavefront schedule
+    off = align_up(off + sizeof(unsigned) * vlb::wave_counter_words(p->n_theta), 256);
   }
   L.total = off;
   return L;
@@ -218,6 +223,15 @@ vlb_status sync_member_n0(vlb_handle* h) {
   return VLB_OK;
 }
 
+constexpr long long kWaveBudget = 1ll << 31;  // SM clock cycles per dependency wait, about a second
+
+// Whether vlb_step takes the wavefront schedule: only when asked for (VLB_SCHED_WAVE) on a grid that
+// has its counters and the stage tensor maps.  VLB_SCHED_AUTO takes the per-stage launches, which
+// measured faster on GB300 (0.236 against 0.469 ms per step at 1024 x 2048).
+bool wave_active(const vlb_handle* h) {
+  return h->kind == 0 && h->wave_cnt && h->maps && h->sched == VLB_SCHED_WAVE;
+}
+
 template <typename T>
 vlb_status run_steps(vlb_handle* h, int64_t nsteps) {
   const vlb_params& p = h->p;
@@ -257,15 +271,34 @@ vlb_status run_steps(vlb_handle* h, int64_t nsteps) {
   // stabilised Cahn-Hilliard: the stage kernel writes dt L_phi, the Fourier solve forms phi
   T* dphi = p.ch_stab ? (T*)h->dphi : nullptr;
   a.dphi = dphi;
-  const double h_t = p.r * (2.0 * M_PI / p.n_theta);
-  const double h_p = (p.geometry == VLB_TORUS ? p.R - p.r : p.R) * (2.0 * M_PI / p.n_phi);
   const double* Jrow = h->coefD + (size_t)vlb::C_J * p.n_theta;
   auto solve = [&](const T* fin, const T* f0, T* fout, T b) -> cudaError_t {
     if (!dphi) return cudaSuccess;
-    return vlb::launch_ch_stab<T>(p.n_theta, p.n_phi, p.dt * p.M * p.kappa, h_t, h_p, Jrow, dphi, h->fft,
+    return vlb::launch_ch_stab<T>(p.n_theta, p.n_phi, p.dt * p.M * p.kappa, Jrow, dphi, h->fft,
                                   fin + vlb::NPOP * h->stride, f0 ? f0 + vlb::NPOP * h->stride : nullptr,
                                   fout + vlb::NPOP * h->stride, h->stride, b, h->stream);
   };
+  if constexpr (sizeof(T) == 4) {
+    if (wave_active(h)) {
+      // whole steps per persistent launch (the wavefront schedule), cut at the diagnostic steps
+      int64_t n = 0;
+      while (n < nsteps) {
+        int64_t chunk = std::min<int64_t>(nsteps - n, vlb::kWaveMaxSteps);
+        if (p.diag_every > 0) chunk = std::min<int64_t>(chunk, p.diag_every - h->steps_done % p.diag_every);
+        VLB_CUDA(h, vlb::launch_wave(a, p.ch_mode, U0, U1, U2, (int)chunk, h->wave_cnt,
+                                     h->wave_budget > 0 ? h->wave_budget : kWaveBudget, h->wave_skip, h->stream,
+                                     h->maps, nullptr));
+        h->steps_done += chunk;
+        n += chunk;
+        if (p.diag_every > 0 && (h->steps_done % p.diag_every == 0 || n == nsteps)) {
+          VLB_CUDA(h, vlb::launch_totals<T>(U0, h->stride, h->coefD, p.n_theta, p.n_phi, p.R, p.r, p.A, p.kappa,
+                                            h->n0, p.geometry, h->partials, vlb::totals_blocks(), h->diag, h->stream));
+          VLB_CUDA(h, vlb_internal_flag(h->diag, h->flag, h->stream));
+        }
+      }
+      return VLB_OK;
+    }
+  }
   for (int64_t n = 0; n < nsteps; ++n) {
     // SSP-RK3 (Shu & Osher 1988): U1 = U + dt L(U); U2 = 3/4 U + 1/4 (U1 + dt L(U1));
     // U <- 1/3 U + 2/3 (U2 + dt L(U2))
@@ -516,6 +549,7 @@ vlb_status vlb_create(const vlb_params* p, void* d_workspace, size_t bytes, void
   h->flag = (int*)(h->ws + L.off_flag);
   h->dphi = p->ch_stab ? h->ws + L.off_dphi : nullptr;
   h->fft = p->ch_stab ? h->ws + L.off_fft : nullptr;
+  h->wave_cnt = L.off_wave ? (unsigned*)(h->ws + L.off_wave) : nullptr;
   h->steps_done = 0;
   h->n0 = 1.0;
   h->err[0] = 0;
@@ -546,6 +580,17 @@ vlb_status vlb_create(const vlb_params* p, void* d_workspace, size_t bytes, void
     e = cudaMemcpyAsync(h->coefT, tabT, L.esize * vlb::NCOEF * nt, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + L.off_U[0], 0, L.off_staging - L.off_U[0], h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream);
+  std::vector<double> lam;
+  if (e == cudaSuccess && p->ch_stab) {
+    // the stabiliser's factor tables of lambda at the finest spacings (r dtheta; (R - r) dvarphi on
+    // the torus, R dvarphi flat), after the spectrum
+    const double h_t = p->r * (2.0 * M_PI / p->n_theta);
+    const double h_p = (p->geometry == VLB_TORUS ? p->R - p->r : p->R) * (2.0 * M_PI / p->n_phi);
+    lam.resize((size_t)p->n_theta + p->n_phi);
+    vlb::ch_stab_tables(p->n_theta, p->n_phi, h_t, h_p, L.esize, lam.data());
+    e = cudaMemcpyAsync((unsigned char*)h->fft + vlb::ch_stab_table_offset(p->n_theta, p->n_phi, L.esize), lam.data(),
+                        L.esize * lam.size(), cudaMemcpyHostToDevice, h->stream);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   free(tab);
   free(tabT);
@@ -702,6 +747,39 @@ vlb_status vlb_interface_length(vlb_handle* h, double* out) {
   st = sync_and_check(h, "vlb_interface_length", false);
   *out = t[5];
   return st;
+}
+
+vlb_status vlb_set_schedule(vlb_handle* h, int32_t schedule) {
+  if (!h) return fail(nullptr, VLB_ERR_ARG, "handle is NULL");
+  if (h->kind != 0) return fail(h, VLB_ERR_ARG, "vlb_set_schedule: solver handles only");
+  if (schedule != VLB_SCHED_AUTO && schedule != VLB_SCHED_STAGES && schedule != VLB_SCHED_WAVE)
+    return fail(h, VLB_ERR_ARG, "vlb_set_schedule: unknown schedule %d", (int)schedule);
+  if (schedule == VLB_SCHED_WAVE && !(h->wave_cnt && h->maps))
+    return fail(h, VLB_ERR_ARG, "vlb_set_schedule: the wavefront schedule needs an FP32 UW3 explicit grid with "
+                                "n_theta a multiple of 16 (at least 176) and n_phi a multiple of 32");
+  h->sched = schedule;
+  return VLB_OK;
+}
+
+vlb_status vlb_get_schedule(const vlb_handle* h, int32_t* active) {
+  if (!h) return fail(nullptr, VLB_ERR_ARG, "handle is NULL");
+  if (!active) return fail(const_cast<vlb_handle*>(h), VLB_ERR_ARG, "NULL output");
+  *active = wave_active(h) ? VLB_SCHED_WAVE : VLB_SCHED_STAGES;
+  return VLB_OK;
+}
+
+vlb_status vlb_test_wave_timeout(vlb_handle* h, int32_t skip_cta, int64_t budget) {
+  if (!h) return fail(nullptr, VLB_ERR_ARG, "handle is NULL");
+  if (h->kind != 0) return fail(h, VLB_ERR_ARG, "vlb_test_wave_timeout: solver handles only");
+  if (budget < 0) return fail(h, VLB_ERR_ARG, "vlb_test_wave_timeout: budget < 0");
+  h->wave_skip = skip_cta < 0 ? -1 : skip_cta;
+  h->wave_budget = budget;
+  return VLB_OK;
+}
+
+vlb_status vlb_test_wave_schedule(int32_t n_bands, int32_t lag, int32_t nsteps) {
+  return vlb::wave_schedule_ok(n_bands, lag, nsteps) ? VLB_OK
+                                                     : fail(nullptr, VLB_ERR_ARG, "wavefront ticket order invalid");
 }
 
 vlb_status vlb_structure_length(vlb_handle* h, double* out) {

@@ -14,7 +14,10 @@
 //   3. transform every row back, take the real part / (N_theta N_phi J), and form phi_out (in FP32 as
 //      the float pair hi + lo with an error-free sum, as the stage kernel does).
 // The FFTs are in-place radix-2 (decimation in time, bit-reversed load) in shared memory, in the
-// state's precision, with twiddles from sincospi; N_theta and N_phi are powers of two <= 4096.
+// state's precision, with twiddles from sincospi; N_theta and N_phi are powers of two <= 4096.  The
+// two factors of lambda, (4/h_theta^2) sin^2(pi m/N_theta) and (4/h_phi^2) sin^2(pi n/N_phi), are
+// tabulated once in FP64 on the host (ch_stab_tables) and rounded to the state precision, so the
+// division runs in that precision with no transcendental per mode.
 #include <math.h>
 
 #include "vlb_internal.cuh"
@@ -44,17 +47,18 @@ __device__ void twiddles(C2<T>* tw, int n) {
   }
 }
 
-// In-place radix-2 FFT along the first index of a[i * w + c] (w interleaved sequences of length n,
-// loaded in bit-reversed order of i).  inverse: conjugate twiddles (unnormalised).
+// In-place radix-2 FFT along the first index of a[i * w + c] (w = 2^logw interleaved sequences of
+// length n, loaded in bit-reversed order of i).  inverse: conjugate twiddles (unnormalised).
 template <typename T>
-__device__ void fft_strided(C2<T>* a, int n, int logn, int w, const C2<T>* tw, bool inverse) {
-  const int nb = (n >> 1) * w;
+__device__ void fft_strided(C2<T>* a, int n, int logn, int logw, const C2<T>* tw, bool inverse) {
+  const int w = 1 << logw;
+  const int nb = (n >> 1) << logw;
   for (int l = 1; l <= logn; ++l) {
     const int half = 1 << (l - 1), step = n >> l;
     for (int idx = threadIdx.x; idx < nb; idx += blockDim.x) {
-      const int i = idx / w, c = idx - i * w;
-      const int grp = i / half, j = i - grp * half;
-      const int i0 = grp * 2 * half + j, i1 = i0 + half;
+      const int i = idx >> logw, c = idx & (w - 1);
+      const int j = i & (half - 1);
+      const int i0 = ((i >> (l - 1)) << l) + j, i1 = i0 + half;
       C2<T> t = tw[j * step];
       if (inverse) t.y = -t.y;
       const C2<T> u = a[i0 * w + c], v = a[i1 * w + c];
@@ -78,47 +82,47 @@ __global__ void __launch_bounds__(256) row_fwd_kernel(int ns, int logns, const T
   const T jq = (T)J[q];
   for (int s = threadIdx.x; s < ns; s += blockDim.x) a[bitrev(s, logns)] = {jq * dphi[(int64_t)q * ns + s], T(0)};
   __syncthreads();
-  fft_strided(a, ns, logns, 1, tw, false);
+  fft_strided(a, ns, logns, 0, tw, false);
   for (int s = threadIdx.x; s < ns; s += blockDim.x) buf[(int64_t)q * ns + s] = a[s];
 }
 
 // 2. Columns n0 .. n0 + cw - 1: F_theta, division by 1 + s lambda(m, n), inverse F_theta.
 template <typename T>
-__global__ void __launch_bounds__(256) col_solve_kernel(int nt, int lognt, int ns, int cw, double sfac, double ct,
-                                                        double cp, C2<T>* buf) {
+__global__ void __launch_bounds__(256) col_solve_kernel(int nt, int lognt, int ns, int lcw, T sfac, const T* lam_t,
+                                                        const T* lam_p, C2<T>* buf) {
   extern __shared__ __align__(16) unsigned char raw[];
   C2<T>* a = reinterpret_cast<C2<T>*>(raw);
-  C2<T>* tw = a + (size_t)nt * cw;
-  const int n0 = blockIdx.x * cw;
+  const int cw = 1 << lcw;
+  C2<T>* tw = a + ((size_t)nt << lcw);
+  const int n0 = blockIdx.x << lcw;
   twiddles(tw, nt);
-  for (int idx = threadIdx.x; idx < nt * cw; idx += blockDim.x) {
-    const int q = idx / cw, c = idx - q * cw;
-    a[bitrev(q, lognt) * cw + c] = buf[(int64_t)q * ns + n0 + c];
+  for (int idx = threadIdx.x; idx < (nt << lcw); idx += blockDim.x) {
+    const int q = idx >> lcw, c = idx & (cw - 1);
+    a[(bitrev(q, lognt) << lcw) + c] = buf[(int64_t)q * ns + n0 + c];
   }
   __syncthreads();
-  fft_strided(a, nt, lognt, cw, tw, false);
-  for (int idx = threadIdx.x; idx < nt * cw; idx += blockDim.x) {
-    const int m = idx / cw, c = idx - m * cw;
-    const double sm = sinpi((double)m / nt), sn = sinpi((double)(n0 + c) / ns);
-    const double lap = ct * sm * sm + cp * sn * sn;
-    const T g = (T)(1.0 / (1.0 + sfac * lap * lap));
+  fft_strided(a, nt, lognt, lcw, tw, false);
+  for (int idx = threadIdx.x; idx < (nt << lcw); idx += blockDim.x) {
+    const int m = idx >> lcw, c = idx & (cw - 1);
+    const T lap = lam_t[m] + lam_p[n0 + c];
+    const T g = T(1) / (T(1) + sfac * lap * lap);
     a[idx].x *= g;
     a[idx].y *= g;
   }
   __syncthreads();
   // back to bit-reversed order for the inverse transform: in-place swaps of the pairs (m, rev(m))
-  for (int idx = threadIdx.x; idx < nt * cw; idx += blockDim.x) {
-    const int m = idx / cw, c = idx - m * cw, r = bitrev(m, lognt);
+  for (int idx = threadIdx.x; idx < (nt << lcw); idx += blockDim.x) {
+    const int m = idx >> lcw, c = idx & (cw - 1), r = bitrev(m, lognt);
     if (m < r) {
       const C2<T> t = a[idx];
-      a[idx] = a[r * cw + c];
-      a[r * cw + c] = t;
+      a[idx] = a[(r << lcw) + c];
+      a[(r << lcw) + c] = t;
     }
   }
   __syncthreads();
-  fft_strided(a, nt, lognt, cw, tw, true);
-  for (int idx = threadIdx.x; idx < nt * cw; idx += blockDim.x) {
-    const int q = idx / cw, c = idx - q * cw;
+  fft_strided(a, nt, lognt, lcw, tw, true);
+  for (int idx = threadIdx.x; idx < (nt << lcw); idx += blockDim.x) {
+    const int q = idx >> lcw, c = idx & (cw - 1);
     buf[(int64_t)q * ns + n0 + c] = a[idx];
   }
 }
@@ -146,7 +150,7 @@ __global__ void __launch_bounds__(256) row_inv_kernel(int ns, int logns, double 
   twiddles(tw, ns);
   for (int s = threadIdx.x; s < ns; s += blockDim.x) a[bitrev(s, logns)] = buf[(int64_t)q * ns + s];
   __syncthreads();
-  fft_strided(a, ns, logns, 1, tw, true);
+  fft_strided(a, ns, logns, 0, tw, true);
   const T scale = (T)(inv_n / J[q]);
   for (int s = threadIdx.x; s < ns; s += blockDim.x) {
     const int64_t g = (int64_t)q * ns + s;
@@ -195,18 +199,33 @@ bool ch_stab_shape_ok(int nt, int ns) {
   return pow2(nt) && pow2(ns);
 }
 
-size_t ch_stab_buffer_bytes(int nt, int ns, size_t esize) { return (size_t)nt * ns * 2 * esize; }
+// the complex spectrum, then the two factor tables of lambda
+size_t ch_stab_buffer_bytes(int nt, int ns, size_t esize) { return ((size_t)nt * ns * 2 + nt + ns) * esize; }
+size_t ch_stab_table_offset(int nt, int ns, size_t esize) { return (size_t)nt * ns * 2 * esize; }
+
+void ch_stab_tables(int nt, int ns, double h_t, double h_p, size_t esize, void* host_out) {
+  for (int i = 0; i < nt + ns; ++i) {
+    const bool th = i < nt;
+    const double sn = sin(M_PI * (th ? i : i - nt) / (th ? nt : ns));
+    const double v = (th ? 4.0 / (h_t * h_t) : 4.0 / (h_p * h_p)) * sn * sn;
+    if (esize == 8)
+      ((double*)host_out)[i] = v;
+    else
+      ((float*)host_out)[i] = (float)v;
+  }
+}
 
 template <typename T>
-cudaError_t launch_ch_stab(int nt, int ns, double dt_m_kappa, double h_t, double h_p, const double* J, const T* dphi,
-                           void* buf, const T* phin, const T* phi0, T* phiout, int64_t lo_off, T b, cudaStream_t st) {
+cudaError_t launch_ch_stab(int nt, int ns, double dt_m_kappa, const double* J, const T* dphi, void* buf, const T* phin,
+                           const T* phi0, T* phiout, int64_t lo_off, T b, cudaStream_t st) {
   if (!ch_stab_shape_ok(nt, ns)) return cudaErrorInvalidValue;
   const int lognt = ilog2(nt), logns = ilog2(ns);
   C2<T>* cb = reinterpret_cast<C2<T>*>(buf);
+  const T* lam = reinterpret_cast<const T*>(buf) + (size_t)nt * ns * 2;  // ch_stab_tables
   const size_t row_bytes = sizeof(C2<T>) * (size_t)ns * 3 / 2;
-  int cw = 1;
-  while (cw < 32 && cw * 2 <= ns && (size_t)nt * cw * 2 * sizeof(C2<T>) <= kColBudget) cw *= 2;
-  const size_t col_bytes = sizeof(C2<T>) * ((size_t)nt * cw + nt / 2);
+  int lcw = 0;
+  while (lcw < 5 && (2 << lcw) <= ns && ((size_t)nt << lcw) * 2 * sizeof(C2<T>) <= kColBudget) ++lcw;
+  const size_t col_bytes = sizeof(C2<T>) * (((size_t)nt << lcw) + nt / 2);
   // the attribute is set once per device to the largest size any grid needs (setting it to a
   // smaller size would cap later launches on larger grids)
   constexpr size_t row_max = sizeof(C2<T>) * 4096 * 3 / 2;
@@ -218,8 +237,7 @@ cudaError_t launch_ch_stab(int nt, int ns, double dt_m_kappa, double h_t, double
   if ((e = smem_attr(row_inv_kernel<T>, row_max, m3)) != cudaSuccess) return e;
   row_fwd_kernel<T><<<nt, 256, row_bytes, st>>>(ns, logns, dphi, J, cb);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  col_solve_kernel<T><<<ns / cw, 256, col_bytes, st>>>(nt, lognt, ns, cw, dt_m_kappa, 4.0 / (h_t * h_t),
-                                                      4.0 / (h_p * h_p), cb);
+  col_solve_kernel<T><<<ns >> lcw, 256, col_bytes, st>>>(nt, lognt, ns, lcw, (T)dt_m_kappa, lam, lam + nt, cb);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   row_inv_kernel<T><<<nt, 256, row_bytes, st>>>(ns, logns, 1.0 / ((double)nt * ns), J, cb, phin, phi0, phiout, lo_off,
                                                b);
@@ -248,7 +266,7 @@ __global__ void __launch_bounds__(256) sf_row_kernel(int ns, int logns, const T*
     a[bitrev(s, logns)] = {v, 0.0};
   }
   __syncthreads();
-  fft_strided(a, ns, logns, 1, tw, false);
+  fft_strided(a, ns, logns, 0, tw, false);
   for (int s = threadIdx.x; s < ns; s += blockDim.x) buf[(int64_t)q * ns + s] = a[s];
 }
 
@@ -265,7 +283,7 @@ __global__ void __launch_bounds__(256) sf_col_kernel(int nt, int lognt, int ns, 
     a[bitrev(q, lognt) * cw + c] = buf[(int64_t)q * ns + n0 + c];
   }
   __syncthreads();
-  fft_strided(a, nt, lognt, cw, tw, false);
+  fft_strided(a, nt, lognt, __ffs(cw) - 1, tw, false);  // cw is a power of two
   double s_sum = 0.0, k_sum = 0.0;
   for (int idx = threadIdx.x; idx < nt * cw; idx += blockDim.x) {
     const int m = idx / cw, n = n0 + idx - m * cw;
@@ -331,9 +349,9 @@ template cudaError_t launch_structure_sums<float>(int, int, double, double, cons
 template cudaError_t launch_structure_sums<double>(int, int, double, double, const double*, const double*, void*,
                                                    double*, cudaStream_t);
 
-template cudaError_t launch_ch_stab<float>(int, int, double, double, double, const double*, const float*, void*,
-                                           const float*, const float*, float*, int64_t, float, cudaStream_t);
-template cudaError_t launch_ch_stab<double>(int, int, double, double, double, const double*, const double*, void*,
-                                            const double*, const double*, double*, int64_t, double, cudaStream_t);
+template cudaError_t launch_ch_stab<float>(int, int, double, const double*, const float*, void*, const float*,
+                                           const float*, float*, int64_t, float, cudaStream_t);
+template cudaError_t launch_ch_stab<double>(int, int, double, const double*, const double*, void*, const double*,
+                                            const double*, double*, int64_t, double, cudaStream_t);
 
 }  // namespace vlb

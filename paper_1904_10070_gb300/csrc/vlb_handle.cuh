@@ -24,6 +24,10 @@ struct vlb_handle {
   void* dphi = nullptr;  // stabilised Cahn-Hilliard: dt L_phi of a stage (state precision, N)
   void* fft = nullptr;   // stabilised Cahn-Hilliard: complex spectrum (N complex)
   vlb::StageMaps* maps = nullptr;  // FP32 UW3: tensor maps of the three stage inputs (NULL: per-thread copies)
+  unsigned* wave_cnt = nullptr;    // FP32 UW3: counters of the wavefront schedule (NULL: not available)
+  int sched = 0;                   // VLB_SCHED_AUTO / STAGES / WAVE (vlb_set_schedule)
+  int wave_skip = -1;              // test hook: a wavefront CTA that never reports its tiles
+  long long wave_budget = 0;       // wavefront dependency-wait budget in SM cycles (0 = default)
   vlb::EnsembleMaps* ens_maps = nullptr;  // ensemble: members' tensor maps, passed to each launch
   double n0;           // reference density of the stored deviations g = f - n0 w_i w_j
   int64_t steps_done;

@@ -119,6 +119,19 @@ cudaError_t launch_ensemble_persistent(const EnsembleMember* members, const int2
                                        int only0, int tile_rows, int ch_mode, unsigned* bar, int* err, long long budget,
                                        int skip_cta, int ctas_per_sm, cudaStream_t s, const EnsembleMaps* maps,
                                        int* grid_out);
+// Wavefront schedule of whole steps in one persistent cooperative launch (FP32 UW3 one torus; see
+// wave_kernel): grids with wave_apply, up to kWaveMaxSteps steps per launch.  cnt: wave_counter_words
+// unsigned words of device scratch (zeroed by the launcher).  A dependency wait that exceeds `budget`
+// SM cycles raises a.err (2) and ends the launch.  stage_maps: the three stages' tensor maps.
+// skip_cta >= 0 makes that CTA never report its tiles (a test of the timeout path).
+constexpr int kWaveLag = 4;
+constexpr int kWaveMaxSteps = 4096;
+bool wave_apply(int nt, int ns);
+bool wave_schedule_ok(int nb, int lag, int nsteps);  // host check of the ticket order
+int wave_counter_words(int nt);
+cudaError_t launch_wave(const StageArgs<float>& a, int ch_mode, float* U0, float* U1, float* U2, int nsteps,
+                        unsigned* cnt, long long budget, int skip_cta, cudaStream_t st, const StageMaps* stage_maps,
+                        int* grid_out);
 // maps: tensor maps for this stage's fin / f0 (FP32 UW3 only), or NULL for per-thread copies.
 template <typename T>
 cudaError_t launch_stage(const StageArgs<T>& a, int advection, int ch_mode, cudaStream_t s,
@@ -134,12 +147,16 @@ cudaError_t launch_axi(const StageArgs<T>& a, int advection, int ch_mode, T* U0,
 // Stabilised semi-implicit Cahn-Hilliard (vlb_chsolve.cu): phi_out = phi^n + b (phi_in - phi^n +
 // P(dphi)) with P = J^{-1} (I + dt M kappa D^2)^{-1} J (D: the constant-coefficient periodic Laplacian
 // with spacings h_t, h_p); phi0 NULL in the first stage (phi^n = phi_in).  FP32: phi is a float pair,
-// the low word lo_off elements after the high word.  buf: ch_stab_buffer_bytes of scratch.
+// the low word lo_off elements after the high word.  buf: ch_stab_buffer_bytes of scratch whose tail
+// holds the N_theta + N_phi factor tables of lambda, written once by ch_stab_tables (host, FP64 then
+// rounded to esize) and copied to the device by the caller.
 bool ch_stab_shape_ok(int nt, int ns);
 size_t ch_stab_buffer_bytes(int nt, int ns, size_t esize);
+size_t ch_stab_table_offset(int nt, int ns, size_t esize);  // bytes from buf to the tables
+void ch_stab_tables(int nt, int ns, double h_t, double h_p, size_t esize, void* host_out);
 template <typename T>
-cudaError_t launch_ch_stab(int nt, int ns, double dt_m_kappa, double h_t, double h_p, const double* J, const T* dphi,
-                           void* buf, const T* phin, const T* phi0, T* phiout, int64_t lo_off, T b, cudaStream_t st);
+cudaError_t launch_ch_stab(int nt, int ns, double dt_m_kappa, const double* J, const T* dphi, void* buf, const T* phin,
+                           const T* phi0, T* phiout, int64_t lo_off, T b, cudaStream_t st);
 
 // Structure-factor sums (vlb_chsolve.cu, same power-of-two shapes): FP64 transform of phi (+ phi_lo
 // when not NULL) into buf (n_theta * n_phi complex doubles), then structure_blocks(nt, ns) CTAs write

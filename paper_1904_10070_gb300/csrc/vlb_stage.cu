@@ -22,6 +22,8 @@
 // 12 warps per SM and all warps issuing copies and shared loads in the same phase, the memory-
 // input queue throttled issue to 30%.
 // Periodic wrap-around is resolved on the copy addresses, so ragged tiles need no special case.
+#include <vector>
+
 #include "vlb_internal.cuh"
 
 namespace vlb {
@@ -1109,6 +1111,187 @@ __global__ void __launch_bounds__(TQR * (TS / 2), TQR == 16 ? 2 : 3) ensemble_pe
 }
 
 // ---------------------------------------------------------------------------------------------
+// Wavefront schedule (FP32 UW3, one torus): `nsteps` whole SSP-RK3 steps in one persistent launch,
+// so that the two intermediate stages of a step are consumed from L2 instead of HBM.
+//
+// A band is the 16 rows of one row of tiles (nb = n_theta / 16 bands, tiles_s tiles each).  Sweep
+// sigma = 3 n + k (step n, stage k) visits the bands in the rotated order b = (sigma + i) mod nb,
+// i = 0 .. nb - 1, and stage k of band b may run once stage k - 1 (stage 2 of step n - 1 for k = 0)
+// has finished bands b - 1, b, b + 1 (the stencil reaches 2 rows, under one band).  The rotation
+// makes position i of a sweep depend only on positions i .. i + 2 of the previous sweep, also across
+// the periodic seam.  Band item (n, k, i) is placed in slot n nb + k lag + i, and CTAs take tiles from
+// one ticket counter in slot order (stage 2 first within a slot), so that the three sweeps of a step
+// trail each other by `lag` bands: the U^(1) and U^(2) a band produces is read again within about
+// 2 lag bands of work, while the state U^n is read once and written once per step from HBM.
+// Every dependency sits in an earlier slot when lag >= 3 and nb > 2 lag + 2, and the CTAs are all
+// resident (cooperative launch), so the CTA holding the oldest unfinished ticket can always proceed.
+//
+// cnt[k nb + b] counts the finished tiles of stage k in band b over the launch (monotone); a wait
+// polls it with acquire loads for at most `budget` SM cycles, then raises err (2) and returns, and
+// every CTA that sees err == 2 while waiting returns too.  Once no reader of an intermediate band is
+// left (stage 2 of band b has waited for stage 1 of b - 1 .. b + 1; stage 0 of the next step for
+// stage 2 of the previous one), its lines are discarded from L2 without write-back.
+// ---------------------------------------------------------------------------------------------
+struct WaveMaps {
+  CUtensorMap box[3];  // halo boxes of U^n, U^(1), U^(2)
+  CUtensorMap tile;    // the U^n tile
+};
+
+// Band item j (0 <= j < 3 nsteps nb) in ticket order -> (n, k, i).  Slots [0, lag) hold stage 0
+// only, [lag, 2 lag) stages 1, 0, [2 lag, nsteps nb) stages 2, 1, 0, then stages 2, 1 for lag
+// slots and stage 2 alone for lag slots (requires nsteps nb >= 2 lag).
+__host__ __device__ __forceinline__ void wave_decode(int j, int nb, int lag, int nsteps, int& n, int& k, int& i) {
+  int s;
+  const int steady_end = 3 * lag + 3 * (nsteps * nb - 2 * lag);
+  if (j < lag) {
+    s = j;
+    k = 0;
+  } else if (j < 3 * lag) {
+    s = lag + (j - lag) / 2;
+    k = 1 - (j - lag) % 2;
+  } else if (j < steady_end) {
+    s = 2 * lag + (j - 3 * lag) / 3;
+    k = 2 - (j - 3 * lag) % 3;
+  } else {
+    const int jj = j - steady_end;
+    if (jj < 2 * lag) {
+      s = nsteps * nb + jj / 2;
+      k = 2 - jj % 2;
+    } else {
+      s = nsteps * nb + lag + (jj - 2 * lag);
+      k = 2;
+    }
+  }
+  const int x = s - k * lag;
+  n = x / nb;
+  i = x - n * nb;
+}
+
+// waits until *c >= need; false if the wait gave up or another CTA did
+__device__ __forceinline__ bool wave_wait(const unsigned* c, unsigned need, int* err, long long budget) {
+  if (ld_acquire_u32(c) >= need) return true;
+  const long long t0 = clock64();
+  while (ld_acquire_u32(c) < need) {
+    if (ld_volatile_i32(err) == 2) return false;
+    if (clock64() - t0 > budget) {
+      atomicCAS(err, 0, 2);
+      atomicCAS(err, 1, 2);
+      return false;
+    }
+    __nanosleep(32);
+  }
+  return true;
+}
+
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+}
+
+// the 18 state arrays of one 16 x 32 tile (128-byte row segments) leave L2 without write-back
+__device__ __forceinline__ void discard_tile(const float* U, int64_t stride, int ns, int q0, int s0, int tid) {
+  constexpr int LINES = (NARR + 1) * 16;
+  for (int l = tid; l < LINES; l += 256) {
+    const int arr = l / 16, row = l % 16;
+    const float* p = U + arr * stride + (int64_t)(q0 + row) * ns + s0;
+    asm volatile("discard.global.L2 [%0], 128;\n" ::"l"(p) : "memory");
+  }
+}
+
+template <int CH>
+__global__ void __launch_bounds__(256, 2) wave_kernel(StageArgs<float> base, float* U0, float* U1, float* U2,
+                                                      int nsteps, int lag, unsigned* cnt, int* err, long long budget,
+                                                      int skip_cta, VConst<float> vc,
+                                                      const __grid_constant__ WaveMaps maps) {
+  using L = GenericLay<float, VLB_UW3>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ int s_item[2], s_go;
+  float* sm = reinterpret_cast<float*>(smem_raw);
+  const int tid = threadIdx.x;
+  const int nb = base.nt / L::TQ, tiles_s = base.ns / TS;
+  const int total = 3 * nsteps * nb * tiles_s;
+  unsigned* tickets = cnt + 3 * nb;
+  if (tid == 0) {
+    uint64_t* mb = reinterpret_cast<uint64_t*>(sm + L::MB_OFF);
+    mbar_init(mb, 1);
+    mbar_init(mb + 1, 1);
+    fence_mbar_init();
+    s_item[0] = (int)atomicAdd(tickets, 1u);
+    s_item[1] = (int)atomicAdd(tickets, 1u);
+  }
+  __syncthreads();
+  unsigned ph_box = 0, ph_u0 = 0;
+  int t = s_item[0], tn = s_item[1];
+  while (t < total) {
+    const int j = t / tiles_s, c = t - j * tiles_s;
+    int n, k, i;
+    wave_decode(j, nb, lag, nsteps, n, k, i);
+    const int b = (3 * n + k + i) % nb;
+    const int q0 = b * L::TQ, s0 = c * TS;
+    if (tid == 0) {
+      // dependencies: the previous sweep on bands b - 1, b, b + 1
+      bool ok = true;
+      const int kp = k == 0 ? 2 : k - 1;
+      const unsigned need = (unsigned)((k == 0 ? n : n + 1) * tiles_s);
+      if (k > 0 || n > 0) {
+        for (int d = -1; d <= 1 && ok; ++d) ok = wave_wait(cnt + kp * nb + (b + d + nb) % nb, need, err, budget);
+      }
+      fence_proxy_async_all();  // the other CTAs' stores, before this CTA's bulk copies read them
+      // the next tile of this CTA, into L2 (a hint: its inputs may not be final yet)
+      if (ok && tn < total) {
+        const int jn = tn / tiles_s, cn = tn - jn * tiles_s;
+        int nn, kn, in_;
+        wave_decode(jn, nb, lag, nsteps, nn, kn, in_);
+        const int qn = ((3 * nn + kn + in_) % nb) * L::TQ, sn = cn * TS;
+        if (qn >= L::H && qn + L::TQ + L::H <= base.nt && sn >= L::HS && sn + TS + L::HS <= base.ns) {
+          tma_prefetch_3d(&maps.box[kn], sn - L::HS, qn - L::H, 0);
+          if (kn > 0) tma_prefetch_3d(&maps.tile, sn, qn, 0);
+        }
+      }
+      s_go = ok;
+      s_item[0] = (int)atomicAdd(tickets, 1u);  // the ticket after next, used at the end of the tile
+    }
+    __syncthreads();
+    if (!s_go) return;
+    // no reader of these intermediate bands is left
+    if (k == 2) discard_tile(U1, base.stride, base.ns, q0, s0, tid);
+    if (k == 0 && n > 0) discard_tile(U2, base.stride, base.ns, q0, s0, tid);
+    StageArgs<float> a = base;
+    a.fin = k == 0 ? U0 : (k == 1 ? U1 : U2);
+    a.f0 = k == 0 ? nullptr : U0;
+    a.fout = k == 0 ? U1 : (k == 1 ? U2 : U0);
+    a.b = k == 0 ? 1.0f : (k == 1 ? 0.25f : 2.0f / 3.0f);
+    a.ahead = 0;
+    a.err = err;
+    const bool tma = q0 >= L::H && q0 + L::TQ + L::H <= a.nt && s0 >= L::HS && s0 + TS + L::HS <= a.ns;
+    if (tma) {
+      if (k == 0)
+        tile_body_tma<L, CH, false>(a, vc, sm, tid, q0, s0, &maps.box[0], &maps.tile, false, ph_box, ph_u0);
+      else
+        tile_body_tma<L, CH, true>(a, vc, sm, tid, q0, s0, &maps.box[k], &maps.tile, false, ph_box, ph_u0);
+      ph_box ^= 1u;
+      if (k > 0) ph_u0 ^= 1u;
+    } else {
+      if (k == 0)
+        tile_body<L, float, VLB_UW3, CH, false, 1>(a, vc, sm, tid, q0, s0);
+      else
+        tile_body<L, float, VLB_UW3, CH, true, 1>(a, vc, sm, tid, q0, s0);
+    }
+    // this tile's stores, before the consumers' bulk copies; the CTA's shared-memory reads, before
+    // the next tile's copies land
+    fence_proxy_async_all();
+    __syncthreads();
+    if (ld_volatile_i32(err) == 2) return;  // a copy of this CTA (or another) gave up
+    if (tid == 0 && (int)blockIdx.x != skip_cta) {  // skip_cta: test hook, a CTA that never reports
+      __threadfence();
+      red_release_add(cnt + k * nb + b, 1u);
+    }
+    t = tn;
+    tn = s_item[0];
+    __syncthreads();  // every thread has read s_item before thread 0 rewrites it
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
 // Axisymmetric special case, n_phi = 1.  With one varphi column every varphi difference is zero:
 // the varphi flux of f and of u^phi phi, the varphi part of the Laplace-Beltrami operator and the
 // force component F^phi all vanish, while u^phi itself (a swirl) and the inertial terms through
@@ -1548,6 +1731,90 @@ cudaError_t launch_ensemble_persistent(const EnsembleMember* members, const int2
                                                             skip_cta, ctas_per_sm, s, m, grid_out)
                               : launch_pers<16, VLB_DIFFUSIVE>(members, items, nitems, nsteps, only0, bar, err, budget,
                                                                 skip_cta, ctas_per_sm, s, m, grid_out);
+}
+
+bool wave_schedule_ok(int nb, int lag, int nsteps) {
+  if (lag < 3 || nb <= 2 * lag + 2 || nsteps < 1) return false;
+  // every band item's dependencies sit in earlier tickets (checked by enumeration for small launches)
+  if ((int64_t)3 * nsteps * nb > (int64_t)1 << 20) return true;
+  std::vector<int> pos((size_t)3 * nsteps * nb, -1);  // ticket position of (n, k, band)
+  for (int j = 0; j < 3 * nsteps * nb; ++j) {
+    int n, k, i;
+    wave_decode(j, nb, lag, nsteps, n, k, i);
+    if (n < 0 || n >= nsteps || k < 0 || k > 2 || i < 0 || i >= nb) return false;
+    const size_t at = ((size_t)n * 3 + k) * nb + (3 * n + k + i) % nb;
+    if (pos[at] != -1) return false;  // each band item exactly once
+    pos[at] = j;
+  }
+  for (int n = 0; n < nsteps; ++n)
+    for (int k = 0; k < 3; ++k)
+      for (int b = 0; b < nb; ++b) {
+        if (k == 0 && n == 0) continue;
+        const int np = k == 0 ? n - 1 : n, kp = k == 0 ? 2 : k - 1;
+        for (int d = -1; d <= 1; ++d)
+          if (pos[((size_t)np * 3 + kp) * nb + (b + d + nb) % nb] >= pos[((size_t)n * 3 + k) * nb + b]) return false;
+      }
+  return true;
+}
+
+bool wave_apply(int nt, int ns) {
+  using L = GenericLay<float, VLB_UW3>;
+  return stage_maps_apply(nt, ns) && nt % L::TQ == 0 && ns % TS == 0 && nt / L::TQ > 2 * kWaveLag + 2;
+}
+
+int wave_counter_words(int nt) { return 3 * (nt / 16) + 1; }
+
+template <int CH>
+cudaError_t launch_wave_t(const StageArgs<float>& a, float* U0, float* U1, float* U2, int nsteps, unsigned* cnt,
+                          long long budget, int skip_cta, cudaStream_t st, const WaveMaps& maps, int* grid_out) {
+  using L = GenericLay<float, VLB_UW3>;
+  static int mask = 0;
+  cudaError_t e = ensure_smem(wave_kernel<CH>, L::BYTES, mask);
+  if (e != cudaSuccess) return e;
+  static const VConst<float> vc = make_vconst<float>();
+  static int occ[32] = {0}, sms[32] = {0};
+  int dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if (dev >= 32) return cudaErrorInvalidDevice;
+  if (occ[dev] == 0) {
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[dev], wave_kernel<CH>, 256, L::BYTES)) != cudaSuccess)
+      return e;
+    if ((e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if (occ[dev] < 1) return cudaErrorInvalidConfiguration;
+  }
+  const int nb = a.nt / L::TQ, tiles = nb * (a.ns / TS);
+  int grid = occ[dev] * sms[dev];
+  if (grid > 3 * tiles) grid = 3 * tiles;
+  if (grid_out) *grid_out = grid;
+  if ((e = cudaMemsetAsync(cnt, 0, sizeof(unsigned) * wave_counter_words(a.nt), st)) != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = L::BYTES;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;  // every ticket holder is resident: the waits end
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, wave_kernel<CH>, a, U0, U1, U2, nsteps, kWaveLag, cnt, a.err, budget, skip_cta, vc,
+                            maps);
+}
+
+cudaError_t launch_wave(const StageArgs<float>& a, int ch_mode, float* U0, float* U1, float* U2, int nsteps,
+                        unsigned* cnt, long long budget, int skip_cta, cudaStream_t st, const StageMaps* stage_maps,
+                        int* grid_out) {
+  if (!wave_apply(a.nt, a.ns) || !stage_maps || nsteps < 1 || nsteps > kWaveMaxSteps) return cudaErrorInvalidValue;
+  for (float* u : {U0, U1, U2})
+    if (((uintptr_t)u) % 128 != 0 || a.stride % 32 != 0) return cudaErrorInvalidValue;  // discarded lines
+  WaveMaps m;
+  m.box[0] = stage_maps[0].box;
+  m.box[1] = stage_maps[1].box;
+  m.box[2] = stage_maps[2].box;
+  m.tile = stage_maps[1].tile;
+  return ch_mode == VLB_HYDRO
+             ? launch_wave_t<VLB_HYDRO>(a, U0, U1, U2, nsteps, cnt, budget, skip_cta, st, m, grid_out)
+             : launch_wave_t<VLB_DIFFUSIVE>(a, U0, U1, U2, nsteps, cnt, budget, skip_cta, st, m, grid_out);
 }
 
 template <typename T>

@@ -31,7 +31,8 @@ EXPORTS = ["vlb_workspace_bytes", "vlb_max_stable_dt", "vlb_create", "vlb_destro
            "vlb_surrogate_apply", "vlb_snapshot_compare", "vlb_channel_sums", "vlb_mse_loss", "vlb_adam_step", "vlb_to_bf16",
            "vlb_conv_status", "vlb_test_raise_flag", "vlb_surrogate_workspace_bytes", "vlb_surrogate_create",
            "vlb_surrogate_advance", "vlb_surrogate_stats", "vlb_ensemble_configure", "vlb_ensemble_get_config",
-           "vlb_structure_length"]
+           "vlb_structure_length", "vlb_set_schedule", "vlb_get_schedule", "vlb_test_wave_schedule",
+           "vlb_test_wave_timeout"]
 
 NOALLOC_SCRATCH_BYTES = 24 * 1024 * 1024
 
@@ -101,6 +102,11 @@ def lib() -> ctypes.CDLL:
     L.vlb_get_totals.argtypes, L.vlb_get_totals.restype = [P, D], I32
     L.vlb_interface_length.argtypes, L.vlb_interface_length.restype = [P, D], I32
     L.vlb_structure_length.argtypes, L.vlb_structure_length.restype = [P, D], I32
+    L.vlb_set_schedule.argtypes, L.vlb_set_schedule.restype = [P, ctypes.c_int32], I32
+    L.vlb_get_schedule.argtypes, L.vlb_get_schedule.restype = [P, ctypes.POINTER(ctypes.c_int32)], I32
+    L.vlb_test_wave_schedule.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+    L.vlb_test_wave_schedule.restype = I32
+    L.vlb_test_wave_timeout.argtypes, L.vlb_test_wave_timeout.restype = [P, ctypes.c_int32, I64], I32
     L.vlb_state_device.argtypes, L.vlb_state_device.restype = [P, ctypes.POINTER(P), ctypes.POINTER(I64)], I32
     L.vlb_steps_done.argtypes, L.vlb_steps_done.restype = [P, ctypes.POINTER(I64)], I32
     L.vlb_last_error.argtypes, L.vlb_last_error.restype = [P], ctypes.c_char_p
@@ -228,6 +234,28 @@ def vlb_interface_length(h) -> float:
     out = ctypes.c_double()
     _check(lib().vlb_interface_length(h, ctypes.byref(out)), h)
     return out.value
+
+
+SCHED_AUTO, SCHED_STAGES, SCHED_WAVE = 0, 1, 2
+
+
+def vlb_set_schedule(h, schedule: int):
+    _check(lib().vlb_set_schedule(h, int(schedule)), h)
+
+
+def vlb_get_schedule(h) -> int:
+    out = ctypes.c_int32()
+    _check(lib().vlb_get_schedule(h, ctypes.byref(out)), h)
+    return out.value
+
+
+def vlb_test_wave_schedule(n_bands: int, lag: int, nsteps: int) -> bool:
+    """Host-only check of the wavefront ticket order (no GPU needed)."""
+    return lib().vlb_test_wave_schedule(int(n_bands), int(lag), int(nsteps)) == 0
+
+
+def vlb_test_wave_timeout(h, skip_cta: int, budget: int):
+    _check(lib().vlb_test_wave_timeout(h, int(skip_cta), int(budget)), h)
 
 
 def vlb_structure_length(h) -> float:
@@ -464,6 +492,12 @@ class Solver:
 
     def structure_length(self):
         return vlb_structure_length(self.h)
+
+    def set_schedule(self, schedule: int):
+        vlb_set_schedule(self.h, schedule)
+
+    def schedule(self) -> int:
+        return vlb_get_schedule(self.h)
 
     def close(self):
         if self.h is not None:
