@@ -1,0 +1,104 @@
+"""The paper's torus physics runs that need long horizons, on the CUDA path (FP32).
+
+* Drops on a torus (Sec. 3.4, Fig. drops): a phi = -1 drop of Eq. drop_init at theta_0 = pi/2 or
+  9 pi/10 (R_0 = 0.938, 0.910: the equal-area radii printed with the figure), r = 0.8, R = 2,
+  kappa = 5e-4, A = 0.5, tau = M = 2.5e-3.  The paper: drops drift to the outer equator theta = 0,
+  overshoot it and relax there in a damped oscillation.  Run with the stabilised Cahn-Hilliard stages
+  (their own stable step; 256 x 1024) to t = 300.
+* Thin and reference tori (Sec. 4.1.2, Fig. tscal-ev-fat): even-mixture coarsening from noise +-0.1 at
+  n0 = 20 on R = 2.5, r = 1 and R = 5, r = 0.5 (equal areas), 400 x 800 as in the paper, explicit step.
+  The paper: finite-size effects (departure from the 2/3 growth) appear sooner on the thinner torus,
+  whose poloidal circumference 2 pi r is smaller.  Both tori coarsen alike while domains are small, and
+  the apparent exponent of L_d = A/L_I over t = 140 .. 250 is near 2/3 on the reference torus and
+  clearly below it on the thin one."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1904_10070_gb300 import inputs, vlb
+
+pytestmark = pytest.mark.gpu
+
+
+def _drop_run(theta0, R0, t_end=300.0, every=25.0):
+    R, r, A, kappa = 2.0, 0.8, 0.5, 5e-4
+    nt, ns = 256, 1024
+    xi = math.sqrt(kappa / A)
+    p = dict(geometry=0, R=R, r=r, n_theta=nt, n_phi=ns, dt=1.0, tau=2.5e-3, M=2.5e-3, A=A, kappa=kappa,
+             advection=0, ch_mode=0)
+    p["dt"] = 0.8 * vlb.vlb_max_stable_dt(vlb.make_params(**p, ch_stab=1))
+    s = vlb.Solver(vlb.make_params(**p, precision=vlb.FP32, ch_stab=1))
+    phi = inputs.drop_phi(R, r, nt, ns, theta0, R0, xi, inside=-1.0)
+    z = np.zeros_like(phi)
+    s.set_fields(np.ones_like(phi), z, z, phi)
+    th = (np.arange(nt) * 2 * math.pi / nt)[:, None]
+    J = 1 + (r / R) * np.cos(th)
+    tot0 = s.totals()
+
+    def centre():
+        ph = s.fields()[3]
+        wgt = np.clip(-ph, 0, None) * J
+        return math.atan2(float(np.sum(wgt * np.sin(th))), float(np.sum(wgt * np.cos(th)))) / math.pi, ph
+
+    traj, done = [], 0
+    for k in range(int(t_end / every) + 1):
+        n = int(round(k * every / p["dt"])) - done
+        if n > 0:
+            s.step(n)
+            done += n
+        c, ph = centre()
+        traj.append((k * every, c))
+    tot1 = s.totals()
+    s.close()
+    return np.array(traj), tot0, tot1, float(ph.min())
+
+
+@pytest.mark.parametrize("theta0,R0", [(0.5 * math.pi, 0.938), (0.9 * math.pi, 0.910)])
+def test_drop_drifts_to_the_outer_equator_and_settles(theta0, R0):
+    traj, tot0, tot1, phimin = _drop_run(theta0, R0)
+    t, c = traj[:, 0], traj[:, 1]
+    print("theta_c / pi:", [(int(a), round(b, 3)) for a, b in traj])
+    assert abs(c[0] - theta0 / math.pi) < 0.03
+    assert c[t == 50][0] < theta0 / math.pi - 0.3  # it has moved towards theta = 0
+    assert np.min(c[t <= 175]) < -0.1              # and overshot the outer equator
+    assert np.all(np.abs(c[t >= 275]) < 0.15)       # settling there
+    assert phimin < -0.9                            # the drop is still there
+    assert abs(tot1[1] - tot0[1]) <= 1e-5 * abs(tot0[1])
+
+
+def _coarsen(R, r, t_marks):
+    nt, ns = 400, 800
+    p = dict(geometry=0, R=R, r=r, n_theta=nt, n_phi=ns, dt=1.0, tau=2.5e-3, M=2.5e-3, A=0.5, kappa=5e-4,
+             advection=0, ch_mode=0)
+    p["dt"] = min(5e-4, 0.9 * vlb.vlb_max_stable_dt(vlb.make_params(**p)))
+    s = vlb.Solver(vlb.make_params(**p, precision=vlb.FP32))
+    phi = inputs.noise(3, nt, ns, 0.1)
+    z = np.zeros_like(phi)
+    s.set_fields(np.full_like(phi, 20.0), z, z, phi)
+    area = 4 * math.pi ** 2 * R * r
+    done, Ld = 0, []
+    for t in t_marks:
+        n = int(round(t / p["dt"])) - done
+        s.step(n)
+        done += n
+        Ld.append(area / s.interface_length())
+    assert np.all(np.isfinite(s.totals()))
+    s.close()
+    return np.array(Ld)
+
+
+def test_thin_torus_shows_finite_size_effects_sooner():
+    t_marks = np.array([10, 20, 30, 40, 50, 70, 100, 140, 170, 200, 225, 250], dtype=float)
+    ref = _coarsen(2.5, 1.0, t_marks)
+    thin = _coarsen(5.0, 0.5, t_marks)
+    print("L_d ref :", np.round(ref, 4).tolist())
+    print("L_d thin:", np.round(thin, 4).tolist())
+    early = t_marks <= 50
+    assert np.all(np.abs(thin[early] / ref[early] - 1.0) < 0.1)  # small domains: the same coarsening
+    late = t_marks >= 140
+    e_ref = np.polyfit(np.log(t_marks[late]), np.log(ref[late]), 1)[0]
+    e_thin = np.polyfit(np.log(t_marks[late]), np.log(thin[late]), 1)[0]
+    print(f"apparent exponents over t = 140 .. 250: reference {e_ref:.3f}, thin {e_thin:.3f}")
+    assert 0.45 < e_ref < 0.9          # near the 2/3 of the inertial-hydrodynamic regime
+    assert e_thin < e_ref - 0.1        # the thin torus has left it
