@@ -446,6 +446,55 @@ struct WgLay {
   static_assert(DY % 1024 == 0 && XR % 1024 == 0, "swizzle atoms stay aligned");
 };
 
+// Bias gradient folded into the weight-gradient kernels: in the CTAs of tap row 1 (every pixel row
+// once) the epilogue warps, idle until the accumulators are done, add up the staged dY segments.
+// Thread t (0 .. 127) sums channel t % DC over the pixels t / DC, t / DC + 128 / DC, ... of a segment
+// (DC = 64: 128-byte rows, chunk c at c ^ (j % 8); DC = 16: 32-byte rows, chunk c at c ^ ((j / 4) % 2)),
+// then releases the stage together with the MMAs (the stage's empty barrier counts both).
+template <int DC>
+__device__ __forceinline__ float dy_column_sum(const unsigned char* dyb, int t) {
+  const int c = t % DC, j0 = t / DC;
+  float s = 0.0f;
+#pragma unroll 8
+  for (int j = j0; j < TPX; j += 128 / DC) {
+    const int chunk = DC == 64 ? ((c >> 3) ^ (j & 7)) : ((c >> 3) ^ ((j >> 2) & 1));
+    s += __bfloat162float(*reinterpret_cast<const bf16*>(dyb + j * (DC * 2) + (chunk << 4) + (c & 7) * 2));
+  }
+  return s;
+}
+
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;\n" ::: "memory"); }
+
+// the epilogue warps' share of a bias-gradient CTA: per segment, wait for its stage (one thread
+// waits, the verdict is broadcast), add it up, release it; returns false if a wait gave up
+template <int DC, int NS>
+__device__ __forceinline__ bool bias_segments(const unsigned char* sm, int stage_bytes, uint64_t* full,
+                                              uint64_t* empty, int nmine, int tid, uint32_t* flag, float& acc) {
+  for (int k = 0; k < nmine; ++k) {
+    const int b = k % NS;
+    if (tid == 0) *flag = mbar_wait(full + b, (k / NS) & 1) ? 1u : 0u;
+    epi_sync();
+    if (!*flag) return false;
+    acc += dy_column_sum<DC>(sm + b * stage_bytes, tid);
+    epi_sync();
+    if (tid == 0) mbar_arrive(empty + b);
+  }
+  return true;
+}
+
+// the CTA's partial bias sums, once every MMA is done (stage 0 serves as scratch): bpart[group][co]
+template <int DC>
+__device__ __forceinline__ void bias_store(unsigned char* sm, float acc, int tid, float* bpart) {
+  float* red = reinterpret_cast<float*>(sm);
+  red[tid] = acc;
+  epi_sync();
+  if (tid < DC) {
+    float t = 0.0f;
+    for (int r = 0; r < 128 / DC; ++r) t += red[r * DC + tid];
+    bpart[(size_t)blockIdx.x * DC + tid] = t;
+  }
+}
+
 // MN-major, 128-byte swizzle: 8-pixel groups of 128-byte rows 1024 bytes apart (one 64-wide atom in MN)
 __device__ __forceinline__ uint64_t sdesc_mn_sw128(uint32_t addr) {
   return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
@@ -453,7 +502,8 @@ __device__ __forceinline__ uint64_t sdesc_mn_sw128(uint32_t addr) {
 }
 
 __global__ void __launch_bounds__(TTHR)
-    conv_wgrad_tc_kernel(int H, int W, int segs_per_group, const bf16* __restrict__ x, float* partial, int* err,
+    conv_wgrad_tc_kernel(int H, int W, int segs_per_group, const bf16* __restrict__ x, float* partial, float* bpart,
+                         int* err,
                          const __grid_constant__ CUtensorMap dymap, const __grid_constant__ CUtensorMap xmap) {
   using L = WgLay;
   constexpr int NS = L::NSTAGE;
@@ -464,6 +514,7 @@ __global__ void __launch_bounds__(TTHR)
   uint64_t *tma = bars, *full = bars + NS, *empty = bars + 2 * NS, *done = bars + 3 * NS;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::TSLOT_OFF);
   const int dyr = blockIdx.y;  // tap row: taps 3 dyr + dx
+  const bool bias = bpart != nullptr && dyr == 1;
   if (warp == MMA_WARP) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(tslot)), "r"(COLS)
                  : "memory");
@@ -473,7 +524,7 @@ __global__ void __launch_bounds__(TTHR)
     for (int b = 0; b < NS; ++b) {
       mbar_init(tma + b, 1);
       mbar_init(full + b, 1);
-      mbar_init(empty + b, 1);
+      mbar_init(empty + b, bias ? 2 : 1);  // the MMAs (and the bias sums) release a stage
     }
     mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -543,8 +594,11 @@ __global__ void __launch_bounds__(TTHR)
       if (ok) umma_commit(done);
     }
     __syncwarp();
-  } else {  // warps 0-3: the partial sums of this group, once every segment is in
-    ok = nmine == 0 || mbar_wait(done, 0);
+  } else {  // warps 0-3: the bias sums as the segments arrive, then this group's partial sums
+    float bacc = 0.0f;
+    if (bias) ok = bias_segments<64, NS>(sm, L::STAGE, full, empty, nmine, tid, tslot + 1, bacc);
+    ok = ok && (nmine == 0 || mbar_wait(done, 0));
+    if (ok && bias) bias_store<64>(sm, bacc, tid, bpart);
     if (ok && nmine > 0) {
       tc_fence_after();
       for (int dx = 0; dx < 3; ++dx) {
@@ -561,6 +615,180 @@ __global__ void __launch_bounds__(TTHR)
           for (int q = 0; q < 16; ++q)
             dst[q] = make_float4(__uint_as_float(raw[4 * q]), __uint_as_float(raw[4 * q + 1]),
                                  __uint_as_float(raw[4 * q + 2]), __uint_as_float(raw[4 * q + 3]));
+        }
+      }
+    }
+  }
+  if (!ok && lane == 0 && err) atomicExch(err, 1);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == MMA_WARP) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(COLS) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Weight gradient of the 16 -> 64 (first) and 64 -> 16 (last) layers, the same scheme as the 64 -> 64
+// kernel with the 64-channel tensor as the M = 64 operand and the 16-channel one as N = 16:
+//   16 -> 64 (XC = 16, DC = 64): D_t[co][ci] = sum_p dY[p][co] X[p + d_t][ci],  A = dY, B = X_t;
+//   64 -> 16 (XC = 64, DC = 16): D_t[ci][co] = sum_p X[p + d_t][ci] dY[p][co],  A = X_t, B = dY,
+// written transposed.  Both operands stay pixel-major (MN-major): 64-channel pixel rows of 128 bytes
+// with the 128-byte swizzle (SBO = 1024), 16-channel rows of 32 bytes with the 32-byte swizzle
+// (SBO = 256: eight pixels); a tap's shift moves the X operand's start by whole pixel rows.
+// ---------------------------------------------------------------------------------------------
+template <int XC, int DC>
+struct Wg16Lay {
+  static constexpr int NSTAGE = 3;
+  static constexpr int DY = (TPX * DC * 2 + 1023) / 1024 * 1024;  // dY segment
+  static constexpr int XR = (TPW * XC * 2 + 1023) / 1024 * 1024;  // one input row of 130 pixels
+  static constexpr int STAGE = DY + XR;
+  static constexpr int BAR_OFF = NSTAGE * STAGE;
+  static constexpr int TSLOT_OFF = BAR_OFF + 8 * (3 * NSTAGE + 1);
+  static constexpr int BYTES = TSLOT_OFF + 16;
+  static_assert((XC == 16 && DC == 64) || (XC == 64 && DC == 16), "one 16-channel and one 64-channel side");
+};
+
+// MN-major, 32-byte swizzle: 8-pixel groups of 32-byte rows 256 bytes apart (one 16-wide atom in MN)
+__device__ __forceinline__ uint64_t sdesc_mn_sw32(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(256 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)6 << 61);
+}
+
+template <int XC, int DC>
+__global__ void __launch_bounds__(TTHR)
+    conv_wgrad16_tc_kernel(int H, int W, int segs_per_group, const bf16* __restrict__ x, float* partial,
+                           float* bpart, int* err,
+                           const __grid_constant__ CUtensorMap dymap, const __grid_constant__ CUtensorMap xmap) {
+  using L = Wg16Lay<XC, DC>;
+  constexpr int NS = L::NSTAGE;
+  constexpr uint32_t COLS = 64;  // three 16-column accumulators
+  constexpr int XROW = XC * 2;   // bytes of one input pixel row
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + L::BAR_OFF);
+  uint64_t *tma = bars, *full = bars + NS, *empty = bars + 2 * NS, *done = bars + 3 * NS;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::TSLOT_OFF);
+  const int dyr = blockIdx.y;  // tap row: taps 3 dyr + dx
+  const bool bias = bpart != nullptr && dyr == 1;
+  if (warp == MMA_WARP) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(tslot)), "r"(COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int b = 0; b < NS; ++b) {
+      mbar_init(tma + b, 1);
+      mbar_init(full + b, 1);
+      mbar_init(empty + b, bias ? 2 : 1);  // the MMAs (and the bias sums) release a stage
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const int segs_row = W / TPX, nseg = H * segs_row;
+  const int seg0 = blockIdx.x * segs_per_group;
+  const int nmine = seg0 < nseg ? min(segs_per_group, nseg - seg0) : 0;
+  bool ok = true;
+  if (warp == LOAD_WARP) {
+    for (int k = 0; k < nmine && ok; ++k) {
+      const int b = k % NS, use = k / NS, sg = seg0 + k, row = sg / segs_row, x0 = (sg % segs_row) * TPX;
+      if (k >= NS) ok = mbar_wait(empty + b, (use - 1) & 1);  // the MMAs of step k - NS read it
+      if (!ok) break;
+      const int yy = row + dyr - 1, gy = yy < 0 ? yy + H : (yy >= H ? yy - H : yy);
+      if (lane == 0) {
+        unsigned char* dyb = sm + b * L::STAGE;
+        mbar_expect_tx(tma + b, TPX * DC * 2 + TPW * XROW);
+        tma_load_3d(dyb, &dymap, tma + b, x0, row);
+        tma_load_3d(dyb + L::DY, &xmap, tma + b, x0 - 1, gy);  // the row index is wrapped here already
+      }
+      __syncwarp();
+    }
+  } else if (warp == FIX_WARP) {
+    constexpr int CPP = XROW / 16;  // 16-byte chunks per input pixel (2 or 8)
+    for (int k = 0; k < nmine && ok; ++k) {
+      const int b = k % NS, use = k / NS, sg = seg0 + k, row = sg / segs_row, x0 = (sg % segs_row) * TPX;
+      unsigned char* xb = sm + b * L::STAGE + L::DY;
+      const int yy = row + dyr - 1, gy = yy < 0 ? yy + H : (yy >= H ? yy - H : yy);
+      // the edge pixels of a wrapped segment, loaded into registers before the copy lands: lanes
+      // 0 .. CPP-1 the left wrap (pixel j = 0 <- column W - 1), CPP .. 2 CPP - 1 the right wrap
+      // (j = TPW - 1 <- column 0).  Chunk c of pixel j sits at chunk c ^ (j % 8) of its 128-byte row
+      // (128-byte swizzle) or c ^ ((j / 4) % 2) of its 32-byte row (32-byte swizzle).
+      const bool left = x0 == 0, right = x0 + TPX == W;
+      const int c = lane % CPP, side = lane / CPP, j = side == 0 ? 0 : TPW - 1;
+      const bool mine = lane < 2 * CPP && ((side == 0 && left) || (side == 1 && right));
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (mine) v = *reinterpret_cast<const uint4*>(x + ((size_t)gy * W + (side == 0 ? W - 1 : 0)) * XC + c * 8);
+      ok = mbar_wait(tma + b, use & 1);
+      if (!ok) break;
+      if (left || right) {
+        const int cs = XC == 64 ? (c ^ (j & 7)) : (c ^ ((j >> 2) & 1));
+        if (mine) *reinterpret_cast<uint4*>(xb + j * XROW + (cs << 4)) = v;
+        fence_async_smem();
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(full + b);
+    }
+  } else if (warp == MMA_WARP) {
+    if (lane == 0) {
+      // BF16 x BF16 -> F32, both operands MN-major (transpose bits 15, 16), N = 16, M = 64
+      constexpr uint32_t ID = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((16u >> 3) << 17) |
+                              ((64u >> 4) << 24);
+      for (int k = 0; k < nmine && ok; ++k) {
+        const int b = k % NS;
+        ok = mbar_wait(full + b, (k / NS) & 1);
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t dyb = su32(sm + b * L::STAGE), xb = dyb + L::DY;
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+          for (int s2 = 0; s2 < TPX / 16; ++s2) {
+            uint64_t da, db;
+            if (XC == 16) {  // A = dY (64 channels), B = the shifted X window (16 channels)
+              da = sdesc_mn_sw128(dyb + 2048u * s2);
+              db = sdesc_mn_sw32(xb + 32u * dx + 512u * s2);
+            } else {         // A = the shifted X window (64 channels), B = dY (16 channels)
+              da = sdesc_mn_sw128(xb + 128u * dx + 2048u * s2);
+              db = sdesc_mn_sw32(dyb + 512u * s2);
+            }
+            umma(tmem + 16u * dx, da, db, ID, (k | s2) != 0);
+          }
+        umma_commit(empty + b);
+      }
+      if (ok) umma_commit(done);
+    }
+    __syncwarp();
+  } else {  // warps 0-3: the bias sums as the segments arrive, then this group's partial sums
+    float bacc = 0.0f;
+    if (bias) ok = bias_segments<DC, NS>(sm, L::STAGE, full, empty, nmine, tid, tslot + 1, bacc);
+    ok = ok && (nmine == 0 || mbar_wait(done, 0));
+    if (ok && bias) bias_store<DC>(sm, bacc, tid, bpart);
+    if (ok && nmine > 0) {
+      tc_fence_after();
+      uint32_t raw[48];
+#pragma unroll
+      for (int dx = 0; dx < 3; ++dx) tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + 16u * dx, raw + 16 * dx);
+      tmem_wait_ld();
+      if (lane < 16) {  // lanes 0-15 of warp w hold rows m = 16 w .. 16 w + 15 of the M = 64 side
+        const int m = 16 * warp + lane;
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+          float* tap = partial + ((size_t)blockIdx.x * 9 + 3 * dyr + dx) * 64 * 16;  // [co][ci]
+          if (XC == 16) {  // m = co, n = ci: 16 consecutive floats
+            float4* dst = reinterpret_cast<float4*>(tap + (size_t)m * 16);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              dst[q] = make_float4(__uint_as_float(raw[16 * dx + 4 * q]), __uint_as_float(raw[16 * dx + 4 * q + 1]),
+                                   __uint_as_float(raw[16 * dx + 4 * q + 2]),
+                                   __uint_as_float(raw[16 * dx + 4 * q + 3]));
+          } else {  // m = ci, n = co: partial[co][ci], consecutive lanes on consecutive ci
+#pragma unroll
+            for (int n = 0; n < 16; ++n) tap[(size_t)n * 64 + m] = __uint_as_float(raw[16 * dx + n]);
+          }
         }
       }
     }
@@ -660,7 +888,7 @@ cudaError_t tc_launch(int H, int W, const void* x, const void* w, const float* b
   return cudaGetLastError();
 }
 
-cudaError_t wg64_launch(int H, int W, const void* x, const void* dy, float* partial, int segs_per_group,
+cudaError_t wg64_launch(int H, int W, const void* x, const void* dy, float* partial, float* bpart, int segs_per_group,
                         cudaStream_t st) {
   static int ready[32] = {0};
   static int* err[32] = {nullptr};
@@ -690,7 +918,47 @@ cudaError_t wg64_launch(int H, int W, const void* x, const void* dy, float* part
     return cudaErrorInvalidValue;
   const int nseg = H * (W / TPX), groups = (nseg + segs_per_group - 1) / segs_per_group;
   conv_wgrad_tc_kernel<<<dim3(groups, 3), TTHR, WgLay::BYTES, st>>>(H, W, segs_per_group, (const bf16*)x, partial,
-                                                                  err[dev], dymap, xmap);
+                                                                  bpart, err[dev], dymap, xmap);
+  return cudaGetLastError();
+}
+
+template <int XC, int DC>
+cudaError_t wg16_launch(int H, int W, const void* x, const void* dy, float* partial, float* bpart, int segs_per_group,
+                        cudaStream_t st) {
+  using L = Wg16Lay<XC, DC>;
+  static int ready[32] = {0};
+  static int* err[32] = {nullptr};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 32) return cudaErrorInvalidDevice;
+  if (!ready[dev]) {
+    e = cudaFuncSetAttribute(conv_wgrad16_tc_kernel<XC, DC>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::BYTES);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaGetSymbolAddress((void**)&err[dev], g_conv_tc_err)) != cudaSuccess) return e;
+    ready[dev] = 1;
+  }
+  EncodeTiled enc = encoder();
+  if (!enc) return cudaErrorNotSupported;
+  alignas(64) CUtensorMap dymap, xmap;
+  const cuuint64_t ddims[3] = {(cuuint64_t)DC, (cuuint64_t)W, (cuuint64_t)H};
+  const cuuint64_t dstr[2] = {(cuuint64_t)DC * 2, (cuuint64_t)W * DC * 2};
+  const cuuint64_t xdims[3] = {(cuuint64_t)XC, (cuuint64_t)W, (cuuint64_t)H};
+  const cuuint64_t xstr[2] = {(cuuint64_t)XC * 2, (cuuint64_t)W * XC * 2};
+  const cuuint32_t box_dy[3] = {(cuuint32_t)DC, (cuuint32_t)TPX, 1}, box_x[3] = {(cuuint32_t)XC, (cuuint32_t)TPW, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUtensorMapSwizzle dsw = DC == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_32B;
+  const CUtensorMapSwizzle xsw = XC == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_32B;
+  if (enc(&dymap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(dy), ddims, dstr, box_dy, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, dsw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+      enc(&xmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(x), xdims, xstr, box_x, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, xsw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  const int nseg = H * (W / TPX), groups = (nseg + segs_per_group - 1) / segs_per_group;
+  conv_wgrad16_tc_kernel<XC, DC><<<dim3(groups, 3), TTHR, L::BYTES, st>>>(H, W, segs_per_group, (const bf16*)x,
+                                                                         partial, bpart, err[dev], dymap, xmap);
   return cudaGetLastError();
 }
 
@@ -703,9 +971,12 @@ cudaError_t conv_fwd_tc(int H, int W, int cin, int cout, const void* x, const vo
   return tc_launch<64, 16>(H, W, x, w, b, mask, relu, y, yf, st);
 }
 
-cudaError_t conv_wgrad_tc64(int H, int W, const void* x, const void* dy, float* partial, int segs_per_group,
-                            cudaStream_t st) {
-  return wg64_launch(H, W, x, dy, partial, segs_per_group, st);
+cudaError_t conv_wgrad_tc(int H, int W, int cin, int cout, const void* x, const void* dy, float* partial, float* bpart,
+                          int segs_per_group, cudaStream_t st) {
+  if (cin == 64 && cout == 64) return wg64_launch(H, W, x, dy, partial, bpart, segs_per_group, st);
+  if (cin == 16 && cout == 64) return wg16_launch<16, 64>(H, W, x, dy, partial, bpart, segs_per_group, st);
+  if (cin == 64 && cout == 16) return wg16_launch<64, 16>(H, W, x, dy, partial, bpart, segs_per_group, st);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t conv_tc_status(cudaStream_t st, int clear, int* raised) {
