@@ -582,11 +582,11 @@ vlb_status vlb_create(const vlb_params* p, void* d_workspace, size_t bytes, void
   if (e == cudaSuccess) e = cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream);
   std::vector<double> lam;
   if (e == cudaSuccess && p->ch_stab) {
-    // the stabiliser's factor tables of lambda at the finest spacings (r dtheta; (R - r) dvarphi on
-    // the torus, R dvarphi flat), after the spectrum
+    // the stabiliser's tables after the spectrum: the factors of lambda at the finest spacings
+    // (r dtheta; (R - r) dvarphi on the torus, R dvarphi flat) and the twiddles
     const double h_t = p->r * (2.0 * M_PI / p->n_theta);
     const double h_p = (p->geometry == VLB_TORUS ? p->R - p->r : p->R) * (2.0 * M_PI / p->n_phi);
-    lam.resize((size_t)p->n_theta + p->n_phi);
+    lam.resize(vlb::ch_stab_table_elems(p->n_theta, p->n_phi));
     vlb::ch_stab_tables(p->n_theta, p->n_phi, h_t, h_p, L.esize, lam.data());
     e = cudaMemcpyAsync((unsigned char*)h->fft + vlb::ch_stab_table_offset(p->n_theta, p->n_phi, L.esize), lam.data(),
                         L.esize * lam.size(), cudaMemcpyHostToDevice, h->stream);

@@ -17,8 +17,11 @@
 // state's precision, with twiddles from sincospi; N_theta and N_phi are powers of two <= 4096.  The
 // two factors of lambda, (4/h_theta^2) sin^2(pi m/N_theta) and (4/h_phi^2) sin^2(pi n/N_phi), are
 // tabulated once in FP64 on the host (ch_stab_tables) and rounded to the state precision, so the
-// division runs in that precision with no transcendental per mode.
+// division runs in that precision with no transcendental per mode; so are the twiddles of both
+// transform lengths, which each CTA copies from global memory (L2) into shared memory.
 #include <math.h>
+
+#include <vector>
 
 #include "vlb_internal.cuh"
 
@@ -36,73 +39,129 @@ __device__ __forceinline__ void sincospi_t(float a, float* s, float* c) { sincos
 
 __device__ __forceinline__ int bitrev(int i, int logn) { return (int)(__brev((unsigned)i) >> (32 - logn)); }
 
-// tw[k] = exp(-2 pi i k / n), k < n / 2
+// Twiddles stored level by level, so that the butterflies of one level read consecutive entries
+// (a single table indexed by j n / 2^l puts a warp's reads on one shared-memory bank at the middle
+// levels): tw[2^(l-1) - 1 + j] = exp(-2 pi i j / 2^l), j < 2^(l-1), l = 1 .. log2 n; n - 1 entries.
 template <typename T>
 __device__ void twiddles(C2<T>* tw, int n) {
-  for (int k = threadIdx.x; k < n / 2; k += blockDim.x) {
+  for (int k = threadIdx.x; k < n - 1; k += blockDim.x) {
+    const int half = 1 << (31 - __clz(k + 1));  // 2^(l-1), the level's first entry is half - 1
+    const int j = k + 1 - half;
     T s, c;
-    sincospi_t((T)(-2.0 * k / n), &s, &c);
+    sincospi_t((T)(-(double)j / half), &s, &c);  // -2 pi j / 2^l = -pi j / half
     tw[k].x = c;
     tw[k].y = s;
   }
 }
 
+// Shared-memory position of element e of a row transform: one pad element every 2^sh elements, so
+// that the bit-reversed scatter of 32 consecutive indices (multiples of n / 32) and the butterflies
+// spread over the banks.  Column strips use sh = 31 (no padding).
+__device__ __forceinline__ int padded(int e, int sh) { return e + (e >> sh); }
+__host__ __device__ inline int row_pad_shift(int logn) { return logn >= 5 ? logn - 5 : 31; }
+
 // In-place radix-2 FFT along the first index of a[i * w + c] (w = 2^logw interleaved sequences of
-// length n, loaded in bit-reversed order of i).  inverse: conjugate twiddles (unnormalised).
+// length n, loaded in bit-reversed order of i; element e stored at padded(e, sh)).  inverse:
+// conjugate twiddles (unnormalised).
 template <typename T>
-__device__ void fft_strided(C2<T>* a, int n, int logn, int logw, const C2<T>* tw, bool inverse) {
+__device__ void fft_strided(C2<T>* a, int n, int logn, int logw, int sh, const C2<T>* tw, bool inverse) {
   const int w = 1 << logw;
   const int nb = (n >> 1) << logw;
   for (int l = 1; l <= logn; ++l) {
-    const int half = 1 << (l - 1), step = n >> l;
+    const int half = 1 << (l - 1);
     for (int idx = threadIdx.x; idx < nb; idx += blockDim.x) {
       const int i = idx >> logw, c = idx & (w - 1);
       const int j = i & (half - 1);
       const int i0 = ((i >> (l - 1)) << l) + j, i1 = i0 + half;
-      C2<T> t = tw[j * step];
+      C2<T> t = tw[half - 1 + j];
       if (inverse) t.y = -t.y;
-      const C2<T> u = a[i0 * w + c], v = a[i1 * w + c];
+      const int e0 = padded((i0 << logw) + c, sh), e1 = padded((i1 << logw) + c, sh);
+      const C2<T> u = a[e0], v = a[e1];
       const C2<T> vt = {v.x * t.x - v.y * t.y, v.x * t.y + v.y * t.x};
-      a[i0 * w + c] = {u.x + vt.x, u.y + vt.y};
-      a[i1 * w + c] = {u.x - vt.x, u.y - vt.y};
+      a[e0] = {u.x + vt.x, u.y + vt.y};
+      a[e1] = {u.x - vt.x, u.y - vt.y};
     }
     __syncthreads();
+  }
+}
+
+constexpr int kBatch = 8;  // global loads a thread keeps in flight before it stores them
+
+// the n - 1 per-level twiddles of a transform, from the host-computed table
+template <typename T>
+__device__ __forceinline__ void load_twiddles(C2<T>* tw, const C2<T>* table, int n) {
+  for (int k0 = threadIdx.x; k0 < n - 1; k0 += kBatch * blockDim.x) {
+    C2<T> v[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int k = k0 + u * blockDim.x;
+      if (k < n - 1) v[u] = table[k];
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int k = k0 + u * blockDim.x;
+      if (k < n - 1) tw[k] = v[u];
+    }
   }
 }
 
 // 1. Row q: F_phi[J_q dt L_phi(q, .)] -> buf row q.
 template <typename T>
 __global__ void __launch_bounds__(256) row_fwd_kernel(int ns, int logns, const T* dphi, const double* J,
-                                                      C2<T>* buf) {
+                                                      const C2<T>* tw_s, C2<T>* buf) {
   extern __shared__ __align__(16) unsigned char raw[];
   C2<T>* a = reinterpret_cast<C2<T>*>(raw);
-  C2<T>* tw = a + ns;
+  const int sh = row_pad_shift(logns);
+  C2<T>* tw = a + padded(ns, sh);
   const int q = blockIdx.x;
-  twiddles(tw, ns);
   const T jq = (T)J[q];
-  for (int s = threadIdx.x; s < ns; s += blockDim.x) a[bitrev(s, logns)] = {jq * dphi[(int64_t)q * ns + s], T(0)};
+  const T* row = dphi + (int64_t)q * ns;
+  for (int s0 = threadIdx.x; s0 < ns; s0 += kBatch * blockDim.x) {
+    T v[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int s = s0 + u * blockDim.x;
+      if (s < ns) v[u] = row[s];
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int s = s0 + u * blockDim.x;
+      if (s < ns) a[padded(bitrev(s, logns), sh)] = {jq * v[u], T(0)};
+    }
+  }
+  load_twiddles(tw, tw_s, ns);
   __syncthreads();
-  fft_strided(a, ns, logns, 0, tw, false);
-  for (int s = threadIdx.x; s < ns; s += blockDim.x) buf[(int64_t)q * ns + s] = a[s];
+  fft_strided(a, ns, logns, 0, sh, tw, false);
+  for (int s = threadIdx.x; s < ns; s += blockDim.x) buf[(int64_t)q * ns + s] = a[padded(s, sh)];
 }
 
 // 2. Columns n0 .. n0 + cw - 1: F_theta, division by 1 + s lambda(m, n), inverse F_theta.
 template <typename T>
 __global__ void __launch_bounds__(256) col_solve_kernel(int nt, int lognt, int ns, int lcw, T sfac, const T* lam_t,
-                                                        const T* lam_p, C2<T>* buf) {
+                                                        const T* lam_p, const C2<T>* tw_t, C2<T>* buf) {
   extern __shared__ __align__(16) unsigned char raw[];
   C2<T>* a = reinterpret_cast<C2<T>*>(raw);
   const int cw = 1 << lcw;
   C2<T>* tw = a + ((size_t)nt << lcw);
   const int n0 = blockIdx.x << lcw;
-  twiddles(tw, nt);
-  for (int idx = threadIdx.x; idx < (nt << lcw); idx += blockDim.x) {
-    const int q = idx >> lcw, c = idx & (cw - 1);
-    a[(bitrev(q, lognt) << lcw) + c] = buf[(int64_t)q * ns + n0 + c];
+  const int total = nt << lcw;
+  for (int i0 = threadIdx.x; i0 < total; i0 += kBatch * blockDim.x) {
+    C2<T> v[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int idx = i0 + u * blockDim.x;
+      if (idx < total) v[u] = buf[(int64_t)(idx >> lcw) * ns + n0 + (idx & (cw - 1))];
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int idx = i0 + u * blockDim.x;
+      if (idx < total) a[(bitrev(idx >> lcw, lognt) << lcw) + (idx & (cw - 1))] = v[u];
+    }
   }
+  load_twiddles(tw, tw_t, nt);
   __syncthreads();
-  fft_strided(a, nt, lognt, lcw, tw, false);
-  for (int idx = threadIdx.x; idx < (nt << lcw); idx += blockDim.x) {
+  fft_strided(a, nt, lognt, lcw, 31, tw, false);
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     const int m = idx >> lcw, c = idx & (cw - 1);
     const T lap = lam_t[m] + lam_p[n0 + c];
     const T g = T(1) / (T(1) + sfac * lap * lap);
@@ -111,7 +170,7 @@ __global__ void __launch_bounds__(256) col_solve_kernel(int nt, int lognt, int n
   }
   __syncthreads();
   // back to bit-reversed order for the inverse transform: in-place swaps of the pairs (m, rev(m))
-  for (int idx = threadIdx.x; idx < (nt << lcw); idx += blockDim.x) {
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     const int m = idx >> lcw, c = idx & (cw - 1), r = bitrev(m, lognt);
     if (m < r) {
       const C2<T> t = a[idx];
@@ -120,8 +179,8 @@ __global__ void __launch_bounds__(256) col_solve_kernel(int nt, int lognt, int n
     }
   }
   __syncthreads();
-  fft_strided(a, nt, lognt, lcw, tw, true);
-  for (int idx = threadIdx.x; idx < (nt << lcw); idx += blockDim.x) {
+  fft_strided(a, nt, lognt, lcw, 31, tw, true);
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     const int q = idx >> lcw, c = idx & (cw - 1);
     buf[(int64_t)q * ns + n0 + c] = a[idx];
   }
@@ -140,35 +199,61 @@ __device__ __forceinline__ void pair_add(float base, float base_lo, float inc, f
 // 3. Row q: inverse F_phi, y = Re / (N J_q), phi_out = phi^n + b (phi_in - phi^n + y).
 template <typename T>
 __global__ void __launch_bounds__(256) row_inv_kernel(int ns, int logns, double inv_n, const double* J,
-                                                      const C2<T>* buf, const T* phin, const T* phi0, T* phiout,
-                                                      int64_t lo_off, T b) {
+                                                      const C2<T>* tw_s, const C2<T>* buf, const T* phin,
+                                                      const T* phi0, T* phiout, int64_t lo_off, T b) {
   constexpr bool DF = sizeof(T) == 4;  // phi as a float pair
+  constexpr int U = 4;                 // nodes per batch of loads (four state words each)
   extern __shared__ __align__(16) unsigned char raw[];
   C2<T>* a = reinterpret_cast<C2<T>*>(raw);
-  C2<T>* tw = a + ns;
+  const int sh = row_pad_shift(logns);
+  C2<T>* tw = a + padded(ns, sh);
   const int q = blockIdx.x;
-  twiddles(tw, ns);
-  for (int s = threadIdx.x; s < ns; s += blockDim.x) a[bitrev(s, logns)] = buf[(int64_t)q * ns + s];
-  __syncthreads();
-  fft_strided(a, ns, logns, 0, tw, true);
-  const T scale = (T)(inv_n / J[q]);
-  for (int s = threadIdx.x; s < ns; s += blockDim.x) {
-    const int64_t g = (int64_t)q * ns + s;
-    const T y = a[s].x * scale;
-    const T ph = phin[g], lo = DF ? phin[g + lo_off] : T(0);
-    T base = ph, base_lo = lo, inc = y;
-    if (phi0) {
-      base = phi0[g];
-      base_lo = DF ? phi0[g + lo_off] : T(0);
-      inc = b * (((ph - base) + (lo - base_lo)) + y);
+  const C2<T>* row = buf + (int64_t)q * ns;
+  for (int s0 = threadIdx.x; s0 < ns; s0 += kBatch * blockDim.x) {
+    C2<T> v[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int s = s0 + u * blockDim.x;
+      if (s < ns) v[u] = row[s];
     }
-    if constexpr (DF) {
-      float hi_o, lo_o;
-      pair_add(base, base_lo, inc, hi_o, lo_o);
-      phiout[g] = hi_o;
-      phiout[g + lo_off] = lo_o;
-    } else {
-      phiout[g] = base + inc;
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int s = s0 + u * blockDim.x;
+      if (s < ns) a[padded(bitrev(s, logns), sh)] = v[u];
+    }
+  }
+  load_twiddles(tw, tw_s, ns);
+  __syncthreads();
+  fft_strided(a, ns, logns, 0, sh, tw, true);
+  const T scale = (T)(inv_n / J[q]);
+  for (int s0 = threadIdx.x; s0 < ns; s0 += U * blockDim.x) {
+    T ph[U], lo[U], base[U], base_lo[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int s = s0 + u * blockDim.x;
+      if (s < ns) {
+        const int64_t g = (int64_t)q * ns + s;
+        ph[u] = phin[g];
+        lo[u] = DF ? phin[g + lo_off] : T(0);
+        base[u] = phi0 ? phi0[g] : ph[u];
+        base_lo[u] = phi0 ? (DF ? phi0[g + lo_off] : T(0)) : lo[u];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int s = s0 + u * blockDim.x;
+      if (s >= ns) continue;
+      const int64_t g = (int64_t)q * ns + s;
+      const T y = a[padded(s, sh)].x * scale;
+      const T inc = phi0 ? b * (((ph[u] - base[u]) + (lo[u] - base_lo[u])) + y) : y;
+      if constexpr (DF) {
+        float hi_o, lo_o;
+        pair_add(base[u], base_lo[u], inc, hi_o, lo_o);
+        phiout[g] = hi_o;
+        phiout[g + lo_off] = lo_o;
+      } else {
+        phiout[g] = base[u] + inc;
+      }
     }
   }
 }
@@ -199,19 +284,34 @@ bool ch_stab_shape_ok(int nt, int ns) {
   return pow2(nt) && pow2(ns);
 }
 
-// the complex spectrum, then the two factor tables of lambda
-size_t ch_stab_buffer_bytes(int nt, int ns, size_t esize) { return ((size_t)nt * ns * 2 + nt + ns) * esize; }
+// the complex spectrum, then the tables: the two factors of lambda (N_theta + N_phi values) and the
+// per-level twiddles of both transform lengths ((N_theta - 1) + (N_phi - 1) complex values)
+size_t ch_stab_table_elems(int nt, int ns) { return (size_t)(nt + ns) + 2 * (size_t)(nt - 1 + ns - 1); }
+size_t ch_stab_buffer_bytes(int nt, int ns, size_t esize) {
+  return ((size_t)nt * ns * 2 + ch_stab_table_elems(nt, ns)) * esize;
+}
 size_t ch_stab_table_offset(int nt, int ns, size_t esize) { return (size_t)nt * ns * 2 * esize; }
 
 void ch_stab_tables(int nt, int ns, double h_t, double h_p, size_t esize, void* host_out) {
+  std::vector<double> v;
+  v.reserve(ch_stab_table_elems(nt, ns));
   for (int i = 0; i < nt + ns; ++i) {
     const bool th = i < nt;
     const double sn = sin(M_PI * (th ? i : i - nt) / (th ? nt : ns));
-    const double v = (th ? 4.0 / (h_t * h_t) : 4.0 / (h_p * h_p)) * sn * sn;
+    v.push_back((th ? 4.0 / (h_t * h_t) : 4.0 / (h_p * h_p)) * sn * sn);
+  }
+  // twiddles level by level: entry 2^(l-1) - 1 + j = exp(-2 pi i j / 2^l), j < 2^(l-1)
+  for (int n : {nt, ns})
+    for (int half = 1; half < n; half *= 2)
+      for (int j = 0; j < half; ++j) {
+        v.push_back(cos(M_PI * j / half));
+        v.push_back(-sin(M_PI * j / half));
+      }
+  for (size_t i = 0; i < v.size(); ++i) {
     if (esize == 8)
-      ((double*)host_out)[i] = v;
+      ((double*)host_out)[i] = v[i];
     else
-      ((float*)host_out)[i] = (float)v;
+      ((float*)host_out)[i] = (float)v[i];
   }
 }
 
@@ -222,25 +322,27 @@ cudaError_t launch_ch_stab(int nt, int ns, double dt_m_kappa, const double* J, c
   const int lognt = ilog2(nt), logns = ilog2(ns);
   C2<T>* cb = reinterpret_cast<C2<T>*>(buf);
   const T* lam = reinterpret_cast<const T*>(buf) + (size_t)nt * ns * 2;  // ch_stab_tables
-  const size_t row_bytes = sizeof(C2<T>) * (size_t)ns * 3 / 2;
+  const C2<T>* tw_t = reinterpret_cast<const C2<T>*>(lam + nt + ns);      // 8- or 16-byte aligned
+  const C2<T>* tw_s = tw_t + (nt - 1);
+  const size_t row_bytes = sizeof(C2<T>) * ((size_t)ns * 2 + 32);  // data (with its pads) and twiddles
   int lcw = 0;
   while (lcw < 5 && (2 << lcw) <= ns && ((size_t)nt << lcw) * 2 * sizeof(C2<T>) <= kColBudget) ++lcw;
-  const size_t col_bytes = sizeof(C2<T>) * (((size_t)nt << lcw) + nt / 2);
+  const size_t col_bytes = sizeof(C2<T>) * (((size_t)nt << lcw) + nt);
   // the attribute is set once per device to the largest size any grid needs (setting it to a
   // smaller size would cap later launches on larger grids)
-  constexpr size_t row_max = sizeof(C2<T>) * 4096 * 3 / 2;
-  constexpr size_t col_max = kColBudget + sizeof(C2<T>) * 2048;
+  constexpr size_t row_max = sizeof(C2<T>) * (4096 * 2 + 32);
+  constexpr size_t col_max = kColBudget + sizeof(C2<T>) * 4096;
   static int m1 = 0, m2 = 0, m3 = 0;
   cudaError_t e;
   if ((e = smem_attr(row_fwd_kernel<T>, row_max, m1)) != cudaSuccess) return e;
   if ((e = smem_attr(col_solve_kernel<T>, col_max, m2)) != cudaSuccess) return e;
   if ((e = smem_attr(row_inv_kernel<T>, row_max, m3)) != cudaSuccess) return e;
-  row_fwd_kernel<T><<<nt, 256, row_bytes, st>>>(ns, logns, dphi, J, cb);
+  row_fwd_kernel<T><<<nt, 256, row_bytes, st>>>(ns, logns, dphi, J, tw_s, cb);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  col_solve_kernel<T><<<ns >> lcw, 256, col_bytes, st>>>(nt, lognt, ns, lcw, (T)dt_m_kappa, lam, lam + nt, cb);
+  col_solve_kernel<T><<<ns >> lcw, 256, col_bytes, st>>>(nt, lognt, ns, lcw, (T)dt_m_kappa, lam, lam + nt, tw_t, cb);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  row_inv_kernel<T><<<nt, 256, row_bytes, st>>>(ns, logns, 1.0 / ((double)nt * ns), J, cb, phin, phi0, phiout, lo_off,
-                                               b);
+  row_inv_kernel<T><<<nt, 256, row_bytes, st>>>(ns, logns, 1.0 / ((double)nt * ns), J, tw_s, cb, phin, phi0, phiout,
+                                               lo_off, b);
   return cudaGetLastError();
 }
 
@@ -266,7 +368,7 @@ __global__ void __launch_bounds__(256) sf_row_kernel(int ns, int logns, const T*
     a[bitrev(s, logns)] = {v, 0.0};
   }
   __syncthreads();
-  fft_strided(a, ns, logns, 0, tw, false);
+  fft_strided(a, ns, logns, 0, 31, tw, false);
   for (int s = threadIdx.x; s < ns; s += blockDim.x) buf[(int64_t)q * ns + s] = a[s];
 }
 
@@ -283,7 +385,7 @@ __global__ void __launch_bounds__(256) sf_col_kernel(int nt, int lognt, int ns, 
     a[bitrev(q, lognt) * cw + c] = buf[(int64_t)q * ns + n0 + c];
   }
   __syncthreads();
-  fft_strided(a, nt, lognt, __ffs(cw) - 1, tw, false);  // cw is a power of two
+  fft_strided(a, nt, lognt, __ffs(cw) - 1, 31, tw, false);  // cw is a power of two
   double s_sum = 0.0, k_sum = 0.0;
   for (int idx = threadIdx.x; idx < nt * cw; idx += blockDim.x) {
     const int m = idx / cw, n = n0 + idx - m * cw;
@@ -330,10 +432,10 @@ cudaError_t launch_structure_sums(int nt, int ns, double r, double R, const T* p
   const int lognt = ilog2(nt), logns = ilog2(ns);
   const int cw = ns / structure_blocks(nt, ns);
   C2<double>* cb = reinterpret_cast<C2<double>*>(buf);
-  const size_t row_bytes = sizeof(C2<double>) * (size_t)ns * 3 / 2;
-  const size_t col_bytes = sizeof(C2<double>) * ((size_t)nt * cw + nt / 2);
-  constexpr size_t row_max = sizeof(C2<double>) * 4096 * 3 / 2;
-  constexpr size_t col_max = kColBudget + sizeof(C2<double>) * 2048;
+  const size_t row_bytes = sizeof(C2<double>) * (size_t)ns * 2;
+  const size_t col_bytes = sizeof(C2<double>) * ((size_t)nt * cw + nt);
+  constexpr size_t row_max = sizeof(C2<double>) * 4096 * 2;
+  constexpr size_t col_max = kColBudget + sizeof(C2<double>) * 4096;
   static int m1 = 0, m2 = 0;
   cudaError_t e;
   if ((e = smem_attr(sf_row_kernel<T>, row_max, m1)) != cudaSuccess) return e;

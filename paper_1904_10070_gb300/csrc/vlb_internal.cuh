@@ -146,13 +146,14 @@ cudaError_t launch_axi(const StageArgs<T>& a, int advection, int ch_mode, T* U0,
 
 // Stabilised semi-implicit Cahn-Hilliard (vlb_chsolve.cu): phi_out = phi^n + b (phi_in - phi^n +
 // P(dphi)) with P = J^{-1} (I + dt M kappa D^2)^{-1} J (D: the constant-coefficient periodic Laplacian
-// with spacings h_t, h_p); phi0 NULL in the first stage (phi^n = phi_in).  FP32: phi is a float pair,
+// at the finest spacings); phi0 NULL in the first stage (phi^n = phi_in).  FP32: phi is a float pair,
 // the low word lo_off elements after the high word.  buf: ch_stab_buffer_bytes of scratch whose tail
-// holds the N_theta + N_phi factor tables of lambda, written once by ch_stab_tables (host, FP64 then
-// rounded to esize) and copied to the device by the caller.
+// holds the factor tables of lambda and the twiddles of both transform lengths, written once by
+// ch_stab_tables (host, FP64 then rounded to esize) and copied to the device by the caller.
 bool ch_stab_shape_ok(int nt, int ns);
 size_t ch_stab_buffer_bytes(int nt, int ns, size_t esize);
 size_t ch_stab_table_offset(int nt, int ns, size_t esize);  // bytes from buf to the tables
+size_t ch_stab_table_elems(int nt, int ns);                   // elements of esize in the tables
 void ch_stab_tables(int nt, int ns, double h_t, double h_p, size_t esize, void* host_out);
 template <typename T>
 cudaError_t launch_ch_stab(int nt, int ns, double dt_m_kappa, const double* J, const T* dphi, void* buf, const T* phin,
@@ -202,10 +203,11 @@ size_t conv_wgrad_workspace_bytes(int H, int W, int cin, int cout);
 // the forward on the tcgen05 tensor cores (vlb_conv_tc.cu)
 cudaError_t conv_fwd_tc(int H, int W, int cin, int cout, const void* x, const void* w, const float* b,
                         const void* mask, int relu, void* y, float* yf, cudaStream_t st);
-// partial[group][tap][co][ci] of a 64 -> 64 weight gradient on tcgen05 (vlb_conv_tc.cu); group g
-// covers row segments (128 pixels) g * segs_per_group ..
-cudaError_t conv_wgrad_tc64(int H, int W, const void* x, const void* dy, float* partial, int segs_per_group,
-                            cudaStream_t st);
+// partial[group][tap][co][ci] of a weight gradient on tcgen05 (vlb_conv_tc.cu; (c_in, c_out) = (64, 64),
+// (16, 64) or (64, 16)); group g covers row segments (128 pixels) g * segs_per_group ..  With bpart,
+// also bpart[group][co] = the group's sum of dY[p][co] (the bias gradient's partials).
+cudaError_t conv_wgrad_tc(int H, int W, int cin, int cout, const void* x, const void* dy, float* partial, float* bpart,
+                          int segs_per_group, cudaStream_t st);
 // The device-wide flag raised (1) when a bounded wait of a tensor-core convolution gives up: read
 // after synchronising st (and cleared if `clear`); conv_tc_raise sets it (tests of the status path).
 cudaError_t conv_tc_status(cudaStream_t st, int clear, int* raised);
