@@ -64,6 +64,15 @@ struct TcLay {
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// Programmatic dependent launch: the convolutions are launched so that a kernel's CTAs may start (tensor
+// memory, mbarriers) while the previous kernel of the stream drains; every global access comes after
+// the wait, which returns once the previous kernel has completed and its memory is visible.  The
+// trigger lets the next convolution start the same way.
+__device__ __forceinline__ void pdl_wait_and_trigger() {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
 __device__ __forceinline__ void cp16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(su32(dst)), "l"(src));
 }
@@ -292,6 +301,7 @@ __global__ void __launch_bounds__(TTHR, 1)
     mbar_init(wbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
+  pdl_wait_and_trigger();
   for (int i = tid; i < COUT; i += TTHR) sbias[i] = bias ? bias[i] : 0.0f;
   if constexpr (!L::SW) {
     // 16-channel weights (18 KB), chunk-major [t][c][co]: per-thread copies before the roles split
@@ -529,6 +539,7 @@ __global__ void __launch_bounds__(TTHR)
     mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
+  pdl_wait_and_trigger();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -685,6 +696,7 @@ __global__ void __launch_bounds__(TTHR)
     mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
+  pdl_wait_and_trigger();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -822,6 +834,22 @@ EncodeTiled encoder() {
   return fn;
 }
 
+cudaLaunchConfig_t pdl_config(dim3 grid, size_t smem, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(TTHR);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  return cfg;
+}
+
+void pdl_attr(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr) {
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+}
+
 template <int CIN, int COUT>
 cudaError_t tc_launch(int H, int W, const void* x, const void* w, const float* b, const void* mask, int relu, void* y,
                       float* yf, cudaStream_t st) {
@@ -882,10 +910,11 @@ cudaError_t tc_launch(int H, int W, const void* x, const void* w, const float* b
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
   const int nitems = H * (W / TPX);
   const int grid = nitems < grid_max[dev] ? nitems : grid_max[dev];
-  conv_fwd_tc_kernel<CIN, COUT><<<grid, TTHR, L::BYTES, st>>>(H, W, (const bf16*)x, (const bf16*)w, b,
-                                                               (const bf16*)mask, relu, (bf16*)y, yf, err[dev], xmap,
-                                                               wmap);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = pdl_config(dim3(grid), L::BYTES, st);
+  cudaLaunchAttribute attr[1];
+  pdl_attr(cfg, attr);
+  return cudaLaunchKernelEx(&cfg, conv_fwd_tc_kernel<CIN, COUT>, H, W, (const bf16*)x, (const bf16*)w, b,
+                            (const bf16*)mask, relu, (bf16*)y, yf, err[dev], xmap, wmap);
 }
 
 cudaError_t wg64_launch(int H, int W, const void* x, const void* dy, float* partial, float* bpart, int segs_per_group,
@@ -917,9 +946,11 @@ cudaError_t wg64_launch(int H, int W, const void* x, const void* dy, float* part
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
   const int nseg = H * (W / TPX), groups = (nseg + segs_per_group - 1) / segs_per_group;
-  conv_wgrad_tc_kernel<<<dim3(groups, 3), TTHR, WgLay::BYTES, st>>>(H, W, segs_per_group, (const bf16*)x, partial,
-                                                                  bpart, err[dev], dymap, xmap);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = pdl_config(dim3(groups, 3), WgLay::BYTES, st);
+  cudaLaunchAttribute attr[1];
+  pdl_attr(cfg, attr);
+  return cudaLaunchKernelEx(&cfg, conv_wgrad_tc_kernel, H, W, segs_per_group, (const bf16*)x, partial, bpart, err[dev],
+                            dymap, xmap);
 }
 
 template <int XC, int DC>
@@ -957,9 +988,11 @@ cudaError_t wg16_launch(int H, int W, const void* x, const void* dy, float* part
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
   const int nseg = H * (W / TPX), groups = (nseg + segs_per_group - 1) / segs_per_group;
-  conv_wgrad16_tc_kernel<XC, DC><<<dim3(groups, 3), TTHR, L::BYTES, st>>>(H, W, segs_per_group, (const bf16*)x,
-                                                                         partial, bpart, err[dev], dymap, xmap);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = pdl_config(dim3(groups, 3), L::BYTES, st);
+  cudaLaunchAttribute attr[1];
+  pdl_attr(cfg, attr);
+  return cudaLaunchKernelEx(&cfg, conv_wgrad16_tc_kernel<XC, DC>, H, W, segs_per_group, (const bf16*)x, partial, bpart,
+                            err[dev], dymap, xmap);
 }
 
 }  // namespace
