@@ -314,8 +314,9 @@ def ensemble_measurement(steps: int = 60, seq_steps: int = 10):
                     "between stages), 16- or 8-row tiles, vs per-member launches"}
 
 
-def surrogate_measurement(ntraj: int = 2000, pairs: int = 4, spacing: int = 400, start: int = 100, epochs: int = 3,
-                          seeds=(20001, 20002, 20003, 20004), warm: int = 400, nwin: int = 1000, check: int = 4):
+def surrogate_measurement(ntraj: int = 2000, pairs: int = 4, spacing: int = 600, start: int = 300, epochs: int = 3,
+                          seeds=(20001, 20002, 20003, 20004), warm: int = 400, nwin: int = 1000, check: int = 4,
+                          corr=(4.0, 14.0), judges=("l2", "linf")):
     """The learned surrogate on 256 x 512 tori (R / r in [1.5, 4], seeded quenched noise): trained here on
     `ntraj` solver trajectories by the library's kernels, then advancing each held-out torus by `nwin`
     windows of 50 steps through vlb_surrogate_advance, judged by the solver every `check` windows --
@@ -327,7 +328,8 @@ def surrogate_measurement(ntraj: int = 2000, pairs: int = 4, spacing: int = 400,
     from paper_1904_10070_gb300 import vlb
     H, W = 256, 512
     t0 = time.perf_counter()
-    ds = S.generate(list(range(10000, 10000 + ntraj)), H, W, window=50, pairs=pairs, spacing=spacing, start=start)
+    ds = S.generate(list(range(10000, 10000 + ntraj)), H, W, window=50, pairs=pairs, spacing=spacing, start=start,
+                    corr=corr)
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - t0
     tr = S.Trainer(S.SurrogateNet(H, W, seed=1), S.target_ratios(ds), ds.s_n, ds.s_u,
@@ -395,8 +397,9 @@ def surrogate_measurement(ntraj: int = 2000, pairs: int = 4, spacing: int = 400,
            "train_trajectories": ntraj, "train_pairs": n_pairs, "train_iters": n_pairs * epochs,
            "gen_s": gen_s, "train_s": train_s, "window_steps": 50, "check_every": check,
            "held_out_tori": len(seeds), "windows_per_torus": nwin, "warm_start_steps": warm}
-    out["l2_judge"] = run("l2")
-    out["linf_judge"] = run("linf")
+    out["train_domain_scale_cells"] = list(corr) if corr else S.CORR_CELLS
+    for j in judges:
+        out[f"{j}_judge"] = run(j)
     # headline figures: the L2 judge
     for k in ("speedup", "fallbacks", "Ld_max_rel_dev", "phi_l2_err_max", "phi_linf_err_max", "solver_ms_per_window",
               "surrogate_ms_per_window"):

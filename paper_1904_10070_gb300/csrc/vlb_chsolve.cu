@@ -161,9 +161,10 @@ __global__ void __launch_bounds__(256) col_solve_kernel(int nt, int lognt, int n
   load_twiddles(tw, tw_t, nt);
   __syncthreads();
   fft_strided(a, nt, lognt, lcw, 31, tw, false);
+  const T lp = lam_p[n0 + (threadIdx.x & (cw - 1))];  // a thread keeps its column (blockDim % cw == 0)
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int m = idx >> lcw, c = idx & (cw - 1);
-    const T lap = lam_t[m] + lam_p[n0 + c];
+    const int m = idx >> lcw;
+    const T lap = lam_t[m] + lp;
     const T g = T(1) / (T(1) + sfac * lap * lap);
     a[idx].x *= g;
     a[idx].y *= g;
@@ -325,8 +326,12 @@ cudaError_t launch_ch_stab(int nt, int ns, double dt_m_kappa, const double* J, c
   const C2<T>* tw_t = reinterpret_cast<const C2<T>*>(lam + nt + ns);      // 8- or 16-byte aligned
   const C2<T>* tw_s = tw_t + (nt - 1);
   const size_t row_bytes = sizeof(C2<T>) * ((size_t)ns * 2 + 32);  // data (with its pads) and twiddles
+  // column strips of 2^lcw columns: wide enough for whole 32-byte segments, narrow enough that the
+  // launch keeps at least 512 CTAs (about three per SM) when the grid allows
   int lcw = 0;
-  while (lcw < 5 && (2 << lcw) <= ns && ((size_t)nt << lcw) * 2 * sizeof(C2<T>) <= kColBudget) ++lcw;
+  while (lcw < 5 && (2 << lcw) <= ns && ((size_t)nt << lcw) * 2 * sizeof(C2<T>) <= kColBudget &&
+         (lcw < 2 || (ns >> (lcw + 1)) >= 512))
+    ++lcw;
   const size_t col_bytes = sizeof(C2<T>) * (((size_t)nt << lcw) + nt);
   // the attribute is set once per device to the largest size any grid needs (setting it to a
   // smaller size would cap later launches on larger grids)

@@ -131,10 +131,17 @@ def radius_for(seed: int) -> float:
 CORR_CELLS, WALL_CELLS = 4.0, 1.8
 
 
-def initial_phi(seed: int, H: int, W: int) -> np.ndarray:
-    """Start of a surrogate trajectory: seeded noise quenched into domains of a few cells
-    (inputs.quenched_noise), i.e. a torus early in coarsening."""
-    return inputs.quenched_noise(seed, H, W, CORR_CELLS, WALL_CELLS)
+def initial_phi(seed: int, H: int, W: int, corr: float = CORR_CELLS) -> np.ndarray:
+    """Start of a surrogate trajectory: seeded noise quenched into domains about `corr` cells across
+    (inputs.quenched_noise); the default is a torus early in coarsening, larger values stand for later
+    stages."""
+    return inputs.quenched_noise(seed, H, W, corr, WALL_CELLS)
+
+
+def corr_for(seed: int, lo: float, hi: float) -> float:
+    """Domain scale of a training trajectory, uniform in [lo, hi] from the counter-based generator
+    (an element of the seed's stream other than the one radius_for uses)."""
+    return lo + (hi - lo) * float(inputs.uniform01(seed, 1, 2)[0, 1])
 
 
 class Normaliser:
@@ -174,10 +181,11 @@ class Dataset:
         return len(self.radii)
 
 
-def generate(seeds, H=256, W=512, window=50, pairs=8, spacing=100, start=100, batch=48):
+def generate(seeds, H=256, W=512, window=50, pairs=8, spacing=100, start=100, batch=48, corr=None):
     """Runs one trajectory per seed from initial_phi(seed) at rest (batched through the ensemble path)
     and keeps `pairs` windows of each: snapshots at steps start + k spacing and start + k spacing +
-    window, k = 0 .. pairs - 1."""
+    window, k = 0 .. pairs - 1.  corr = (lo, hi) draws each trajectory's initial domain scale from
+    corr_for (larger domains stand for later coarsening); None keeps CORR_CELLS."""
     import torch
     N = H * W
     stat = Normaliser()
@@ -187,7 +195,7 @@ def generate(seeds, H=256, W=512, window=50, pairs=8, spacing=100, start=100, ba
         ps = [member_params(radius_for(s), H, W) for s in sel]
         ens = vlb.Ensemble([vlb.make_params(**p, precision=vlb.FP32) for p in ps])
         for v, s in zip(ens.views, sel):
-            phi = initial_phi(s, H, W)
+            phi = initial_phi(s, H, W, CORR_CELLS if corr is None else corr_for(s, *corr))
             z = np.zeros_like(phi)
             vlb.vlb_set_fields(v, np.ones_like(phi), z, z, phi)
         snaps = {}
