@@ -60,26 +60,58 @@ __device__ void twiddles(C2<T>* tw, int n) {
 __device__ __forceinline__ int padded(int e, int sh) { return e + (e >> sh); }
 __host__ __device__ inline int row_pad_shift(int logn) { return logn >= 5 ? logn - 5 : 31; }
 
-// In-place radix-2 FFT along the first index of a[i * w + c] (w = 2^logw interleaved sequences of
-// length n, loaded in bit-reversed order of i; element e stored at padded(e, sh)).  inverse:
-// conjugate twiddles (unnormalised).
+template <typename T>
+__device__ __forceinline__ C2<T> cmul(C2<T> v, C2<T> t) {
+  return {v.x * t.x - v.y * t.y, v.x * t.y + v.y * t.x};
+}
+
+// In-place FFT along the first index of a[i * w + c] (w = 2^logw interleaved sequences of length n,
+// loaded in bit-reversed order of i; element e stored at padded(e, sh)), decimation in time: the
+// radix-2 levels l = 1 .. log2 n, taken two at a time as one radix-4 pass (one radix-2 pass first when
+// log2 n is odd), which halves the shared-memory passes and barriers.  A radix-4 group of levels
+// (l, l + 1) holds the elements i0 + {0, 1, 2, 3} h (h = 2^(l-1), i0 = 4h (g / h) + g % h, j = g % h):
+// level l pairs (0, 1) and (2, 3) with twiddle t1 = W_2h^j, level l + 1 pairs (0, 2) with
+// t2 = W_4h^j and (1, 3) with W_4h^(j + h) = -i t2 (+i t2 for the inverse).  inverse: conjugate
+// twiddles (unnormalised).
 template <typename T>
 __device__ void fft_strided(C2<T>* a, int n, int logn, int logw, int sh, const C2<T>* tw, bool inverse) {
   const int w = 1 << logw;
-  const int nb = (n >> 1) << logw;
-  for (int l = 1; l <= logn; ++l) {
-    const int half = 1 << (l - 1);
+  int l = 1;
+  if (logn & 1) {  // level 1 alone: pairs (2 g, 2 g + 1), twiddle 1
+    const int nb = (n >> 1) << logw;
     for (int idx = threadIdx.x; idx < nb; idx += blockDim.x) {
-      const int i = idx >> logw, c = idx & (w - 1);
-      const int j = i & (half - 1);
-      const int i0 = ((i >> (l - 1)) << l) + j, i1 = i0 + half;
-      C2<T> t = tw[half - 1 + j];
-      if (inverse) t.y = -t.y;
-      const int e0 = padded((i0 << logw) + c, sh), e1 = padded((i1 << logw) + c, sh);
+      const int g = idx >> logw, c = idx & (w - 1);
+      const int e0 = padded(((2 * g) << logw) + c, sh), e1 = padded(((2 * g + 1) << logw) + c, sh);
       const C2<T> u = a[e0], v = a[e1];
-      const C2<T> vt = {v.x * t.x - v.y * t.y, v.x * t.y + v.y * t.x};
-      a[e0] = {u.x + vt.x, u.y + vt.y};
-      a[e1] = {u.x - vt.x, u.y - vt.y};
+      a[e0] = {u.x + v.x, u.y + v.y};
+      a[e1] = {u.x - v.x, u.y - v.y};
+    }
+    __syncthreads();
+    l = 2;
+  }
+  const int nq = (n >> 2) << logw;
+  for (; l < logn; l += 2) {
+    const int h = 1 << (l - 1);
+    for (int idx = threadIdx.x; idx < nq; idx += blockDim.x) {
+      const int g = idx >> logw, c = idx & (w - 1);
+      const int j = g & (h - 1);
+      const int i0 = ((g >> (l - 1)) << (l + 1)) + j;
+      C2<T> t1 = tw[h - 1 + j], t2 = tw[2 * h - 1 + j];
+      if (inverse) {
+        t1.y = -t1.y;
+        t2.y = -t2.y;
+      }
+      const int e0 = padded((i0 << logw) + c, sh), e1 = padded(((i0 + h) << logw) + c, sh);
+      const int e2 = padded(((i0 + 2 * h) << logw) + c, sh), e3 = padded(((i0 + 3 * h) << logw) + c, sh);
+      const C2<T> a0 = a[e0], a1 = cmul(a[e1], t1), a2 = a[e2], a3 = cmul(a[e3], t1);
+      const C2<T> b0 = {a0.x + a1.x, a0.y + a1.y}, b1 = {a0.x - a1.x, a0.y - a1.y};
+      const C2<T> b2 = cmul(C2<T>{a2.x + a3.x, a2.y + a3.y}, t2);
+      C2<T> b3 = cmul(C2<T>{a2.x - a3.x, a2.y - a3.y}, t2);
+      b3 = inverse ? C2<T>{-b3.y, b3.x} : C2<T>{b3.y, -b3.x};  // times +i / -i
+      a[e0] = {b0.x + b2.x, b0.y + b2.y};
+      a[e2] = {b0.x - b2.x, b0.y - b2.y};
+      a[e1] = {b1.x + b3.x, b1.y + b3.y};
+      a[e3] = {b1.x - b3.x, b1.y - b3.y};
     }
     __syncthreads();
   }
