@@ -315,7 +315,7 @@ def ensemble_measurement(steps: int = 60, seq_steps: int = 10):
 
 
 def surrogate_measurement(ntraj: int = 2000, pairs: int = 4, spacing: int = 600, start: int = 300, epochs: int = 3,
-                          seeds=(20001, 20002, 20003, 20004), warm: int = 400, nwin: int = 1000, check: int = 4,
+                          seeds=(20001, 20002, 20003, 20004), warm: int = 400, nwin: int = 1000, check: int = 3,
                           corr=(4.0, 20.0), judges=("l2", "linf")):
     """The learned surrogate on 256 x 512 tori (R / r in [1.5, 4], seeded quenched noise): trained here on
     `ntraj` solver trajectories by the library's kernels, then advancing each held-out torus by `nwin`
@@ -392,6 +392,9 @@ def surrogate_measurement(ntraj: int = 2000, pairs: int = 4, spacing: int = 600,
             if twin is not None:
                 twin.close()
         n = len(seeds) * nwin
+        # a prediction that overflowed has a non-finite error: the judge rejected it (a fallback)
+        fin = [float(e) for e in errs if math.isfinite(e)]
+        fin_inf = [float(e) for e in errs_inf if math.isfinite(e)]
         # the coarsening curve: L_d averaged over the held-out tori, window by window
         mean_ref = np.mean(np.reshape(ld_ref_all, (len(seeds), nwin)), axis=0)
         mean_sur = np.mean(np.reshape(ld_sur_all, (len(seeds), nwin)), axis=0)
@@ -410,8 +413,9 @@ def surrogate_measurement(ntraj: int = 2000, pairs: int = 4, spacing: int = 600,
                 "windows": n, "predicted_windows": kinds_all.count("surrogate"),
                 "fallbacks": kinds_all.count("fallback"), "fallback_rate_of_judged": kinds_all.count("fallback") / max(judged, 1),
                 "solver_ms_per_window": t_ref / n, "surrogate_ms_per_window": t_sur / n, "speedup": t_ref / t_sur,
-                "phi_l2_err_max": max(errs) if errs else None, "phi_l2_err_median": float(np.median(errs)) if errs else None,
-                "phi_linf_err_max": max(errs_inf) if errs_inf else None,
+                "phi_l2_err_max": max(fin) if fin else None, "phi_l2_err_median": float(np.median(fin)) if fin else None,
+                "phi_linf_err_max": max(fin_inf) if fin_inf else None,
+                "nonfinite_predictions": len(errs) - len(fin),
                 "Ld_max_rel_dev": max(ld_dev), "Ld_rel_dev_final_mean": float(np.mean(ld_dev[nwin - 1::nwin])),
                 "mean_curve_max_rel_dev": float(np.max(np.abs(mean_sur / mean_ref - 1.0))),
                 "mean_curve_final_rel_dev": float(mean_sur[-1] / mean_ref[-1] - 1.0),
