@@ -49,21 +49,26 @@ __device__ __forceinline__ double load_phi(const T* state, int64_t stride, int64
   return v;
 }
 
-// f := f^eq(rho, u) (Eq. feq), phi := phi; evaluated in FP64, rounded once.
+// f := f^eq(rho, u) (Eq. feq), phi := phi, stored as the deviation g = f^eq - n0 w_i w_j
+// = w_i w_j ((n - n0) + n (poly - 1)).  FP64 state: evaluated in FP64.  FP32 state: n - n0 is formed in
+// FP64 (exact enough that its rounding to FP32 is the only error), the Hermite polynomial and the
+// product in FP32 -- every term is small next to the stored value's own rounding -- so the
+// initialisation does not run on GB300's FP64 units.
 template <typename T>
 __global__ void init_feq_kernel(T* state, int64_t stride, const double* rho, const double* ut, const double* up,
                                 const double* phi, int64_t n, double n0, VD vd) {
+  using C = T;  // arithmetic of the polynomial: the state precision
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
-    const double nn = rho[idx], a = ut[idx], b = up[idx];
-    const double usq = a * a + b * b;
+    const double nn = rho[idx];
+    const C a = (C)ut[idx], b = (C)up[idx], dn = (C)(nn - n0), nc = (C)nn;
+    const C usq = a * a + b * b;
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const double xi = vd.v[i] * a + vd.v[j] * b;
-        const double pm1 = xi + 0.5 * (xi * xi - usq) + xi * (xi * xi - 3.0 * usq) / 6.0;
-        // stored deviation g = f^eq - n0 w_i w_j = w_i w_j ((n - n0) + n (poly - 1))
-        state[(4 * i + j) * stride + idx] = (T)(vd.w[i] * vd.w[j] * ((nn - n0) + nn * pm1));
+        const C xi = (C)vd.v[i] * a + (C)vd.v[j] * b;
+        const C pm1 = xi + C(0.5) * (xi * xi - usq) + xi * (xi * xi - C(3) * usq) * C(1.0 / 6.0);
+        state[(4 * i + j) * stride + idx] = (T)((C)(vd.w[i] * vd.w[j]) * (dn + nc * pm1));
       }
     store_phi(state, stride, idx, phi[idx]);
   }
