@@ -172,8 +172,13 @@ bool reference_density(const vlb_params& p, F n_at, double* out) {
   double num = 0.0, den = 0.0;
   for (int q = 0; q < p.n_theta; ++q) {
     const double J = 1.0 + a * cos(q * dth);
-    double row = 0.0;
-    for (int s = 0; s < p.n_phi; ++s) row += n_at(q, s);
+    // four interleaved partial sums (a fixed order), so the row sum is not one serial chain of adds
+    double r4[4] = {0.0, 0.0, 0.0, 0.0};
+    int s = 0;
+    for (; s + 4 <= p.n_phi; s += 4)
+      for (int k = 0; k < 4; ++k) r4[k] += n_at(q, s + k);
+    for (; s < p.n_phi; ++s) r4[0] += n_at(q, s);
+    const double row = (r4[0] + r4[1]) + (r4[2] + r4[3]);
     num += J * row;
     den += J * p.n_phi;
   }
@@ -632,14 +637,18 @@ vlb_status vlb_set_fields(vlb_handle* h, const double* rho, const double* u_th, 
   if (st) return st;
   if (!rho || !u_th || !u_ph || !phi) return fail(h, VLB_ERR_ARG, "vlb_set_fields: NULL input");
   const int ns = h->p.n_phi;
-  if (!reference_density(h->p, [&](int q, int s) { return rho[(int64_t)q * ns + s]; }, &h->n0))
-    return fail(h, VLB_ERR_ARG, "vlb_set_fields: density must be finite with a positive mean");
+  // the copies into the staging area run while the host forms the reference density; nothing
+  // reads the staging area before the initialisation kernel below
   const size_t nb = sizeof(double) * h->N;
   double* s = h->staging;
   VLB_CUDA(h, cudaMemcpyAsync(s, rho, nb, cudaMemcpyHostToDevice, h->stream));
   VLB_CUDA(h, cudaMemcpyAsync(s + h->N, u_th, nb, cudaMemcpyHostToDevice, h->stream));
   VLB_CUDA(h, cudaMemcpyAsync(s + 2 * h->N, u_ph, nb, cudaMemcpyHostToDevice, h->stream));
   VLB_CUDA(h, cudaMemcpyAsync(s + 3 * h->N, phi, nb, cudaMemcpyHostToDevice, h->stream));
+  if (!reference_density(h->p, [&](int q, int s_) { return rho[(int64_t)q * ns + s_]; }, &h->n0)) {
+    cudaStreamSynchronize(h->stream);  // the copies read the caller's arrays until they finish
+    return fail(h, VLB_ERR_ARG, "vlb_set_fields: density must be finite with a positive mean");
+  }
   if (h->esize == 8)
     VLB_CUDA(h, vlb::launch_init_feq<double>((double*)h->U[0], h->stride, s, s + h->N, s + 2 * h->N, s + 3 * h->N,
                                              h->N, h->n0, h->stream));
