@@ -112,32 +112,34 @@ __device__ __forceinline__ void node_moments(const T* state, int64_t stride, int
       col[j] += x;
     }
   n = n0 + ((row[0] + row[1]) + (row[2] + row[3]));
-  ut = (vd.v[0] * row[0] + vd.v[1] * row[1] + vd.v[2] * row[2] + vd.v[3] * row[3]) / n;
-  up = (vd.v[0] * col[0] + vd.v[1] * col[1] + vd.v[2] * col[2] + vd.v[3] * col[3]) / n;
+  const double inv_n = 1.0 / n;  // one FP64 division per node
+  ut = (vd.v[0] * row[0] + vd.v[1] * row[1] + vd.v[2] * row[2] + vd.v[3] * row[3]) * inv_n;
+  up = (vd.v[0] * col[0] + vd.v[1] * col[1] + vd.v[2] * col[2] + vd.v[3] * col[3]) * inv_n;
 }
 
-// rho, u (Sec. 2.3 moments), phi and mu (Eq. mu) in FP64.
+// rho, u (Sec. 2.3 moments), phi and mu (Eq. mu) in FP64; one CTA row per theta row (blockIdx.y).
 template <typename T>
 __global__ void fields_kernel(const T* state, int64_t stride, const double* coefd, int nt, int ns, double A,
                               double kappa, double n0, double* rho, double* ut, double* up, double* phi, double* mu, VD vd) {
-  const int64_t n = (int64_t)nt * ns;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
-    const int q = (int)(idx / ns), s = (int)(idx - (int64_t)q * ns);
-    double nn, a, b;
-    node_moments(state, stride, idx, vd, n0, nn, a, b);
-    rho[idx] = nn;
-    ut[idx] = a;
-    up[idx] = b;
-    const double p0 = load_phi(state, stride, idx);
-    const double pn = load_phi(state, stride, (int64_t)wrapi(q + 1, nt) * ns + s);
-    const double ps = load_phi(state, stride, (int64_t)wrapi(q - 1, nt) * ns + s);
-    const double pe = load_phi(state, stride, (int64_t)q * ns + wrapi(s + 1, ns));
-    const double pw = load_phi(state, stride, (int64_t)q * ns + wrapi(s - 1, ns));
-    const double lap = coefd[C_LT * nt + q] * (coefd[C_JP * nt + q] * (pn - p0) - coefd[C_JM * nt + q] * (p0 - ps)) +
-                       coefd[C_LP * nt + q] * (pe - 2.0 * p0 + pw);
-    phi[idx] = p0;
-    mu[idx] = -A * p0 * (1.0 - p0 * p0) - kappa * lap;
-  }
+  const int q = blockIdx.y, s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= ns) return;
+  const int64_t idx = (int64_t)q * ns + s;
+  double nn, a, b;
+  node_moments(state, stride, idx, vd, n0, nn, a, b);
+  rho[idx] = nn;
+  ut[idx] = a;
+  up[idx] = b;
+  const int qn = q + 1 == nt ? 0 : q + 1, qs = q == 0 ? nt - 1 : q - 1;
+  const int se = s + 1 == ns ? 0 : s + 1, sw = s == 0 ? ns - 1 : s - 1;
+  const double p0 = load_phi(state, stride, idx);
+  const double pn = load_phi(state, stride, (int64_t)qn * ns + s);
+  const double ps = load_phi(state, stride, (int64_t)qs * ns + s);
+  const double pe = load_phi(state, stride, (int64_t)q * ns + se);
+  const double pw = load_phi(state, stride, (int64_t)q * ns + sw);
+  const double lap = coefd[C_LT * nt + q] * (coefd[C_JP * nt + q] * (pn - p0) - coefd[C_JM * nt + q] * (p0 - ps)) +
+                     coefd[C_LP * nt + q] * (pe - 2.0 * p0 + pw);
+  phi[idx] = p0;
+  mu[idx] = -A * p0 * (1.0 - p0 * p0) - kappa * lap;
 }
 
 // Per-block FP64 partial sums: mass, phi total, Psi (Eq. Landau), max |u|, non-finite count, L_I.
@@ -335,6 +337,27 @@ int grid_for(int64_t n) {
 
 int totals_blocks() { return TOTAL_BLOCKS; }
 
+// out[q] = sum over s of x[q][s], one CTA per row: each thread adds its strided elements in order,
+// then a fixed-order tree in shared memory (deterministic).
+__global__ void __launch_bounds__(256) row_sums_kernel(const double* x, int ns, double* out) {
+  __shared__ double red[256];
+  const double* row = x + (int64_t)blockIdx.x * ns;
+  double acc = 0.0;
+  for (int s = threadIdx.x; s < ns; s += blockDim.x) acc += row[s];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = red[0];
+}
+
+cudaError_t launch_row_sums(const double* x, int nt, int ns, double* out, cudaStream_t s) {
+  row_sums_kernel<<<nt, 256, 0, s>>>(x, ns, out);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_init_feq(T* state, int64_t stride, const double* rho, const double* ut, const double* up,
                             const double* phi, int64_t n, double n0, cudaStream_t s) {
@@ -357,8 +380,8 @@ cudaError_t launch_convert_out(double* dst, const T* state, int64_t stride, int6
 template <typename T>
 cudaError_t launch_fields(const T* state, int64_t stride, const double* coefd, int nt, int ns, double A, double kappa,
                           double n0, double* rho, double* ut, double* up, double* phi, double* mu, cudaStream_t s) {
-  fields_kernel<T><<<grid_for((int64_t)nt * ns), 256, 0, s>>>(state, stride, coefd, nt, ns, A, kappa, n0, rho, ut,
-                                                             up, phi, mu, make_vd());
+  fields_kernel<T><<<dim3((ns + 255) / 256, nt), 256, 0, s>>>(state, stride, coefd, nt, ns, A, kappa, n0, rho, ut, up,
+                                                             phi, mu, make_vd());
   return cudaGetLastError();
 }
 

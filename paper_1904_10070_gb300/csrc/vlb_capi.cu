@@ -161,25 +161,16 @@ void row_tables(const vlb_params* p, double* out) {
   }
 }
 
-// Reference density n0 of the stored deviations: the area-weighted mean density
-// sum_q J_q sum_s n_qs / (N_phi sum_q J_q), rounded to 20 significant bits.  The scheme conserves
-// sum n sqrt(g), so a state restored from a checkpoint reproduces the same n0 (and bitwise the same
-// stored deviations).  `n_at(q, s)` returns the density at a node.
-template <typename F>
-bool reference_density(const vlb_params& p, F n_at, double* out) {
+// The reference density n0 of the stored deviations from the row sums of n: the area-weighted mean
+// sum_q J_q row_q / sum_q J_q N_phi (J_q = 1 + (r/R) cos theta_q), rounded to 20 significant bits so
+// that it is exact in FP32.  False if it is not finite and positive.
+bool reference_density_rows(const vlb_params& p, const double* rows, double* out) {
   const double dth = 2.0 * M_PI / p.n_theta;
   const double a = p.geometry == VLB_TORUS ? p.r / p.R : 0.0;
   double num = 0.0, den = 0.0;
   for (int q = 0; q < p.n_theta; ++q) {
     const double J = 1.0 + a * cos(q * dth);
-    // four interleaved partial sums (a fixed order), so the row sum is not one serial chain of adds
-    double r4[4] = {0.0, 0.0, 0.0, 0.0};
-    int s = 0;
-    for (; s + 4 <= p.n_phi; s += 4)
-      for (int k = 0; k < 4; ++k) r4[k] += n_at(q, s + k);
-    for (; s < p.n_phi; ++s) r4[0] += n_at(q, s);
-    const double row = (r4[0] + r4[1]) + (r4[2] + r4[3]);
-    num += J * row;
+    num += J * rows[q];
     den += J * p.n_phi;
   }
   const double mean = num / den;
@@ -188,6 +179,25 @@ bool reference_density(const vlb_params& p, F n_at, double* out) {
   const double m = frexp(mean, &e);
   *out = ldexp(nearbyint(ldexp(m, 20)), e - 20);
   return true;
+}
+
+// Reference density n0 of the stored deviations: the area-weighted mean density
+// sum_q J_q sum_s n_qs / (N_phi sum_q J_q), rounded to 20 significant bits.  The scheme conserves
+// sum n sqrt(g), so a state restored from a checkpoint reproduces the same n0 (and bitwise the same
+// stored deviations).  `n_at(q, s)` returns the density at a node.
+template <typename F>
+bool reference_density(const vlb_params& p, F n_at, double* out) {
+  std::vector<double> rows((size_t)p.n_theta);
+  for (int q = 0; q < p.n_theta; ++q) {
+    // four interleaved partial sums (a fixed order), so the row sum is not one serial chain of adds
+    double r4[4] = {0.0, 0.0, 0.0, 0.0};
+    int s = 0;
+    for (; s + 4 <= p.n_phi; s += 4)
+      for (int k = 0; k < 4; ++k) r4[k] += n_at(q, s + k);
+    for (; s < p.n_phi; ++s) r4[0] += n_at(q, s);
+    rows[q] = (r4[0] + r4[1]) + (r4[2] + r4[3]);
+  }
+  return reference_density_rows(p, rows.data(), out);
 }
 
 // Uploads the FP64 and state-precision row tables of h (synchronous on h's stream).
@@ -637,18 +647,22 @@ vlb_status vlb_set_fields(vlb_handle* h, const double* rho, const double* u_th, 
   if (st) return st;
   if (!rho || !u_th || !u_ph || !phi) return fail(h, VLB_ERR_ARG, "vlb_set_fields: NULL input");
   const int ns = h->p.n_phi;
-  // the copies into the staging area run while the host forms the reference density; nothing
-  // reads the staging area before the initialisation kernel below
   const size_t nb = sizeof(double) * h->N;
   double* s = h->staging;
   VLB_CUDA(h, cudaMemcpyAsync(s, rho, nb, cudaMemcpyHostToDevice, h->stream));
   VLB_CUDA(h, cudaMemcpyAsync(s + h->N, u_th, nb, cudaMemcpyHostToDevice, h->stream));
   VLB_CUDA(h, cudaMemcpyAsync(s + 2 * h->N, u_ph, nb, cudaMemcpyHostToDevice, h->stream));
   VLB_CUDA(h, cudaMemcpyAsync(s + 3 * h->N, phi, nb, cudaMemcpyHostToDevice, h->stream));
-  if (!reference_density(h->p, [&](int q, int s_) { return rho[(int64_t)q * ns + s_]; }, &h->n0)) {
-    cudaStreamSynchronize(h->stream);  // the copies read the caller's arrays until they finish
+  // the reference density from row sums formed on the device (one small read-back) rather than a
+  // pass of the host over the caller's array
+  std::vector<double> rows((size_t)h->p.n_theta);
+  double* row_sums = s + 4 * h->N;  // the staging area holds 17 N doubles
+  VLB_CUDA(h, vlb::launch_row_sums(s, h->p.n_theta, ns, row_sums, h->stream));
+  VLB_CUDA(h, cudaMemcpyAsync(rows.data(), row_sums, sizeof(double) * rows.size(), cudaMemcpyDeviceToHost,
+                              h->stream));
+  VLB_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (!reference_density_rows(h->p, rows.data(), &h->n0))
     return fail(h, VLB_ERR_ARG, "vlb_set_fields: density must be finite with a positive mean");
-  }
   if (h->esize == 8)
     VLB_CUDA(h, vlb::launch_init_feq<double>((double*)h->U[0], h->stride, s, s + h->N, s + 2 * h->N, s + 3 * h->N,
                                              h->N, h->n0, h->stream));

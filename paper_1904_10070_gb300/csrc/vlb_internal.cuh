@@ -168,6 +168,8 @@ cudaError_t launch_structure_sums(int nt, int ns, double r, double R, const T* p
                                   double* part, cudaStream_t st);
 
 // Auxiliary kernels (vlb_aux.cu).  Staging arrays are FP64 [n_theta][n_phi].
+// out[q] = the sum of row q of x (FP64 [nt][ns]), in a fixed order.
+cudaError_t launch_row_sums(const double* x, int nt, int ns, double* out, cudaStream_t s);
 template <typename T>
 cudaError_t launch_init_feq(T* state, int64_t stride, const double* rho, const double* ut,
                             const double* up, const double* phi, int64_t n, double n0, cudaStream_t s);
