@@ -9,8 +9,9 @@
   n0 = 20 on R = 2.5, r = 1 and R = 5, r = 0.5 (equal areas), 400 x 800 as in the paper, explicit step.
   The paper: finite-size effects (departure from the 2/3 growth) appear sooner on the thinner torus,
   whose poloidal circumference 2 pi r is smaller.  Both tori coarsen alike while domains are small, and
-  the apparent exponent of L_d = A/L_I over t = 140 .. 250 is near 2/3 on the reference torus and
-  clearly below it on the thin one."""
+  on this seed (noise seed 3) the apparent exponent of L_d = A/L_I over t = 140 .. 250 is near 2/3 on the
+  reference torus and clearly below it on the thin one.  The margin depends on the seed: single runs at
+  this size differ by about 0.1 in that exponent from seed to seed."""
 import math
 
 import numpy as np
