@@ -7,11 +7,11 @@
   (their own stable step; 256 x 1024) to t = 300.
 * Thin and reference tori (Sec. 4.1.2, Fig. tscal-ev-fat): even-mixture coarsening from noise +-0.1 at
   n0 = 20 on R = 2.5, r = 1 and R = 5, r = 0.5 (equal areas), 400 x 800 as in the paper, explicit step.
-  The paper: finite-size effects (departure from the 2/3 growth) appear sooner on the thinner torus,
-  whose poloidal circumference 2 pi r is smaller.  Both tori coarsen alike while domains are small, and
-  on this seed (noise seed 3) the apparent exponent of L_d = A/L_I over t = 140 .. 250 is near 2/3 on the
-  reference torus and clearly below it on the thin one.  The margin depends on the seed: single runs at
-  this size differ by about 0.1 in that exponent from seed to seed."""
+  What holds on every noise seed we ran: both tori coarsen alike while the domains are small (L_d within
+  10% up to t = 50), L_d grows monotonically, and its apparent exponent over t = 140 .. 250 lies in the
+  hydrodynamic range (0.2 .. 0.9).  The paper's finite-size ordering (the thinner torus leaves the 2/3
+  growth sooner) is not pinned: over six seeds the two exponents differ by 0.02 +- 0.06, less than the
+  seed-to-seed spread of a single run."""
 import math
 
 import numpy as np
@@ -89,7 +89,7 @@ def _coarsen(R, r, t_marks):
     return np.array(Ld)
 
 
-def test_thin_torus_shows_finite_size_effects_sooner():
+def test_thin_and_reference_tori_coarsen_alike_while_domains_are_small():
     t_marks = np.array([10, 20, 30, 40, 50, 70, 100, 140, 170, 200, 225, 250], dtype=float)
     ref = _coarsen(2.5, 1.0, t_marks)
     thin = _coarsen(5.0, 0.5, t_marks)
@@ -97,9 +97,9 @@ def test_thin_torus_shows_finite_size_effects_sooner():
     print("L_d thin:", np.round(thin, 4).tolist())
     early = t_marks <= 50
     assert np.all(np.abs(thin[early] / ref[early] - 1.0) < 0.1)  # small domains: the same coarsening
+    assert np.all(np.diff(ref) > 0) and np.all(np.diff(thin) > 0)
     late = t_marks >= 140
     e_ref = np.polyfit(np.log(t_marks[late]), np.log(ref[late]), 1)[0]
     e_thin = np.polyfit(np.log(t_marks[late]), np.log(thin[late]), 1)[0]
     print(f"apparent exponents over t = 140 .. 250: reference {e_ref:.3f}, thin {e_thin:.3f}")
-    assert 0.45 < e_ref < 0.9          # near the 2/3 of the inertial-hydrodynamic regime
-    assert e_thin < e_ref - 0.1        # the thin torus has left it
+    assert 0.2 < e_ref < 0.9 and 0.2 < e_thin < 0.9
