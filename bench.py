@@ -54,6 +54,8 @@ def _args():
     ap.add_argument("--coarsening", type=int, default=0, metavar="STEPS",
                     help="run only the three 1024x2048 coarsening runs for STEPS steps each and print their L(t)")
     ap.add_argument("--coarsening-every", type=int, default=1000)
+    ap.add_argument("--torus-sizes", action="store_true",
+                    help="run only the thin-against-reference torus coarsening over six noise seeds (one ensemble)")
     return ap.parse_args()
 
 
@@ -525,6 +527,51 @@ def coarsening_runs(steps: int = 50000, every: int = 1000, dt_cap: float = 5e-4)
     return out
 
 
+def torus_size_seeds(seeds=(6, 7, 8, 9, 10, 11), t_marks=(10, 30, 50, 70, 100, 140, 170, 200, 225, 250)):
+    """Thin against reference torus (Sec. 4.1.2): even-mixture coarsening from noise +-0.1 at n0 = 20 on
+    R = 2.5, r = 1 and R = 5, r = 0.5, 400 x 800, one ensemble member per (torus, seed) in one launch per
+    stage at a common dt (0.9 of the smaller stable step, at most 5e-4).  L_d = A / L_I at each mark; the
+    apparent exponent over t >= 140 per member, its mean and spread per torus, and the exponent of the
+    seed-averaged curve."""
+    from paper_1904_10070_gb300 import inputs, vlb
+    tori = (("reference", 2.5, 1.0), ("thin", 5.0, 0.5))
+
+    def pd(R, r):
+        return dict(geometry=0, R=R, r=r, n_theta=400, n_phi=800, dt=1.0, tau=2.5e-3, M=2.5e-3, A=0.5, kappa=5e-4,
+                    advection=0, ch_mode=0)
+
+    dt = min([5e-4] + [0.9 * vlb.vlb_max_stable_dt(vlb.make_params(**pd(R, r))) for _, R, r in tori])
+    mem = [(name, R, r, seed) for seed in seeds for name, R, r in tori]
+    ens = vlb.Ensemble([vlb.make_params(**dict(pd(R, r), dt=dt), precision=vlb.FP32) for _, R, r, _ in mem])
+    for v, (_, _, _, seed) in zip(ens.views, mem):
+        phi = inputs.noise(seed, 400, 800, 0.1)
+        z = np.zeros_like(phi)
+        vlb.vlb_set_fields(v, np.full_like(phi, 20.0), z, z, phi)
+    done, Ld = 0, [[] for _ in mem]
+    t0 = time.perf_counter()
+    for t in t_marks:
+        n = int(round(t / dt)) - done
+        ens.step(n)
+        done += n
+        for k, (v, (_, R, r, _)) in enumerate(zip(ens.views, mem)):
+            Ld[k].append(4 * math.pi ** 2 * R * r / vlb.vlb_interface_length(v))
+    wall = time.perf_counter() - t0
+    ens.close()
+    t = np.array(t_marks, float)
+    late = t >= 140
+    out = {"dt": dt, "steps": done, "wall_s": wall, "t": list(t_marks), "members": []}
+    for k, (name, _, _, seed) in enumerate(mem):
+        e = float(np.polyfit(np.log(t[late]), np.log(np.array(Ld[k])[late]), 1)[0])
+        out["members"].append({"torus": name, "seed": seed, "exponent_late": e, "L_d": [round(x, 4) for x in Ld[k]]})
+    for name, _, _ in tori:
+        es = [m["exponent_late"] for m in out["members"] if m["torus"] == name]
+        curve = np.mean([Ld[k] for k, m in enumerate(mem) if m[0] == name], axis=0)
+        out[name] = {"exponent_mean": float(np.mean(es)), "exponent_spread": float(np.std(es)),
+                     "exponent_of_mean_curve": float(np.polyfit(np.log(t[late]), np.log(curve[late]), 1)[0]),
+                     "mean_L_d": [round(float(x), 4) for x in curve]}
+    return out
+
+
 def main():
     args = _args()
     world, rank, local = _dist()
@@ -541,6 +588,10 @@ def main():
     if args.coarsening > 0:
         if rank == 0:
             print(json.dumps({"coarsening": coarsening_runs(args.coarsening, args.coarsening_every)}), flush=True)
+        return
+    if args.torus_sizes:
+        if rank == 0:
+            print(json.dumps({"torus_sizes": torus_size_seeds()}), flush=True)
         return
     dist = None
     if world > 1:
