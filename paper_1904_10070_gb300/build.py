@@ -46,7 +46,9 @@ def build(verbose_ptxas: bool = False) -> str:
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(lambda s: _compile(s, verbose_ptxas), SOURCES))
     tmp = LIB + ".tmp"
-    cmd = [nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
+    # only the C ABI (vlb_*) is exported; the kernels' C++ symbols stay internal to the library
+    vmap = os.path.join(CSRC, "libvlb.map")
+    cmd = [nvcc(), *ARCH, "-shared", "-cudart", "static", "-Xlinker", f"--version-script={vmap}", "-o", tmp, *objs]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")
