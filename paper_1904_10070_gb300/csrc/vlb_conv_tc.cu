@@ -476,7 +476,7 @@ __device__ __forceinline__ float dy_column_sum(const unsigned char* dyb, int t) 
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;\n" ::: "memory"); }
 
 // the epilogue warps' share of a bias-gradient CTA: per segment, wait for its stage (one thread
-// waits, the verdict is broadcast), add it up, release it; returns false if a wait gave up
+// waits, the outcome is broadcast), add it up, release it; returns false if a wait gave up
 template <int DC, int NS>
 __device__ __forceinline__ bool bias_segments(const unsigned char* sm, int stage_bytes, uint64_t* full,
                                               uint64_t* empty, int nmine, int tid, uint32_t* flag, float& acc) {
